@@ -1,0 +1,159 @@
+"""FP64 CPU oracle for the modal heat current -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of bench.py
+may import this package.  The CUDA library never calls it and shares no code
+with it.  ``mhc_oracle.c`` holds the plain FP64 loops (Eqs. 10, 13, 16, 17,
+19 and frequency binning); ``brute.py`` restates the same definitions with
+per-atom 3-vectors in scalar Python for tiny systems.
+
+This module compiles ``mhc_oracle.c`` with gcc on first use (or through
+``build()``) and wraps it with ctypes and numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mhc_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_dbl = ctypes.c_double
+_p = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile mhc_oracle.c into oracle/liboracle.so (gcc, OpenMP, no fast-math,
+    no FMA contraction so x86 and Arm give identical results)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
+            L.orc_bins_uniform.argtypes = [_i64, _p, _dbl, _dbl, _i32, _p]
+            L.orc_modal_current.argtypes = [_i64, _i64, _p, _p, _i64, _p, _p, _p, _i32,
+                                            _p, _p, _p, _p]
+            L.orc_gkma_corr.argtypes = [_i64, _i32, _p, _p, _i32, _p, _p]
+            L.orc_gk_kappa.argtypes = [_i32, _i32, _p, _p, _dbl, _dbl, _dbl, _p]
+            L.orc_kappa_window.argtypes = [_i32, _i32, _p, _dbl, _dbl, _dbl, _p]
+            L.orc_kappa_window.restype = _i32
+            L.orc_hnema.argtypes = [_i64, _i32, _p, _dbl, _dbl, _p, _p, _p]
+            L.orc_orthonormality.argtypes = [_i64, _i64, _p]
+            L.orc_orthonormality.restype = _dbl
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    lib().orc_set_num_threads(int(n))
+
+
+def bins_uniform(f_THz, f_min: float, f_max: float, B: int) -> np.ndarray:
+    f = np.ascontiguousarray(f_THz, dtype=np.float64)
+    out = np.empty(f.shape[0], dtype=np.int32)
+    lib().orc_bins_uniform(f.shape[0], _ptr(f), f_min, f_max, B, _ptr(out))
+    return out
+
+
+def modal_current(E: np.ndarray, mass, v, W, bin_of_mode, B: int,
+                  want_modes: bool = False):
+    """E: dof-major [3N][M] float64 (E[3i+b, n] = e^b_{i,n}); v [T][N][3] and
+    W [T][N][9] float32.  Returns dict with Jb [T][B][3], J [T][3] and, when
+    want_modes, xdot [T][M] and Jn [T][M][3]."""
+    E = np.asarray(E, dtype=np.float64)
+    D, M = E.shape
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    N = mass.shape[0]
+    if D != 3 * N:
+        raise ValueError("E must have 3N rows")
+    Et = np.ascontiguousarray(E.T)
+    v = np.ascontiguousarray(v, dtype=np.float32).reshape(-1, N, 3)
+    W = np.ascontiguousarray(W, dtype=np.float32).reshape(-1, N, 9)
+    T = v.shape[0]
+    bins = np.ascontiguousarray(bin_of_mode, dtype=np.int32)
+    Jb = np.empty((T, B, 3))
+    J = np.empty((T, 3))
+    xd = np.empty((T, M)) if want_modes else None
+    Jn = np.empty((T, M, 3)) if want_modes else None
+    lib().orc_modal_current(N, M, _ptr(Et), _ptr(mass), T, _ptr(v), _ptr(W), _ptr(bins),
+                            B, _ptr(Jb), _ptr(J), _ptr(xd), _ptr(Jn))
+    out = {"Jb": Jb, "J": J}
+    if want_modes:
+        out["xdot"] = xd
+        out["Jn"] = Jn
+    return out
+
+
+def gkma_corr(Jb: np.ndarray, J: np.ndarray, L: int):
+    """Raw correlation sums Csum [B][3][3][L] and origin counts [L] (Eq. 17)."""
+    Jb = np.ascontiguousarray(Jb, dtype=np.float64)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    T, B, _ = Jb.shape
+    C = np.empty((B, 3, 3, L))
+    cnt = np.empty(L, dtype=np.int64)
+    lib().orc_gkma_corr(T, B, _ptr(Jb), _ptr(J), L, _ptr(C), _ptr(cnt))
+    return C, cnt
+
+
+def gk_kappa(Csum: np.ndarray, count: np.ndarray, dt_ps: float, T_K: float, V_A3: float):
+    """Running Green-Kubo integral kappa_b^{mu nu}(l) in W/(m K) (Eq. 17)."""
+    Csum = np.ascontiguousarray(Csum, dtype=np.float64)
+    count = np.ascontiguousarray(count, dtype=np.int64)
+    B, _, _, L = Csum.shape
+    out = np.empty_like(Csum)
+    lib().orc_gk_kappa(B, L, _ptr(Csum), _ptr(count), dt_ps, T_K, V_A3, _ptr(out))
+    return out
+
+
+def kappa_window(kappa: np.ndarray, dt_ps: float, tau_lo: float, tau_hi: float):
+    kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+    B, _, _, L = kappa.shape
+    out = np.empty((B, 3, 3))
+    n = lib().orc_kappa_window(B, L, _ptr(kappa), dt_ps, tau_lo, tau_hi, _ptr(out))
+    return out, int(n)
+
+
+def hnema(Jb: np.ndarray, T_K: float, V_A3: float, Fe):
+    """Time-averaged binned current and kappa_b^mu (Eq. 19), W/(m K)."""
+    Jb = np.ascontiguousarray(Jb, dtype=np.float64)
+    T, B, _ = Jb.shape
+    fe = np.ascontiguousarray(Fe, dtype=np.float64)
+    mean = np.empty((B, 3))
+    kap = np.empty((B, 3))
+    lib().orc_hnema(T, B, _ptr(Jb), T_K, V_A3, _ptr(fe), _ptr(mean), _ptr(kap))
+    return mean, kap
+
+
+def orthonormality(E: np.ndarray) -> float:
+    Et = np.ascontiguousarray(np.asarray(E, dtype=np.float64).T)
+    M, D = Et.shape
+    return float(lib().orc_orthonormality(D, M, _ptr(Et)))

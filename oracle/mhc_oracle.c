@@ -1,0 +1,260 @@
+/*
+ * FP64 CPU oracle for the modal heat current (GKMA / HNEMA).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code:
+ * only the tests, the smoke check and the benchmark's CPU-baseline leg load it.
+ * It shares no code with the CUDA library.
+ *
+ * Every routine is the plain definition from the paper, written out as straight
+ * FP64 loops in the paper's notation.  Inputs v and W arrive as float32 (the
+ * precision an MD engine hands over) and are widened to double exactly.
+ *
+ *   Eq. 10   J^a       = sum_i sum_b W_i^{ab} v_i^b               (total current)
+ *   Eq. 13   Xdot_n    = sum_i sqrt(m_i) e_{i,n} . v_i            (modal velocity)
+ *   Eq. 16   J_n^a     = (sum_i m_i^{-1/2} (W_i e_{i,n})^a) Xdot_n (modal current)
+ *   binning  J_b^a     = sum_{n in b} J_n^a   (frequency bins, Sec. III.A)
+ *   Eq. 17   kappa_n^{mu nu}(tau) = (k_B T^2 V)^{-1} int_0^tau <J_n^mu(t') J^nu(0)> dt'
+ *   Eq. 19   <J_n^mu>/(T V) = sum_nu kappa_n^{mu nu} F_e^nu
+ *
+ * Readings where the paper is silent (each stated where it is used):
+ *   - e is real (Gamma point), so e* = e in Eq. 13.
+ *   - W is stored row-major [alpha][beta]; (W e)^a = sum_b W^{ab} e^b (Eq. 10).
+ *   - correlation average over all origins t with t - lag >= 0, divided by the
+ *     number of origins; trapezoid rule with kappa(0) = 0.
+ *
+ * Layouts: E is passed mode-major, Et[n * D + (3 i + b)] = e^b_{i,n} (column n of
+ * the dof-major eigenvector matrix stored contiguously).  v is [T][N][3],
+ * W is [T][N][9] with W[t][i][3 a + b] = W_i^{ab}.
+ *
+ * Parity pins for every function live in tests/test_oracle_pins.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_KB_EV_PER_K 8.617333262145179e-5 /* k_B = 1.380649e-23 J/K over e = 1.602176634e-19 C (SI exact) */
+#define ORC_WMK_PER_EV_PS_A_K 1602.176634 /* 1 eV/(ps A K) in W/(m K) */
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/*
+ * Frequency binning (Sec. III.A: bins of fixed width in THz).
+ * Bin b covers [f_min + b*w, f_min + (b+1)*w) with w = (f_max - f_min)/B; the
+ * last bin also takes f == f_max.  Frequencies outside [f_min, f_max] (or not
+ * finite) get -1 (mode excluded).  The bin index is floor((f - f_min) / w)
+ * evaluated in double precision.
+ */
+void orc_bins_uniform(int64_t M, const double *f_THz, double f_min, double f_max,
+                      int32_t B, int32_t *bin_of_mode)
+{
+    double w = (f_max - f_min) / (double)B;
+    for (int64_t n = 0; n < M; ++n) {
+        double f = f_THz[n];
+        if (!isfinite(f) || f < f_min || f > f_max) {
+            bin_of_mode[n] = -1;
+            continue;
+        }
+        int64_t b = (int64_t)floor((f - f_min) / w);
+        if (b >= B) b = B - 1;
+        if (b < 0) b = 0;
+        bin_of_mode[n] = (int32_t)b;
+    }
+}
+
+/* Eq. 10: total potential heat current of one step, J^a = sum_i sum_b W_i^{ab} v_i^b. */
+static void total_current(int64_t N, const float *v, const float *W, double J[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        double s = 0.0;
+        for (int64_t i = 0; i < N; ++i)
+            for (int b = 0; b < 3; ++b)
+                s += (double)W[i * 9 + 3 * a + b] * (double)v[i * 3 + b];
+        J[a] = s;
+    }
+}
+
+/*
+ * Modal heat current for T steps (Eqs. 10, 13, 16 and frequency binning).
+ *   Jb    [T][B][3]  binned modal current, sum over modes in ascending n
+ *   J     [T][3]     total current (Eq. 10)
+ *   xdot  [T][M]     modal velocities (optional, may be NULL)
+ *   Jn    [T][M][3]  per-mode currents (optional, may be NULL)
+ * Modes with bin -1 are excluded from Jb (their Jn/xdot are still produced).
+ */
+void orc_modal_current(int64_t N, int64_t M, const double *Et, const double *mass,
+                       int64_t T, const float *v, const float *W,
+                       const int32_t *bin_of_mode, int32_t B,
+                       double *Jb, double *J, double *xdot, double *Jn)
+{
+    const int64_t D = 3 * N;
+    double *sqm = (double *)malloc(sizeof(double) * (size_t)N);
+    double *isqm = (double *)malloc(sizeof(double) * (size_t)N);
+    double *jn = (double *)malloc(sizeof(double) * (size_t)M * 3);
+    for (int64_t i = 0; i < N; ++i) {
+        sqm[i] = sqrt(mass[i]);
+        isqm[i] = 1.0 / sqrt(mass[i]);
+    }
+    for (int64_t t = 0; t < T; ++t) {
+        const float *vt = v + t * N * 3;
+        const float *Wt = W + t * N * 9;
+        total_current(N, vt, Wt, J + t * 3);
+
+#pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < M; ++n) {
+            const double *e = Et + n * D;
+            /* Eq. 13 with real e: Xdot_n = sum_i sqrt(m_i) sum_b e^b_{i,n} v_i^b */
+            double x = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                double ev = 0.0;
+                for (int b = 0; b < 3; ++b) ev += e[3 * i + b] * (double)vt[i * 3 + b];
+                x += sqm[i] * ev;
+            }
+            /* Eq. 16 bracket: y^a = sum_i m_i^{-1/2} sum_b W_i^{ab} e^b_{i,n} */
+            double y[3] = {0.0, 0.0, 0.0};
+            for (int64_t i = 0; i < N; ++i) {
+                for (int a = 0; a < 3; ++a) {
+                    double we = 0.0;
+                    for (int b = 0; b < 3; ++b)
+                        we += (double)Wt[i * 9 + 3 * a + b] * e[3 * i + b];
+                    y[a] += isqm[i] * we;
+                }
+            }
+            for (int a = 0; a < 3; ++a) jn[n * 3 + a] = y[a] * x;
+            if (xdot) xdot[t * M + n] = x;
+        }
+        if (Jn) memcpy(Jn + t * M * 3, jn, sizeof(double) * (size_t)M * 3);
+        /* binning: modes in ascending order within each bin */
+        double *jb = Jb + t * (int64_t)B * 3;
+        for (int64_t k = 0; k < (int64_t)B * 3; ++k) jb[k] = 0.0;
+        for (int64_t n = 0; n < M; ++n) {
+            int32_t b = bin_of_mode[n];
+            if (b < 0 || b >= B) continue;
+            for (int a = 0; a < 3; ++a) jb[b * 3 + a] += jn[n * 3 + a];
+        }
+    }
+    free(sqm);
+    free(isqm);
+    free(jn);
+}
+
+/*
+ * GKMA correlation sums (Eq. 17 integrand, reading: the modal current is lagged,
+ * the total current sits at the time origin, all origins with t - lag >= 0):
+ *   Csum[b][mu][nu][l] = sum_{t=l}^{T-1} Jb[t][b][mu] * J[t-l][nu]
+ *   count[l]           = max(T - l, 0)
+ */
+void orc_gkma_corr(int64_t T, int32_t B, const double *Jb, const double *J, int32_t L,
+                   double *Csum, int64_t *count)
+{
+    for (int32_t l = 0; l < L; ++l) count[l] = T > l ? T - l : 0;
+#pragma omp parallel for schedule(static)
+    for (int32_t b = 0; b < B; ++b)
+        for (int mu = 0; mu < 3; ++mu)
+            for (int nu = 0; nu < 3; ++nu)
+                for (int32_t l = 0; l < L; ++l) {
+                    double s = 0.0;
+                    for (int64_t t = l; t < T; ++t)
+                        s += Jb[(t * B + b) * 3 + mu] * J[(t - l) * 3 + nu];
+                    Csum[(((int64_t)b * 3 + mu) * 3 + nu) * L + l] = s;
+                }
+}
+
+/*
+ * Eq. 17 running integral by the trapezoid rule, kappa(0) = 0:
+ *   C(l)      = Csum(l) / count(l)          (0 where count is 0)
+ *   kappa(l)  = c * dt * sum_{j=1}^{l} (C(j-1) + C(j)) / 2
+ *   c         = 1 / (k_B T^2 V), converted to W/(m K)
+ * Output kappa[b][mu][nu][l] in W/(m K) for dt in ps, T in K, V in A^3.
+ */
+void orc_gk_kappa(int32_t B, int32_t L, const double *Csum, const int64_t *count,
+                  double dt_ps, double T_K, double V_A3, double *kappa)
+{
+    double c = ORC_WMK_PER_EV_PS_A_K / (ORC_KB_EV_PER_K * T_K * T_K * V_A3);
+    for (int64_t r = 0; r < (int64_t)B * 9; ++r) {
+        const double *cs = Csum + r * L;
+        double *kp = kappa + r * L;
+        double acc = 0.0, prev = 0.0;
+        for (int32_t l = 0; l < L; ++l) {
+            double C = count[l] > 0 ? cs[l] / (double)count[l] : 0.0;
+            if (l > 0) acc += 0.5 * (prev + C) * dt_ps;
+            kp[l] = c * acc;
+            prev = C;
+        }
+    }
+}
+
+/*
+ * kappa(omega) for GKMA: the running integral averaged over the lags whose
+ * correlation time l*dt lies in [tau_lo, tau_hi] (the paper averages kappa_n(tau)
+ * over a tau window, Sec. III.A.i-iii).  Returns the number of lags averaged.
+ */
+int32_t orc_kappa_window(int32_t B, int32_t L, const double *kappa, double dt_ps,
+                         double tau_lo, double tau_hi, double *kappa_w)
+{
+    int32_t n = 0;
+    for (int64_t r = 0; r < (int64_t)B * 9; ++r) {
+        double s = 0.0;
+        n = 0;
+        for (int32_t l = 0; l < L; ++l) {
+            double tau = l * dt_ps;
+            if (tau >= tau_lo && tau <= tau_hi) {
+                s += kappa[r * L + l];
+                ++n;
+            }
+        }
+        kappa_w[r] = n > 0 ? s / n : 0.0;
+    }
+    return n;
+}
+
+/*
+ * HNEMA (Eq. 19): time average of the binned modal current and
+ *   kappa_b^mu = <J_b^mu> / (T V |F_e|)   in W/(m K)
+ * i.e. sum_nu kappa_b^{mu nu} Fhat^nu; for F_e along x this is kappa_b^{mu x}.
+ */
+void orc_hnema(int64_t T, int32_t B, const double *Jb, double T_K, double V_A3,
+               const double Fe[3], double *meanJ, double *kappa)
+{
+    double fe = sqrt(Fe[0] * Fe[0] + Fe[1] * Fe[1] + Fe[2] * Fe[2]);
+    for (int64_t k = 0; k < (int64_t)B * 3; ++k) {
+        double s = 0.0;
+        for (int64_t t = 0; t < T; ++t) s += Jb[t * B * 3 + k];
+        meanJ[k] = T > 0 ? s / (double)T : 0.0;
+        kappa[k] = fe > 0 ? meanJ[k] / (T_K * V_A3 * fe) * ORC_WMK_PER_EV_PS_A_K : 0.0;
+    }
+}
+
+/* Orthonormality residual of the mode-major eigenvectors: max |E^T E - I|. */
+double orc_orthonormality(int64_t D, int64_t M, const double *Et)
+{
+    double worst = 0.0;
+#pragma omp parallel for schedule(dynamic) reduction(max : worst)
+    for (int64_t n = 0; n < M; ++n)
+        for (int64_t m = n; m < M; ++m) {
+            double s = 0.0;
+            for (int64_t d = 0; d < D; ++d) s += Et[n * D + d] * Et[m * D + d];
+            double r = fabs(s - (n == m ? 1.0 : 0.0));
+            if (r > worst) worst = r;
+        }
+    return worst;
+}
