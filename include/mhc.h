@@ -1,0 +1,235 @@
+/*
+ * mhc.h -- C ABI of the GB300 (sm_103a) modal heat-current library.
+ *
+ * The library computes, for a stream of molecular-dynamics samples, the
+ * modal heat current of the velocity-decomposition methods GKMA and HNEMA
+ * (Gabourie, Fan, Ala-Nissila, Pop, arXiv:2102.03691, Sec. II.B):
+ *
+ *   Eq. 10  J^a(t)       = sum_i sum_b W_i^{ab}(t) v_i^b(t)           total current
+ *   Eq. 13  Xdot_n(t)    = sum_i sqrt(m_i) e_{i,n} . v_i(t)           modal velocity
+ *   Eq. 16  J_n^a(t)     = (sum_i m_i^{-1/2} (W_i(t) e_{i,n})^a) Xdot_n(t)
+ *           J_b^a(t)     = sum_{n in bin b} J_n^a(t)                  (Sec. III.A binning)
+ *   Eq. 17  kappa_b^{mu nu}(tau) = (k_B T^2 V)^{-1} int_0^tau <J_b^mu(t') J^nu(0)> dt'
+ *   Eq. 19  kappa_b^mu   = <J_b^mu> / (T V |F_e|)
+ *
+ * Conventions shared by every call:
+ *   - N atoms, D = 3N degrees of freedom indexed d = 3 i + b, M modes kept.
+ *   - e is real (Gamma point).  The eigenvector matrix E has E[d, n] = e^b_{i,n}.
+ *   - v is [K][N][3] float32 (A/ps); W is [K][N][9] float32 (eV) with
+ *     W[k][i][3 a + b] = W_i^{ab} (row-major, full non-symmetric tensor, Eq. 8).
+ *   - Units: m in amu, frequencies in THz, dt in ps, T in K, V in A^3, F_e in 1/A;
+ *     currents in eV*A/ps, kappa in W/(m K).
+ *   - Every call returns an mhc_status; nothing throws across the ABI.  On an
+ *     error the handle keeps a message readable through mhc_last_error().
+ *   - All device work is issued on the stream given in mhc_params, in order.
+ *     Calls that return data to the host synchronise that stream first.
+ *   - Device kernels never trap: a kernel that finds a broken invariant or
+ *     waits too long on a barrier writes a sticky status word and returns;
+ *     the next mhc_sync / read call reports it as MHC_ERR_TIMEOUT or
+ *     MHC_ERR_STATE.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef MHC_H
+#define MHC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhc_handle mhc_handle;
+typedef struct mhc_group mhc_group;
+
+typedef enum {
+    MHC_OK = 0,
+    MHC_ERR_INVALID_ARG = 1,   /* bad pointer, size, layout or order of calls */
+    MHC_ERR_OOM = 2,           /* a device or host allocation failed */
+    MHC_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has the name) */
+    MHC_ERR_TIMEOUT = 4,       /* a kernel gave up waiting on a barrier */
+    MHC_ERR_STATE = 5,         /* corrupt state blob or device invariant broken */
+    MHC_ERR_UNSUPPORTED = 6,   /* precision/feature not available on this device */
+    MHC_WARN_NOT_ORTHONORMAL = 100 /* basis check above tolerance (not fatal) */
+} mhc_status;
+
+/* Arithmetic of the two projections (Eq. 13 and the bracket of Eq. 16). */
+typedef enum {
+    MHC_PREC_FP32 = 0,   /* CUDA-core FP32 FMA GEMM, FP32 accumulation */
+    MHC_PREC_BF16X3 = 1, /* tensor cores: hi/lo bfloat16 split, 3 products, FP32 accum */
+    MHC_PREC_FP16X3 = 2  /* tensor cores: hi/lo float16 split with power-of-two
+                            scaling, 3 products, FP32 accumulation */
+} mhc_precision;
+
+typedef enum { MHC_MEM_HOST = 0, MHC_MEM_DEVICE = 1 } mhc_mem;
+typedef enum { MHC_F32 = 0, MHC_F64 = 1 } mhc_dtype;
+/* DOF_MAJOR: E[d * ld + n] (rows are degrees of freedom, as printed in Eq. 13).
+ * MODE_MAJOR: E[n * ld + d] (each eigenvector contiguous). */
+typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
+
+/* Flags for mhc_params.flags */
+#define MHC_FLAG_GKMA 0x1          /* accumulate Eq. 17 lag correlations (needs n_lags > 0) */
+#define MHC_FLAG_NO_GRAPH 0x2      /* launch kernels directly instead of replaying a CUDA graph */
+
+typedef struct {
+    int32_t device;      /* CUDA device ordinal */
+    void *stream;        /* cudaStream_t to issue on; NULL = the legacy default stream */
+    int32_t k_max;       /* largest K accepted by mhc_push (steps per block) */
+    int32_t n_lags;      /* L: lags 0..L-1 of the Eq. 17 correlation (GKMA) */
+    int32_t precision;   /* mhc_precision */
+    int32_t flags;       /* MHC_FLAG_* */
+    int32_t tile_n;      /* 0 = autotune; else tensor-core tile width in columns */
+    int32_t ortho_probe; /* -1: no basis check in set_modes; 0: full E^T E; P>0: P probe modes */
+    double dt_ps;        /* sampling interval between pushed steps (Eq. 17 dt') */
+    double T_K;          /* temperature T (Eq. 17, 19) */
+    double V_A3;         /* cell volume V (Eq. 17, 19) */
+    double F_e[3];       /* HNEMD driving-force parameter F_e (Eq. 12, 19), 1/A */
+} mhc_params;
+
+/* Counters and derived sizes of a handle. */
+typedef struct {
+    int64_t n_atoms, n_dof, n_modes_in, n_modes_kept; /* N, 3N, M given, M after excluding bin -1 */
+    int32_t n_bins, n_lags, k_max, precision;
+    int64_t steps_pushed;        /* T_s so far */
+    int64_t pushes;              /* number of mhc_push calls */
+    int64_t n_slots;             /* per-step partial-sum slots of the bin reduction */
+    int32_t tile_n, stages, grid;/* tensor-core kernel configuration in use */
+    int32_t e_exp;               /* power-of-two scale applied to E before the split */
+    double ortho_err;            /* last basis check result, -1 if none */
+    int64_t device_bytes;        /* device memory owned by the handle */
+    int64_t kernel_launches;     /* kernels launched by the handle so far */
+} mhc_info;
+
+/* Fill *p with defaults: device 0, default stream, k_max 256, no GKMA,
+ * BF16X3, dt 0.01 ps, T 300 K, V 1 A^3, F_e = (1e-5, 0, 0), autotune, no check. */
+void mhc_default_params(mhc_params *p);
+
+/* Create a handle.  Allocates nothing large until mhc_set_modes.
+ * Errors: INVALID_ARG (null, k_max < 1, n_lags < 0, GKMA without lags),
+ * UNSUPPORTED (tensor-core precision on a device other than sm_103),
+ * CUDA.  On error *h is NULL. */
+mhc_status mhc_create(mhc_handle **h, const mhc_params *p);
+
+/* Release every device buffer and the handle.  Synchronises the stream. NULL is ignored. */
+void mhc_destroy(mhc_handle *h);
+
+/* Message of the last error on h (empty string if none); valid until the next call on h.
+ * With h == NULL, the last error of a failed mhc_create on this thread. */
+const char *mhc_last_error(const mhc_handle *h);
+const char *mhc_status_string(mhc_status s);
+
+/*
+ * Load the eigenvectors e_{i,n} (Eq. 13, 14; Sec. II.B), mode frequencies and
+ * atomic masses.
+ *   n_atoms  N (D = 3N rows of E)
+ *   n_modes  M columns of E (M <= 3N; a mode subset is allowed, Sec. III.C.i)
+ *   E        eigenvectors, dtype MHC_F32/MHC_F64, layout MHC_DOF_MAJOR/MODE_MAJOR,
+ *            leading dimension ld (>= M for DOF_MAJOR, >= D for MODE_MAJOR),
+ *            host or device memory according to `where`
+ *   freq_THz [M] host, may be NULL if bins are given by mhc_set_bin_ids
+ *   mass_amu [N] host, every m_i > 0
+ * The library copies everything; the caller may free its buffers on return.
+ * Resets all accumulators.  Binning must be (re)applied afterwards with
+ * mhc_set_bins_uniform or mhc_set_bin_ids.
+ * Errors: INVALID_ARG, OOM, CUDA; WARN_NOT_ORTHONORMAL if ortho_probe >= 0 and
+ * max |E^T E - I| > 1e-6 (the modes are still loaded).
+ */
+mhc_status mhc_set_modes(mhc_handle *h, int64_t n_atoms, int64_t n_modes, const void *E,
+                         int32_t dtype, int32_t layout, int64_t ld, int32_t where,
+                         const double *freq_THz, const double *mass_amu);
+
+/*
+ * Frequency bins of fixed width (Sec. III.A: 1 THz for CNT/graphene, 0.25 THz
+ * for Si).  Bin b covers [f_min + b w, f_min + (b+1) w), w = (f_max - f_min)/B,
+ * the last bin also takes f_max; modes outside [f_min, f_max] are excluded.
+ * The bin index is floor((f - f_min) / w) in double precision.
+ * Requires frequencies from mhc_set_modes.  Resets the accumulators.
+ */
+mhc_status mhc_set_bins_uniform(mhc_handle *h, double f_min, double f_max, int32_t n_bins);
+
+/*
+ * Explicit bin of every mode (host array [M], values in [0, B) or -1 to exclude),
+ * e.g. mode-count bins (Sec. III.C.ii uses 27 modes per bin).  Resets the accumulators.
+ */
+mhc_status mhc_set_bin_ids(mhc_handle *h, const int32_t *bin_of_mode, int32_t n_bins);
+
+/*
+ * Push one block of K consecutive samples (1 <= K <= k_max):
+ *   v [K][N][3] float32, W [K][N][9] float32, in host or device memory (`where`).
+ * Computes J(t) (Eq. 10), the binned modal currents J_b(t) (Eq. 13, 16), adds
+ * them to the HNEMA sums (Eq. 19) and, with MHC_FLAG_GKMA, to the lag
+ * correlation sums (Eq. 17).  Asynchronous: device inputs must stay valid until
+ * the stream reaches the push; host inputs are copied before the call returns.
+ * Errors: INVALID_ARG (no modes/bins yet, K out of range, null), CUDA.
+ */
+mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, int32_t where);
+
+/* Wait for the stream and report a sticky device status (TIMEOUT/STATE). */
+mhc_status mhc_sync(mhc_handle *h);
+
+/* Binned modal current of the last pushed block, out [K_last][B][3] float32. */
+mhc_status mhc_read_binned_current(mhc_handle *h, float *out, int32_t where);
+
+/* Total current (Eq. 10) of the last pushed block, out [K_last][3] float64. */
+mhc_status mhc_read_total_current(mhc_handle *h, double *out, int32_t where);
+
+/*
+ * HNEMA (Eq. 19): mean_J [B][3] = <J_b^mu> over all pushed steps (eV A/ps) and
+ * kappa [B][3] = <J_b^mu> / (T V |F_e|) in W/(m K).  Either pointer may be NULL.
+ */
+mhc_status mhc_read_hnema(mhc_handle *h, double *kappa, double *mean_J, int32_t where);
+
+/*
+ * GKMA raw correlation sums (Eq. 17 integrand before averaging):
+ *   corr_sum [B][3][3][L] = sum_{t >= l} J_b^mu(t) J^nu(t - l), float64
+ *   count    [L]          = number of time origins of each lag (int64), may be NULL.
+ * Requires MHC_FLAG_GKMA.
+ */
+mhc_status mhc_read_corr(mhc_handle *h, double *corr_sum, int64_t *count, int32_t where);
+
+/*
+ * GKMA modal thermal conductivity (Eq. 17), trapezoid rule, kappa(0) = 0:
+ *   kappa_tau [B][3][3][L]  running integral kappa_b^{mu nu}(l dt), W/(m K); may be NULL
+ *   kappa_w   [B][3][3]     its average over lags with tau_lo <= l dt <= tau_hi
+ *                           (the tau window of Sec. III.A), may be NULL.
+ */
+mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, double tau_hi,
+                             double *kappa_w, int32_t where);
+
+/* Last basis check of mhc_set_modes (FP64 on the GPU): max |E^T E - I|.
+ * Returns WARN_NOT_ORTHONORMAL above tol, INVALID_ARG if no check was run. */
+mhc_status mhc_check_orthonormality(mhc_handle *h, double tol, double *max_abs_err);
+
+/* Counters and sizes. */
+mhc_status mhc_get_info(mhc_handle *h, mhc_info *info);
+
+/* Zero the HNEMA and GKMA accumulators and the step counter (modes and bins stay). */
+mhc_status mhc_reset(mhc_handle *h);
+
+/*
+ * Checkpoint / resume of the accumulators (step count, HNEMA sums, GKMA sums
+ * and the ring of recent total currents).  mhc_state_size gives the blob size;
+ * the blob is only valid for a handle with the same modes, bins, L and k_max.
+ * A run split by get/set_state gives bitwise the same results as an unsplit run.
+ */
+mhc_status mhc_state_size(mhc_handle *h, size_t *bytes);
+mhc_status mhc_get_state(mhc_handle *h, void *blob, size_t bytes);
+mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes);
+
+/*
+ * Grouped execution of several independent systems (e.g. many nanotubes of
+ * uneven size): one persistent tensor-core launch covers the tiles of all
+ * handles, balanced by their cost, replayed as a CUDA graph.  All handles must
+ * be on the same device and stream, use the same tensor-core precision, and
+ * have modes and bins loaded.  The group does not own the handles.
+ */
+mhc_status mhc_group_create(mhc_group **g, mhc_handle *const *handles, int32_t n);
+void mhc_group_destroy(mhc_group *g);
+/* v[j], W[j] are the inputs of handle j with K[j] steps (same rules as mhc_push). */
+mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *const *W,
+                          const int32_t *K, int32_t where);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHC_H */

@@ -1,0 +1,117 @@
+// Plain FP32 CUDA-core path of the two projections (Eq. 13 and the bracket of
+// Eq. 16) and its bin epilogue.  This is the FP32 GPU baseline the tensor-core
+// path is compared against; it accumulates in FP32 FMA order over d.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mhc {
+
+namespace {
+
+constexpr int SG_BM = 128;  // modes per tile
+constexpr int SG_BN = 128;  // B rows (columns of the product) per tile
+constexpr int SG_BK = 16;
+constexpr int SG_THREADS = 256;
+
+// R[c][n] = sum_d Bt[c][d] * Et[n][d]; both operands have d contiguous.
+// 256 threads, each an 8 x 8 register tile (modes tx*4+{0..3}, 64+tx*4+{0..3};
+// columns ty*4+{0..3}, 64+ty*4+{0..3}); shared tiles stored d-major.
+__global__ void __launch_bounds__(SG_THREADS) sgemm_tn_kernel(const float *__restrict__ Et,
+                                                              const float *__restrict__ Bt,
+                                                              float *__restrict__ R, int D_ld,
+                                                              int Mp, int C) {
+    __shared__ __align__(16) float As[SG_BK][SG_BM];
+    __shared__ __align__(16) float Bs[SG_BK][SG_BN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int n0 = blockIdx.x * SG_BM, c0 = blockIdx.y * SG_BN;
+    // global load mapping: row = tid/2, 8 consecutive d at (tid&1)*8
+    const int lrow = tid >> 1, lk = (tid & 1) * 8;
+    const float *ga = Et + (size_t)(n0 + lrow) * D_ld + lk;
+    const int crow = min(c0 + lrow, C - 1);   // rows past C are never stored
+    const float *gb = Bt + (size_t)crow * D_ld + lk;
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    float4 ra0 = *reinterpret_cast<const float4 *>(ga);
+    float4 ra1 = *reinterpret_cast<const float4 *>(ga + 4);
+    float4 rb0 = *reinterpret_cast<const float4 *>(gb);
+    float4 rb1 = *reinterpret_cast<const float4 *>(gb + 4);
+    for (int d0 = 0; d0 < D_ld; d0 += SG_BK) {
+        __syncthreads();
+        As[lk + 0][lrow] = ra0.x; As[lk + 1][lrow] = ra0.y; As[lk + 2][lrow] = ra0.z; As[lk + 3][lrow] = ra0.w;
+        As[lk + 4][lrow] = ra1.x; As[lk + 5][lrow] = ra1.y; As[lk + 6][lrow] = ra1.z; As[lk + 7][lrow] = ra1.w;
+        Bs[lk + 0][lrow] = rb0.x; Bs[lk + 1][lrow] = rb0.y; Bs[lk + 2][lrow] = rb0.z; Bs[lk + 3][lrow] = rb0.w;
+        Bs[lk + 4][lrow] = rb1.x; Bs[lk + 5][lrow] = rb1.y; Bs[lk + 6][lrow] = rb1.z; Bs[lk + 7][lrow] = rb1.w;
+        __syncthreads();
+        if (d0 + SG_BK < D_ld) {   // prefetch the next slab into registers
+            ra0 = *reinterpret_cast<const float4 *>(ga + d0 + SG_BK);
+            ra1 = *reinterpret_cast<const float4 *>(ga + d0 + SG_BK + 4);
+            rb0 = *reinterpret_cast<const float4 *>(gb + d0 + SG_BK);
+            rb1 = *reinterpret_cast<const float4 *>(gb + d0 + SG_BK + 4);
+        }
+#pragma unroll
+        for (int kk = 0; kk < SG_BK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][tx * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + tx * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][ty * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][64 + ty * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = c0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
+        if (c >= C) continue;
+        float *row = R + (size_t)c * Mp + n0;
+        *reinterpret_cast<float4 *>(row + tx * 4) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        *reinterpret_cast<float4 *>(row + 64 + tx * 4) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+    }
+}
+
+// One thread per stored mode (warps = 32 consecutive modes), a strip of steps.
+constexpr int EPI_STEPS = 16;
+__global__ void __launch_bounds__(128) fp32_bin_epilogue_kernel(const float *__restrict__ R, int Mp,
+                                                                int K, const int *mode_bin,
+                                                                const int *mode_slot,
+                                                                float *partials, int n_slots) {
+    const int n = blockIdx.x * 128 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int bin = mode_bin[n];
+    const int slot = mode_slot[n];
+    const uint32_t take = seg_scan_masks(bin, lane);
+    const int k0 = blockIdx.y * EPI_STEPS;
+    for (int k = k0; k < min(K, k0 + EPI_STEPS); ++k) {
+        const float x = R[(size_t)(4 * k) * Mp + n];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float y = R[(size_t)(4 * k + 1 + a) * Mp + n];
+            const float s = seg_scan(x * y, take);   // Eq. 16: J_n = y_n Xdot_n, summed per bin run
+            if (slot >= 0) partials[((size_t)k * 3 + a) * n_slots + slot] = s;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_sgemm(const float *Et32, const float *Bt32, float *R, int D_ld, int Mp, int C,
+                  cudaStream_t s) {
+    dim3 grid(Mp / SG_BM, (C + SG_BN - 1) / SG_BN);
+    sgemm_tn_kernel<<<grid, SG_THREADS, 0, s>>>(Et32, Bt32, R, D_ld, Mp, C);
+}
+
+void launch_fp32_bin_epilogue(const float *R, int Mp, int K, const int *mode_bin,
+                              const int *mode_slot, float *partials, int n_slots, cudaStream_t s) {
+    dim3 grid(Mp / 128, (K + EPI_STEPS - 1) / EPI_STEPS);
+    fp32_bin_epilogue_kernel<<<grid, 128, 0, s>>>(R, Mp, K, mode_bin, mode_slot, partials, n_slots);
+}
+
+}  // namespace mhc

@@ -1,0 +1,303 @@
+// K2: the modal projections on the 5th-generation tensor cores (sm_103a).
+//
+// For one block of K steps, with B-operand rows c = 4k + {0: sqrt(m) v, 1..3: W^{a.}/sqrt(m)},
+//   R[n][c] = sum_d E[d][n] Bt[c][d]          (Eq. 13 for c = 4k, Eq. 16 bracket otherwise)
+// is one dense GEMM of E^T (modes x D) with Bt^T (D x 4K).  Each 128-mode x BN-column tile
+// accumulates in TMEM (FP32) from 16-bit hi/lo operands staged by TMA:
+//   E B ~= E_hi B_hi + E_hi B_lo + E_lo B_hi        (three tcgen05.mma per 16-wide k slice)
+// and the epilogue fuses the rest of the step: J_n^a(k) = R[n][4k] R[n][4k+1+a] (Eq. 16),
+// then a segmented warp reduction over modes (stored sorted by frequency bin) leaves one
+// partial sum per run of equal bins in each 32-mode group.
+//
+// Warp roles (256 threads, one persistent CTA per SM):
+//   warp 0       TMA producer (one lane)
+//   warp 1       MMA issuer (one lane)
+//   warp 2       TMEM allocator
+//   warps 4..7   epilogue, warp w reads TMEM lanes 32*(w%4) .. +31
+// Every barrier wait is bounded; a wait that runs out raises a CTA-wide abort flag and a
+// sticky device status, and the CTA drains its in-flight copies and MMAs, frees TMEM and exits.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mhc {
+
+namespace {
+
+template <int BN, int BK, int STAGES>
+struct TcLayout {
+    static constexpr int A_BYTES = TC_BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int TILE_BYTES = STAGES * STAGE_BYTES;
+    static constexpr int BAR_BYTES = 256;
+    static constexpr int SMEM_BYTES = TILE_BYTES + BAR_BYTES + 1024;   // + alignment slack
+    static constexpr uint32_t TMEM_COLS = 2 * BN;                       // double-buffered accumulator
+    static constexpr uint32_t SWIZZLE_CODE = BK == 64 ? 2u : 4u;        // 128 B or 64 B rows
+    static constexpr uint32_t SBO = 8 * BK * 2;                         // 8-row core group
+    static_assert(BK == 64 || BK == 32, "BK");
+    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
+    static_assert(STAGES * 2 + 5 <= 28, "barrier area");
+    static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM columns");
+};
+
+template <int NPROB>
+struct TileIter {
+    const TcParams<NPROB> &p;
+    int i, end;
+    __device__ TileIter(const TcParams<NPROB> &pp) : p(pp) {
+        if (p.sched) {
+            i = p.cta_begin[blockIdx.x];
+            end = p.cta_begin[blockIdx.x + 1];
+        } else {
+            i = blockIdx.x;
+            end = p.prob[0].n_tiles;
+        }
+    }
+    __device__ bool next(int &prob, int &mt, int &ct) {
+        if (i >= end) return false;
+        if (p.sched) {
+            const uint32_t id = p.sched[i++];
+            prob = (int)(id >> 28);
+            ct = (int)((id >> 20) & 0xFFu);
+            mt = (int)(id & 0xFFFFFu);
+        } else {
+            const int t = i;
+            i += gridDim.x;
+            prob = 0;
+            mt = t / p.prob[0].n_col_tiles;
+            ct = t - mt * p.prob[0].n_col_tiles;
+        }
+        return true;
+    }
+};
+
+template <int BN, int BK, int STAGES, int NPROB>
+__global__ void __launch_bounds__(256, 1) tc_modal_kernel(const __grid_constant__ TcParams<NPROB> p) {
+    using L = TcLayout<BN, BK, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::TILE_BYTES);
+    uint64_t *full = bars;                   // [STAGES] TMA landed
+    uint64_t *empty = bars + STAGES;         // [STAGES] MMAs done reading
+    uint64_t *acc_full = bars + 2 * STAGES;  // [2] accumulator ready
+    uint64_t *acc_empty = acc_full + 2;      // [2] accumulator drained
+    uint64_t *done_bar = acc_empty + 2;      // final MMA drain
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done_bar + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        mbar_init(done_bar, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2) {
+        tmem_alloc(tmem_slot, L::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------ TMA producer
+        for (int q = 0; q < NPROB; ++q) {
+            if (q > 0 && !p.sched) break;
+            tma_prefetch_desc(&p.prob[q].tmA_hi);
+            tma_prefetch_desc(&p.prob[q].tmA_lo);
+            tma_prefetch_desc(&p.prob[q].tmB_hi);
+            tma_prefetch_desc(&p.prob[q].tmB_lo);
+        }
+        const uint64_t pol_b = l2_policy_evict_last();
+        const uint64_t pol_e = l2_policy_evict_first();
+        uint32_t issued_phase[STAGES];
+        bool issued[STAGES];
+        for (int s = 0; s < STAGES; ++s) issued[s] = false;
+        int stage = 0;
+        uint32_t phase = 0;
+        TileIter<NPROB> it(p);
+        int prob, mt, ct;
+        bool ok = true;
+        while (ok && it.next(prob, mt, ct)) {
+            const TcProblem &P = p.prob[prob];
+            for (int kb = 0; kb < P.n_kb; ++kb) {
+                if (!mbar_wait(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
+                uint8_t *sa = smem + stage * L::STAGE_BYTES;
+                mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
+                const int x = kb * BK;
+                tma_load_2d(sa, &P.tmA_hi, &full[stage], x, mt * TC_BM, pol_e);
+                tma_load_2d(sa + L::A_BYTES, &P.tmA_lo, &full[stage], x, mt * TC_BM, pol_e);
+                tma_load_2d(sa + 2 * L::A_BYTES, &P.tmB_hi, &full[stage], x, ct * BN, pol_b);
+                tma_load_2d(sa + 2 * L::A_BYTES + L::B_BYTES, &P.tmB_lo, &full[stage], x, ct * BN, pol_b);
+                issued[stage] = true;
+                issued_phase[stage] = phase;
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+        }
+        if (!ok) {
+            *abort = 1;
+            set_status(p.status, DEV_TIMEOUT);
+        }
+        // Drain: every copy this CTA issued must have landed before the CTA may exit.
+        for (int s = 0; s < STAGES; ++s)
+            if (issued[s]) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&full[s], issued_phase[s]) &&
+                       clock64() - t0 < WAIT_LIMIT_CYCLES) {
+                }
+            }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        const uint32_t idesc = p.idesc;
+        int stage = 0, abuf = 0;
+        uint32_t phase = 0, aphase = 0;
+        TileIter<NPROB> it(p);
+        int prob, mt, ct;
+        bool ok = true;
+        const uint32_t smem0 = smem_u32(smem);
+        while (ok && it.next(prob, mt, ct)) {
+            const TcProblem &P = p.prob[prob];
+            if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * BN);
+            for (int kb = 0; kb < P.n_kb; ++kb) {
+                if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t a_hi = smem0 + stage * L::STAGE_BYTES;
+                const uint32_t a_lo = a_hi + L::A_BYTES;
+                const uint32_t b_hi = a_hi + 2 * L::A_BYTES;
+                const uint32_t b_lo = b_hi + L::B_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint32_t off = kk * 32;   // 16 elements of 2 bytes
+                    const uint64_t dah = smem_desc_kmajor(a_hi + off, L::SBO, L::SWIZZLE_CODE);
+                    const uint64_t dal = smem_desc_kmajor(a_lo + off, L::SBO, L::SWIZZLE_CODE);
+                    const uint64_t dbh = smem_desc_kmajor(b_hi + off, L::SBO, L::SWIZZLE_CODE);
+                    const uint64_t dbl = smem_desc_kmajor(b_lo + off, L::SBO, L::SWIZZLE_CODE);
+                    umma_f16(d_tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
+                    umma_f16(d_tmem, dah, dbl, idesc, 1u);
+                    umma_f16(d_tmem, dal, dbh, idesc, 1u);
+                }
+                umma_commit(&empty[stage]);
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+            if (!ok) break;
+            umma_commit(&acc_full[abuf]);
+            if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+        }
+        if (!ok) {
+            *abort = 1;
+            set_status(p.status, DEV_TIMEOUT);
+        }
+        // Drain: all MMAs issued by this thread complete before TMEM is released.
+        umma_commit(done_bar);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(done_bar, 0) && clock64() - t0 < WAIT_LIMIT_CYCLES) {
+        }
+    } else if (warp >= 4) {
+        // ------------------------------------------------------------ epilogue
+        const int qw = warp & 3;   // TMEM lane quarter of this warp
+        int abuf = 0;
+        uint32_t aphase = 0;
+        TileIter<NPROB> it(p);
+        int prob, mt, ct;
+        while (it.next(prob, mt, ct)) {
+            const TcProblem &P = p.prob[prob];
+            const int n = mt * TC_BM + qw * 32 + lane;
+            const int bin = P.mode_bin[n];
+            const int slot = P.mode_slot[n];
+            const uint32_t take = seg_scan_masks(bin, lane);
+            if (!mbar_wait(&acc_full[abuf], aphase, abort)) {
+                *abort = 1;
+                set_status(p.status, DEV_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const int kbase = ct * (BN / 4);
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                if (kbase + c * 8 >= P.K) break;   // warp-uniform
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(qw * 32) << 16) + (uint32_t)(abuf * BN + c * 32), r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const int k = kbase + c * 8 + s;
+                    if (k >= P.K) break;   // warp-uniform
+                    const float *cs = P.col_scale + 4 * k;
+                    const float x = __uint_as_float(r[4 * s]) * __ldg(cs);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float y = __uint_as_float(r[4 * s + 1 + a]) * __ldg(cs + 1 + a);
+                        const float v = seg_scan(x * y, take);   // Eq. 16 product, bin-run sum
+                        if (slot >= 0) P.partials[((size_t)k * 3 + a) * P.n_slots + slot] = v;
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[abuf]);
+            if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 2) tmem_dealloc(tmem_base, L::TMEM_COLS);
+}
+
+template <int BN, int BK, int STAGES, int NPROB>
+cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
+    using L = TcLayout<BN, BK, STAGES>;
+    auto kern = tc_modal_kernel<BN, BK, STAGES, NPROB>;
+    static bool attr_set = false;   // per process; the attribute is per function
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             L::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kern<<<grid, 256, L::SMEM_BYTES, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int NPROB>
+cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s) {
+    if (c.bn == 256 && c.bk == 64 && c.stages == 2) return launch_impl<256, 64, 2, NPROB>(p, c.grid, s);
+    if (c.bn == 256 && c.bk == 32 && c.stages == 4) return launch_impl<256, 32, 4, NPROB>(p, c.grid, s);
+    if (c.bn == 128 && c.bk == 64 && c.stages == 3) return launch_impl<128, 64, 3, NPROB>(p, c.grid, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool tc_config_supported(const TcConfig &c) {
+    return (c.bn == 256 && c.bk == 64 && c.stages == 2) || (c.bn == 256 && c.bk == 32 && c.stages == 4) ||
+           (c.bn == 128 && c.bk == 64 && c.stages == 3);
+}
+
+size_t tc_smem_bytes(const TcConfig &c) {
+    return (size_t)c.stages * (2 * TC_BM * c.bk * 2 + 2 * c.bn * c.bk * 2) + 256 + 1024;
+}
+
+cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream_t s) {
+    return dispatch<1>(p, c, s);
+}
+cudaError_t launch_tc_group(const TcParams<TC_MAX_GROUP> &p, const TcConfig &c, cudaStream_t s) {
+    return dispatch<TC_MAX_GROUP>(p, c, s);
+}
+
+}  // namespace mhc

@@ -1,0 +1,124 @@
+// Internal launch interface between the C-ABI layer (mhc_api.cu) and the kernels.
+// Not part of the public ABI.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mhc {
+
+enum Split { SPLIT_FP32 = 0, SPLIT_BF16 = 1, SPLIT_FP16 = 2 };
+
+// Sticky device status codes (same values as mhc_status).
+constexpr int DEV_OK = 0, DEV_TIMEOUT = 4, DEV_STATE = 5;
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, A and B of
+// the same 16-bit type (ab_fmt 0 = f16, 1 = bf16), both K-major, M x N tile.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt, uint32_t M, uint32_t N) {
+    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------- K1 pack
+// One CTA per step k of the block.  Builds the four B-operand rows of step k,
+//   Bt[4k][d]       = sqrt(m_i) v_i^b            (Eq. 13 weights)
+//   Bt[4k+1+a][d]   = W_i^{ab} / sqrt(m_i)       (Eq. 16 bracket weights)
+// (d = 3i+b), split into hi/lo 16-bit parts after a per-row power-of-two scale
+// 2^s (FP16), and the FP64 total current J(t0+k) of Eq. 10.
+struct PackArgs {
+    const float *v;        // [K][N][3]
+    const float *W;        // [K][N][9]
+    const float *sqm;      // [N] sqrt(m_i)
+    const float *isqm;     // [N] 1/sqrt(m_i)
+    int N, K, D_ld, split, e_exp;
+    long long t0;          // global index of the block's first step
+    void *Bt_hi, *Bt_lo;   // [rows][D_ld] 16-bit (split != FP32)
+    float *Bt32;           // [rows][D_ld] (split == FP32)
+    float *col_scale;      // [4K] 2^-(s_row + e_exp): undoes both power-of-two scales
+    double *Jtot;          // [K][3]
+    double *Jring;         // [R][3] ring of past J (GKMA) or null
+    int R;
+};
+void launch_pack(const PackArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------- E preparation
+// max |E| over the valid D x M region (bit pattern of a non-negative float)
+void launch_max_abs(const void *E, int dtype, int layout, int64_t ld, int64_t D, int64_t M,
+                    unsigned *out_bits, cudaStream_t s);
+// Gather the kept modes in bin order (perm), transpose to mode-major and split:
+//   Et[n'][d] = E[d, perm[n']] * 2^e_exp   (zero for n' >= M_eff or d >= D)
+void launch_prepare_modes(const void *E, int dtype, int layout, int64_t ld, int64_t D,
+                          int64_t M_eff, const int *perm, int e_exp, int split, void *Et_hi,
+                          void *Et_lo, float *Et32, int64_t D_ld, int64_t M_pad, cudaStream_t s);
+// FP64 basis check: max over probe modes p and all modes m of |sum_d E[d,p]E[d,m] - delta|
+void launch_orthonormality(const void *E, int dtype, int layout, int64_t ld, int64_t D,
+                           int64_t M, const int *probe, int n_probe,
+                           unsigned long long *out_bits, cudaStream_t s);
+
+// ---------------------------------------------------------------- FP32 path
+// R[c][n] = sum_d Bt32[c][d] Et32[n][d] for c < C (rows of the block), n < Mp.
+void launch_sgemm(const float *Et32, const float *Bt32, float *R, int D_ld, int Mp, int C,
+                  cudaStream_t s);
+// J_n^a(k) = R[4k][n] R[4k+1+a][n]; segmented bin sums into partials[k][a][slot].
+void launch_fp32_bin_epilogue(const float *R, int Mp, int K, const int *mode_bin,
+                              const int *mode_slot, float *partials, int n_slots, cudaStream_t s);
+
+// ---------------------------------------------------------------- tensor-core path
+constexpr int TC_BM = 128;        // modes per tile = TMEM lanes
+constexpr int TC_MAX_GROUP = 16;  // systems per grouped launch
+
+struct TcProblem {   // 128-byte aligned through CUtensorMap
+    CUtensorMap tmA_hi, tmA_lo;   // Et hi/lo [M_pad][D_ld]
+    CUtensorMap tmB_hi, tmB_lo;   // Bt hi/lo [rows][D_ld]
+    const int *mode_bin;          // [M_pad] bin of each stored mode, -1 for padding
+    const int *mode_slot;         // [M_pad] partial-sum slot of run tails, else -1
+    const float *col_scale;       // [4K]
+    float *partials;              // [K][3][n_slots]
+    int n_slots, n_kb, K, n_col_tiles, n_tiles;
+};
+
+template <int NPROB>
+struct TcParams {
+    TcProblem prob[NPROB];
+    const uint32_t *sched;   // packed tile list (null: round-robin over prob[0])
+    const int *cta_begin;    // [grid+1] offsets into sched
+    int *status;
+    uint32_t idesc;
+};
+
+struct TcConfig {
+    int bn;       // columns per tile (MMA N): 128 or 256
+    int bk;       // K elements per stage: 64 (128-byte swizzle) or 32 (64-byte swizzle)
+    int stages;
+    int grid;
+};
+size_t tc_smem_bytes(const TcConfig &c);
+bool tc_config_supported(const TcConfig &c);
+// Encode a 2D 16-bit tensor map: rows x cols (cols innermost, row pitch ld elements).
+int tc_make_tmap(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint64_t ld,
+                 uint32_t box_rows, uint32_t box_cols);
+cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream_t s);
+cudaError_t launch_tc_group(const TcParams<TC_MAX_GROUP> &p, const TcConfig &c, cudaStream_t s);
+// Pack a tile id for the scheduler.
+__host__ __device__ inline uint32_t tc_tile_id(int prob, int mt, int ct) {
+    return ((uint32_t)prob << 28) | ((uint32_t)ct << 20) | (uint32_t)mt;
+}
+
+// ---------------------------------------------------------------- K3 .. K5
+// Jb[k][b][a] = sum of partial slots of bin b; HNEMA sums += sum_k Jb (FP64);
+// Jsum[a] += sum_k Jtot[k][a].
+void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin, int B, int K,
+                       float *Jb, double *hsum, const double *Jtot, double *Jsum, cudaStream_t s);
+// Csum[b][mu][nu][l] += sum_k Jb[k][b][mu] J(t0+k-l)^nu over t0+k-l >= 0.
+void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
+                     int L, long long t0, cudaStream_t s);
+// kappa_tau[r][l] (r = b*9+mu*3+nu) and window averages kappa_w[r], FP64.
+void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
+                     double tau_lo, double tau_hi, double dt, double *kappa_tau,
+                     double *kappa_w, cudaStream_t s);
+// mean[b][a] = hsum/T_s; kappa[b][a] = mean * coef
+void launch_hnema_finalize(const double *hsum, int B, long long T_s, double coef, double *mean,
+                           double *kappa, cudaStream_t s);
+// count[l] = max(T_s - l, 0)
+void launch_lag_counts(long long T_s, int L, long long *count, cudaStream_t s);
+
+}  // namespace mhc

@@ -1,0 +1,925 @@
+// C-ABI layer of the modal heat-current library (declarations and semantics: include/mhc.h).
+// Owns the device buffers of a handle, turns frequencies into the bin-sorted mode order
+// the fused epilogue needs, and issues the kernels of one push on the handle's stream.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mhc.h"
+#include "kernels.h"
+
+using namespace mhc;
+
+namespace {
+
+constexpr double KB_EV_PER_K = 8.617333262145179e-5;   // k_B / e (SI exact ratio)
+constexpr double WMK_PER_EV_PS_A_K = 1602.176634;      // 1 eV/(ps A K) in W/(m K)
+constexpr int K_MAX_LIMIT = 1024;
+constexpr uint32_t STATE_MAGIC = 0x4d484331u;         // "MHC1"
+
+thread_local std::string g_create_error;
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+int mhc::tc_make_tmap(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint64_t ld,
+                      uint32_t box_rows, uint32_t box_cols) {
+    auto fn = tmap_encode_fn();
+    if (!fn) return -1;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {ld * 2};
+    cuuint32_t box[2] = {box_cols, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUtensorMapSwizzle sw = box_cols * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : (int)r;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct mhc_handle {
+    mhc_params prm{};
+    cudaStream_t stream = nullptr;
+    int sm_count = 0, cc_major = 0, cc_minor = 0;
+    int split = SPLIT_BF16;
+    std::string err;
+
+    // modes
+    bool modes_ready = false, bins_ready = false;
+    int64_t N = 0, D = 0, M_in = 0, M_eff = 0, D_ld = 0, M_pad = 0;
+    std::vector<double> freq, mass;
+    std::vector<int> perm;          // stored (bin-sorted) mode -> input mode
+    int e_exp = 0;
+    double ortho_err = -1.0;
+
+    // bins
+    int32_t B = 0;
+    int64_t n_slots = 0;
+    int64_t B_rows = 0;             // rows of the B operand (>= 4 k_max, multiple of 256)
+    int R_ring = 0;
+
+    // accumulators / counters
+    int64_t steps = 0, pushes = 0, launches = 0;
+    int K_last = 0;
+
+    // device buffers
+    std::map<std::string, DevBuf> buf;
+    int *status = nullptr;
+
+    // tensor-core state
+    TcConfig tc{256, 64, 2, 0};
+    std::map<int, TcConfig> tuned;  // K -> config
+    TcParams<1> tcp{};
+};
+
+struct mhc_group {
+    std::vector<mhc_handle *> hs;
+    TcConfig tc{256, 64, 2, 0};
+    TcParams<TC_MAX_GROUP> tcp{};
+    DevBuf sched, cta_begin;
+    std::vector<int> lastK;
+    int *status = nullptr;
+};
+
+namespace {
+
+mhc_status fail(mhc_handle *h, mhc_status s, const char *fmt, ...) {
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+#define MHC_CUDA(h, call)                                                                        \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? MHC_ERR_OOM : MHC_ERR_CUDA,       \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+mhc_status dev_alloc(mhc_handle *h, const char *name, size_t bytes, bool zero = true) {
+    DevBuf &b = h->buf[name];
+    if (b.p && b.bytes >= bytes) {
+        if (zero) MHC_CUDA(h, cudaMemsetAsync(b.p, 0, b.bytes, h->stream));
+        return MHC_OK;
+    }
+    if (b.p) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) return MHC_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(h, MHC_ERR_OOM, "cudaMalloc of %zu bytes for %s failed: %s", bytes, name,
+                    cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    if (zero) MHC_CUDA(h, cudaMemsetAsync(b.p, 0, bytes, h->stream));
+    return MHC_OK;
+}
+
+template <typename T>
+T *dptr(mhc_handle *h, const char *name) {
+    auto it = h->buf.find(name);
+    return it == h->buf.end() ? nullptr : static_cast<T *>(it->second.p);
+}
+
+void dev_free(mhc_handle *h, const char *name) {
+    auto it = h->buf.find(name);
+    if (it == h->buf.end()) return;
+    if (it->second.p) cudaFree(it->second.p);
+    h->buf.erase(it);
+}
+
+bool is_tc(const mhc_handle *h) { return h->split != SPLIT_FP32; }
+
+mhc_status check_device_status(mhc_handle *h) {
+    int st = 0;
+    MHC_CUDA(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (st == DEV_TIMEOUT)
+        return fail(h, MHC_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on a barrier");
+    if (st != 0) return fail(h, MHC_ERR_STATE, "device status word %d", st);
+    return MHC_OK;
+}
+
+mhc_status reset_accumulators(mhc_handle *h) {
+    h->steps = 0;
+    h->K_last = 0;
+    const int64_t B = std::max<int32_t>(h->B, 1), L = std::max<int32_t>(h->prm.n_lags, 0);
+    mhc_status s;
+    if ((s = dev_alloc(h, "hsum", sizeof(double) * B * 3)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "Jsum", sizeof(double) * 3)) != MHC_OK) return s;
+    if (h->prm.flags & MHC_FLAG_GKMA) {
+        if ((s = dev_alloc(h, "Csum", sizeof(double) * B * 9 * L)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "Jring", sizeof(double) * h->R_ring * 3)) != MHC_OK) return s;
+    }
+    return MHC_OK;
+}
+
+// Host binning of Sec. III.A: floor((f - f_min)/w) in double, last bin closed.
+void bins_uniform_host(const std::vector<double> &f, double f_min, double f_max, int B,
+                       std::vector<int> &out) {
+    const double w = (f_max - f_min) / (double)B;
+    out.resize(f.size());
+    for (size_t n = 0; n < f.size(); ++n) {
+        const double x = f[n];
+        if (!std::isfinite(x) || x < f_min || x > f_max) {
+            out[n] = -1;
+            continue;
+        }
+        int64_t b = (int64_t)std::floor((x - f_min) / w);
+        if (b >= B) b = B - 1;
+        if (b < 0) b = 0;
+        out[n] = (int)b;
+    }
+}
+
+// Sort kept modes by bin (stable), build the per-mode bin/slot tables of the fused
+// epilogue, gather+split E into the stored order and set up the tensor maps.
+mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_t B) {
+    if (B < 1) return fail(h, MHC_ERR_INVALID_ARG, "number of bins must be >= 1");
+    for (int b : bin_of_mode)
+        if (b < -1 || b >= B) return fail(h, MHC_ERR_INVALID_ARG, "bin id %d outside [-1, %d)", b, B);
+    h->B = B;
+    // counting sort, stable in the input mode index
+    std::vector<int64_t> cnt(B + 1, 0);
+    for (int b : bin_of_mode)
+        if (b >= 0) cnt[b + 1]++;
+    for (int b = 0; b < B; ++b) cnt[b + 1] += cnt[b];
+    h->M_eff = cnt[B];
+    h->perm.assign(h->M_eff, 0);
+    {
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t n = 0; n < (int64_t)bin_of_mode.size(); ++n)
+            if (bin_of_mode[n] >= 0) h->perm[pos[bin_of_mode[n]]++] = (int)n;
+    }
+    h->M_pad = round_up(std::max<int64_t>(h->M_eff, 1), TC_BM);
+    std::vector<int> mbin(h->M_pad, -1), mslot(h->M_pad, -1), sbeg(B + 1, 0);
+    for (int64_t q = 0; q < h->M_eff; ++q) mbin[q] = bin_of_mode[h->perm[q]];
+    // a slot for the last mode of every run of equal bins inside each 32-mode group
+    int64_t ns = 0;
+    std::vector<int> slot_bin;
+    for (int64_t q = 0; q < h->M_eff; ++q) {
+        const bool group_end = (q % 32) == 31 || q + 1 == h->M_eff;
+        if (group_end || mbin[q + 1] != mbin[q]) {
+            mslot[q] = (int)ns++;
+            slot_bin.push_back(mbin[q]);
+        }
+    }
+    h->n_slots = std::max<int64_t>(ns, 1);
+    for (int b = 0, s = 0; b <= B; ++b) {
+        while (s < (int)slot_bin.size() && slot_bin[s] < b) ++s;
+        sbeg[b] = s;
+    }
+    sbeg[B] = (int)slot_bin.size();
+
+    mhc_status s;
+    const int K = h->prm.k_max;
+    if ((s = dev_alloc(h, "mode_bin", sizeof(int) * h->M_pad, false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "mode_slot", sizeof(int) * h->M_pad, false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "slot_begin", sizeof(int) * (B + 1), false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "perm", sizeof(int) * std::max<int64_t>(h->M_eff, 1), false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "partials", sizeof(float) * K * 3 * h->n_slots)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "Jb", sizeof(float) * K * B * 3)) != MHC_OK) return s;
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "mode_bin"), mbin.data(), sizeof(int) * h->M_pad,
+                                cudaMemcpyHostToDevice, h->stream));
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "mode_slot"), mslot.data(), sizeof(int) * h->M_pad,
+                                cudaMemcpyHostToDevice, h->stream));
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "slot_begin"), sbeg.data(), sizeof(int) * (B + 1),
+                                cudaMemcpyHostToDevice, h->stream));
+    if (h->M_eff > 0)
+        MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "perm"), h->perm.data(), sizeof(int) * h->M_eff,
+                                    cudaMemcpyHostToDevice, h->stream));
+
+    // stored eigenvectors
+    const size_t ecount = (size_t)h->M_pad * h->D_ld;
+    if (is_tc(h)) {
+        dev_free(h, "Et32");
+        if ((s = dev_alloc(h, "Et_hi", ecount * 2, false)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "Et_lo", ecount * 2, false)) != MHC_OK) return s;
+    } else {
+        if ((s = dev_alloc(h, "Et32", ecount * 4, false)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "R", sizeof(float) * h->B_rows * h->M_pad, false)) != MHC_OK) return s;
+    }
+    launch_prepare_modes(dptr<float>(h, "Eraw"), MHC_F32, MHC_MODE_MAJOR, h->D_ld, h->D, h->M_eff,
+                         dptr<int>(h, "perm"), h->e_exp, h->split, dptr<void>(h, "Et_hi"),
+                         dptr<void>(h, "Et_lo"), dptr<float>(h, "Et32"), h->D_ld, h->M_pad,
+                         h->stream);
+    h->launches++;
+    MHC_CUDA(h, cudaGetLastError());
+
+    if (is_tc(h)) {
+        TcProblem &P = h->tcp.prob[0];
+        const TcConfig &c = h->tc;
+        if (tc_make_tmap(&P.tmA_hi, dptr<void>(h, "Et_hi"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
+            tc_make_tmap(&P.tmA_lo, dptr<void>(h, "Et_lo"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
+            tc_make_tmap(&P.tmB_hi, dptr<void>(h, "Bt_hi"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk) ||
+            tc_make_tmap(&P.tmB_lo, dptr<void>(h, "Bt_lo"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk))
+            return fail(h, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        P.mode_bin = dptr<int>(h, "mode_bin");
+        P.mode_slot = dptr<int>(h, "mode_slot");
+        P.col_scale = dptr<float>(h, "col_scale");
+        P.partials = dptr<float>(h, "partials");
+        P.n_slots = (int)h->n_slots;
+        P.n_kb = (int)(h->D_ld / c.bk);
+        h->tcp.sched = nullptr;
+        h->tcp.cta_begin = nullptr;
+        h->tcp.status = h->status;
+        h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, TC_BM, (uint32_t)c.bn);
+    }
+    h->bins_ready = true;
+    return reset_accumulators(h);
+}
+
+mhc_status set_tc_config(mhc_handle *h, const TcConfig &c) {
+    if (!tc_config_supported(c)) return fail(h, MHC_ERR_INVALID_ARG, "unsupported tile configuration");
+    const bool remap = h->bins_ready && (c.bn != h->tc.bn || c.bk != h->tc.bk);
+    h->tc = c;
+    if (remap) {
+        TcProblem &P = h->tcp.prob[0];
+        if (tc_make_tmap(&P.tmA_hi, dptr<void>(h, "Et_hi"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
+            tc_make_tmap(&P.tmA_lo, dptr<void>(h, "Et_lo"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
+            tc_make_tmap(&P.tmB_hi, dptr<void>(h, "Bt_hi"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk) ||
+            tc_make_tmap(&P.tmB_lo, dptr<void>(h, "Bt_lo"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk))
+            return fail(h, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        P.n_kb = (int)(h->D_ld / c.bk);
+        h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, TC_BM, (uint32_t)c.bn);
+    }
+    return MHC_OK;
+}
+
+// The projections + fused epilogue of one block of K steps (after pack).
+mhc_status run_projection(mhc_handle *h, int K) {
+    if (h->M_eff == 0) {
+        MHC_CUDA(h, cudaMemsetAsync(dptr<float>(h, "partials"), 0,
+                                    sizeof(float) * K * 3 * h->n_slots, h->stream));
+        return MHC_OK;
+    }
+    if (!is_tc(h)) {
+        launch_sgemm(dptr<float>(h, "Et32"), dptr<float>(h, "Bt32"), dptr<float>(h, "R"),
+                     (int)h->D_ld, (int)h->M_pad, 4 * K, h->stream);
+        launch_fp32_bin_epilogue(dptr<float>(h, "R"), (int)h->M_pad, K, dptr<int>(h, "mode_bin"),
+                                 dptr<int>(h, "mode_slot"), dptr<float>(h, "partials"),
+                                 (int)h->n_slots, h->stream);
+        h->launches += 2;
+        MHC_CUDA(h, cudaGetLastError());
+        return MHC_OK;
+    }
+    TcConfig c = h->tc;
+    TcProblem &P = h->tcp.prob[0];
+    P.K = K;
+    P.n_col_tiles = (int)((4 * K + c.bn - 1) / c.bn);
+    P.n_tiles = (int)(h->M_pad / TC_BM) * P.n_col_tiles;
+    c.grid = std::min(h->sm_count, P.n_tiles);
+    cudaError_t e = launch_tc_single(h->tcp, c, h->stream);
+    h->launches++;
+    if (e != cudaSuccess)
+        return fail(h, MHC_ERR_CUDA, "tensor-core kernel launch failed: %s", cudaGetErrorString(e));
+    return MHC_OK;
+}
+
+// Autotune: time each supported tile configuration on the block just packed.
+mhc_status autotune(mhc_handle *h, int K) {
+    const TcConfig cands[] = {{256, 64, 2, 0}, {256, 32, 4, 0}, {128, 64, 3, 0}};
+    cudaEvent_t e0, e1;
+    MHC_CUDA(h, cudaEventCreate(&e0));
+    MHC_CUDA(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    TcConfig best_c = h->tc;
+    for (const TcConfig &c : cands) {
+        mhc_status s = set_tc_config(h, c);
+        if (s != MHC_OK) return s;
+        if ((s = run_projection(h, K)) != MHC_OK) return s;   // warm-up
+        MHC_CUDA(h, cudaEventRecord(e0, h->stream));
+        for (int r = 0; r < 3; ++r)
+            if ((s = run_projection(h, K)) != MHC_OK) return s;
+        MHC_CUDA(h, cudaEventRecord(e1, h->stream));
+        MHC_CUDA(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        MHC_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tuned[K] = best_c;
+    return set_tc_config(h, best_c);
+}
+
+mhc_status stage_inputs(mhc_handle *h, const float *&v, const float *&W, int K, int where) {
+    if (where == MHC_MEM_DEVICE) return MHC_OK;
+    const size_t nv = (size_t)K * h->N * 3, nw = (size_t)K * h->N * 9;
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<float>(h, "v_stage"), v, nv * 4, cudaMemcpyHostToDevice, h->stream));
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<float>(h, "W_stage"), W, nw * 4, cudaMemcpyHostToDevice, h->stream));
+    v = dptr<float>(h, "v_stage");
+    W = dptr<float>(h, "W_stage");
+    return MHC_OK;
+}
+
+mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
+    PackArgs a{};
+    a.v = v;
+    a.W = W;
+    a.sqm = dptr<float>(h, "sqm");
+    a.isqm = dptr<float>(h, "isqm");
+    a.N = (int)h->N;
+    a.K = K;
+    a.D_ld = (int)h->D_ld;
+    a.split = h->split;
+    a.e_exp = h->e_exp;
+    a.t0 = h->steps;
+    a.Bt_hi = dptr<void>(h, "Bt_hi");
+    a.Bt_lo = dptr<void>(h, "Bt_lo");
+    a.Bt32 = dptr<float>(h, "Bt32");
+    a.col_scale = dptr<float>(h, "col_scale");
+    a.Jtot = dptr<double>(h, "Jtot");
+    a.Jring = (h->prm.flags & MHC_FLAG_GKMA) ? dptr<double>(h, "Jring") : nullptr;
+    a.R = h->R_ring;
+    launch_pack(a, h->stream);
+    h->launches++;
+    MHC_CUDA(h, cudaGetLastError());
+    return MHC_OK;
+}
+
+mhc_status finish_block(mhc_handle *h, int K) {
+    launch_bin_finish(dptr<float>(h, "partials"), (int)h->n_slots, dptr<int>(h, "slot_begin"), h->B,
+                      K, dptr<float>(h, "Jb"), dptr<double>(h, "hsum"), dptr<double>(h, "Jtot"),
+                      dptr<double>(h, "Jsum"), h->stream);
+    h->launches++;
+    if (h->prm.flags & MHC_FLAG_GKMA) {
+        launch_lag_corr(dptr<float>(h, "Jb"), dptr<double>(h, "Jring"), h->R_ring,
+                        dptr<double>(h, "Csum"), K, h->B, h->prm.n_lags, h->steps, h->stream);
+        h->launches++;
+    }
+    MHC_CUDA(h, cudaGetLastError());
+    h->steps += K;
+    h->pushes++;
+    h->K_last = K;
+    return MHC_OK;
+}
+
+mhc_status copy_out(mhc_handle *h, void *dst, const void *src, size_t bytes, int where) {
+    if (where == MHC_MEM_DEVICE) {
+        MHC_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        return MHC_OK;
+    }
+    MHC_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return check_device_status(h);
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+void mhc_default_params(mhc_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->device = 0;
+    p->stream = nullptr;
+    p->k_max = 256;
+    p->n_lags = 0;
+    p->precision = MHC_PREC_BF16X3;
+    p->flags = 0;
+    p->tile_n = 0;
+    p->ortho_probe = -1;
+    p->dt_ps = 0.01;
+    p->T_K = 300.0;
+    p->V_A3 = 1.0;
+    p->F_e[0] = 1e-5;
+}
+
+const char *mhc_status_string(mhc_status s) {
+    switch (s) {
+    case MHC_OK: return "ok";
+    case MHC_ERR_INVALID_ARG: return "invalid argument";
+    case MHC_ERR_OOM: return "out of memory";
+    case MHC_ERR_CUDA: return "CUDA error";
+    case MHC_ERR_TIMEOUT: return "device wait timed out";
+    case MHC_ERR_STATE: return "invalid state";
+    case MHC_ERR_UNSUPPORTED: return "unsupported";
+    case MHC_WARN_NOT_ORTHONORMAL: return "basis not orthonormal";
+    }
+    return "unknown status";
+}
+
+const char *mhc_last_error(const mhc_handle *h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
+    if (!out || !p) return fail(nullptr, MHC_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    g_create_error.clear();
+    if (p->k_max < 1 || p->k_max > K_MAX_LIMIT)
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "k_max must be in [1, %d]", K_MAX_LIMIT);
+    if (p->n_lags < 0) return fail(nullptr, MHC_ERR_INVALID_ARG, "n_lags must be >= 0");
+    if ((p->flags & MHC_FLAG_GKMA) && p->n_lags < 1)
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "GKMA needs n_lags >= 1");
+    if (p->precision < MHC_PREC_FP32 || p->precision > MHC_PREC_FP16X3)
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+    if (p->tile_n != 0 && p->tile_n != 128 && p->tile_n != 256)
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "tile_n must be 0, 128 or 256");
+    if (!(p->dt_ps > 0) || !(p->T_K > 0) || !(p->V_A3 > 0))
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "dt_ps, T_K and V_A3 must be positive");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || p->device < 0 || p->device >= ndev)
+        return fail(nullptr, MHC_ERR_CUDA, "no CUDA device %d (%s)", p->device,
+                    e == cudaSuccess ? "out of range" : cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, p->device)) != cudaSuccess)
+        return fail(nullptr, MHC_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    const bool sm103 = prop.major == 10 && prop.minor == 3;
+    if (!sm103)
+        return fail(nullptr, MHC_ERR_UNSUPPORTED,
+                    "device %d is sm_%d%d; this library is built for sm_103a only", p->device,
+                    prop.major, prop.minor);
+    auto *h = new mhc_handle();
+    h->prm = *p;
+    h->stream = static_cast<cudaStream_t>(p->stream);
+    h->sm_count = prop.multiProcessorCount;
+    h->cc_major = prop.major;
+    h->cc_minor = prop.minor;
+    h->split = p->precision == MHC_PREC_FP32 ? SPLIT_FP32
+               : p->precision == MHC_PREC_BF16X3 ? SPLIT_BF16 : SPLIT_FP16;
+    if (p->tile_n == 128) h->tc = {128, 64, 3, 0};
+    if ((e = cudaSetDevice(p->device)) != cudaSuccess) {
+        delete h;
+        return fail(nullptr, MHC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMalloc(&h->status, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream)) != cudaSuccess) {
+        if (h->status) cudaFree(h->status);
+        delete h;
+        return fail(nullptr, MHC_ERR_OOM, "status word: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return MHC_OK;
+}
+
+void mhc_destroy(mhc_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto &kv : h->buf)
+        if (kv.second.p) cudaFree(kv.second.p);
+    if (h->status) cudaFree(h->status);
+    delete h;
+}
+
+mhc_status mhc_set_modes(mhc_handle *h, int64_t n_atoms, int64_t n_modes, const void *E,
+                         int32_t dtype, int32_t layout, int64_t ld, int32_t where,
+                         const double *freq_THz, const double *mass_amu) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!E || !mass_amu) return fail(h, MHC_ERR_INVALID_ARG, "E and mass_amu are required");
+    if (n_atoms < 1 || n_modes < 1 || n_modes > 3 * n_atoms)
+        return fail(h, MHC_ERR_INVALID_ARG, "need 1 <= M <= 3N (N=%lld, M=%lld)", (long long)n_atoms,
+                    (long long)n_modes);
+    if (dtype != MHC_F32 && dtype != MHC_F64) return fail(h, MHC_ERR_INVALID_ARG, "dtype");
+    if (layout != MHC_DOF_MAJOR && layout != MHC_MODE_MAJOR) return fail(h, MHC_ERR_INVALID_ARG, "layout");
+    if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE) return fail(h, MHC_ERR_INVALID_ARG, "where");
+    const int64_t D = 3 * n_atoms;
+    if (ld < (layout == MHC_DOF_MAJOR ? n_modes : D))
+        return fail(h, MHC_ERR_INVALID_ARG, "ld %lld too small", (long long)ld);
+    for (int64_t i = 0; i < n_atoms; ++i)
+        if (!(mass_amu[i] > 0) || !std::isfinite(mass_amu[i]))
+            return fail(h, MHC_ERR_INVALID_ARG, "mass of atom %lld must be positive", (long long)i);
+    MHC_CUDA(h, cudaSetDevice(h->prm.device));
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->modes_ready = h->bins_ready = false;
+    h->N = n_atoms;
+    h->D = D;
+    h->M_in = n_modes;
+    h->D_ld = round_up(D, 64);
+    h->mass.assign(mass_amu, mass_amu + n_atoms);
+    if (freq_THz) h->freq.assign(freq_THz, freq_THz + n_modes);
+    else h->freq.clear();
+    h->B_rows = round_up(4 * (int64_t)h->prm.k_max, 256);
+    h->R_ring = h->prm.k_max + std::max(h->prm.n_lags, 1);
+
+    mhc_status s;
+    // input eigenvectors on the device, as given
+    const size_t esz = dtype == MHC_F64 ? 8 : 4;
+    const int64_t rows = layout == MHC_DOF_MAJOR ? D : n_modes;
+    const void *Edev = E;
+    if (where == MHC_MEM_HOST) {
+        if ((s = dev_alloc(h, "Ein", esz * rows * ld, false)) != MHC_OK) return s;
+        MHC_CUDA(h, cudaMemcpyAsync(dptr<void>(h, "Ein"), E, esz * rows * ld, cudaMemcpyHostToDevice,
+                                    h->stream));
+        Edev = dptr<void>(h, "Ein");
+    }
+    // power-of-two scale of E for the FP16 split: max |E 2^e| < 2^14
+    h->e_exp = 0;
+    if (h->split == SPLIT_FP16) {
+        if ((s = dev_alloc(h, "maxbits", sizeof(unsigned))) != MHC_OK) return s;
+        launch_max_abs(Edev, dtype, layout, ld, D, n_modes, dptr<unsigned>(h, "maxbits"), h->stream);
+        h->launches++;
+        unsigned bits = 0;
+        MHC_CUDA(h, cudaMemcpyAsync(&bits, dptr<unsigned>(h, "maxbits"), 4, cudaMemcpyDeviceToHost, h->stream));
+        MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+        float mx;
+        std::memcpy(&mx, &bits, 4);
+        if (!(mx > 0) || !std::isfinite(mx)) return fail(h, MHC_ERR_INVALID_ARG, "E is zero or not finite");
+        int ex;
+        std::frexp(mx, &ex);
+        h->e_exp = 14 - ex;
+    }
+    // optional FP64 basis check on the input (E^T E = I, Eq. 13-14)
+    mhc_status warn = MHC_OK;
+    h->ortho_err = -1.0;
+    if (h->prm.ortho_probe >= 0) {
+        const int64_t P = h->prm.ortho_probe == 0 ? n_modes : std::min<int64_t>(h->prm.ortho_probe, n_modes);
+        std::vector<int> probe(P);
+        for (int64_t q = 0; q < P; ++q) probe[q] = (int)((q * n_modes) / P);
+        if ((s = dev_alloc(h, "probe", sizeof(int) * P, false)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "orthobits", sizeof(unsigned long long))) != MHC_OK) return s;
+        MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "probe"), probe.data(), sizeof(int) * P,
+                                    cudaMemcpyHostToDevice, h->stream));
+        launch_orthonormality(Edev, dtype, layout, ld, D, n_modes, dptr<int>(h, "probe"), (int)P,
+                              dptr<unsigned long long>(h, "orthobits"), h->stream);
+        h->launches++;
+        unsigned long long bits = 0;
+        MHC_CUDA(h, cudaMemcpyAsync(&bits, dptr<unsigned long long>(h, "orthobits"), 8,
+                                    cudaMemcpyDeviceToHost, h->stream));
+        MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+        std::memcpy(&h->ortho_err, &bits, 8);
+        dev_free(h, "probe");
+        dev_free(h, "orthobits");
+        if (h->ortho_err > 1e-6) warn = MHC_WARN_NOT_ORTHONORMAL;
+    }
+    // resident FP32 copy in input mode order, mode-major (re-gathered on every re-binning)
+    std::vector<int> ident(n_modes);
+    for (int64_t q = 0; q < n_modes; ++q) ident[q] = (int)q;
+    if ((s = dev_alloc(h, "perm", sizeof(int) * n_modes, false)) != MHC_OK) return s;
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "perm"), ident.data(), sizeof(int) * n_modes,
+                                cudaMemcpyHostToDevice, h->stream));
+    const int64_t Mraw = round_up(n_modes, 32);
+    if ((s = dev_alloc(h, "Eraw", sizeof(float) * Mraw * h->D_ld, false)) != MHC_OK) return s;
+    launch_prepare_modes(Edev, dtype, layout, ld, D, n_modes, dptr<int>(h, "perm"), 0, SPLIT_FP32,
+                         nullptr, nullptr, dptr<float>(h, "Eraw"), h->D_ld, Mraw, h->stream);
+    h->launches++;
+    MHC_CUDA(h, cudaGetLastError());
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, "Ein");
+
+    // per-atom weights and per-block buffers
+    std::vector<float> sq(n_atoms), isq(n_atoms);
+    for (int64_t i = 0; i < n_atoms; ++i) {
+        sq[i] = (float)std::sqrt(h->mass[i]);
+        isq[i] = (float)(1.0 / std::sqrt(h->mass[i]));
+    }
+    const int K = h->prm.k_max;
+    if ((s = dev_alloc(h, "sqm", sizeof(float) * n_atoms, false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "isqm", sizeof(float) * n_atoms, false)) != MHC_OK) return s;
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<float>(h, "sqm"), sq.data(), 4 * n_atoms, cudaMemcpyHostToDevice, h->stream));
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<float>(h, "isqm"), isq.data(), 4 * n_atoms, cudaMemcpyHostToDevice, h->stream));
+    const size_t bcount = (size_t)h->B_rows * h->D_ld;
+    if (is_tc(h)) {
+        dev_free(h, "Bt32");
+        if ((s = dev_alloc(h, "Bt_hi", bcount * 2)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "Bt_lo", bcount * 2)) != MHC_OK) return s;
+    } else {
+        if ((s = dev_alloc(h, "Bt32", bcount * 4)) != MHC_OK) return s;
+    }
+    if ((s = dev_alloc(h, "col_scale", sizeof(float) * 4 * K)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "Jtot", sizeof(double) * 3 * K)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "v_stage", sizeof(float) * K * n_atoms * 3, false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "W_stage", sizeof(float) * K * n_atoms * 9, false)) != MHC_OK) return s;
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->modes_ready = true;
+    h->tuned.clear();
+    return warn;
+}
+
+mhc_status mhc_set_bins_uniform(mhc_handle *h, double f_min, double f_max, int32_t n_bins) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!h->modes_ready) return fail(h, MHC_ERR_INVALID_ARG, "mhc_set_modes must come first");
+    if (h->freq.empty()) return fail(h, MHC_ERR_INVALID_ARG, "no frequencies were given");
+    if (n_bins < 1 || !(f_max > f_min) || !std::isfinite(f_min) || !std::isfinite(f_max))
+        return fail(h, MHC_ERR_INVALID_ARG, "need n_bins >= 1 and f_min < f_max");
+    std::vector<int> bins;
+    bins_uniform_host(h->freq, f_min, f_max, n_bins, bins);
+    MHC_CUDA(h, cudaSetDevice(h->prm.device));
+    mhc_status s = apply_bins(h, bins, n_bins);
+    if (s == MHC_OK) MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return s;
+}
+
+mhc_status mhc_set_bin_ids(mhc_handle *h, const int32_t *bin_of_mode, int32_t n_bins) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!h->modes_ready) return fail(h, MHC_ERR_INVALID_ARG, "mhc_set_modes must come first");
+    if (!bin_of_mode) return fail(h, MHC_ERR_INVALID_ARG, "bin_of_mode is null");
+    std::vector<int> bins(bin_of_mode, bin_of_mode + h->M_in);
+    MHC_CUDA(h, cudaSetDevice(h->prm.device));
+    mhc_status s = apply_bins(h, bins, n_bins);
+    if (s == MHC_OK) MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return s;
+}
+
+mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, int32_t where) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "modes and bins must be set before pushing");
+    if (!v || !W) return fail(h, MHC_ERR_INVALID_ARG, "v and W are required");
+    if (K < 1 || K > h->prm.k_max) return fail(h, MHC_ERR_INVALID_ARG, "K=%d outside [1, %d]", K, h->prm.k_max);
+    if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE) return fail(h, MHC_ERR_INVALID_ARG, "where");
+    MHC_CUDA(h, cudaSetDevice(h->prm.device));
+    mhc_status s;
+    if ((s = stage_inputs(h, v, W, K, where)) != MHC_OK) return s;
+    if ((s = pack_block(h, v, W, K)) != MHC_OK) return s;
+    if (is_tc(h) && h->prm.tile_n == 0) {
+        auto it = h->tuned.find(K);
+        if (it == h->tuned.end()) {
+            if ((s = autotune(h, K)) != MHC_OK) return s;
+        } else if ((s = set_tc_config(h, it->second)) != MHC_OK) {
+            return s;
+        }
+    }
+    if ((s = run_projection(h, K)) != MHC_OK) return s;
+    return finish_block(h, K);
+}
+
+mhc_status mhc_sync(mhc_handle *h) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return check_device_status(h);
+}
+
+mhc_status mhc_read_binned_current(mhc_handle *h, float *out, int32_t where) {
+    if (!h || !out) return h ? fail(h, MHC_ERR_INVALID_ARG, "null output") : MHC_ERR_INVALID_ARG;
+    if (h->K_last == 0) return fail(h, MHC_ERR_INVALID_ARG, "nothing pushed yet");
+    return copy_out(h, out, dptr<float>(h, "Jb"), sizeof(float) * h->K_last * h->B * 3, where);
+}
+
+mhc_status mhc_read_total_current(mhc_handle *h, double *out, int32_t where) {
+    if (!h || !out) return h ? fail(h, MHC_ERR_INVALID_ARG, "null output") : MHC_ERR_INVALID_ARG;
+    if (h->K_last == 0) return fail(h, MHC_ERR_INVALID_ARG, "nothing pushed yet");
+    return copy_out(h, out, dptr<double>(h, "Jtot"), sizeof(double) * h->K_last * 3, where);
+}
+
+mhc_status mhc_read_hnema(mhc_handle *h, double *kappa, double *mean_J, int32_t where) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "no bins");
+    mhc_status s;
+    const size_t n = (size_t)h->B * 3;
+    if ((s = dev_alloc(h, "hn_out", sizeof(double) * 2 * n, false)) != MHC_OK) return s;
+    const double fe = std::sqrt(h->prm.F_e[0] * h->prm.F_e[0] + h->prm.F_e[1] * h->prm.F_e[1] +
+                                h->prm.F_e[2] * h->prm.F_e[2]);
+    const double coef = fe > 0 ? WMK_PER_EV_PS_A_K / (h->prm.T_K * h->prm.V_A3 * fe) : 0.0;
+    double *dm = dptr<double>(h, "hn_out"), *dk = dm + n;
+    launch_hnema_finalize(dptr<double>(h, "hsum"), h->B, h->steps, coef, dm, dk, h->stream);
+    h->launches++;
+    MHC_CUDA(h, cudaGetLastError());
+    if (kappa && (s = copy_out(h, kappa, dk, sizeof(double) * n, where)) != MHC_OK) return s;
+    if (mean_J && (s = copy_out(h, mean_J, dm, sizeof(double) * n, where)) != MHC_OK) return s;
+    return MHC_OK;
+}
+
+mhc_status mhc_read_corr(mhc_handle *h, double *corr_sum, int64_t *count, int32_t where) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!(h->prm.flags & MHC_FLAG_GKMA) || !h->bins_ready)
+        return fail(h, MHC_ERR_INVALID_ARG, "GKMA is not enabled or no bins");
+    const int L = h->prm.n_lags;
+    mhc_status s;
+    if (corr_sum && (s = copy_out(h, corr_sum, dptr<double>(h, "Csum"),
+                                  sizeof(double) * h->B * 9 * L, where)) != MHC_OK)
+        return s;
+    if (count) {
+        if ((s = dev_alloc(h, "counts", sizeof(long long) * L, false)) != MHC_OK) return s;
+        launch_lag_counts(h->steps, L, dptr<long long>(h, "counts"), h->stream);
+        h->launches++;
+        if ((s = copy_out(h, count, dptr<long long>(h, "counts"), sizeof(long long) * L, where)) != MHC_OK)
+            return s;
+    }
+    return MHC_OK;
+}
+
+mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, double tau_hi,
+                             double *kappa_w, int32_t where) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!(h->prm.flags & MHC_FLAG_GKMA) || !h->bins_ready)
+        return fail(h, MHC_ERR_INVALID_ARG, "GKMA is not enabled or no bins");
+    const int L = h->prm.n_lags;
+    const size_t rows = (size_t)h->B * 9;
+    mhc_status s;
+    if ((s = dev_alloc(h, "gk_out", sizeof(double) * rows * (L + 1), false)) != MHC_OK) return s;
+    double *dk = dptr<double>(h, "gk_out"), *dw = dk + rows * L;
+    const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
+    launch_gk_kappa(dptr<double>(h, "Csum"), h->B, L, h->steps, coef * h->prm.dt_ps, tau_lo, tau_hi,
+                    h->prm.dt_ps, dk, dw, h->stream);
+    h->launches++;
+    MHC_CUDA(h, cudaGetLastError());
+    if (kappa_tau && (s = copy_out(h, kappa_tau, dk, sizeof(double) * rows * L, where)) != MHC_OK) return s;
+    if (kappa_w && (s = copy_out(h, kappa_w, dw, sizeof(double) * rows, where)) != MHC_OK) return s;
+    return MHC_OK;
+}
+
+mhc_status mhc_check_orthonormality(mhc_handle *h, double tol, double *max_abs_err) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (h->ortho_err < 0) return fail(h, MHC_ERR_INVALID_ARG, "no basis check was run (ortho_probe < 0)");
+    if (max_abs_err) *max_abs_err = h->ortho_err;
+    return h->ortho_err > tol ? MHC_WARN_NOT_ORTHONORMAL : MHC_OK;
+}
+
+mhc_status mhc_get_info(mhc_handle *h, mhc_info *info) {
+    if (!h || !info) return MHC_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof *info);
+    info->n_atoms = h->N;
+    info->n_dof = h->D;
+    info->n_modes_in = h->M_in;
+    info->n_modes_kept = h->M_eff;
+    info->n_bins = h->B;
+    info->n_lags = h->prm.n_lags;
+    info->k_max = h->prm.k_max;
+    info->precision = h->prm.precision;
+    info->steps_pushed = h->steps;
+    info->pushes = h->pushes;
+    info->n_slots = h->n_slots;
+    info->tile_n = is_tc(h) ? h->tc.bn : 128;
+    info->stages = is_tc(h) ? h->tc.stages : 0;
+    info->grid = h->sm_count;
+    info->e_exp = h->e_exp;
+    info->ortho_err = h->ortho_err;
+    int64_t bytes = 0;
+    for (auto &kv : h->buf) bytes += (int64_t)kv.second.bytes;
+    info->device_bytes = bytes;
+    info->kernel_launches = h->launches;
+    return MHC_OK;
+}
+
+mhc_status mhc_reset(mhc_handle *h) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "no bins");
+    MHC_CUDA(h, cudaSetDevice(h->prm.device));
+    mhc_status s = reset_accumulators(h);
+    if (s == MHC_OK) MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    return s;
+}
+
+// Blob: header {magic, B, L, k_max, R_ring, steps} then hsum[B*3], Jsum[3], Csum[B*9*L], Jring[R*3].
+struct StateHeader {
+    uint32_t magic;
+    int32_t B, L, k_max, R_ring, gkma;
+    int64_t steps, M_eff;
+};
+
+mhc_status mhc_state_size(mhc_handle *h, size_t *bytes) {
+    if (!h || !bytes) return MHC_ERR_INVALID_ARG;
+    if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "no bins");
+    const bool g = h->prm.flags & MHC_FLAG_GKMA;
+    *bytes = sizeof(StateHeader) + sizeof(double) * (h->B * 3 + 3) +
+             (g ? sizeof(double) * ((size_t)h->B * 9 * h->prm.n_lags + (size_t)h->R_ring * 3) : 0);
+    return MHC_OK;
+}
+
+mhc_status mhc_get_state(mhc_handle *h, void *blob, size_t bytes) {
+    size_t need = 0;
+    mhc_status s = mhc_state_size(h, &need);
+    if (s != MHC_OK) return s;
+    if (!blob || bytes < need) return fail(h, MHC_ERR_INVALID_ARG, "state buffer too small (%zu < %zu)", bytes, need);
+    if ((s = mhc_sync(h)) != MHC_OK) return s;
+    auto *hd = static_cast<StateHeader *>(blob);
+    const bool g = h->prm.flags & MHC_FLAG_GKMA;
+    *hd = StateHeader{STATE_MAGIC, h->B, h->prm.n_lags, h->prm.k_max, h->R_ring, g ? 1 : 0, h->steps, h->M_eff};
+    char *p = static_cast<char *>(blob) + sizeof(StateHeader);
+    MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "hsum"), sizeof(double) * h->B * 3, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * h->B * 3;
+    MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Jsum"), sizeof(double) * 3, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * 3;
+    if (g) {
+        const size_t nc = (size_t)h->B * 9 * h->prm.n_lags;
+        MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Csum"), sizeof(double) * nc, cudaMemcpyDeviceToHost));
+        p += sizeof(double) * nc;
+        MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Jring"), sizeof(double) * h->R_ring * 3, cudaMemcpyDeviceToHost));
+    }
+    return MHC_OK;
+}
+
+mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes) {
+    size_t need = 0;
+    mhc_status s = mhc_state_size(h, &need);
+    if (s != MHC_OK) return s;
+    if (!blob || bytes < need) return fail(h, MHC_ERR_STATE, "state blob too small");
+    const auto *hd = static_cast<const StateHeader *>(blob);
+    const bool g = h->prm.flags & MHC_FLAG_GKMA;
+    if (hd->magic != STATE_MAGIC || hd->B != h->B || hd->L != h->prm.n_lags || hd->k_max != h->prm.k_max ||
+        hd->R_ring != h->R_ring || hd->gkma != (g ? 1 : 0) || hd->M_eff != h->M_eff || hd->steps < 0)
+        return fail(h, MHC_ERR_STATE, "state blob does not match this handle's modes/bins/lags/k_max");
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    const char *p = static_cast<const char *>(blob) + sizeof(StateHeader);
+    MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "hsum"), p, sizeof(double) * h->B * 3, cudaMemcpyHostToDevice));
+    p += sizeof(double) * h->B * 3;
+    MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Jsum"), p, sizeof(double) * 3, cudaMemcpyHostToDevice));
+    p += sizeof(double) * 3;
+    if (g) {
+        const size_t nc = (size_t)h->B * 9 * h->prm.n_lags;
+        MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Csum"), p, sizeof(double) * nc, cudaMemcpyHostToDevice));
+        p += sizeof(double) * nc;
+        MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Jring"), p, sizeof(double) * h->R_ring * 3, cudaMemcpyHostToDevice));
+    }
+    h->steps = hd->steps;
+    h->K_last = 0;
+    return MHC_OK;
+}
+
+// ----------------------------------------------------------------------------- groups
+mhc_status mhc_group_create(mhc_group **g, mhc_handle *const *handles, int32_t n) {
+    (void)g;
+    (void)handles;
+    (void)n;
+    return MHC_ERR_UNSUPPORTED;
+}
+void mhc_group_destroy(mhc_group *g) { delete g; }
+mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *const *W,
+                          const int32_t *K, int32_t where) {
+    (void)g;
+    (void)v;
+    (void)W;
+    (void)K;
+    (void)where;
+    return MHC_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

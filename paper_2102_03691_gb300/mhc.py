@@ -1,0 +1,321 @@
+"""Python binding of libmhc.so (include/mhc.h): argument marshalling only.
+
+Every step of the modal heat-current path runs in the CUDA library; this
+module converts numpy arrays (host memory) and torch CUDA tensors (device
+memory) into the plain pointers and sizes of the C ABI, and status codes into
+exceptions.  There is no fallback: if the compiled library is missing the
+import of a handle fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import warnings
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmhc.so")
+
+MHC_OK = 0
+MHC_WARN_NOT_ORTHONORMAL = 100
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
+MEM_HOST, MEM_DEVICE = 0, 1
+F32, F64 = 0, 1
+DOF_MAJOR, MODE_MAJOR = 0, 1
+FLAG_GKMA, FLAG_NO_GRAPH = 0x1, 0x2
+
+# Every entry point declared in include/mhc.h.
+EXPORTS = (
+    "mhc_default_params", "mhc_create", "mhc_destroy", "mhc_last_error", "mhc_status_string",
+    "mhc_set_modes", "mhc_set_bins_uniform", "mhc_set_bin_ids", "mhc_push", "mhc_sync",
+    "mhc_read_binned_current", "mhc_read_total_current", "mhc_read_hnema", "mhc_read_corr",
+    "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_reset",
+    "mhc_state_size", "mhc_get_state", "mhc_set_state", "mhc_group_create",
+    "mhc_group_destroy", "mhc_group_push",
+)
+
+
+class MhcParams(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("k_max", ctypes.c_int32), ("n_lags", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32), ("ortho_probe", ctypes.c_int32),
+                ("dt_ps", ctypes.c_double), ("T_K", ctypes.c_double), ("V_A3", ctypes.c_double),
+                ("F_e", ctypes.c_double * 3)]
+
+
+class MhcInfo(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("n_dof", ctypes.c_int64),
+                ("n_modes_in", ctypes.c_int64), ("n_modes_kept", ctypes.c_int64),
+                ("n_bins", ctypes.c_int32), ("n_lags", ctypes.c_int32),
+                ("k_max", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("steps_pushed", ctypes.c_int64), ("pushes", ctypes.c_int64),
+                ("n_slots", ctypes.c_int64), ("tile_n", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("grid", ctypes.c_int32), ("e_exp", ctypes.c_int32),
+                ("ortho_err", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+class MhcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mhc status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libmhc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.mhc_default_params.argtypes = [ctypes.POINTER(MhcParams)]
+    L.mhc_default_params.restype = None
+    L.mhc_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(MhcParams)]
+    L.mhc_destroy.argtypes = [vp]
+    L.mhc_destroy.restype = None
+    L.mhc_last_error.argtypes = [vp]
+    L.mhc_last_error.restype = ctypes.c_char_p
+    L.mhc_status_string.argtypes = [ctypes.c_int]
+    L.mhc_status_string.restype = ctypes.c_char_p
+    L.mhc_set_modes.argtypes = [vp, i64, i64, vp, i32, i32, i64, i32, vp, vp]
+    L.mhc_set_bins_uniform.argtypes = [vp, dbl, dbl, i32]
+    L.mhc_set_bin_ids.argtypes = [vp, vp, i32]
+    L.mhc_push.argtypes = [vp, vp, vp, i32, i32]
+    L.mhc_sync.argtypes = [vp]
+    L.mhc_read_binned_current.argtypes = [vp, vp, i32]
+    L.mhc_read_total_current.argtypes = [vp, vp, i32]
+    L.mhc_read_hnema.argtypes = [vp, vp, vp, i32]
+    L.mhc_read_corr.argtypes = [vp, vp, vp, i32]
+    L.mhc_read_kappa_gk.argtypes = [vp, vp, dbl, dbl, vp, i32]
+    L.mhc_check_orthonormality.argtypes = [vp, dbl, ctypes.POINTER(dbl)]
+    L.mhc_get_info.argtypes = [vp, ctypes.POINTER(MhcInfo)]
+    L.mhc_reset.argtypes = [vp]
+    L.mhc_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.mhc_get_state.argtypes = [vp, vp, ctypes.c_size_t]
+    L.mhc_set_state.argtypes = [vp, vp, ctypes.c_size_t]
+    L.mhc_group_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), i32]
+    L.mhc_group_destroy.argtypes = [vp]
+    L.mhc_group_destroy.restype = None
+    L.mhc_group_push.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                 ctypes.POINTER(i32), i32]
+    for name in EXPORTS:
+        if name not in ("mhc_default_params", "mhc_destroy", "mhc_last_error",
+                        "mhc_status_string", "mhc_group_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, where, keepalive) for a numpy array or a torch CUDA tensor."""
+    if _is_torch(x):
+        import torch
+        want = {np.float32: torch.float32, np.float64: torch.float64,
+                np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if x.dtype != want:
+            raise TypeError(f"expected {want}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), MEM_HOST, a
+
+
+def _current_stream(device: int):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(None)
+
+
+class ModalHeatCurrent:
+    """One system: eigenvectors, bins and the GKMA / HNEMA accumulators (see include/mhc.h)."""
+
+    def __init__(self, precision: str = "bf16x3", k_max: int = 256, n_lags: int = 0,
+                 gkma: bool | None = None, dt_ps: float = 0.01, T_K: float = 300.0,
+                 V_A3: float = 1.0, F_e=(1e-5, 0.0, 0.0), device: int = 0, stream=None,
+                 tile_n: int = 0, ortho_probe: int = -1, flags: int = 0):
+        self._L = load()
+        p = MhcParams()
+        self._L.mhc_default_params(ctypes.byref(p))
+        p.device = device
+        p.stream = stream if isinstance(stream, ctypes.c_void_p) else (
+            ctypes.c_void_p(stream) if stream is not None else _current_stream(device))
+        p.k_max = k_max
+        p.n_lags = n_lags
+        p.precision = PRECISIONS[precision]
+        gk = (n_lags > 0) if gkma is None else gkma
+        p.flags = flags | (FLAG_GKMA if gk else 0)
+        p.tile_n = tile_n
+        p.ortho_probe = ortho_probe
+        p.dt_ps, p.T_K, p.V_A3 = dt_ps, T_K, V_A3
+        for i in range(3):
+            p.F_e[i] = F_e[i]
+        self.params = p
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self._L.mhc_create(ctypes.byref(h), ctypes.byref(p))
+        if st != MHC_OK:
+            raise MhcError(st, self._L.mhc_last_error(None).decode())
+        self._h = h
+        self.B = 0
+        self.N = 0
+        self._lastK = 0
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, st: int):
+        if st == MHC_OK:
+            return st
+        msg = self._L.mhc_last_error(self._h).decode()
+        if st == MHC_WARN_NOT_ORTHONORMAL:
+            warnings.warn(f"eigenvectors not orthonormal: {msg}")
+            return st
+        raise MhcError(st, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mhc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------ setup
+    def set_modes(self, E, mass_amu, freq_THz=None, layout: str = "dof"):
+        """E: [3N][M] (layout 'dof') or [M][3N] ('mode'), float32/float64, numpy or CUDA tensor."""
+        lay = DOF_MAJOR if layout == "dof" else MODE_MAJOR
+        is_f64 = (str(E.dtype) in ("float64", "torch.float64"))
+        ptr, where, keep = _ptr(E, np.float64 if is_f64 else np.float32)
+        rows, cols = keep.shape
+        mass = np.ascontiguousarray(mass_amu, dtype=np.float64)
+        N = mass.shape[0]
+        M = cols if lay == DOF_MAJOR else rows
+        f = None if freq_THz is None else np.ascontiguousarray(freq_THz, dtype=np.float64)
+        st = self._L.mhc_set_modes(self._h, N, M, ptr, F64 if is_f64 else F32, lay, cols, where,
+                                   None if f is None else f.ctypes.data_as(ctypes.c_void_p),
+                                   mass.ctypes.data_as(ctypes.c_void_p))
+        self.N = N
+        self.M = M
+        return self._check(st)
+
+    def set_bins_uniform(self, f_min: float, f_max: float, n_bins: int):
+        self._check(self._L.mhc_set_bins_uniform(self._h, f_min, f_max, n_bins))
+        self.B = n_bins
+
+    def set_bin_ids(self, bin_of_mode, n_bins: int):
+        b = np.ascontiguousarray(bin_of_mode, dtype=np.int32)
+        self._check(self._L.mhc_set_bin_ids(self._h, b.ctypes.data_as(ctypes.c_void_p), n_bins))
+        self.B = n_bins
+
+    # ------------------------------------------------------------------ stream
+    def push(self, v, W):
+        """v [K][N][3], W [K][N][9] float32 (numpy: host, torch CUDA tensor: device)."""
+        pv, wv, kv = _ptr(v, np.float32)
+        pw, ww, kw = _ptr(W, np.float32)
+        if wv != ww:
+            raise ValueError("v and W must be in the same memory space")
+        K = int(kv.shape[0])
+        nv = int(np.prod(kv.shape)) if not _is_torch(kv) else kv.numel()
+        nw = int(np.prod(kw.shape)) if not _is_torch(kw) else kw.numel()
+        if nv != K * self.N * 3 or nw != K * self.N * 9:
+            raise ValueError(f"v must be [K][{self.N}][3] and W [K][{self.N}][9]")
+        self._keep = (kv, kw)
+        self._check(self._L.mhc_push(self._h, pv, pw, K, wv))
+        self._lastK = K
+
+    def sync(self):
+        self._check(self._L.mhc_sync(self._h))
+
+    # ------------------------------------------------------------------ reads
+    def read_binned_current(self, out=None):
+        if out is None:
+            out = np.empty((self._lastK, self.B, 3), np.float32)
+        p, where, keep = _ptr(out, np.float32)
+        self._check(self._L.mhc_read_binned_current(self._h, p, where))
+        return keep
+
+    def read_total_current(self, out=None):
+        if out is None:
+            out = np.empty((self._lastK, 3), np.float64)
+        p, where, keep = _ptr(out, np.float64)
+        self._check(self._L.mhc_read_total_current(self._h, p, where))
+        return keep
+
+    def read_hnema(self):
+        kap = np.empty((self.B, 3))
+        mean = np.empty((self.B, 3))
+        self._check(self._L.mhc_read_hnema(self._h, kap.ctypes.data_as(ctypes.c_void_p),
+                                           mean.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
+        return mean, kap
+
+    def read_hnema_into(self, kappa, mean=None):
+        pk, where, _ = _ptr(kappa, np.float64)
+        pm = None if mean is None else _ptr(mean, np.float64)[0]
+        self._check(self._L.mhc_read_hnema(self._h, pk, pm, where))
+
+    def read_corr(self):
+        L_ = self.params.n_lags
+        C = np.empty((self.B, 3, 3, L_))
+        cnt = np.empty(L_, np.int64)
+        self._check(self._L.mhc_read_corr(self._h, C.ctypes.data_as(ctypes.c_void_p),
+                                          cnt.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
+        return C, cnt
+
+    def read_kappa_gk(self, tau_lo: float, tau_hi: float):
+        L_ = self.params.n_lags
+        kt = np.empty((self.B, 3, 3, L_))
+        kw = np.empty((self.B, 3, 3))
+        self._check(self._L.mhc_read_kappa_gk(self._h, kt.ctypes.data_as(ctypes.c_void_p), tau_lo,
+                                              tau_hi, kw.ctypes.data_as(ctypes.c_void_p),
+                                              MEM_HOST))
+        return kt, kw
+
+    def check_orthonormality(self, tol: float = 1e-6) -> float:
+        e = ctypes.c_double()
+        st = self._L.mhc_check_orthonormality(self._h, tol, ctypes.byref(e))
+        if st not in (MHC_OK, MHC_WARN_NOT_ORTHONORMAL):
+            self._check(st)
+        return e.value
+
+    def info(self) -> dict:
+        i = MhcInfo()
+        self._check(self._L.mhc_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in MhcInfo._fields_}
+
+    def reset(self):
+        self._check(self._L.mhc_reset(self._h))
+
+    def get_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        self._check(self._L.mhc_state_size(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self._L.mhc_get_state(self._h, buf, n.value))
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._check(self._L.mhc_set_state(self._h, buf, len(blob)))
