@@ -78,7 +78,9 @@ typedef struct {
     int32_t n_lags;      /* L: lags 0..L-1 of the Eq. 17 correlation (GKMA) */
     int32_t precision;   /* mhc_precision */
     int32_t flags;       /* MHC_FLAG_* */
-    int32_t tile_n;      /* 0 = autotune; else tensor-core tile width in columns */
+    int32_t tile_config; /* tensor-core tile: 0 = autotune on the first push of each K;
+                            1..4 = (columns, k per stage, stages) of (256,64,2), (256,32,4),
+                            (128,64,3), (128,32,6).  All give bitwise the same results. */
     int32_t ortho_probe; /* -1: no basis check in set_modes; 0: full E^T E; P>0: P probe modes */
     double dt_ps;        /* sampling interval between pushed steps (Eq. 17 dt') */
     double T_K;          /* temperature T (Eq. 17, 19) */
@@ -93,7 +95,8 @@ typedef struct {
     int64_t steps_pushed;        /* T_s so far */
     int64_t pushes;              /* number of mhc_push calls */
     int64_t n_slots;             /* per-step partial-sum slots of the bin reduction */
-    int32_t tile_n, stages, grid;/* tensor-core kernel configuration in use */
+    int32_t tile_n, tile_k;      /* tensor-core tile: columns per tile, d elements per stage */
+    int32_t stages, grid;        /* pipeline depth, SM count */
     int32_t e_exp;               /* power-of-two scale applied to E before the split */
     double ortho_err;            /* last basis check result, -1 if none */
     int64_t device_bytes;        /* device memory owned by the handle */

@@ -9,11 +9,20 @@
 // then a segmented warp reduction over modes (stored sorted by frequency bin) leaves one
 // partial sum per run of equal bins in each 32-mode group.
 //
-// Warp roles (256 threads, one persistent CTA per SM):
-//   warp 0       TMA producer (one lane)
-//   warp 1       MMA issuer (one lane)
-//   warp 2       TMEM allocator
-//   warps 4..7   epilogue, warp w reads TMEM lanes 32*(w%4) .. +31
+// Accumulation precision: the tensor core adds each MMA's products into the FP32
+// accumulator with truncation, so its error grows linearly with the number of MMAs that
+// feed one accumulator.  The d loop is therefore cut into chunks of PROMOTE_D = 128
+// elements; each chunk accumulates into a fresh TMEM buffer (two buffers alternate) and
+// the epilogue warps promote it into FP32 registers with round-to-nearest adds while the
+// next chunk runs.  The per-tile sums never leave registers.  Because the chunk is fixed
+// in elements, every pipeline shape (BK, STAGES) gives bitwise the same result.
+//
+// Warp roles (128 + BN threads, one persistent CTA per SM):
+//   warp 0          TMA producer (one lane)
+//   warp 1          MMA issuer (one lane)
+//   warp 2          TMEM allocator
+//   warps 4..4+BN/32  promotion + epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 and
+//                  the 128 columns starting at 128*((w-4)/4) of each chunk accumulator
 // Every barrier wait is bounded; a wait that runs out raises a CTA-wide abort flag and a
 // sticky device status, and the CTA drains its in-flight copies and MMAs, frees TMEM and exits.
 #include <cuda_runtime.h>
@@ -33,11 +42,13 @@ struct TcLayout {
     static constexpr int TILE_BYTES = STAGES * STAGE_BYTES;
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM_BYTES = TILE_BYTES + BAR_BYTES + 1024;   // + alignment slack
-    static constexpr uint32_t TMEM_COLS = 2 * BN;                       // double-buffered accumulator
+    static constexpr uint32_t TMEM_COLS = 2 * BN;                       // two chunk accumulators
     static constexpr uint32_t SWIZZLE_CODE = BK == 64 ? 2u : 4u;        // 128 B or 64 B rows
     static constexpr uint32_t SBO = 8 * BK * 2;                         // 8-row core group
     static_assert(BK == 64 || BK == 32, "BK");
-    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
+    static constexpr int EPI_WARPS = BN / 32;   // each holds 128 columns of 32 lanes
+    static constexpr int THREADS = 128 + 32 * EPI_WARPS;
+    static_assert(BN == 128 || BN == 256, "BN");
     static_assert(STAGES * 2 + 5 <= 28, "barrier area");
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM columns");
 };
@@ -73,17 +84,20 @@ struct TileIter {
     }
 };
 
+constexpr int PROMOTE_D = 128;   // d elements per TMEM chunk accumulator
+
 template <int BN, int BK, int STAGES, int NPROB>
-__global__ void __launch_bounds__(256, 1) tc_modal_kernel(const __grid_constant__ TcParams<NPROB> p) {
+__global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_constant__ TcParams<NPROB> p) {
     using L = TcLayout<BN, BK, STAGES>;
+    constexpr int CHUNK_KB = PROMOTE_D / BK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::TILE_BYTES);
     uint64_t *full = bars;                   // [STAGES] TMA landed
     uint64_t *empty = bars + STAGES;         // [STAGES] MMAs done reading
-    uint64_t *acc_full = bars + 2 * STAGES;  // [2] accumulator ready
-    uint64_t *acc_empty = acc_full + 2;      // [2] accumulator drained
+    uint64_t *acc_full = bars + 2 * STAGES;  // [2] chunk accumulator ready
+    uint64_t *acc_empty = acc_full + 2;      // [2] chunk accumulator promoted
     uint64_t *done_bar = acc_empty + 2;      // final MMA drain
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done_bar + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -97,7 +111,7 @@ __global__ void __launch_bounds__(256, 1) tc_modal_kernel(const __grid_constant_
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 128);
+            mbar_init(&acc_empty[b], 32 * L::EPI_WARPS);
         }
         mbar_init(done_bar, 1);
         *abort = 0;
@@ -170,33 +184,37 @@ __global__ void __launch_bounds__(256, 1) tc_modal_kernel(const __grid_constant_
         const uint32_t smem0 = smem_u32(smem);
         while (ok && it.next(prob, mt, ct)) {
             const TcProblem &P = p.prob[prob];
-            if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * BN);
-            for (int kb = 0; kb < P.n_kb; ++kb) {
-                if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+            for (int kb0 = 0; ok && kb0 < P.n_kb; kb0 += CHUNK_KB) {
+                if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t a_hi = smem0 + stage * L::STAGE_BYTES;
-                const uint32_t a_lo = a_hi + L::A_BYTES;
-                const uint32_t b_hi = a_hi + 2 * L::A_BYTES;
-                const uint32_t b_lo = b_hi + L::B_BYTES;
+                const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * BN);
+                const int kb1 = min(kb0 + CHUNK_KB, P.n_kb);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_hi = smem0 + stage * L::STAGE_BYTES;
+                    const uint32_t a_lo = a_hi + L::A_BYTES;
+                    const uint32_t b_hi = a_hi + 2 * L::A_BYTES;
+                    const uint32_t b_lo = b_hi + L::B_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    const uint32_t off = kk * 32;   // 16 elements of 2 bytes
-                    const uint64_t dah = smem_desc_kmajor(a_hi + off, L::SBO, L::SWIZZLE_CODE);
-                    const uint64_t dal = smem_desc_kmajor(a_lo + off, L::SBO, L::SWIZZLE_CODE);
-                    const uint64_t dbh = smem_desc_kmajor(b_hi + off, L::SBO, L::SWIZZLE_CODE);
-                    const uint64_t dbl = smem_desc_kmajor(b_lo + off, L::SBO, L::SWIZZLE_CODE);
-                    umma_f16(d_tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
-                    umma_f16(d_tmem, dah, dbl, idesc, 1u);
-                    umma_f16(d_tmem, dal, dbh, idesc, 1u);
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;   // 16 elements of 2 bytes
+                        const uint64_t dah = smem_desc_kmajor(a_hi + off, L::SBO, L::SWIZZLE_CODE);
+                        const uint64_t dal = smem_desc_kmajor(a_lo + off, L::SBO, L::SWIZZLE_CODE);
+                        const uint64_t dbh = smem_desc_kmajor(b_hi + off, L::SBO, L::SWIZZLE_CODE);
+                        const uint64_t dbl = smem_desc_kmajor(b_lo + off, L::SBO, L::SWIZZLE_CODE);
+                        // small cross terms first, the dominant hi*hi product last
+                        umma_f16(d_tmem, dah, dbl, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
+                        umma_f16(d_tmem, dal, dbh, idesc, 1u);
+                        umma_f16(d_tmem, dah, dbh, idesc, 1u);
+                    }
+                    umma_commit(&empty[stage]);
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
-                umma_commit(&empty[stage]);
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                if (!ok) break;
+                umma_commit(&acc_full[abuf]);
+                if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
             }
-            if (!ok) break;
-            umma_commit(&acc_full[abuf]);
-            if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
         }
         if (!ok) {
             *abort = 1;
@@ -208,48 +226,61 @@ __global__ void __launch_bounds__(256, 1) tc_modal_kernel(const __grid_constant_
         while (!mbar_try_wait(done_bar, 0) && clock64() - t0 < WAIT_LIMIT_CYCLES) {
         }
     } else if (warp >= 4) {
-        // ------------------------------------------------------------ epilogue
-        const int qw = warp & 3;   // TMEM lane quarter of this warp
+        // ------------------------------------------------------------ promotion + epilogue
+        const int qw = warp & 3;          // TMEM lane quarter of this warp
+        const int ch = (warp - 4) >> 2;   // which 128-column half of the tile
         int abuf = 0;
         uint32_t aphase = 0;
         TileIter<NPROB> it(p);
         int prob, mt, ct;
-        while (it.next(prob, mt, ct)) {
+        bool ok = true;
+        while (ok && it.next(prob, mt, ct)) {
             const TcProblem &P = p.prob[prob];
             const int n = mt * TC_BM + qw * 32 + lane;
             const int bin = P.mode_bin[n];
             const int slot = P.mode_slot[n];
             const uint32_t take = seg_scan_masks(bin, lane);
-            if (!mbar_wait(&acc_full[abuf], aphase, abort)) {
-                *abort = 1;
-                set_status(p.status, DEV_TIMEOUT);
-                break;
+            float acc[128];
+#pragma unroll
+            for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+            // promotion of every chunk accumulator into FP32 registers
+            for (int kb0 = 0; kb0 < P.n_kb; kb0 += CHUNK_KB) {
+                if (!mbar_wait(&acc_full[abuf], aphase, abort)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + ((uint32_t)(qw * 32) << 16) +
+                                       (uint32_t)(abuf * BN + ch * 128);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    uint32_t r[16];
+                    tmem_ld_32x32b_x16(tbase + (uint32_t)(c * 16), r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[c * 16 + j] += __uint_as_float(r[j]);
+                }
+                tc_fence_before();
+                mbar_arrive(&acc_empty[abuf]);
+                if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
             }
-            tc_fence_after();
-            const int kbase = ct * (BN / 4);
-#pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                if (kbase + c * 8 >= P.K) break;   // warp-uniform
-                uint32_t r[32];
-                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(qw * 32) << 16) + (uint32_t)(abuf * BN + c * 32), r);
-                tmem_ld_wait();
+            if (!ok) break;
+            // Eq. 16 product and the bin-run sums of this warp's 32 steps
+            const int kbase = ct * (BN / 4) + ch * 32;
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const int k = kbase + c * 8 + s;
-                    if (k >= P.K) break;   // warp-uniform
-                    const float *cs = P.col_scale + 4 * k;
-                    const float x = __uint_as_float(r[4 * s]) * __ldg(cs);
+            for (int s4 = 0; s4 < 32; ++s4) {
+                const int k = kbase + s4;
+                if (k >= P.K) break;   // warp-uniform
+                const float *cs = P.col_scale + 4 * k;
+                const float x = acc[4 * s4] * __ldg(cs);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const float y = __uint_as_float(r[4 * s + 1 + a]) * __ldg(cs + 1 + a);
-                        const float v = seg_scan(x * y, take);   // Eq. 16 product, bin-run sum
-                        if (slot >= 0) P.partials[((size_t)k * 3 + a) * P.n_slots + slot] = v;
-                    }
+                for (int a = 0; a < 3; ++a) {
+                    const float y = acc[4 * s4 + 1 + a] * __ldg(cs + 1 + a);
+                    const float v = seg_scan(x * y, take);
+                    if (slot >= 0) P.partials[((size_t)k * 3 + a) * P.n_slots + slot] = v;
                 }
             }
-            tc_fence_before();
-            mbar_arrive(&acc_empty[abuf]);
-            if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+        }
+        if (!ok) {
+            *abort = 1;
+            set_status(p.status, DEV_TIMEOUT);
         }
     }
 
@@ -270,7 +301,7 @@ cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    kern<<<grid, 256, L::SMEM_BYTES, s>>>(p);
+    kern<<<grid, L::THREADS, L::SMEM_BYTES, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -279,17 +310,22 @@ cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s
     if (c.bn == 256 && c.bk == 64 && c.stages == 2) return launch_impl<256, 64, 2, NPROB>(p, c.grid, s);
     if (c.bn == 256 && c.bk == 32 && c.stages == 4) return launch_impl<256, 32, 4, NPROB>(p, c.grid, s);
     if (c.bn == 128 && c.bk == 64 && c.stages == 3) return launch_impl<128, 64, 3, NPROB>(p, c.grid, s);
+    if (c.bn == 128 && c.bk == 32 && c.stages == 6) return launch_impl<128, 32, 6, NPROB>(p, c.grid, s);
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
+const TcConfig TC_CONFIGS[TC_NUM_CONFIGS] = {
+    {256, 64, 2, 0}, {256, 32, 4, 0}, {128, 64, 3, 0}, {128, 32, 6, 0}};
+
 bool tc_config_supported(const TcConfig &c) {
-    return (c.bn == 256 && c.bk == 64 && c.stages == 2) || (c.bn == 256 && c.bk == 32 && c.stages == 4) ||
-           (c.bn == 128 && c.bk == 64 && c.stages == 3);
+    for (const TcConfig &k : TC_CONFIGS)
+        if (k.bn == c.bn && k.bk == c.bk && k.stages == c.stages) return true;
+    return false;
 }
 
-size_t tc_smem_bytes(const TcConfig &c) {
+size_t tc_smem_bytes(const TcConfig &c) {   // must match TcLayout::SMEM_BYTES
     return (size_t)c.stages * (2 * TC_BM * c.bk * 2 + 2 * c.bn * c.bk * 2) + 256 + 1024;
 }
 

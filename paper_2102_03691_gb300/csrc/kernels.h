@@ -88,9 +88,12 @@ struct TcParams {
 struct TcConfig {
     int bn;       // columns per tile (MMA N): 128 or 256
     int bk;       // K elements per stage: 64 (128-byte swizzle) or 32 (64-byte swizzle)
-    int stages;
+    int stages;   // shared-memory pipeline depth
     int grid;
 };
+// Pipeline shapes the autotuner chooses from (index + 1 = mhc_params.tile_config).
+constexpr int TC_NUM_CONFIGS = 4;
+extern const TcConfig TC_CONFIGS[TC_NUM_CONFIGS];
 size_t tc_smem_bytes(const TcConfig &c);
 bool tc_config_supported(const TcConfig &c);
 // Encode a 2D 16-bit tensor map: rows x cols (cols innermost, row pitch ld elements).

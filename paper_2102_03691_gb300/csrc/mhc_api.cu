@@ -360,13 +360,12 @@ mhc_status run_projection(mhc_handle *h, int K) {
 
 // Autotune: time each supported tile configuration on the block just packed.
 mhc_status autotune(mhc_handle *h, int K) {
-    const TcConfig cands[] = {{256, 64, 2, 0}, {256, 32, 4, 0}, {128, 64, 3, 0}};
     cudaEvent_t e0, e1;
     MHC_CUDA(h, cudaEventCreate(&e0));
     MHC_CUDA(h, cudaEventCreate(&e1));
     float best = 1e30f;
     TcConfig best_c = h->tc;
-    for (const TcConfig &c : cands) {
+    for (const TcConfig &c : TC_CONFIGS) {
         mhc_status s = set_tc_config(h, c);
         if (s != MHC_OK) return s;
         if ((s = run_projection(h, K)) != MHC_OK) return s;   // warm-up
@@ -464,7 +463,7 @@ void mhc_default_params(mhc_params *p) {
     p->n_lags = 0;
     p->precision = MHC_PREC_BF16X3;
     p->flags = 0;
-    p->tile_n = 0;
+    p->tile_config = 0;
     p->ortho_probe = -1;
     p->dt_ps = 0.01;
     p->T_K = 300.0;
@@ -501,8 +500,8 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
         return fail(nullptr, MHC_ERR_INVALID_ARG, "GKMA needs n_lags >= 1");
     if (p->precision < MHC_PREC_FP32 || p->precision > MHC_PREC_FP16X3)
         return fail(nullptr, MHC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
-    if (p->tile_n != 0 && p->tile_n != 128 && p->tile_n != 256)
-        return fail(nullptr, MHC_ERR_INVALID_ARG, "tile_n must be 0, 128 or 256");
+    if (p->tile_config < 0 || p->tile_config > TC_NUM_CONFIGS)
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "tile_config must be in [0, %d]", TC_NUM_CONFIGS);
     if (!(p->dt_ps > 0) || !(p->T_K > 0) || !(p->V_A3 > 0))
         return fail(nullptr, MHC_ERR_INVALID_ARG, "dt_ps, T_K and V_A3 must be positive");
     int ndev = 0;
@@ -526,7 +525,7 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
     h->cc_minor = prop.minor;
     h->split = p->precision == MHC_PREC_FP32 ? SPLIT_FP32
                : p->precision == MHC_PREC_BF16X3 ? SPLIT_BF16 : SPLIT_FP16;
-    if (p->tile_n == 128) h->tc = {128, 64, 3, 0};
+    if (p->tile_config > 0) h->tc = TC_CONFIGS[p->tile_config - 1];
     if ((e = cudaSetDevice(p->device)) != cudaSuccess) {
         delete h;
         return fail(nullptr, MHC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -709,7 +708,7 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     mhc_status s;
     if ((s = stage_inputs(h, v, W, K, where)) != MHC_OK) return s;
     if ((s = pack_block(h, v, W, K)) != MHC_OK) return s;
-    if (is_tc(h) && h->prm.tile_n == 0) {
+    if (is_tc(h) && h->prm.tile_config == 0) {
         auto it = h->tuned.find(K);
         if (it == h->tuned.end()) {
             if ((s = autotune(h, K)) != MHC_OK) return s;
@@ -818,6 +817,7 @@ mhc_status mhc_get_info(mhc_handle *h, mhc_info *info) {
     info->pushes = h->pushes;
     info->n_slots = h->n_slots;
     info->tile_n = is_tc(h) ? h->tc.bn : 128;
+    info->tile_k = is_tc(h) ? h->tc.bk : 16;
     info->stages = is_tc(h) ? h->tc.stages : 0;
     info->grid = h->sm_count;
     info->e_exp = h->e_exp;

@@ -40,7 +40,7 @@ class MhcParams(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("k_max", ctypes.c_int32), ("n_lags", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("tile_n", ctypes.c_int32), ("ortho_probe", ctypes.c_int32),
+                ("tile_config", ctypes.c_int32), ("ortho_probe", ctypes.c_int32),
                 ("dt_ps", ctypes.c_double), ("T_K", ctypes.c_double), ("V_A3", ctypes.c_double),
                 ("F_e", ctypes.c_double * 3)]
 
@@ -51,7 +51,7 @@ class MhcInfo(ctypes.Structure):
                 ("n_bins", ctypes.c_int32), ("n_lags", ctypes.c_int32),
                 ("k_max", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("steps_pushed", ctypes.c_int64), ("pushes", ctypes.c_int64),
-                ("n_slots", ctypes.c_int64), ("tile_n", ctypes.c_int32),
+                ("n_slots", ctypes.c_int64), ("tile_n", ctypes.c_int32), ("tile_k", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("grid", ctypes.c_int32), ("e_exp", ctypes.c_int32),
                 ("ortho_err", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64)]
@@ -149,7 +149,7 @@ class ModalHeatCurrent:
     def __init__(self, precision: str = "bf16x3", k_max: int = 256, n_lags: int = 0,
                  gkma: bool | None = None, dt_ps: float = 0.01, T_K: float = 300.0,
                  V_A3: float = 1.0, F_e=(1e-5, 0.0, 0.0), device: int = 0, stream=None,
-                 tile_n: int = 0, ortho_probe: int = -1, flags: int = 0):
+                 tile_config: int = 0, ortho_probe: int = -1, flags: int = 0):
         self._L = load()
         p = MhcParams()
         self._L.mhc_default_params(ctypes.byref(p))
@@ -161,7 +161,7 @@ class ModalHeatCurrent:
         p.precision = PRECISIONS[precision]
         gk = (n_lags > 0) if gkma is None else gkma
         p.flags = flags | (FLAG_GKMA if gk else 0)
-        p.tile_n = tile_n
+        p.tile_config = tile_config
         p.ortho_probe = ortho_probe
         p.dt_ps, p.T_K, p.V_A3 = dt_ps, T_K, V_A3
         for i in range(3):
