@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Throughput of the modal heat-current hot path (GKMA / HNEMA) on GB300.
+
+One bench step = one block of K MD samples through the whole path: pack +
+FP64 total current (Eq. 10), the two modal projections with the fused x*y
+product and frequency-bin reduction (Eq. 13, 16), the bin finish and HNEMA
+sums (Eq. 19), the GKMA lag correlation (Eq. 17), and the read-out kernels
+(running Green-Kubo integral and its tau-window average, HNEMA kappa).
+
+Prints one JSON line.  `value` is whole-job mode*atom*steps/s with inputs
+resident in HBM (a pool of distinct blocks cycled); `e2e` is the same metric
+through the public API from pinned host buffers with the host->device copy of
+every block and the device->host read of kappa inside the timed region.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+Under torchrun every rank runs its own independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2102_03691_gb300 import synth  # noqa: E402
+
+METRIC = ("modal heat-current mode·atom·steps/s, mixed vs FP32 GPU at 1e-5 rel; "
+          "tensor-pipe %")
+UNIT = "mode·atom·steps/s"
+POOL = 8   # distinct input blocks cycled through
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="gkma_si_n8000", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "bf16x3", "fp32"])
+    ap.add_argument("--fp32-steps", type=int, default=12)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--basis", default="qr", choices=["qr", "gaussian"],
+                    help="qr: orthonormal E from a seeded QR; gaussian: seeded N(0, 1/3N) "
+                         "entries (same sizes and work, for tools that cannot load torch.linalg)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def aggregate(elapsed_s: float, units: float, world: int):
+    """Max elapsed time and total units over ranks (plain values when world == 1)."""
+    if world == 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.path = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def tc_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("k_tc.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2102_03691_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, precision: str):
+    """DRAM bytes per projection launch from a committed ncu summary, if it was
+    taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t[f"{workload}/{precision}"]
+        if e.get("source_hash") == tc_source_hash():
+            return e
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(w: dict, budget_s: float, seed: int):
+    """Time the FP64 oracle on a bounded sample of the workload: S MD steps of the
+    full atom count N, restricted to the first Ms modes, plus the GKMA correlation
+    of those steps.  Sized from a one-step calibration to take about budget_s."""
+    import oracle
+    N, M, L, B = w["N"], w["M"], w["L"], w["B"]
+    D = 3 * N
+    mass = synth.masses(N, w["mass"])
+    ms0 = min(M, 256)
+    E0 = synth.eigvecs(D, ms0, seed)
+    f = synth.frequencies(M, *w["f"], seed)
+    tr = synth.Trajectory(mass, seed=seed)
+    v, W = tr.next_block(1)
+    bins = oracle.bins_uniform(f, w["f"][0], w["f"][1], B)
+    t = time.perf_counter()
+    oracle.modal_current(E0, mass, v, W, bins[:ms0], B)
+    c = (time.perf_counter() - t) / ms0          # seconds per (step * mode)
+    Ms = int(max(32, min(M, budget_s / c)))
+    S = int(max(1, min(w["K"], budget_s / (c * Ms))))
+    E = synth.eigvecs(D, Ms, seed) if Ms != ms0 else E0
+    v, W = tr.next_block(S)
+    t = time.perf_counter()
+    r = oracle.modal_current(E, mass, v, W, bins[:Ms], B)
+    if L:
+        oracle.gkma_corr(r["Jb"], r["J"], min(L, S))
+    el = time.perf_counter() - t
+    return {"value": Ms * N * S / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{S} MD steps x {Ms} of {M} modes x {N} atoms (FP64 oracle: Eq. 10/13/16, "
+                      f"binning, GKMA correlation), {el:.1f} s"}
+
+
+def run_reference(args, w):
+    """--impl reference: the oracle, timed per bench step on a bounded sample."""
+    world, rank, _ = dist_init(args)
+    if rank != 0:
+        return
+    import oracle
+    N, M, B = w["N"], w["M"], w["B"]
+    D = 3 * N
+    seed = w["seed"]
+    total_budget = 150.0
+    per_step = total_budget / max(1, args.steps + args.warmup)
+    mass = synth.masses(N, w["mass"])
+    f = synth.frequencies(M, *w["f"], seed)
+    bins = oracle.bins_uniform(f, w["f"][0], w["f"][1], B)
+    tr = synth.Trajectory(mass, seed=seed)
+    ms0 = min(M, 128)
+    E0 = synth.eigvecs(D, ms0, seed)
+    v, W = tr.next_block(1)
+    t = time.perf_counter()
+    oracle.modal_current(E0, mass, v, W, bins[:ms0], B)
+    c = (time.perf_counter() - t) / ms0
+    Ms = int(max(16, min(M, per_step / c)))
+    S = int(max(1, min(w["K"], per_step / (c * Ms))))
+    E = synth.eigvecs(D, Ms, seed) if Ms != ms0 else E0
+    blocks = [tr.next_block(S) for _ in range(2)]
+    for i in range(args.warmup):
+        oracle.modal_current(E, mass, *blocks[i % 2], bins[:Ms], B)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        r = oracle.modal_current(E, mass, *blocks[i % 2], bins[:Ms], B)
+        if w["L"]:
+            oracle.gkma_corr(r["Jb"], r["J"], min(w["L"], S))
+    el = time.perf_counter() - t
+    value = Ms * N * S * args.steps / el
+    sample = f"{S} MD steps x {Ms} of {M} modes x {N} atoms per bench step (FP64 oracle)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(w, args, "fp64-oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def config_dict(w, args, precision):
+    return {"workload": args.workload, "N_atoms": w["N"], "M_modes": w["M"], "K_steps_per_block": w["K"],
+            "bins": w["B"], "lags": w["L"], "gkma": bool(w["gkma"]), "precision": precision,
+            "l2": "inputs larger than L2 (eigenvectors streamed every step; 8-block input pool)",
+            "basis": getattr(args, "basis", "qr")}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    world, rank, local = dist_init(args)
+    import torch
+    from paper_2102_03691_gb300.mhc import FLAG_PROFILE, ModalHeatCurrent
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, M, K, L, B = w["N"], w["M"], w["K"], w["L"], w["B"]
+    D = 3 * N
+    seed = w["seed"] + 1000 * rank          # independent replica per rank
+    V = N * w["V_per_atom"]
+    tau_hi = (L - 1) * w["dt_ps"] if L else 0.0
+    tau_lo = 0.8 * tau_hi
+
+    # inputs: eigenvectors (seeded QR on the GPU), frequencies, masses, an input pool
+    if args.basis == "qr":
+        E = synth.eigvecs_device(D, M, seed, device=dev)
+    else:
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        E = torch.randn(D, M, generator=g, device=dev) / D ** 0.5
+    f = synth.frequencies(M, *w["f"], seed)
+    mass = synth.masses(N, w["mass"])
+    drive = 0.0
+    if w.get("kappa_drive"):
+        drive = synth.drive_coupling(w["kappa_drive"], w["T_K"], V, w["Fe"][0], mass)
+    tr = synth.Trajectory(mass, drive_g=drive, seed=seed)
+    host_pool, dev_pool = [], []
+    for _ in range(POOL):
+        v, W = tr.next_block(K)
+        hv = torch.from_numpy(v).pin_memory()
+        hw = torch.from_numpy(W).pin_memory()
+        host_pool.append((hv, hw))
+        dev_pool.append((hv.to(dev), hw.to(dev)))
+
+    def make(precision):
+        h = ModalHeatCurrent(precision=precision, k_max=K, n_lags=L, dt_ps=w["dt_ps"],
+                             T_K=w["T_K"], V_A3=V, F_e=w["Fe"], device=local,
+                             flags=FLAG_PROFILE)
+        h.set_modes(E, mass, f)
+        h.set_bins_uniform(w["f"][0], w["f"][1], B)
+        return h
+
+    h = make(args.precision)
+    kap_w = torch.empty(B * 9 if L else B * 3, dtype=torch.float64, device=dev)
+
+    def step(hh, i, host=False):
+        v, W = (host_pool if host else dev_pool)[i % POOL]
+        hh.push(v, W)
+        if host:
+            return hh.read_kappa_gk(tau_lo, tau_hi)[1] if L else hh.read_hnema()[1]
+        if L:
+            hh.read_kappa_gk_into(kap_w, tau_lo, tau_hi)
+        else:
+            hh.read_hnema_into(kap_w)
+
+    # ---- device-resident timed region
+    for i in range(max(3, args.warmup)):
+        step(h, i)
+    torch.cuda.synchronize()
+    h.kernel_time()
+    launches0 = h.info()["kernel_launches"]
+    gpu_uuid = None
+    try:
+        gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_uuid = gpu_uuid if gpu_uuid.startswith("GPU-") else "GPU-" + gpu_uuid
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_uuid)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        step(h, i)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    launches = h.info()["kernel_launches"] - launches0
+    kms, kn = h.kernel_time()
+    units = float(M) * N * K * args.steps
+    el_max, units_tot = aggregate(elapsed, units, world)
+    value = units_tot / el_max
+
+    # ---- end to end through the API from pinned host memory
+    for i in range(3):
+        step(h, i, host=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    n_e2e = max(3, min(args.e2e_steps, args.steps))
+    for i in range(n_e2e):
+        step(h, i, host=True)
+    torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - t0
+    e2e_max, e2e_units = aggregate(e2e_el, float(M) * N * K * n_e2e, world)
+    h2d = 4 * K * N * 12
+    d2h = 8 * (B * 9 if L else B * 3)
+
+    # ---- FP32 CUDA-core path on the same workload (comparison)
+    fp32 = None
+    if args.precision != "fp32" and args.fp32_steps > 0:
+        h32 = make("fp32")
+        for i in range(2):
+            step(h32, i)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for i in range(args.fp32_steps):
+            step(h32, i)
+        a1.record()
+        torch.cuda.synchronize()
+        el32 = a0.elapsed_time(a1) / 1e3
+        ms32, n32 = h32.kernel_time()
+        fp32 = {"value": float(M) * N * K * args.fp32_steps / el32, "unit": UNIT,
+                "ms_per_step": 1e3 * el32 / args.fp32_steps, "steps": args.fp32_steps,
+                "projection_tflops": 2.0 * M * D * 4 * K * n32 / (ms32 / 1e3) / 1e12 if ms32 else None}
+        h32.close()
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel (the projection GEMM + fused epilogue)
+    peaks, peak_src = measured_peaks()
+    mult = 3 if args.precision != "fp32" else 1
+    flops_launch = mult * 2.0 * M * D * 4 * K
+    achieved = flops_launch * kn / (kms / 1e3) / 1e12 if kms > 0 else None
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    tr_e = profiled_traffic(args.workload, args.precision)
+    roofline = {"bound": "tensor", "kernel": "tc_modal_kernel", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                "traffic": tr_e["dram_bytes_per_launch"] if tr_e else None,
+                "peak_source": f"{peak_src} bf16 dense, sustained (kernel timed inside a long "
+                               "step loop); fp16 has the same dense tensor rate",
+                "flops_per_launch": flops_launch,
+                "kernel_ms_per_launch": kms / kn if kn else None,
+                "tensor_pipe_active_pct": tr_e.get("tensor_pipe_active_pct") if tr_e else None}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, args.cpu_seconds, seed)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": config_dict(w, args, args.precision),
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_units / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": n_e2e},
+        "clocks": clk, "gpu_launches": int(launches) * world,
+        "fp32_path": fp32,
+        "mixed_vs_fp32": (value / world) / fp32["value"] if fp32 else None,
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -70,6 +70,7 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
 /* Flags for mhc_params.flags */
 #define MHC_FLAG_GKMA 0x1          /* accumulate Eq. 17 lag correlations (needs n_lags > 0) */
 #define MHC_FLAG_NO_GRAPH 0x2      /* launch kernels directly instead of replaying a CUDA graph */
+#define MHC_FLAG_PROFILE 0x4       /* time each projection launch with CUDA events (mhc_kernel_time) */
 
 typedef struct {
     int32_t device;      /* CUDA device ordinal */
@@ -205,6 +206,12 @@ mhc_status mhc_check_orthonormality(mhc_handle *h, double tol, double *max_abs_e
 
 /* Counters and sizes. */
 mhc_status mhc_get_info(mhc_handle *h, mhc_info *info);
+
+/* With MHC_FLAG_PROFILE: total device time (ms) of the projection launches (the
+ * tensor-core or FP32 GEMM with its fused epilogue) since the previous call, measured
+ * with CUDA events recorded on the handle's stream around each launch, and their count.
+ * Synchronises the stream; resets the totals. */
+mhc_status mhc_kernel_time(mhc_handle *h, double *ms, int64_t *launches);
 
 /* Zero the HNEMA and GKMA accumulators and the step counter (modes and bins stay). */
 mhc_status mhc_reset(mhc_handle *h);

@@ -34,10 +34,14 @@ __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
     const float *v = a.v + (size_t)k * D;
     const float *W = a.W + (size_t)k * a.N * 9;
 
-    // Phase 1: row maxima (for the power-of-two scales) and Eq. 10 in FP64.
+    // Phase 1: row maxima (for the power-of-two scales) and Eq. 10.  Each product
+    // W^{ab} v^b is split exactly into p + e (TwoProduct via FMA) and summed with
+    // TwoSum into an unevaluated (s, c) float pair per thread, so the per-thread sums
+    // carry about 48 significant bits using FP32 instructions only; they are combined
+    // in FP64 below.  (GB300's FP64 pipe is too narrow for 9 FMAs per atom per step.)
     // Thread-strided over degrees of freedom d = 3i + b.
     float mx[4] = {0.f, 0.f, 0.f, 0.f};
-    double j[3] = {0.0, 0.0, 0.0};
+    float js[3] = {0.f, 0.f, 0.f}, jc[3] = {0.f, 0.f, 0.f};
     for (int d = threadIdx.x; d < D; d += PACK_THREADS) {
         const int i = d / 3, b = d - 3 * (d / 3);
         const float vv = v[d];
@@ -47,9 +51,19 @@ __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
         for (int al = 0; al < 3; ++al) {
             const float w = W[(size_t)i * 9 + 3 * al + b];
             mx[1 + al] = fmaxf(mx[1 + al], fabsf(w * ism));
-            j[al] = fma((double)w, (double)vv, j[al]);   // product exact in FP64
+            // explicit _rn intrinsics: the compiler must not contract these into FMAs
+            const float pr = __fmul_rn(w, vv);
+            const float pe = fmaf(w, vv, -pr);                       // w*vv = pr + pe exactly
+            const float t = __fadd_rn(js[al], pr);                   // TwoSum(js, pr)
+            const float bp = __fsub_rn(t, js[al]);
+            const float er = __fadd_rn(__fsub_rn(js[al], __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+            js[al] = t;
+            jc[al] = __fadd_rn(jc[al], __fadd_rn(er, pe));
         }
     }
+    double j[3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al) j[al] = (double)js[al] + (double)jc[al];
     __shared__ float s_mx[PACK_THREADS / 32][4];
     __shared__ double s_j[PACK_THREADS / 32][3];
     __shared__ float s_mul[4];

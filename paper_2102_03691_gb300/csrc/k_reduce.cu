@@ -124,20 +124,48 @@ __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__res
 }
 
 // ------------------------------------------------------------------ K5
-// Thread per (b, mu, nu): C(l) = Csum(l)/(T_s - l); trapezoid running integral, FP64.
-__global__ void gk_kappa_kernel(const double *Csum, int rows, int L, long long T_s, double coef_dt,
-                                double tau_lo, double tau_hi, double dt, double *kappa_tau,
-                                double *kappa_w) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
+// One CTA per (b, mu, nu) row, GK_THREADS threads, each owning GK_PER consecutive lags.
+// C(l) = Csum(l) * inv_count(l); trapezoid increments (C(l-1)+C(l))/2 for l >= 1;
+// block-wide exclusive scan of the per-thread totals (fixed tree: deterministic);
+// kappa(l) = c dt * prefix(l).  The tau-window average is a block reduction.
+constexpr int GK_THREADS = 128;
+__global__ void __launch_bounds__(GK_THREADS) gk_kappa_kernel(const double *Csum, int L,
+                                                              long long T_s, double coef_dt,
+                                                              double tau_lo, double tau_hi,
+                                                              double dt, double *kappa_tau,
+                                                              double *kappa_w) {
+    const int r = blockIdx.x;
     const double *cs = Csum + (size_t)r * L;
-    double acc = 0.0, prev = 0.0, wsum = 0.0;
-    int wn = 0;
-    for (int l = 0; l < L; ++l) {
+    const int per = (L + GK_THREADS - 1) / GK_THREADS;
+    const int l0 = threadIdx.x * per;
+    auto C = [&](int l) -> double {
         const long long cnt = T_s - l;
-        const double C = cnt > 0 ? cs[l] / (double)cnt : 0.0;
-        if (l > 0) acc += 0.5 * (prev + C);
-        prev = C;
+        return cnt > 0 ? cs[l] / (double)cnt : 0.0;
+    };
+    double prev = (l0 > 0 && l0 <= L) ? C(l0 - 1) : 0.0;
+    double tot = 0.0;
+    for (int l = l0; l < min(L, l0 + per); ++l) {
+        const double c = C(l);
+        if (l > 0) tot += 0.5 * (prev + c);
+        prev = c;
+    }
+    __shared__ double sc[GK_THREADS];
+    sc[threadIdx.x] = tot;
+    __syncthreads();
+    for (int off = 1; off < GK_THREADS; off <<= 1) {   // Hillis-Steele inclusive scan
+        const double add = threadIdx.x >= off ? sc[threadIdx.x - off] : 0.0;
+        __syncthreads();
+        sc[threadIdx.x] += add;
+        __syncthreads();
+    }
+    double acc = threadIdx.x > 0 ? sc[threadIdx.x - 1] : 0.0;   // exclusive prefix
+    double wsum = 0.0;
+    int wn = 0;
+    prev = (l0 > 0 && l0 <= L) ? C(l0 - 1) : 0.0;
+    for (int l = l0; l < min(L, l0 + per); ++l) {
+        const double c = C(l);
+        if (l > 0) acc += 0.5 * (prev + c);
+        prev = c;
         const double kap = coef_dt * acc;
         if (kappa_tau) kappa_tau[(size_t)r * L + l] = kap;
         const double tau = l * dt;
@@ -146,7 +174,19 @@ __global__ void gk_kappa_kernel(const double *Csum, int rows, int L, long long T
             ++wn;
         }
     }
-    if (kappa_w) kappa_w[r] = wn > 0 ? wsum / wn : 0.0;
+    __syncthreads();
+    __shared__ int sn[GK_THREADS];
+    sc[threadIdx.x] = wsum;
+    sn[threadIdx.x] = wn;
+    __syncthreads();
+    for (int off = GK_THREADS / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            sc[threadIdx.x] += sc[threadIdx.x + off];
+            sn[threadIdx.x] += sn[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && kappa_w) kappa_w[r] = sn[0] > 0 ? sc[0] / sn[0] : 0.0;
 }
 
 __global__ void hnema_finalize_kernel(const double *hsum, int n, long long T_s, double coef,
@@ -182,9 +222,8 @@ void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, 
 void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
                      double tau_lo, double tau_hi, double dt, double *kappa_tau, double *kappa_w,
                      cudaStream_t s) {
-    const int rows = B * 9;
-    gk_kappa_kernel<<<(rows + 127) / 128, 128, 0, s>>>(Csum, rows, L, T_s, coef_dt, tau_lo, tau_hi,
-                                                       dt, kappa_tau, kappa_w);
+    gk_kappa_kernel<<<B * 9, GK_THREADS, 0, s>>>(Csum, L, T_s, coef_dt, tau_lo, tau_hi, dt,
+                                                 kappa_tau, kappa_w);
 }
 
 void launch_hnema_finalize(const double *hsum, int B, long long T_s, double coef, double *mean,

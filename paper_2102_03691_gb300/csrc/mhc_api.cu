@@ -96,6 +96,10 @@ struct mhc_handle {
     std::map<std::string, DevBuf> buf;
     int *status = nullptr;
 
+    // optional CUDA-event timing of the projection kernel (MHC_FLAG_PROFILE)
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+    size_t prof_used = 0;
+
     // tensor-core state
     TcConfig tc{256, 64, 2, 0};
     std::map<int, TcConfig> tuned;  // K -> config
@@ -543,6 +547,10 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
 void mhc_destroy(mhc_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    for (auto &e : h->prof_events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
     for (auto &kv : h->buf)
         if (kv.second.p) cudaFree(kv.second.p);
     if (h->status) cudaFree(h->status);
@@ -716,7 +724,21 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
             return s;
         }
     }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (h->prm.flags & MHC_FLAG_PROFILE) {
+        if (h->prof_used == h->prof_events.size()) {
+            cudaEvent_t a0, a1;
+            MHC_CUDA(h, cudaEventCreate(&a0));
+            MHC_CUDA(h, cudaEventCreate(&a1));
+            h->prof_events.emplace_back(a0, a1);
+        }
+        ev0 = h->prof_events[h->prof_used].first;
+        ev1 = h->prof_events[h->prof_used].second;
+        ++h->prof_used;
+        MHC_CUDA(h, cudaEventRecord(ev0, h->stream));
+    }
     if ((s = run_projection(h, K)) != MHC_OK) return s;
+    if (ev1) MHC_CUDA(h, cudaEventRecord(ev1, h->stream));
     return finish_block(h, K);
 }
 
@@ -826,6 +848,22 @@ mhc_status mhc_get_info(mhc_handle *h, mhc_info *info) {
     for (auto &kv : h->buf) bytes += (int64_t)kv.second.bytes;
     info->device_bytes = bytes;
     info->kernel_launches = h->launches;
+    return MHC_OK;
+}
+
+mhc_status mhc_kernel_time(mhc_handle *h, double *ms, int64_t *launches) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!(h->prm.flags & MHC_FLAG_PROFILE)) return fail(h, MHC_ERR_INVALID_ARG, "MHC_FLAG_PROFILE is not set");
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    double total = 0.0;
+    for (size_t q = 0; q < h->prof_used; ++q) {
+        float t = 0.f;
+        MHC_CUDA(h, cudaEventElapsedTime(&t, h->prof_events[q].first, h->prof_events[q].second));
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = (int64_t)h->prof_used;
+    h->prof_used = 0;
     return MHC_OK;
 }
 

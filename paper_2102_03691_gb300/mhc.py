@@ -23,14 +23,15 @@ PRECISIONS = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
 MEM_HOST, MEM_DEVICE = 0, 1
 F32, F64 = 0, 1
 DOF_MAJOR, MODE_MAJOR = 0, 1
-FLAG_GKMA, FLAG_NO_GRAPH = 0x1, 0x2
+FLAG_GKMA, FLAG_NO_GRAPH, FLAG_PROFILE = 0x1, 0x2, 0x4
 
 # Every entry point declared in include/mhc.h.
 EXPORTS = (
     "mhc_default_params", "mhc_create", "mhc_destroy", "mhc_last_error", "mhc_status_string",
     "mhc_set_modes", "mhc_set_bins_uniform", "mhc_set_bin_ids", "mhc_push", "mhc_sync",
     "mhc_read_binned_current", "mhc_read_total_current", "mhc_read_hnema", "mhc_read_corr",
-    "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_reset",
+    "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_kernel_time",
+    "mhc_reset",
     "mhc_state_size", "mhc_get_state", "mhc_set_state", "mhc_group_create",
     "mhc_group_destroy", "mhc_group_push",
 )
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_read_kappa_gk.argtypes = [vp, vp, dbl, dbl, vp, i32]
     L.mhc_check_orthonormality.argtypes = [vp, dbl, ctypes.POINTER(dbl)]
     L.mhc_get_info.argtypes = [vp, ctypes.POINTER(MhcInfo)]
+    L.mhc_kernel_time.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
     L.mhc_reset.argtypes = [vp]
     L.mhc_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.mhc_get_state.argtypes = [vp, vp, ctypes.c_size_t]
@@ -305,6 +307,18 @@ class ModalHeatCurrent:
         i = MhcInfo()
         self._check(self._L.mhc_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in MhcInfo._fields_}
+
+    def kernel_time(self):
+        """(total ms, launches) of the projection kernel since the last call (FLAG_PROFILE)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self._L.mhc_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def read_kappa_gk_into(self, kappa_w, tau_lo: float, tau_hi: float, kappa_tau=None):
+        pw, where, _ = _ptr(kappa_w, np.float64)
+        pt = None if kappa_tau is None else _ptr(kappa_tau, np.float64)[0]
+        self._check(self._L.mhc_read_kappa_gk(self._h, pt, tau_lo, tau_hi, pw, where))
 
     def reset(self):
         self._check(self._L.mhc_reset(self._h))

@@ -64,6 +64,22 @@ def eigvecs(D: int, M: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(Q * s[None, :])
 
 
+def eigvecs_device(D: int, M: int, seed: int, device="cuda"):
+    """The recipe of eigvecs() computed with torch on a GPU (float32 QR), for bases
+    too large to factorise on the host in reasonable time.  Returns a float32
+    [D][M] CUDA tensor with orthonormal columns (to float32 rounding)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    G = torch.randn(D, M, generator=g, device=device, dtype=torch.float32)
+    Q, R = torch.linalg.qr(G, mode="reduced")
+    del G
+    s = torch.sign(torch.diagonal(R))
+    s[s == 0] = 1.0
+    del R
+    return (Q * s[None, :]).contiguous()
+
+
 def frequencies(M: int, f_lo: float, f_hi: float, seed: int) -> np.ndarray:
     """i.i.d. uniform mode frequencies on [f_lo, f_hi) THz, float64."""
     return _rng(seed + 7919).uniform(f_lo, f_hi, size=M)
