@@ -239,6 +239,40 @@ void mhc_group_destroy(mhc_group *g);
 mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *const *W,
                           const int32_t *K, int32_t where);
 
+/*
+ * No-allocation variant of one block's binned modal current.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device memory,
+ * e.g. an MD engine calling from inside its time-step loop (where cudaMalloc would
+ * synchronise the device) or an application that owns all device memory through a pool
+ * reserved at start-up.  It computes what mhc_push + mhc_read_binned_current /
+ * mhc_read_total_current give with MHC_PREC_FP32, for one block, with no handle.
+ *
+ *   E            device, FP32, mode-major E[n * ld + 3i + b] = e^b_{i,n}, ld >= 3N
+ *   bin_of_mode  device [M]: bin of each mode, in [0, B) and non-decreasing (order the
+ *                modes by bin and drop excluded ones before the call)
+ *   mass_amu     device [N] float64, every m_i > 0
+ *   v, W         device [K][N][3] and [K][N][9] float32 (layouts as for mhc_push)
+ *   Jb           device output [K][B][3] float32 (binned modal current)
+ *   J            device output [K][3] float64 (total current, Eq. 10)
+ *   stream       cudaStream_t or NULL
+ * Every intermediate array lives in one static device buffer of
+ * MHC_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until exit; no
+ * call allocates.  The first call on a device looks up the buffer's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Calls share
+ * the buffer and keep the last call's contents (what must start at zero is cleared each
+ * call); calls whose work overlaps on the GPU race.  The call synchronises `stream`.
+ * Errors: INVALID_ARG for bad sizes or pointers, bins that are out of range or
+ * decreasing, non-positive masses, or a problem whose intermediates exceed the buffer
+ * (roughly 4 (M_pad + 4K) D_pad + 16 K M_pad bytes with M_pad = M rounded up to 128 and
+ * D_pad = 3N rounded up to 64); CUDA for runtime errors.
+ */
+#define MHC_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+mhc_status mhc_binned_current_noalloc(int32_t n_atoms, int32_t n_modes, const float *E, int64_t ld,
+                                      const int32_t *bin_of_mode, int32_t n_bins,
+                                      const double *mass_amu, const float *v, const float *W,
+                                      int32_t K, float *Jb, double *J, int32_t device,
+                                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ EXPORTS = (
     "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_kernel_time",
     "mhc_reset",
     "mhc_state_size", "mhc_get_state", "mhc_set_state", "mhc_group_create",
-    "mhc_group_destroy", "mhc_group_push",
+    "mhc_group_destroy", "mhc_group_push", "mhc_binned_current_noalloc",
 )
 
 
@@ -108,12 +108,32 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_group_destroy.restype = None
     L.mhc_group_push.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                  ctypes.POINTER(i32), i32]
+    L.mhc_binned_current_noalloc.argtypes = [i32, i32, vp, i64, vp, i32, vp, vp, vp, i32, vp, vp,
+                                             i32, vp]
     for name in EXPORTS:
         if name not in ("mhc_default_params", "mhc_destroy", "mhc_last_error",
                         "mhc_status_string", "mhc_group_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def binned_current_noalloc(E_mode_major, bin_of_mode, n_bins: int, mass_amu, v, W, Jb, J,
+                           device: int = 0, stream=None) -> None:
+    """mhc_binned_current_noalloc on torch CUDA tensors (see include/mhc.h): one block's
+    binned modal current computed with no device allocation."""
+    L = load()
+    M, ld = E_mode_major.shape
+    N = mass_amu.shape[0]
+    K = v.shape[0]
+    st = L.mhc_binned_current_noalloc(
+        N, M, ctypes.c_void_p(E_mode_major.data_ptr()), ld, ctypes.c_void_p(bin_of_mode.data_ptr()),
+        n_bins, ctypes.c_void_p(mass_amu.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+        ctypes.c_void_p(W.data_ptr()), K, ctypes.c_void_p(Jb.data_ptr()),
+        ctypes.c_void_p(J.data_ptr()), device,
+        stream if stream is not None else _current_stream(device))
+    if st != MHC_OK:
+        raise MhcError(st, "mhc_binned_current_noalloc failed")
 
 
 def _is_torch(x) -> bool:
