@@ -10,7 +10,7 @@ namespace mhc {
 
 namespace {
 
-constexpr int PACK_THREADS = 256;
+constexpr int PACK_THREADS = 512;
 
 __device__ __forceinline__ void store_split(const PackArgs &a, size_t idx, float val) {
     if (a.split == SPLIT_BF16) {
@@ -28,38 +28,46 @@ __device__ __forceinline__ void store_split(const PackArgs &a, size_t idx, float
     }
 }
 
+// TwoProduct + TwoSum: add w*v exactly into the unevaluated float pair (s, c).
+// Explicit _rn intrinsics keep the compiler from contracting these into FMAs.
+__device__ __forceinline__ void acc_exact(float &s, float &c, float w, float v) {
+    const float pr = __fmul_rn(w, v);
+    const float pe = fmaf(w, v, -pr);                       // w*v = pr + pe exactly
+    const float t = __fadd_rn(s, pr);
+    const float bp = __fsub_rn(t, s);
+    const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(er, pe));
+}
+
 __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
     const int k = blockIdx.x;
-    const int D = 3 * a.N;
-    const float *v = a.v + (size_t)k * D;
+    const float *v = a.v + (size_t)k * a.N * 3;
     const float *W = a.W + (size_t)k * a.N * 9;
 
-    // Phase 1: row maxima (for the power-of-two scales) and Eq. 10.  Each product
-    // W^{ab} v^b is split exactly into p + e (TwoProduct via FMA) and summed with
-    // TwoSum into an unevaluated (s, c) float pair per thread, so the per-thread sums
-    // carry about 48 significant bits using FP32 instructions only; they are combined
-    // in FP64 below.  (GB300's FP64 pipe is too narrow for 9 FMAs per atom per step.)
-    // Thread-strided over degrees of freedom d = 3i + b.
+    // Phase 1, one thread per atom: row maxima (for the power-of-two scales) and
+    // Eq. 10, J^a = sum_i sum_b W_i^{ab} v_i^b.  Products are added exactly into an
+    // unevaluated float pair per thread (about 48 significant bits with FP32
+    // instructions only) and the pairs are combined in FP64 below.  (GB300's FP64
+    // pipe is too narrow for 9 FP64 FMAs per atom per step.)
     float mx[4] = {0.f, 0.f, 0.f, 0.f};
     float js[3] = {0.f, 0.f, 0.f}, jc[3] = {0.f, 0.f, 0.f};
-    for (int d = threadIdx.x; d < D; d += PACK_THREADS) {
-        const int i = d / 3, b = d - 3 * (d / 3);
-        const float vv = v[d];
-        const float sm = a.sqm[i], ism = a.isqm[i];
-        mx[0] = fmaxf(mx[0], fabsf(sm * vv));
+    for (int i = threadIdx.x; i < a.N; i += PACK_THREADS) {
+        float vv[3], ww[9];
 #pragma unroll
-        for (int al = 0; al < 3; ++al) {
-            const float w = W[(size_t)i * 9 + 3 * al + b];
-            mx[1 + al] = fmaxf(mx[1 + al], fabsf(w * ism));
-            // explicit _rn intrinsics: the compiler must not contract these into FMAs
-            const float pr = __fmul_rn(w, vv);
-            const float pe = fmaf(w, vv, -pr);                       // w*vv = pr + pe exactly
-            const float t = __fadd_rn(js[al], pr);                   // TwoSum(js, pr)
-            const float bp = __fsub_rn(t, js[al]);
-            const float er = __fadd_rn(__fsub_rn(js[al], __fsub_rn(t, bp)), __fsub_rn(pr, bp));
-            js[al] = t;
-            jc[al] = __fadd_rn(jc[al], __fadd_rn(er, pe));
-        }
+        for (int b = 0; b < 3; ++b) vv[b] = v[(size_t)i * 3 + b];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ww[q] = W[(size_t)i * 9 + q];
+        const float sm = a.sqm[i], ism = a.isqm[i];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) mx[0] = fmaxf(mx[0], fabsf(sm * vv[b]));
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                mx[1 + al] = fmaxf(mx[1 + al], fabsf(ww[3 * al + b] * ism));
+                acc_exact(js[al], jc[al], ww[3 * al + b], vv[b]);
+            }
     }
     double j[3];
 #pragma unroll
@@ -92,8 +100,8 @@ __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
         }
         s_mul[c] = ldexpf(1.f, s);
         a.col_scale[4 * k + c] = ldexpf(1.f, -(s + a.e_exp));
-    } else if (threadIdx.x < 7) {
-        const int c = threadIdx.x - 4;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 35) {
+        const int c = threadIdx.x - 32;
         double t = 0.0;
         for (int w = 0; w < PACK_THREADS / 32; ++w) t += s_j[w][c];
         a.Jtot[3 * k + c] = t;
@@ -101,17 +109,22 @@ __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
     }
     __syncthreads();
 
-    // Phase 2: scaled rows, split into hi/lo (inputs are re-read from L2).
-    const float m0 = s_mul[0], m1 = s_mul[1], m2 = s_mul[2], m3 = s_mul[3];
+    // Phase 2, one thread per atom: the four scaled rows of step k,
+    //   Bt[4k][3i+b] = sqrt(m_i) v_i^b,  Bt[4k+1+a][3i+b] = W_i^{ab} / sqrt(m_i),
+    // split into hi/lo (inputs re-read from L2).
+    const float mul[4] = {s_mul[0], s_mul[1], s_mul[2], s_mul[3]};
     const size_t r0 = (size_t)(4 * k) * a.D_ld;
     const size_t ld = (size_t)a.D_ld;
-    for (int d = threadIdx.x; d < D; d += PACK_THREADS) {
-        const int i = d / 3, b = d - 3 * (d / 3);
+    for (int i = threadIdx.x; i < a.N; i += PACK_THREADS) {
         const float sm = a.sqm[i], ism = a.isqm[i];
-        store_split(a, r0 + d, (sm * v[d]) * m0);
-        store_split(a, r0 + ld + d, (W[(size_t)i * 9 + b] * ism) * m1);
-        store_split(a, r0 + 2 * ld + d, (W[(size_t)i * 9 + 3 + b] * ism) * m2);
-        store_split(a, r0 + 3 * ld + d, (W[(size_t)i * 9 + 6 + b] * ism) * m3);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) store_split(a, r0 + 3 * i + b, (sm * v[(size_t)i * 3 + b]) * mul[0]);
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                store_split(a, r0 + (1 + al) * ld + 3 * i + b,
+                            (W[(size_t)i * 9 + 3 * al + b] * ism) * mul[1 + al]);
     }
 }
 

@@ -47,35 +47,40 @@ __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__r
 // ------------------------------------------------------------------ K4
 // Each warp owns 32 consecutive lags; lane l holds the total current J(t - l) of the
 // current step t in registers.  Moving to step t+1 shifts that window by one lag with a
-// warp shuffle (lane l takes lane l-1's value) and lane 0 loads the one new sample, so the
-// ring of past J is read once per warp per step.  Products and 32-step partial sums are
-// FP32, the lag sums themselves are FP64.
+// warp shuffle (lane l takes lane l-1's value) and lane 0 takes the one new sample from
+// the CTA's copy of the J samples it needs, staged in shared memory from the ring once
+// per launch.  Products and 32-step partial sums are FP32, the lag sums are FP64.
 constexpr int LC_THREADS = 128;
-constexpr int LC_BINS = 4;
+constexpr int LC_BINS = 2;
 __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__restrict__ Jb,
                                                               const double *__restrict__ Jring,
                                                               int R, double *Csum, int K, int B,
                                                               int L, long long t0) {
-    extern __shared__ float sJ[];   // [K][LC_BINS][3]
+    extern __shared__ float sJ[];   // [K][LC_BINS][3] then the J window [K + LC_THREADS - 1][3]
+    float *sW = sJ + K * LC_BINS * 3;
     const int b0 = blockIdx.y * LC_BINS;
     const int nb = min(LC_BINS, B - b0);
     for (int q = threadIdx.x; q < K * LC_BINS * 3; q += LC_THREADS) {
         const int k = q / (LC_BINS * 3), r = q % (LC_BINS * 3), bb = r / 3, mu = r % 3;
         sJ[q] = bb < nb ? Jb[((size_t)k * B + b0 + bb) * 3 + mu] : 0.f;
     }
+    // window entry j holds J(tw0 + j), tw0 = t0 - (first lag of the CTA) - (LC_THREADS - 1)
+    const int lc0 = blockIdx.x * LC_THREADS;
+    const long long tw0 = t0 - lc0 - (LC_THREADS - 1);
+    const int nw = K + LC_THREADS - 1;
+    for (int q = threadIdx.x; q < nw * 3; q += LC_THREADS) {
+        const long long tt = tw0 + q / 3;
+        sW[q] = tt >= 0 ? (float)Jring[(tt % R) * 3 + q % 3] : 0.f;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int l0 = blockIdx.x * LC_THREADS + (threadIdx.x & ~31);   // first lag of this warp
+    const int l0 = lc0 + (threadIdx.x & ~31);   // first lag of this warp
     const int l = l0 + lane;
-    auto load_j = [&](long long tt, float (&j)[3]) {
-        if (tt >= 0) {
-            const double *src = Jring + (tt % R) * 3;
-            j[0] = (float)src[0];
-            j[1] = (float)src[1];
-            j[2] = (float)src[2];
-        } else {
-            j[0] = j[1] = j[2] = 0.f;
-        }
+    auto load_j = [&](long long tt, float (&j)[3]) {   // J(tt) from the staged window
+        const float *src = sW + (tt - tw0) * 3;
+        j[0] = src[0];
+        j[1] = src[1];
+        j[2] = src[2];
     };
     float j[3];
     load_j(t0 - l, j);
@@ -215,7 +220,7 @@ void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, 
                      int L, long long t0, cudaStream_t s) {
     if (L <= 0 || K <= 0 || B <= 0) return;
     dim3 grid((L + LC_THREADS - 1) / LC_THREADS, (B + LC_BINS - 1) / LC_BINS);
-    const size_t sm = (size_t)K * LC_BINS * 3 * sizeof(float);
+    const size_t sm = ((size_t)K * LC_BINS * 3 + (size_t)(K + LC_THREADS - 1) * 3) * sizeof(float);
     lag_corr_kernel<<<grid, LC_THREADS, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0);
 }
 
