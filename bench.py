@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tile-config", type=int, default=0,
+                    help="tensor-core tile shape (0 = autotune, 1..4 as in include/mhc.h)")
     ap.add_argument("--basis", default="qr", choices=["qr", "gaussian"],
                     help="qr: orthonormal E from a seeded QR; gaussian: seeded N(0, 1/3N) "
                          "entries (same sizes and work, for tools that cannot load torch.linalg)")
@@ -305,7 +307,7 @@ def main():
     def make(precision):
         h = ModalHeatCurrent(precision=precision, k_max=K, n_lags=L, dt_ps=w["dt_ps"],
                              T_K=w["T_K"], V_A3=V, F_e=w["Fe"], device=local,
-                             flags=FLAG_PROFILE)
+                             flags=FLAG_PROFILE, tile_config=args.tile_config)
         h.set_modes(E, mass, f)
         h.set_bins_uniform(w["f"][0], w["f"][1], B)
         return h

@@ -227,11 +227,15 @@ mhc_status mhc_get_state(mhc_handle *h, void *blob, size_t bytes);
 mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes);
 
 /*
- * Grouped execution of several independent systems (e.g. many nanotubes of
- * uneven size): one persistent tensor-core launch covers the tiles of all
- * handles, balanced by their cost, replayed as a CUDA graph.  All handles must
- * be on the same device and stream, use the same tensor-core precision, and
- * have modes and bins loaded.  The group does not own the handles.
+ * Grouped execution of up to 16 independent systems of uneven size (e.g. the
+ * replicas or the nanotube batch of Sec. III.A): one persistent tensor-core launch
+ * covers the tiles of all handles, assigned to the SMs by a longest-processing-time
+ * schedule (a tile's cost is proportional to its 3N).  All handles must be on the
+ * same device and stream, use the same tensor-core precision, and have modes and
+ * bins loaded; the group does not own them and must be destroyed before them.  The
+ * tile shape is autotuned on the first group push (tile_config of the first handle
+ * 0) and gives the same results as pushing each handle on its own.  Errors of group
+ * calls are reported through mhc_last_error of the first handle.
  */
 mhc_status mhc_group_create(mhc_group **g, mhc_handle *const *handles, int32_t n);
 void mhc_group_destroy(mhc_group *g);

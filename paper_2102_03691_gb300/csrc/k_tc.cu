@@ -128,8 +128,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------------------ TMA producer
-        for (int q = 0; q < NPROB; ++q) {
-            if (q > 0 && !p.sched) break;
+        for (int q = 0; q < NPROB && q < p.n_prob; ++q) {
             tma_prefetch_desc(&p.prob[q].tmA_hi);
             tma_prefetch_desc(&p.prob[q].tmA_lo);
             tma_prefetch_desc(&p.prob[q].tmB_hi);

@@ -81,6 +81,7 @@ struct TcParams {
     TcProblem prob[NPROB];
     const uint32_t *sched;   // packed tile list (null: round-robin over prob[0])
     const int *cta_begin;    // [grid+1] offsets into sched
+    int n_prob;              // problems in use (prob[0..n_prob-1])
     int *status;
     uint32_t idesc;
 };

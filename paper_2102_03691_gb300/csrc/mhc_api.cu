@@ -12,6 +12,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -106,13 +107,17 @@ struct mhc_handle {
     TcParams<1> tcp{};
 };
 
+struct GroupSchedule {
+    DevBuf sched, cta_begin;   // device copies (owned by the group)
+    int grid = 0;
+};
+
 struct mhc_group {
     std::vector<mhc_handle *> hs;
     TcConfig tc{256, 64, 2, 0};
+    bool tuned = false;
     TcParams<TC_MAX_GROUP> tcp{};
-    DevBuf sched, cta_begin;
-    std::vector<int> lastK;
-    int *status = nullptr;
+    std::map<std::pair<int, std::vector<int>>, GroupSchedule> sched_cache;   // (bn, Ks)
 };
 
 namespace {
@@ -308,6 +313,7 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         P.n_kb = (int)(h->D_ld / c.bk);
         h->tcp.sched = nullptr;
         h->tcp.cta_begin = nullptr;
+        h->tcp.n_prob = 1;
         h->tcp.status = h->status;
         h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, TC_BM, (uint32_t)c.bn);
     }
@@ -942,22 +948,219 @@ mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes) {
     return MHC_OK;
 }
 
+}  // extern "C"
+
 // ----------------------------------------------------------------------------- groups
-mhc_status mhc_group_create(mhc_group **g, mhc_handle *const *handles, int32_t n) {
-    (void)g;
-    (void)handles;
-    (void)n;
-    return MHC_ERR_UNSUPPORTED;
+namespace {
+
+mhc_status group_encode(mhc_group *g) {
+    mhc_handle *h0 = g->hs[0];
+    const TcConfig &c = g->tc;
+    for (size_t j = 0; j < g->hs.size(); ++j) {
+        mhc_handle *h = g->hs[j];
+        TcProblem &P = g->tcp.prob[j];
+        P = h->tcp.prob[0];
+        if (tc_make_tmap(&P.tmA_hi, dptr<void>(h, "Et_hi"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
+            tc_make_tmap(&P.tmA_lo, dptr<void>(h, "Et_lo"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
+            tc_make_tmap(&P.tmB_hi, dptr<void>(h, "Bt_hi"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk) ||
+            tc_make_tmap(&P.tmB_lo, dptr<void>(h, "Bt_lo"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk))
+            return fail(h0, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed (group member %zu)", j);
+        P.n_kb = (int)(h->D_ld / c.bk);
+    }
+    g->tcp.status = h0->status;
+    g->tcp.n_prob = (int)g->hs.size();
+    g->tcp.idesc = idesc_f16(h0->split == SPLIT_BF16 ? 1u : 0u, TC_BM, (uint32_t)c.bn);
+    return MHC_OK;
 }
-void mhc_group_destroy(mhc_group *g) { delete g; }
+
+// Longest-processing-time assignment of every tile of every system to the persistent
+// CTAs.  A tile's cost is its number of k-blocks (proportional to 3N).  Tiles of one
+// system are taken in mode-tile-major order, so the column tiles that share an
+// eigenvector tile land on different CTAs at about the same time (shared through L2).
+mhc_status group_schedule(mhc_group *g, const std::vector<int> &Ks, GroupSchedule *&out) {
+    mhc_handle *h0 = g->hs[0];
+    const TcConfig &c = g->tc;
+    auto key = std::make_pair(c.bn, Ks);
+    auto it = g->sched_cache.find(key);
+    if (it != g->sched_cache.end()) {
+        out = &it->second;
+        return MHC_OK;
+    }
+    struct Tile { int cost; uint32_t id; };
+    std::vector<Tile> tiles;
+    std::vector<int> order(g->hs.size());
+    for (size_t j = 0; j < order.size(); ++j) order[j] = (int)j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return g->hs[a]->D_ld > g->hs[b]->D_ld;
+    });
+    for (int j : order) {
+        mhc_handle *h = g->hs[j];
+        const int n_mt = h->M_eff > 0 ? (int)(h->M_pad / TC_BM) : 0;
+        const int n_ct = (4 * Ks[j] + c.bn - 1) / c.bn;
+        for (int mt = 0; mt < n_mt; ++mt)
+            for (int ct = 0; ct < n_ct; ++ct)
+                tiles.push_back({(int)(h->D_ld / c.bk), tc_tile_id(j, mt, ct)});
+    }
+    const int grid = std::max(1, std::min<int>(h0->sm_count, (int)tiles.size()));
+    std::vector<std::vector<uint32_t>> per(grid);
+    using Load = std::pair<long long, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+    for (int b = 0; b < grid; ++b) pq.push({0, b});
+    for (const Tile &t : tiles) {
+        Load l = pq.top();
+        pq.pop();
+        per[l.second].push_back(t.id);
+        pq.push({l.first + t.cost, l.second});
+    }
+    std::vector<uint32_t> flat;
+    std::vector<int> begin(grid + 1, 0);
+    for (int b = 0; b < grid; ++b) {
+        begin[b] = (int)flat.size();
+        flat.insert(flat.end(), per[b].begin(), per[b].end());
+    }
+    begin[grid] = (int)flat.size();
+    GroupSchedule &gs = g->sched_cache[key];
+    gs.grid = grid;
+    cudaError_t e = cudaMalloc(&gs.sched.p, sizeof(uint32_t) * std::max<size_t>(flat.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&gs.cta_begin.p, sizeof(int) * (grid + 1));
+    if (e != cudaSuccess) {
+        g->sched_cache.erase(key);
+        return fail(h0, MHC_ERR_OOM, "group schedule allocation: %s", cudaGetErrorString(e));
+    }
+    gs.sched.bytes = sizeof(uint32_t) * flat.size();
+    gs.cta_begin.bytes = sizeof(int) * (grid + 1);
+    MHC_CUDA(h0, cudaMemcpyAsync(gs.sched.p, flat.data(), sizeof(uint32_t) * flat.size(),
+                                 cudaMemcpyHostToDevice, h0->stream));
+    MHC_CUDA(h0, cudaMemcpyAsync(gs.cta_begin.p, begin.data(), sizeof(int) * (grid + 1),
+                                 cudaMemcpyHostToDevice, h0->stream));
+    MHC_CUDA(h0, cudaStreamSynchronize(h0->stream));   // host vectors die on return
+    out = &gs;
+    return MHC_OK;
+}
+
+mhc_status group_launch(mhc_group *g, const std::vector<int> &Ks) {
+    mhc_handle *h0 = g->hs[0];
+    GroupSchedule *gs = nullptr;
+    mhc_status s = group_schedule(g, Ks, gs);
+    if (s != MHC_OK) return s;
+    for (size_t j = 0; j < g->hs.size(); ++j) {
+        TcProblem &P = g->tcp.prob[j];
+        P.K = Ks[j];
+        P.n_col_tiles = (4 * Ks[j] + g->tc.bn - 1) / g->tc.bn;
+        P.n_tiles = (g->hs[j]->M_eff > 0 ? (int)(g->hs[j]->M_pad / TC_BM) : 0) * P.n_col_tiles;
+    }
+    g->tcp.sched = static_cast<const uint32_t *>(gs->sched.p);
+    g->tcp.cta_begin = static_cast<const int *>(gs->cta_begin.p);
+    TcConfig c = g->tc;
+    c.grid = gs->grid;
+    cudaError_t e = launch_tc_group(g->tcp, c, h0->stream);
+    h0->launches++;
+    if (e != cudaSuccess)
+        return fail(h0, MHC_ERR_CUDA, "grouped tensor-core launch failed: %s", cudaGetErrorString(e));
+    return MHC_OK;
+}
+
+mhc_status group_autotune(mhc_group *g, const std::vector<int> &Ks) {
+    mhc_handle *h0 = g->hs[0];
+    cudaEvent_t e0, e1;
+    MHC_CUDA(h0, cudaEventCreate(&e0));
+    MHC_CUDA(h0, cudaEventCreate(&e1));
+    float best = 1e30f;
+    TcConfig best_c = g->tc;
+    mhc_status s;
+    for (const TcConfig &c : TC_CONFIGS) {
+        g->tc = c;
+        if ((s = group_encode(g)) != MHC_OK) return s;
+        if ((s = group_launch(g, Ks)) != MHC_OK) return s;   // warm-up
+        MHC_CUDA(h0, cudaEventRecord(e0, h0->stream));
+        for (int r = 0; r < 3; ++r)
+            if ((s = group_launch(g, Ks)) != MHC_OK) return s;
+        MHC_CUDA(h0, cudaEventRecord(e1, h0->stream));
+        MHC_CUDA(h0, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        MHC_CUDA(h0, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->tc = best_c;
+    g->tuned = true;
+    return group_encode(g);
+}
+
+}  // namespace
+
+extern "C" {
+
+mhc_status mhc_group_create(mhc_group **out, mhc_handle *const *handles, int32_t n) {
+    if (!out || !handles || n < 1) return MHC_ERR_INVALID_ARG;
+    *out = nullptr;
+    mhc_handle *h0 = handles[0];
+    if (!h0) return MHC_ERR_INVALID_ARG;
+    if (n > TC_MAX_GROUP) return fail(h0, MHC_ERR_INVALID_ARG, "at most %d systems per group", TC_MAX_GROUP);
+    for (int j = 0; j < n; ++j) {
+        mhc_handle *h = handles[j];
+        if (!h) return fail(h0, MHC_ERR_INVALID_ARG, "handle %d is null", j);
+        if (!h->bins_ready) return fail(h0, MHC_ERR_INVALID_ARG, "handle %d has no modes/bins", j);
+        if (!is_tc(h)) return fail(h0, MHC_ERR_UNSUPPORTED, "grouped launches need a tensor-core precision");
+        if (h->prm.device != h0->prm.device || h->stream != h0->stream || h->split != h0->split)
+            return fail(h0, MHC_ERR_INVALID_ARG, "handle %d differs in device, stream or precision", j);
+        for (int q = 0; q < j; ++q)
+            if (handles[q] == h) return fail(h0, MHC_ERR_INVALID_ARG, "handle %d appears twice", j);
+    }
+    auto *g = new mhc_group();
+    g->hs.assign(handles, handles + n);
+    g->tc = h0->tc;
+    mhc_status s = group_encode(g);
+    if (s != MHC_OK) {
+        delete g;
+        return s;
+    }
+    *out = g;
+    return MHC_OK;
+}
+
+void mhc_group_destroy(mhc_group *g) {
+    if (!g) return;
+    cudaStreamSynchronize(g->hs[0]->stream);
+    for (auto &kv : g->sched_cache) {
+        if (kv.second.sched.p) cudaFree(kv.second.sched.p);
+        if (kv.second.cta_begin.p) cudaFree(kv.second.cta_begin.p);
+    }
+    delete g;
+}
+
 mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *const *W,
                           const int32_t *K, int32_t where) {
-    (void)g;
-    (void)v;
-    (void)W;
-    (void)K;
-    (void)where;
-    return MHC_ERR_UNSUPPORTED;
+    if (!g || !v || !W || !K) return MHC_ERR_INVALID_ARG;
+    mhc_handle *h0 = g->hs[0];
+    if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE) return fail(h0, MHC_ERR_INVALID_ARG, "where");
+    const size_t n = g->hs.size();
+    std::vector<int> Ks(n);
+    for (size_t j = 0; j < n; ++j) {
+        if (!v[j] || !W[j]) return fail(h0, MHC_ERR_INVALID_ARG, "inputs of system %zu are null", j);
+        if (K[j] < 1 || K[j] > g->hs[j]->prm.k_max)
+            return fail(h0, MHC_ERR_INVALID_ARG, "K[%zu]=%d outside [1, %d]", j, K[j], g->hs[j]->prm.k_max);
+        if (!g->hs[j]->bins_ready) return fail(h0, MHC_ERR_INVALID_ARG, "system %zu lost its bins", j);
+        Ks[j] = K[j];
+    }
+    MHC_CUDA(h0, cudaSetDevice(h0->prm.device));
+    mhc_status s;
+    for (size_t j = 0; j < n; ++j) {
+        const float *vj = v[j], *wj = W[j];
+        if ((s = stage_inputs(g->hs[j], vj, wj, Ks[j], where)) != MHC_OK) return s;
+        if ((s = pack_block(g->hs[j], vj, wj, Ks[j])) != MHC_OK) return s;
+    }
+    if (!g->tuned && h0->prm.tile_config == 0) {
+        if ((s = group_autotune(g, Ks)) != MHC_OK) return s;
+    }
+    if ((s = group_launch(g, Ks)) != MHC_OK) return s;
+    for (size_t j = 0; j < n; ++j)
+        if ((s = finish_block(g->hs[j], Ks[j])) != MHC_OK) return s;
+    return MHC_OK;
 }
 
 }  // extern "C"

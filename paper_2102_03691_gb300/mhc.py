@@ -118,6 +118,53 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     return L
 
 
+class ModalHeatCurrentGroup:
+    """mhc_group_*: one grouped tensor-core launch over several ModalHeatCurrent handles."""
+
+    def __init__(self, members):
+        self._L = load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h for m in self.members])
+        g = ctypes.c_void_p()
+        st = self._L.mhc_group_create(ctypes.byref(g), arr, len(self.members))
+        if st != MHC_OK:
+            raise MhcError(st, self._L.mhc_last_error(self.members[0]._h).decode())
+        self._g = g
+
+    def push(self, vs, Ws):
+        n = len(self.members)
+        keep, pv, pw, ks, where = [], [], [], [], None
+        for m, v, W in zip(self.members, vs, Ws):
+            a, wa, ka = _ptr(v, np.float32)
+            b, wb, kb = _ptr(W, np.float32)
+            if where is None:
+                where = wa
+            if wa != where or wb != where:
+                raise ValueError("all inputs of a group push must be in the same memory space")
+            keep += [ka, kb]
+            pv.append(a)
+            pw.append(b)
+            ks.append(int(ka.shape[0]))
+        self._keep = keep
+        st = self._L.mhc_group_push(self._g, (ctypes.c_void_p * n)(*pv), (ctypes.c_void_p * n)(*pw),
+                                    (ctypes.c_int32 * n)(*ks), where)
+        if st != MHC_OK:
+            raise MhcError(st, self._L.mhc_last_error(self.members[0]._h).decode())
+        for m, k in zip(self.members, ks):
+            m._lastK = k
+
+    def close(self):
+        if getattr(self, "_g", None):
+            self._L.mhc_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def binned_current_noalloc(E_mode_major, bin_of_mode, n_bins: int, mass_amu, v, W, Jb, J,
                            device: int = 0, stream=None) -> None:
     """mhc_binned_current_noalloc on torch CUDA tensors (see include/mhc.h): one block's

@@ -174,6 +174,10 @@ WORKLOADS = {
     "subset_si_n20000_m6000": dict(N=20000, M=6000, mass=28.085, f=(0.0, 16.0), B=64,
                                    T_s=50000, K=512, L=1000, dt_ps=0.010, V_per_atom=20.02,
                                    T_K=300.0, Fe=(1e-5, 0.0, 0.0), gkma=True, seed=20210209),
+    # small case of the Si shape for profiler captures (E hi+lo 578 MB, 752 tiles)
+    "profile_si_n4000_m12000": dict(N=4000, M=12000, mass=28.085, f=(0.0, 16.0), B=64,
+                                    T_s=4096, K=512, L=500, dt_ps=0.010, V_per_atom=20.02,
+                                    T_K=300.0, Fe=(1e-5, 0.0, 0.0), gkma=True, seed=20210210),
 }
 
 
