@@ -80,8 +80,9 @@ typedef struct {
     int32_t precision;   /* mhc_precision */
     int32_t flags;       /* MHC_FLAG_* */
     int32_t tile_config; /* tensor-core tile: 0 = autotune on the first push of each K;
-                            1..4 = (columns, k per stage, stages) of (256,64,2), (256,32,4),
-                            (128,64,3), (128,32,6).  All give bitwise the same results. */
+                            1..4 = one-SM tiles of 128 modes x (columns, k per stage, stages)
+                            (256,64,2), (256,32,4), (128,64,3), (128,32,6); 5..6 = two-SM tiles
+                            (CTA pair, 256 modes x 256 columns) with (64,3), (32,6). */
     int32_t ortho_probe; /* -1: no basis check in set_modes; 0: full E^T E; P>0: P probe modes */
     double dt_ps;        /* sampling interval between pushed steps (Eq. 17 dt') */
     double T_K;          /* temperature T (Eq. 17, 19) */
@@ -97,6 +98,7 @@ typedef struct {
     int64_t pushes;              /* number of mhc_push calls */
     int64_t n_slots;             /* per-step partial-sum slots of the bin reduction */
     int32_t tile_n, tile_k;      /* tensor-core tile: columns per tile, d elements per stage */
+    int32_t tile_pair;           /* 1 if the tile spans a CTA pair on two SMs */
     int32_t stages, grid;        /* pipeline depth, SM count */
     int32_t e_exp;               /* power-of-two scale applied to E before the split */
     double ortho_err;            /* last basis check result, -1 if none */

@@ -289,6 +289,333 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
     if (warp == 2) tmem_dealloc(tmem_base, L::TMEM_COLS);
 }
 
+// =====================================================================================
+// CTA-pair variant (tcgen05 cta_group::2).  A cluster of two CTAs on two SMs computes a
+// 256-mode x 256-column tile: each CTA stages its own 128 modes of E and its own half
+// (128 columns) of B, the leader CTA (rank 0) issues M=256 MMAs that read both CTAs'
+// shared memory, and each CTA's TMEM receives the accumulator of its own 128 modes
+// (all 256 columns).  Per SM this halves the B bytes per flop against the one-SM tile
+// (64 KB instead of 96 KB per 64-wide k-block at the same tensor work).
+//   - TMA loads of both CTAs complete on the leader's `full` barrier (armed by the
+//     leader with both CTAs' bytes);
+//   - the leader's commits arrive on `empty`/`acc_full` of both CTAs (multicast);
+//   - each epilogue warp of both CTAs arrives on the leader's `acc_empty` after
+//     promoting a chunk.
+template <int BK, int STAGES>
+struct TcPairLayout {
+    static constexpr int BN = 256;
+    static constexpr int A_BYTES = TC_BM * BK * 2;
+    static constexpr int B_BYTES = (BN / 2) * BK * 2;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int TILE_BYTES = STAGES * STAGE_BYTES;
+    static constexpr int SMEM_BYTES = TILE_BYTES + 256 + 1024;
+    static constexpr uint32_t TMEM_COLS = 512;
+    static constexpr uint32_t SWIZZLE_CODE = BK == 64 ? 2u : 4u;
+    static constexpr uint32_t SBO = 8 * BK * 2;
+    static constexpr int EPI_WARPS = 8;
+    static constexpr int THREADS = 128 + 32 * EPI_WARPS;
+    static_assert(STAGES * 2 + 5 <= 28, "barrier area");
+};
+
+template <int NPROB>
+struct PairTileIter {
+    const TcParams<NPROB> &p;
+    int i, end, step;
+    __device__ PairTileIter(const TcParams<NPROB> &pp, int pair, int npairs) : p(pp) {
+        if (p.sched) {
+            i = p.cta_begin[pair];
+            end = p.cta_begin[pair + 1];
+            step = 1;
+        } else {
+            i = pair;
+            end = p.prob[0].n_tiles;
+            step = npairs;
+        }
+    }
+    __device__ bool next(int &prob, int &mp, int &ct) {
+        if (i >= end) return false;
+        if (p.sched) {
+            const uint32_t id = p.sched[i];
+            prob = (int)(id >> 28);
+            ct = (int)((id >> 20) & 0xFFu);
+            mp = (int)(id & 0xFFFFFu);
+        } else {
+            prob = 0;
+            mp = i / p.prob[0].n_col_tiles;
+            ct = i - mp * p.prob[0].n_col_tiles;
+        }
+        i += step;
+        return true;
+    }
+};
+
+template <int BK, int STAGES, int NPROB>
+__global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_constant__ TcParams<NPROB> p) {
+    using L = TcPairLayout<BK, STAGES>;
+    constexpr int BN = L::BN;
+    constexpr int CHUNK_KB = PROMOTE_D / BK;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::TILE_BYTES);
+    uint64_t *full = bars;                   // [STAGES] leader: both CTAs' TMA bytes landed
+    uint64_t *empty = bars + STAGES;         // [STAGES] this CTA's stage free again
+    uint64_t *acc_full = bars + 2 * STAGES;  // [2] chunk accumulator ready (both CTAs)
+    uint64_t *acc_empty = acc_full + 2;      // [2] leader: chunk promoted by both CTAs
+    uint64_t *done_bar = acc_empty + 2;      // leader: final MMA drain
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done_bar + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+    const int pair = (int)cluster_id_x(), npairs = (int)nclusters_x();
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 2 * L::EPI_WARPS);
+        }
+        mbar_init(done_bar, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2) {
+        tmem_alloc_pair(tmem_slot, L::TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncwarp();
+    cluster_sync_all();   // barriers of both CTAs initialised, TMEM allocated in both
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------ TMA producer (both CTAs)
+        for (int q = 0; q < NPROB && q < p.n_prob; ++q) {
+            tma_prefetch_desc(&p.prob[q].tmA_hi);
+            tma_prefetch_desc(&p.prob[q].tmA_lo);
+            tma_prefetch_desc(&p.prob[q].tmB_hi);
+            tma_prefetch_desc(&p.prob[q].tmB_lo);
+        }
+        const uint64_t pol_b = l2_policy_evict_last();
+        const uint64_t pol_e = l2_policy_evict_first();
+        uint32_t issued_phase[STAGES];
+        bool issued[STAGES];
+        for (int s = 0; s < STAGES; ++s) issued[s] = false;
+        int stage = 0;
+        uint32_t phase = 0;
+        PairTileIter<NPROB> it(p, pair, npairs);
+        int prob, mp, ct;
+        bool ok = true;
+        while (ok && it.next(prob, mp, ct)) {
+            const TcProblem &P = p.prob[prob];
+            const int arow = mp * 2 * TC_BM + (int)rank * TC_BM;
+            const int brow = ct * BN + (int)rank * (BN / 2);
+            for (int kb = 0; kb < P.n_kb; ++kb) {
+                if (!mbar_wait(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
+                if (leader) mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
+                const uint32_t fb = mapa_shared(smem_u32(&full[stage]), 0);
+                uint8_t *sa = smem + stage * L::STAGE_BYTES;
+                const int x = kb * BK;
+                tma_load_2d_pair(sa, &P.tmA_hi, fb, x, arow, pol_e);
+                tma_load_2d_pair(sa + L::A_BYTES, &P.tmA_lo, fb, x, arow, pol_e);
+                tma_load_2d_pair(sa + 2 * L::A_BYTES, &P.tmB_hi, fb, x, brow, pol_b);
+                tma_load_2d_pair(sa + 2 * L::A_BYTES + L::B_BYTES, &P.tmB_lo, fb, x, brow, pol_b);
+                issued[stage] = true;
+                issued_phase[stage] = phase;
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+        }
+        if (!ok) {
+            *abort = 1;
+            set_status(p.status, DEV_TIMEOUT);
+        }
+        if (leader)   // the leader's barriers count both CTAs' copies
+            for (int s = 0; s < STAGES; ++s)
+                if (issued[s]) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&full[s], issued_phase[s]) &&
+                           clock64() - t0 < WAIT_LIMIT_CYCLES) {
+                    }
+                }
+    } else if (warp == 1 && lane == 0 && leader) {
+        // ------------------------------------------------------------ MMA issuer (leader)
+        const uint32_t idesc = p.idesc;
+        int stage = 0, abuf = 0;
+        uint32_t phase = 0, aphase = 0;
+        PairTileIter<NPROB> it(p, pair, npairs);
+        int prob, mp, ct;
+        bool ok = true;
+        const uint32_t smem0 = smem_u32(smem);
+        while (ok && it.next(prob, mp, ct)) {
+            const TcProblem &P = p.prob[prob];
+            for (int kb0 = 0; ok && kb0 < P.n_kb; kb0 += CHUNK_KB) {
+                if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * BN);
+                const int kb1 = min(kb0 + CHUNK_KB, P.n_kb);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_hi = smem0 + stage * L::STAGE_BYTES;
+                    const uint32_t a_lo = a_hi + L::A_BYTES;
+                    const uint32_t b_hi = a_hi + 2 * L::A_BYTES;
+                    const uint32_t b_lo = b_hi + L::B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        const uint64_t dah = smem_desc_kmajor(a_hi + off, L::SBO, L::SWIZZLE_CODE);
+                        const uint64_t dal = smem_desc_kmajor(a_lo + off, L::SBO, L::SWIZZLE_CODE);
+                        const uint64_t dbh = smem_desc_kmajor(b_hi + off, L::SBO, L::SWIZZLE_CODE);
+                        const uint64_t dbl = smem_desc_kmajor(b_lo + off, L::SBO, L::SWIZZLE_CODE);
+                        umma_f16_pair(d_tmem, dah, dbl, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
+                        umma_f16_pair(d_tmem, dal, dbh, idesc, 1u);
+                        umma_f16_pair(d_tmem, dah, dbh, idesc, 1u);
+                    }
+                    umma_commit_pair(&empty[stage], (uint16_t)0x3);
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                umma_commit_pair(&acc_full[abuf], (uint16_t)0x3);
+                if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+            }
+        }
+        if (!ok) {
+            *abort = 1;
+            set_status(p.status, DEV_TIMEOUT);
+        }
+        umma_commit_pair(done_bar, (uint16_t)0x1);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(done_bar, 0) && clock64() - t0 < WAIT_LIMIT_CYCLES) {
+        }
+    } else if (warp >= 4) {
+        // ------------------------------------------------------------ promotion + epilogue (both)
+        const int qw = warp & 3;
+        const int ch = (warp - 4) >> 2;
+        int abuf = 0;
+        uint32_t aphase = 0;
+        const uint32_t empty_leader[2] = {mapa_shared(smem_u32(&acc_empty[0]), 0),
+                                          mapa_shared(smem_u32(&acc_empty[1]), 0)};
+        PairTileIter<NPROB> it(p, pair, npairs);
+        int prob, mp, ct;
+        bool ok = true;
+        while (ok && it.next(prob, mp, ct)) {
+            const TcProblem &P = p.prob[prob];
+            const int n = mp * 2 * TC_BM + (int)rank * TC_BM + qw * 32 + lane;
+            const int bin = P.mode_bin[n];
+            const int slot = P.mode_slot[n];
+            const uint32_t take = seg_scan_masks(bin, lane);
+            float acc[128];
+#pragma unroll
+            for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+            for (int kb0 = 0; kb0 < P.n_kb; kb0 += CHUNK_KB) {
+                if (!mbar_wait(&acc_full[abuf], aphase, abort)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + ((uint32_t)(qw * 32) << 16) +
+                                       (uint32_t)(abuf * BN + ch * 128);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    uint32_t r[16];
+                    tmem_ld_32x32b_x16(tbase + (uint32_t)(c * 16), r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[c * 16 + j] += __uint_as_float(r[j]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                // the chunk's TMEM reads have completed (wait::ld): the leader may reuse it
+                if (lane == 0) {
+                    if (leader) mbar_arrive(&acc_empty[abuf]);
+                    else mbar_arrive_cluster_relaxed(empty_leader[abuf]);
+                }
+                if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+            }
+            if (!ok) break;
+            const int kbase = ct * (BN / 4) + ch * 32;
+#pragma unroll
+            for (int s4 = 0; s4 < 32; ++s4) {
+                const int k = kbase + s4;
+                if (k >= P.K) break;   // warp-uniform
+                const float *cs = P.col_scale + 4 * k;
+                const float x = acc[4 * s4] * __ldg(cs);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float y = acc[4 * s4 + 1 + a] * __ldg(cs + 1 + a);
+                    const float v = seg_scan(x * y, take);
+                    if (slot >= 0) P.partials[((size_t)k * 3 + a) * P.n_slots + slot] = v;
+                }
+            }
+        }
+        if (!ok) {
+            *abort = 1;
+            set_status(p.status, DEV_TIMEOUT);
+        }
+    }
+
+    tc_fence_before();
+    __syncwarp();
+    cluster_sync_all();   // neither CTA leaves while the pair still shares barriers or TMEM
+    tc_fence_after();
+    if (warp == 2) tmem_dealloc_pair(tmem_base, L::TMEM_COLS);
+}
+
+template <int BK, int STAGES, int NPROB>
+cudaError_t launch_pair_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
+    using L = TcPairLayout<BK, STAGES>;
+    auto kern = tc_modal_pair_kernel<BK, STAGES, NPROB>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             L::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(L::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = L::SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+template <int BK, int STAGES, int NPROB>
+int max_pairs_impl() {
+    using L = TcPairLayout<BK, STAGES>;
+    auto kern = tc_modal_pair_kernel<BK, STAGES, NPROB>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES) !=
+        cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(L::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = L::SMEM_BYTES;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 template <int BN, int BK, int STAGES, int NPROB>
 cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
     using L = TcLayout<BN, BK, STAGES>;
@@ -306,6 +633,11 @@ cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
 
 template <int NPROB>
 cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s) {
+    if (c.pair) {
+        if (c.bn == 256 && c.bk == 64 && c.stages == 3) return launch_pair_impl<64, 3, NPROB>(p, c.grid, s);
+        if (c.bn == 256 && c.bk == 32 && c.stages == 6) return launch_pair_impl<32, 6, NPROB>(p, c.grid, s);
+        return cudaErrorInvalidValue;
+    }
     if (c.bn == 256 && c.bk == 64 && c.stages == 2) return launch_impl<256, 64, 2, NPROB>(p, c.grid, s);
     if (c.bn == 256 && c.bk == 32 && c.stages == 4) return launch_impl<256, 32, 4, NPROB>(p, c.grid, s);
     if (c.bn == 128 && c.bk == 64 && c.stages == 3) return launch_impl<128, 64, 3, NPROB>(p, c.grid, s);
@@ -316,16 +648,24 @@ cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s
 }  // namespace
 
 const TcConfig TC_CONFIGS[TC_NUM_CONFIGS] = {
-    {256, 64, 2, 0}, {256, 32, 4, 0}, {128, 64, 3, 0}, {128, 32, 6, 0}};
+    {256, 64, 2, 0, 0}, {256, 32, 4, 0, 0}, {128, 64, 3, 0, 0}, {128, 32, 6, 0, 0},
+    {256, 64, 3, 1, 0}, {256, 32, 6, 1, 0}};
 
 bool tc_config_supported(const TcConfig &c) {
     for (const TcConfig &k : TC_CONFIGS)
-        if (k.bn == c.bn && k.bk == c.bk && k.stages == c.stages) return true;
+        if (k.bn == c.bn && k.bk == c.bk && k.stages == c.stages && k.pair == c.pair) return true;
     return false;
 }
 
-size_t tc_smem_bytes(const TcConfig &c) {   // must match TcLayout::SMEM_BYTES
-    return (size_t)c.stages * (2 * TC_BM * c.bk * 2 + 2 * c.bn * c.bk * 2) + 256 + 1024;
+int tc_max_pairs(const TcConfig &c) {
+    if (!c.pair) return 0;
+    if (c.bk == 64) return max_pairs_impl<64, 3, 1>();
+    return max_pairs_impl<32, 6, 1>();
+}
+
+size_t tc_smem_bytes(const TcConfig &c) {   // must match TcLayout / TcPairLayout::SMEM_BYTES
+    const int brows = c.pair ? c.bn / 2 : c.bn;
+    return (size_t)c.stages * (2 * TC_BM * c.bk * 2 + 2 * brows * c.bk * 2) + 256 + 1024;
 }
 
 cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream_t s) {

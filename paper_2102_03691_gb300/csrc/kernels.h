@@ -90,11 +90,14 @@ struct TcConfig {
     int bn;       // columns per tile (MMA N): 128 or 256
     int bk;       // K elements per stage: 64 (128-byte swizzle) or 32 (64-byte swizzle)
     int stages;   // shared-memory pipeline depth
+    int pair;     // 1: two-SM tile (cta_group::2, 256 modes per CTA pair)
     int grid;
 };
 // Pipeline shapes the autotuner chooses from (index + 1 = mhc_params.tile_config).
-constexpr int TC_NUM_CONFIGS = 4;
+constexpr int TC_NUM_CONFIGS = 6;
 extern const TcConfig TC_CONFIGS[TC_NUM_CONFIGS];
+// Clusters of two CTAs of a two-SM configuration that can be resident at once (0 on error).
+int tc_max_pairs(const TcConfig &c);
 size_t tc_smem_bytes(const TcConfig &c);
 bool tc_config_supported(const TcConfig &c);
 // Encode a 2D 16-bit tensor map: rows x cols (cols innermost, row pitch ld elements).

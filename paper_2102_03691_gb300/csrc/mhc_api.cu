@@ -102,7 +102,7 @@ struct mhc_handle {
     size_t prof_used = 0;
 
     // tensor-core state
-    TcConfig tc{256, 64, 2, 0};
+    TcConfig tc{256, 64, 2, 0, 0};
     std::map<int, TcConfig> tuned;  // K -> config
     TcParams<1> tcp{};
 };
@@ -114,7 +114,7 @@ struct GroupSchedule {
 
 struct mhc_group {
     std::vector<mhc_handle *> hs;
-    TcConfig tc{256, 64, 2, 0};
+    TcConfig tc{256, 64, 2, 0, 0};
     bool tuned = false;
     TcParams<TC_MAX_GROUP> tcp{};
     std::map<std::pair<int, std::vector<int>>, GroupSchedule> sched_cache;   // (bn, Ks)
@@ -223,6 +223,35 @@ void bins_uniform_host(const std::vector<double> &f, double f_min, double f_max,
     }
 }
 
+// Tensor maps of one system for tile configuration c: E hi/lo boxes of 128 modes, B hi/lo
+// boxes of the CTA's columns (all BN columns, or half of them for a two-SM tile).
+int encode_maps(mhc_handle *h, const TcConfig &c, TcProblem &P) {
+    const uint32_t brows = c.pair ? c.bn / 2 : c.bn;
+    int r = tc_make_tmap(&P.tmA_hi, dptr<void>(h, "Et_hi"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk);
+    if (!r) r = tc_make_tmap(&P.tmA_lo, dptr<void>(h, "Et_lo"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk);
+    if (!r) r = tc_make_tmap(&P.tmB_hi, dptr<void>(h, "Bt_hi"), h->B_rows, h->D_ld, h->D_ld, brows, c.bk);
+    if (!r) r = tc_make_tmap(&P.tmB_lo, dptr<void>(h, "Bt_lo"), h->B_rows, h->D_ld, h->D_ld, brows, c.bk);
+    return r;
+}
+
+// Mode tiles of a system for configuration c (128 modes, or 256 for a CTA pair).
+int mode_tiles(const mhc_handle *h, const TcConfig &c) {
+    const int64_t per = (c.pair ? 2 : 1) * TC_BM;
+    return (int)((h->M_eff + per - 1) / per);
+}
+
+// Persistent scheduling units that can run at once: SMs, or resident CTA pairs.
+int sched_units(const mhc_handle *h, const TcConfig &c) {
+    if (!c.pair) return h->sm_count;
+    static int pairs[TC_NUM_CONFIGS] = {};
+    for (int q = 0; q < TC_NUM_CONFIGS; ++q)
+        if (TC_CONFIGS[q].bk == c.bk && TC_CONFIGS[q].pair == c.pair && TC_CONFIGS[q].stages == c.stages) {
+            if (!pairs[q]) pairs[q] = tc_max_pairs(c);
+            return std::max(1, std::min(pairs[q], h->sm_count / 2));
+        }
+    return std::max(1, h->sm_count / 2);
+}
+
 // Sort kept modes by bin (stable), build the per-mode bin/slot tables of the fused
 // epilogue, gather+split E into the stored order and set up the tensor maps.
 mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_t B) {
@@ -242,7 +271,8 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         for (int64_t n = 0; n < (int64_t)bin_of_mode.size(); ++n)
             if (bin_of_mode[n] >= 0) h->perm[pos[bin_of_mode[n]]++] = (int)n;
     }
-    h->M_pad = round_up(std::max<int64_t>(h->M_eff, 1), TC_BM);
+    // a multiple of 256 so that two-SM tiles (256 modes per CTA pair) need no bounds checks
+    h->M_pad = round_up(std::max<int64_t>(h->M_eff, 1), is_tc(h) ? 2 * TC_BM : TC_BM);
     std::vector<int> mbin(h->M_pad, -1), mslot(h->M_pad, -1), sbeg(B + 1, 0);
     for (int64_t q = 0; q < h->M_eff; ++q) mbin[q] = bin_of_mode[h->perm[q]];
     // a slot for the last mode of every run of equal bins inside each 32-mode group
@@ -300,11 +330,7 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
     if (is_tc(h)) {
         TcProblem &P = h->tcp.prob[0];
         const TcConfig &c = h->tc;
-        if (tc_make_tmap(&P.tmA_hi, dptr<void>(h, "Et_hi"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
-            tc_make_tmap(&P.tmA_lo, dptr<void>(h, "Et_lo"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
-            tc_make_tmap(&P.tmB_hi, dptr<void>(h, "Bt_hi"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk) ||
-            tc_make_tmap(&P.tmB_lo, dptr<void>(h, "Bt_lo"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk))
-            return fail(h, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        if (encode_maps(h, c, P)) return fail(h, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         P.mode_bin = dptr<int>(h, "mode_bin");
         P.mode_slot = dptr<int>(h, "mode_slot");
         P.col_scale = dptr<float>(h, "col_scale");
@@ -315,7 +341,7 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         h->tcp.cta_begin = nullptr;
         h->tcp.n_prob = 1;
         h->tcp.status = h->status;
-        h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, TC_BM, (uint32_t)c.bn);
+        h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, (c.pair ? 2 : 1) * TC_BM, (uint32_t)c.bn);
     }
     h->bins_ready = true;
     return reset_accumulators(h);
@@ -323,17 +349,13 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
 
 mhc_status set_tc_config(mhc_handle *h, const TcConfig &c) {
     if (!tc_config_supported(c)) return fail(h, MHC_ERR_INVALID_ARG, "unsupported tile configuration");
-    const bool remap = h->bins_ready && (c.bn != h->tc.bn || c.bk != h->tc.bk);
+    const bool remap = h->bins_ready && (c.bn != h->tc.bn || c.bk != h->tc.bk || c.pair != h->tc.pair);
     h->tc = c;
     if (remap) {
         TcProblem &P = h->tcp.prob[0];
-        if (tc_make_tmap(&P.tmA_hi, dptr<void>(h, "Et_hi"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
-            tc_make_tmap(&P.tmA_lo, dptr<void>(h, "Et_lo"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
-            tc_make_tmap(&P.tmB_hi, dptr<void>(h, "Bt_hi"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk) ||
-            tc_make_tmap(&P.tmB_lo, dptr<void>(h, "Bt_lo"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk))
-            return fail(h, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        if (encode_maps(h, c, P)) return fail(h, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         P.n_kb = (int)(h->D_ld / c.bk);
-        h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, TC_BM, (uint32_t)c.bn);
+        h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, (c.pair ? 2 : 1) * TC_BM, (uint32_t)c.bn);
     }
     return MHC_OK;
 }
@@ -359,8 +381,8 @@ mhc_status run_projection(mhc_handle *h, int K) {
     TcProblem &P = h->tcp.prob[0];
     P.K = K;
     P.n_col_tiles = (int)((4 * K + c.bn - 1) / c.bn);
-    P.n_tiles = (int)(h->M_pad / TC_BM) * P.n_col_tiles;
-    c.grid = std::min(h->sm_count, P.n_tiles);
+    P.n_tiles = mode_tiles(h, c) * P.n_col_tiles;
+    c.grid = std::min(sched_units(h, c), P.n_tiles) * (c.pair ? 2 : 1);
     cudaError_t e = launch_tc_single(h->tcp, c, h->stream);
     h->launches++;
     if (e != cudaSuccess)
@@ -845,6 +867,7 @@ mhc_status mhc_get_info(mhc_handle *h, mhc_info *info) {
     info->pushes = h->pushes;
     info->n_slots = h->n_slots;
     info->tile_n = is_tc(h) ? h->tc.bn : 128;
+    info->tile_pair = is_tc(h) ? h->tc.pair : 0;
     info->tile_k = is_tc(h) ? h->tc.bk : 16;
     info->stages = is_tc(h) ? h->tc.stages : 0;
     info->grid = h->sm_count;
@@ -960,16 +983,13 @@ mhc_status group_encode(mhc_group *g) {
         mhc_handle *h = g->hs[j];
         TcProblem &P = g->tcp.prob[j];
         P = h->tcp.prob[0];
-        if (tc_make_tmap(&P.tmA_hi, dptr<void>(h, "Et_hi"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
-            tc_make_tmap(&P.tmA_lo, dptr<void>(h, "Et_lo"), h->M_pad, h->D_ld, h->D_ld, TC_BM, c.bk) ||
-            tc_make_tmap(&P.tmB_hi, dptr<void>(h, "Bt_hi"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk) ||
-            tc_make_tmap(&P.tmB_lo, dptr<void>(h, "Bt_lo"), h->B_rows, h->D_ld, h->D_ld, c.bn, c.bk))
+        if (encode_maps(h, c, P))
             return fail(h0, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed (group member %zu)", j);
         P.n_kb = (int)(h->D_ld / c.bk);
     }
     g->tcp.status = h0->status;
     g->tcp.n_prob = (int)g->hs.size();
-    g->tcp.idesc = idesc_f16(h0->split == SPLIT_BF16 ? 1u : 0u, TC_BM, (uint32_t)c.bn);
+    g->tcp.idesc = idesc_f16(h0->split == SPLIT_BF16 ? 1u : 0u, (c.pair ? 2 : 1) * TC_BM, (uint32_t)c.bn);
     return MHC_OK;
 }
 
@@ -980,7 +1000,7 @@ mhc_status group_encode(mhc_group *g) {
 mhc_status group_schedule(mhc_group *g, const std::vector<int> &Ks, GroupSchedule *&out) {
     mhc_handle *h0 = g->hs[0];
     const TcConfig &c = g->tc;
-    auto key = std::make_pair(c.bn, Ks);
+    auto key = std::make_pair(c.bn * 2 + c.pair, Ks);
     auto it = g->sched_cache.find(key);
     if (it != g->sched_cache.end()) {
         out = &it->second;
@@ -995,13 +1015,13 @@ mhc_status group_schedule(mhc_group *g, const std::vector<int> &Ks, GroupSchedul
     });
     for (int j : order) {
         mhc_handle *h = g->hs[j];
-        const int n_mt = h->M_eff > 0 ? (int)(h->M_pad / TC_BM) : 0;
+        const int n_mt = mode_tiles(h, c);
         const int n_ct = (4 * Ks[j] + c.bn - 1) / c.bn;
         for (int mt = 0; mt < n_mt; ++mt)
             for (int ct = 0; ct < n_ct; ++ct)
                 tiles.push_back({(int)(h->D_ld / c.bk), tc_tile_id(j, mt, ct)});
     }
-    const int grid = std::max(1, std::min<int>(h0->sm_count, (int)tiles.size()));
+    const int grid = std::max(1, std::min<int>(sched_units(h0, c), (int)tiles.size()));
     std::vector<std::vector<uint32_t>> per(grid);
     using Load = std::pair<long long, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
@@ -1047,12 +1067,12 @@ mhc_status group_launch(mhc_group *g, const std::vector<int> &Ks) {
         TcProblem &P = g->tcp.prob[j];
         P.K = Ks[j];
         P.n_col_tiles = (4 * Ks[j] + g->tc.bn - 1) / g->tc.bn;
-        P.n_tiles = (g->hs[j]->M_eff > 0 ? (int)(g->hs[j]->M_pad / TC_BM) : 0) * P.n_col_tiles;
+        P.n_tiles = mode_tiles(g->hs[j], g->tc) * P.n_col_tiles;
     }
     g->tcp.sched = static_cast<const uint32_t *>(gs->sched.p);
     g->tcp.cta_begin = static_cast<const int *>(gs->cta_begin.p);
     TcConfig c = g->tc;
-    c.grid = gs->grid;
+    c.grid = gs->grid * (c.pair ? 2 : 1);
     cudaError_t e = launch_tc_group(g->tcp, c, h0->stream);
     h0->launches++;
     if (e != cudaSuccess)

@@ -53,6 +53,7 @@ class MhcInfo(ctypes.Structure):
                 ("k_max", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("steps_pushed", ctypes.c_int64), ("pushes", ctypes.c_int64),
                 ("n_slots", ctypes.c_int64), ("tile_n", ctypes.c_int32), ("tile_k", ctypes.c_int32),
+                ("tile_pair", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("grid", ctypes.c_int32), ("e_exp", ctypes.c_int32),
                 ("ortho_err", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64)]
