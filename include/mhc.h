@@ -69,8 +69,13 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
 
 /* Flags for mhc_params.flags */
 #define MHC_FLAG_GKMA 0x1          /* accumulate Eq. 17 lag correlations (needs n_lags > 0) */
-#define MHC_FLAG_NO_GRAPH 0x2      /* launch kernels directly instead of replaying a CUDA graph */
-#define MHC_FLAG_PROFILE 0x4       /* time each projection launch with CUDA events (mhc_kernel_time) */
+#define MHC_FLAG_NO_GRAPH 0x2      /* launch kernels directly instead of replaying a CUDA graph.
+                                      By default each push after the first of a given K (the
+                                      autotuning push) replays a graph captured per (K, input
+                                      pointers, tile shape); host inputs are first copied to
+                                      fixed staging buffers.  Up to 32 graphs are cached. */
+#define MHC_FLAG_PROFILE 0x4       /* time each projection launch with CUDA events (mhc_kernel_time);
+                                      implies direct launches */
 
 typedef struct {
     int32_t device;      /* CUDA device ordinal */
@@ -103,7 +108,8 @@ typedef struct {
     int32_t e_exp;               /* power-of-two scale applied to E before the split */
     double ortho_err;            /* last basis check result, -1 if none */
     int64_t device_bytes;        /* device memory owned by the handle */
-    int64_t kernel_launches;     /* kernels launched by the handle so far */
+    int64_t kernel_launches;     /* kernels launched by the handle so far (graph nodes included) */
+    int64_t graph_replays;       /* pushes executed by replaying a captured CUDA graph */
 } mhc_info;
 
 /* Fill *p with defaults: device 0, default stream, k_max 256, no GKMA,
@@ -208,6 +214,10 @@ mhc_status mhc_check_orthonormality(mhc_handle *h, double tol, double *max_abs_e
 
 /* Counters and sizes. */
 mhc_status mhc_get_info(mhc_handle *h, mhc_info *info);
+
+/* Change the run-time flags MHC_FLAG_NO_GRAPH and MHC_FLAG_PROFILE of a handle (the other
+ * bits of `flags` must equal the handle's).  Takes effect at the next push. */
+mhc_status mhc_set_flags(mhc_handle *h, int32_t flags);
 
 /* With MHC_FLAG_PROFILE: total device time (ms) of the projection launches (the
  * tensor-core or FP32 GEMM with its fused epilogue) since the previous call, measured

@@ -105,7 +105,10 @@ __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
         double t = 0.0;
         for (int w = 0; w < PACK_THREADS / 32; ++w) t += s_j[w][c];
         a.Jtot[3 * k + c] = t;
-        if (a.Jring) a.Jring[((a.t0 + k) % a.R) * 3 + c] = t;
+        if (a.Jring) {
+            const long long t0 = a.t0_dev ? *a.t0_dev : a.t0;
+            a.Jring[((t0 + k) % a.R) * 3 + c] = t;
+        }
     }
     __syncthreads();
 

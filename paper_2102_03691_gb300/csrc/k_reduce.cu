@@ -55,7 +55,9 @@ constexpr int LC_BINS = 2;
 __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__restrict__ Jb,
                                                               const double *__restrict__ Jring,
                                                               int R, double *Csum, int K, int B,
-                                                              int L, long long t0) {
+                                                              int L, long long t0_host,
+                                                              const long long *t0_dev) {
+    const long long t0 = t0_dev ? *t0_dev : t0_host;
     extern __shared__ float sJ[];   // [K][LC_BINS][3] then the J window [K + LC_THREADS - 1][3]
     float *sW = sJ + K * LC_BINS * 3;
     const int b0 = blockIdx.y * LC_BINS;
@@ -203,6 +205,8 @@ __global__ void hnema_finalize_kernel(const double *hsum, int n, long long T_s, 
     if (kappa) kappa[q] = m * coef;
 }
 
+__global__ void advance_steps_kernel(long long *steps, int K) { *steps += K; }
+
 __global__ void lag_counts_kernel(long long T_s, int L, long long *count) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l < L) count[l] = T_s > l ? T_s - l : 0;
@@ -217,11 +221,11 @@ void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin
 }
 
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
-                     int L, long long t0, cudaStream_t s) {
+                     int L, long long t0, const long long *t0_dev, cudaStream_t s) {
     if (L <= 0 || K <= 0 || B <= 0) return;
     dim3 grid((L + LC_THREADS - 1) / LC_THREADS, (B + LC_BINS - 1) / LC_BINS);
     const size_t sm = ((size_t)K * LC_BINS * 3 + (size_t)(K + LC_THREADS - 1) * 3) * sizeof(float);
-    lag_corr_kernel<<<grid, LC_THREADS, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0);
+    lag_corr_kernel<<<grid, LC_THREADS, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0, t0_dev);
 }
 
 void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
@@ -235,6 +239,10 @@ void launch_hnema_finalize(const double *hsum, int B, long long T_s, double coef
                            double *kappa, cudaStream_t s) {
     const int n = B * 3;
     hnema_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(hsum, n, T_s, coef, mean, kappa);
+}
+
+void launch_advance_steps(long long *steps, int K, cudaStream_t s) {
+    advance_steps_kernel<<<1, 1, 0, s>>>(steps, K);
 }
 
 void launch_lag_counts(long long T_s, int L, long long *count, cudaStream_t s) {

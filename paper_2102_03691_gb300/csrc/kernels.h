@@ -30,7 +30,8 @@ struct PackArgs {
     const float *sqm;      // [N] sqrt(m_i)
     const float *isqm;     // [N] 1/sqrt(m_i)
     int N, K, D_ld, split, e_exp;
-    long long t0;          // global index of the block's first step
+    long long t0;          // global index of the block's first step (if t0_dev is null)
+    const long long *t0_dev;   // device step counter read at run time (graph replay)
     void *Bt_hi, *Bt_lo;   // [rows][D_ld] 16-bit (split != FP32)
     float *Bt32;           // [rows][D_ld] (split == FP32)
     float *col_scale;      // [4K] 2^-(s_row + e_exp): undoes both power-of-two scales
@@ -117,7 +118,9 @@ void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin
                        float *Jb, double *hsum, const double *Jtot, double *Jsum, cudaStream_t s);
 // Csum[b][mu][nu][l] += sum_k Jb[k][b][mu] J(t0+k-l)^nu over t0+k-l >= 0.
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
-                     int L, long long t0, cudaStream_t s);
+                     int L, long long t0, const long long *t0_dev, cudaStream_t s);
+// *steps += K (one thread; last kernel of a push)
+void launch_advance_steps(long long *steps, int K, cudaStream_t s);
 // kappa_tau[r][l] (r = b*9+mu*3+nu) and window averages kappa_w[r], FP64.
 void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
                      double tau_lo, double tau_hi, double dt, double *kappa_tau,

@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <queue>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -68,6 +69,9 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+struct mhc_handle;
+using Handle = mhc_handle;
+
 struct mhc_handle {
     mhc_params prm{};
     cudaStream_t stream = nullptr;
@@ -96,6 +100,18 @@ struct mhc_handle {
     // device buffers
     std::map<std::string, DevBuf> buf;
     int *status = nullptr;
+
+    // CUDA graphs of whole pushes, keyed by (K, v, W, tile shape); replayable because the
+    // kernels read the block's first step from a device counter
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        uint64_t last_use = 0;
+        int64_t nodes = 0;
+    };
+    std::map<std::tuple<int, const void *, const void *, int>, GraphEntry> graphs;
+    uint64_t graph_clock = 0;
+    int64_t graph_replays = 0;
+    cudaStream_t cap_stream = nullptr;
 
     // optional CUDA-event timing of the projection kernel (MHC_FLAG_PROFILE)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
@@ -181,6 +197,12 @@ void dev_free(mhc_handle *h, const char *name) {
 
 bool is_tc(const mhc_handle *h) { return h->split != SPLIT_FP32; }
 
+void drop_graphs(mhc_handle *h) {
+    for (auto &kv : h->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
+}
+
 mhc_status check_device_status(mhc_handle *h) {
     int st = 0;
     MHC_CUDA(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -198,6 +220,7 @@ mhc_status reset_accumulators(mhc_handle *h) {
     mhc_status s;
     if ((s = dev_alloc(h, "hsum", sizeof(double) * B * 3)) != MHC_OK) return s;
     if ((s = dev_alloc(h, "Jsum", sizeof(double) * 3)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "steps_dev", sizeof(long long))) != MHC_OK) return s;
     if (h->prm.flags & MHC_FLAG_GKMA) {
         if ((s = dev_alloc(h, "Csum", sizeof(double) * B * 9 * L)) != MHC_OK) return s;
         if ((s = dev_alloc(h, "Jring", sizeof(double) * h->R_ring * 3)) != MHC_OK) return s;
@@ -256,6 +279,8 @@ int sched_units(const mhc_handle *h, const TcConfig &c) {
 // epilogue, gather+split E into the stored order and set up the tensor maps.
 mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_t B) {
     if (B < 1) return fail(h, MHC_ERR_INVALID_ARG, "number of bins must be >= 1");
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
     for (int b : bin_of_mode)
         if (b < -1 || b >= B) return fail(h, MHC_ERR_INVALID_ARG, "bin id %d outside [-1, %d)", b, B);
     h->B = B;
@@ -441,6 +466,7 @@ mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
     a.split = h->split;
     a.e_exp = h->e_exp;
     a.t0 = h->steps;
+    a.t0_dev = dptr<long long>(h, "steps_dev");
     a.Bt_hi = dptr<void>(h, "Bt_hi");
     a.Bt_lo = dptr<void>(h, "Bt_lo");
     a.Bt32 = dptr<float>(h, "Bt32");
@@ -454,20 +480,86 @@ mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
     return MHC_OK;
 }
 
-mhc_status finish_block(mhc_handle *h, int K) {
+// Kernels that close a push: bin finish + HNEMA sums, GKMA lag correlation, step counter.
+mhc_status finish_kernels(mhc_handle *h, int K) {
     launch_bin_finish(dptr<float>(h, "partials"), (int)h->n_slots, dptr<int>(h, "slot_begin"), h->B,
                       K, dptr<float>(h, "Jb"), dptr<double>(h, "hsum"), dptr<double>(h, "Jtot"),
                       dptr<double>(h, "Jsum"), h->stream);
     h->launches++;
     if (h->prm.flags & MHC_FLAG_GKMA) {
         launch_lag_corr(dptr<float>(h, "Jb"), dptr<double>(h, "Jring"), h->R_ring,
-                        dptr<double>(h, "Csum"), K, h->B, h->prm.n_lags, h->steps, h->stream);
+                        dptr<double>(h, "Csum"), K, h->B, h->prm.n_lags, h->steps,
+                        dptr<long long>(h, "steps_dev"), h->stream);
         h->launches++;
     }
+    launch_advance_steps(dptr<long long>(h, "steps_dev"), K, h->stream);
+    h->launches++;
     MHC_CUDA(h, cudaGetLastError());
+    return MHC_OK;
+}
+
+void count_push(mhc_handle *h, int K) {
     h->steps += K;
     h->pushes++;
     h->K_last = K;
+}
+
+mhc_status finish_block(mhc_handle *h, int K) {
+    mhc_status s = finish_kernels(h, K);
+    if (s == MHC_OK) count_push(h, K);
+    return s;
+}
+
+int config_index(const mhc_handle *h) {
+    for (int q = 0; q < TC_NUM_CONFIGS; ++q)
+        if (TC_CONFIGS[q].bn == h->tc.bn && TC_CONFIGS[q].bk == h->tc.bk &&
+            TC_CONFIGS[q].stages == h->tc.stages && TC_CONFIGS[q].pair == h->tc.pair)
+            return q;
+    return -1;
+}
+
+// Capture pack -> projection -> finish of one push into a graph (on a private stream) and
+// replay it on the handle's stream.  Inputs must already be in device memory.
+mhc_status push_graph(mhc_handle *h, const float *v, const float *W, int K) {
+    auto key = std::make_tuple(K, (const void *)v, (const void *)W, is_tc(h) ? config_index(h) : -1);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        if (h->graphs.size() >= 32) {   // evict the least recently used graph
+            auto lru = h->graphs.begin();
+            for (auto g = h->graphs.begin(); g != h->graphs.end(); ++g)
+                if (g->second.last_use < lru->second.last_use) lru = g;
+            cudaGraphExecDestroy(lru->second.exec);
+            h->graphs.erase(lru);
+        }
+        if (!h->cap_stream) MHC_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = h->stream;
+        const int64_t launches0 = h->launches;
+        MHC_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        h->stream = h->cap_stream;
+        mhc_status s = pack_block(h, v, W, K);
+        if (s == MHC_OK) s = run_projection(h, K);
+        if (s == MHC_OK) s = finish_kernels(h, K);
+        h->stream = user;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (s != MHC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(h, MHC_ERR_CUDA, "stream capture of a push failed: %s", cudaGetErrorString(e));
+        Handle::GraphEntry ge;
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(h, MHC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        ge.nodes = h->launches - launches0;
+        h->launches = launches0;
+        it = h->graphs.emplace(key, ge).first;
+    }
+    it->second.last_use = ++h->graph_clock;
+    MHC_CUDA(h, cudaGraphLaunch(it->second.exec, h->stream));
+    h->launches += it->second.nodes;
+    h->graph_replays++;
+    count_push(h, K);
     return MHC_OK;
 }
 
@@ -579,6 +671,8 @@ void mhc_destroy(mhc_handle *h) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
+    drop_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (auto &kv : h->buf)
         if (kv.second.p) cudaFree(kv.second.p);
     if (h->status) cudaFree(h->status);
@@ -604,6 +698,7 @@ mhc_status mhc_set_modes(mhc_handle *h, int64_t n_atoms, int64_t n_modes, const 
             return fail(h, MHC_ERR_INVALID_ARG, "mass of atom %lld must be positive", (long long)i);
     MHC_CUDA(h, cudaSetDevice(h->prm.device));
     MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
     h->modes_ready = h->bins_ready = false;
     h->N = n_atoms;
     h->D = D;
@@ -743,6 +838,11 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     MHC_CUDA(h, cudaSetDevice(h->prm.device));
     mhc_status s;
     if ((s = stage_inputs(h, v, W, K, where)) != MHC_OK) return s;
+    const bool tuned = !is_tc(h) || h->prm.tile_config != 0 || h->tuned.count(K);
+    if (tuned && !(h->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE))) {
+        if (is_tc(h) && h->prm.tile_config == 0 && (s = set_tc_config(h, h->tuned[K])) != MHC_OK) return s;
+        return push_graph(h, v, W, K);
+    }
     if ((s = pack_block(h, v, W, K)) != MHC_OK) return s;
     if (is_tc(h) && h->prm.tile_config == 0) {
         auto it = h->tuned.find(K);
@@ -877,6 +977,16 @@ mhc_status mhc_get_info(mhc_handle *h, mhc_info *info) {
     for (auto &kv : h->buf) bytes += (int64_t)kv.second.bytes;
     info->device_bytes = bytes;
     info->kernel_launches = h->launches;
+    info->graph_replays = h->graph_replays;
+    return MHC_OK;
+}
+
+mhc_status mhc_set_flags(mhc_handle *h, int32_t flags) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    const int32_t mutable_bits = MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE;
+    if ((flags & ~mutable_bits) != (h->prm.flags & ~mutable_bits))
+        return fail(h, MHC_ERR_INVALID_ARG, "only MHC_FLAG_NO_GRAPH and MHC_FLAG_PROFILE can change");
+    h->prm.flags = flags;
     return MHC_OK;
 }
 
@@ -968,6 +1078,8 @@ mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes) {
     }
     h->steps = hd->steps;
     h->K_last = 0;
+    const long long st = hd->steps;
+    MHC_CUDA(h, cudaMemcpy(dptr<long long>(h, "steps_dev"), &st, sizeof st, cudaMemcpyHostToDevice));
     return MHC_OK;
 }
 

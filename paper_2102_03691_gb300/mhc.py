@@ -30,7 +30,8 @@ EXPORTS = (
     "mhc_default_params", "mhc_create", "mhc_destroy", "mhc_last_error", "mhc_status_string",
     "mhc_set_modes", "mhc_set_bins_uniform", "mhc_set_bin_ids", "mhc_push", "mhc_sync",
     "mhc_read_binned_current", "mhc_read_total_current", "mhc_read_hnema", "mhc_read_corr",
-    "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_kernel_time",
+    "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_set_flags",
+    "mhc_kernel_time",
     "mhc_reset",
     "mhc_state_size", "mhc_get_state", "mhc_set_state", "mhc_group_create",
     "mhc_group_destroy", "mhc_group_push", "mhc_binned_current_noalloc",
@@ -56,7 +57,7 @@ class MhcInfo(ctypes.Structure):
                 ("tile_pair", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("grid", ctypes.c_int32), ("e_exp", ctypes.c_int32),
                 ("ortho_err", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64)]
 
 
 class MhcError(RuntimeError):
@@ -100,6 +101,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_check_orthonormality.argtypes = [vp, dbl, ctypes.POINTER(dbl)]
     L.mhc_get_info.argtypes = [vp, ctypes.POINTER(MhcInfo)]
     L.mhc_kernel_time.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
+    L.mhc_set_flags.argtypes = [vp, i32]
     L.mhc_reset.argtypes = [vp]
     L.mhc_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.mhc_get_state.argtypes = [vp, vp, ctypes.c_size_t]
@@ -375,6 +377,11 @@ class ModalHeatCurrent:
         i = MhcInfo()
         self._check(self._L.mhc_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in MhcInfo._fields_}
+
+    def set_flags(self, flags: int):
+        """Change the run-time flags (FLAG_NO_GRAPH, FLAG_PROFILE) of the handle."""
+        self._check(self._L.mhc_set_flags(self._h, flags))
+        self.params.flags = flags
 
     def kernel_time(self):
         """(total ms, launches) of the projection kernel since the last call (FLAG_PROFILE)."""

@@ -124,6 +124,40 @@ def test_layouts_dtypes_and_memory_spaces_agree_bitwise(precision):
     assert np.all(series_rel_err(e, a) <= 1e-5)
 
 
+def test_graph_replay_matches_direct_launches():
+    # pushes after the first of each K replay a captured CUDA graph; device inputs from
+    # two buffers and host inputs through the staging copy, GKMA on
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import FLAG_NO_GRAPH, ModalHeatCurrent
+    c = make_case(N=64, M=192, T=96, B=6, seed=108)
+    K, L = 16, 20
+    outs = []
+    for flags in (FLAG_NO_GRAPH, 0):
+        h = ModalHeatCurrent(precision="fp16x3", k_max=K, n_lags=L, flags=flags)
+        h.set_modes(c["E"], c["mass"], c["f"])
+        h.set_bins_uniform(0.0, 16.0, 6)
+        bufs = [(torch.from_numpy(np.ascontiguousarray(c["v"][t0:t0 + K])).cuda(),
+                 torch.from_numpy(np.ascontiguousarray(c["W"][t0:t0 + K])).cuda()) for t0 in (0, K)]
+        Jb = []
+        for i, t0 in enumerate(range(0, 96, K)):
+            if i % 3 == 2:   # host input
+                v, W = np.ascontiguousarray(c["v"][t0:t0 + K]), np.ascontiguousarray(c["W"][t0:t0 + K])
+            else:
+                v, W = bufs[i % 3]
+                v.copy_(torch.from_numpy(np.ascontiguousarray(c["v"][t0:t0 + K])))
+                W.copy_(torch.from_numpy(np.ascontiguousarray(c["W"][t0:t0 + K])))
+            h.push(v, W)
+            Jb.append(h.read_binned_current().copy())
+        C, cnt = h.read_corr()
+        outs.append((np.concatenate(Jb), C, h.info()["graph_replays"]))
+        h.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == 0 and outs[1][2] == 5
+    o = oracle_run(c, L=L)
+    assert np.all(series_rel_err(outs[1][0], o["Jb"]) <= REL_TOL)
+
+
 def test_deterministic_repeat():
     need_gpu()
     c = make_case(N=64, M=192, T=32, B=6, seed=104)
