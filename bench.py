@@ -165,14 +165,14 @@ def tc_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, precision: str):
+def profiled_traffic(workload: str, precision: str, tile: dict):
     """DRAM bytes per projection launch from a committed ncu summary, if it was
-    taken on the current kernel source."""
+    taken on the current kernel source with the tile shape in use."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         e = t[f"{workload}/{precision}"]
-        if e.get("source_hash") == tc_source_hash():
+        if e.get("source_hash") == tc_source_hash() and e.get("tile") == tile:
             return e
     except Exception:
         pass
@@ -364,6 +364,9 @@ def main():
     torch.cuda.synchronize()
     kms, kn = h.kernel_time()
     h.set_flags(0)
+    info = h.info()
+    tile = {"columns": info["tile_n"], "k_per_stage": info["tile_k"], "stages": info["stages"],
+            "cta_pair": bool(info["tile_pair"])}
 
     # ---- end to end through the API from pinned host memory
     for i in range(3):
@@ -409,7 +412,7 @@ def main():
     flops_launch = mult * 2.0 * M * D * 4 * K
     achieved = flops_launch * kn / (kms / 1e3) / 1e12 if kms > 0 else None
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    tr_e = profiled_traffic(args.workload, args.precision)
+    tr_e = profiled_traffic(args.workload, args.precision, tile)
     roofline = {"bound": "tensor", "kernel": "tc_modal_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
                 "traffic": tr_e["dram_bytes_per_launch"] if tr_e else None,
@@ -417,7 +420,8 @@ def main():
                                "step loop); fp16 has the same dense tensor rate",
                 "flops_per_launch": flops_launch,
                 "kernel_ms_per_launch": kms / kn if kn else None,
-                "tensor_pipe_active_pct": tr_e.get("tensor_pipe_active_pct") if tr_e else None}
+                "tensor_pipe_active_pct": tr_e.get("tensor_pipe_active_pct") if tr_e else None,
+                "tile": tile}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, args.cpu_seconds, seed)

@@ -76,6 +76,11 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
                                       fixed staging buffers.  Up to 32 graphs are cached. */
 #define MHC_FLAG_PROFILE 0x4       /* time each projection launch with CUDA events (mhc_kernel_time);
                                       implies direct launches */
+#define MHC_FLAG_TEST_STALL 0x8    /* fault injection for tests of the failure path: the tensor-core
+                                      kernel arms its first stage barrier 16 bytes short of what its
+                                      copies deliver, so its bounded waits (0.1 s with this flag)
+                                      give up and the next sync/read returns MHC_ERR_TIMEOUT; no
+                                      memory is touched out of bounds.  Implies direct launches. */
 
 typedef struct {
     int32_t device;      /* CUDA device ordinal */
@@ -215,8 +220,8 @@ mhc_status mhc_check_orthonormality(mhc_handle *h, double tol, double *max_abs_e
 /* Counters and sizes. */
 mhc_status mhc_get_info(mhc_handle *h, mhc_info *info);
 
-/* Change the run-time flags MHC_FLAG_NO_GRAPH and MHC_FLAG_PROFILE of a handle (the other
- * bits of `flags` must equal the handle's).  Takes effect at the next push. */
+/* Change the run-time flags MHC_FLAG_NO_GRAPH, MHC_FLAG_PROFILE and MHC_FLAG_TEST_STALL of a
+ * handle (the other bits of `flags` must equal the handle's).  Takes effect at the next push. */
 mhc_status mhc_set_flags(mhc_handle *h, int32_t flags);
 
 /* With MHC_FLAG_PROFILE: total device time (ms) of the projection launches (the
@@ -225,7 +230,8 @@ mhc_status mhc_set_flags(mhc_handle *h, int32_t flags);
  * Synchronises the stream; resets the totals. */
 mhc_status mhc_kernel_time(mhc_handle *h, double *ms, int64_t *launches);
 
-/* Zero the HNEMA and GKMA accumulators and the step counter (modes and bins stay). */
+/* Zero the HNEMA and GKMA accumulators, the step counter and the sticky device status
+ * (modes and bins stay). */
 mhc_status mhc_reset(mhc_handle *h);
 
 /*

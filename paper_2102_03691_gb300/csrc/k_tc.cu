@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
             tma_prefetch_desc(&p.prob[q].tmB_lo);
         }
         const uint64_t pol_b = l2_policy_evict_last();
-        const uint64_t pol_e = l2_policy_evict_first();
+        const uint64_t pol_e = l2_policy_evict_normal();   // E tiles are shared by the CTAs of other column tiles
         uint32_t issued_phase[STAGES];
         bool issued[STAGES];
         for (int s = 0; s < STAGES; ++s) issued[s] = false;
@@ -147,9 +147,10 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         while (ok && it.next(prob, mt, ct)) {
             const TcProblem &P = p.prob[prob];
             for (int kb = 0; kb < P.n_kb; ++kb) {
-                if (!mbar_wait(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
+                if (!mbar_wait(&empty[stage], phase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 uint8_t *sa = smem + stage * L::STAGE_BYTES;
-                mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES);
+                // test hook: 16 bytes more than the copies deliver keeps the barrier pending
+                mbar_arrive_expect_tx(&full[stage], L::STAGE_BYTES + (p.stall_inject && kb == 0 ? 16 : 0));
                 const int x = kb * BK;
                 tma_load_2d(sa, &P.tmA_hi, &full[stage], x, mt * TC_BM, pol_e);
                 tma_load_2d(sa + L::A_BYTES, &P.tmA_lo, &full[stage], x, mt * TC_BM, pol_e);
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
             if (issued[s]) {
                 const long long t0 = clock64();
                 while (!mbar_try_wait(&full[s], issued_phase[s]) &&
-                       clock64() - t0 < WAIT_LIMIT_CYCLES) {
+                       clock64() - t0 < p.wait_limit) {
                 }
             }
     } else if (warp == 1 && lane == 0) {
@@ -184,12 +185,12 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         while (ok && it.next(prob, mt, ct)) {
             const TcProblem &P = p.prob[prob];
             for (int kb0 = 0; ok && kb0 < P.n_kb; kb0 += CHUNK_KB) {
-                if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort)) { ok = false; break; }
+                if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * BN);
                 const int kb1 = min(kb0 + CHUNK_KB, P.n_kb);
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                    if (!mbar_wait(&full[stage], phase, abort, p.wait_limit)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a_hi = smem0 + stage * L::STAGE_BYTES;
                     const uint32_t a_lo = a_hi + L::A_BYTES;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         // Drain: all MMAs issued by this thread complete before TMEM is released.
         umma_commit(done_bar);
         const long long t0 = clock64();
-        while (!mbar_try_wait(done_bar, 0) && clock64() - t0 < WAIT_LIMIT_CYCLES) {
+        while (!mbar_try_wait(done_bar, 0) && clock64() - t0 < p.wait_limit) {
         }
     } else if (warp >= 4) {
         // ------------------------------------------------------------ promotion + epilogue
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
             for (int j = 0; j < 128; ++j) acc[j] = 0.f;
             // promotion of every chunk accumulator into FP32 registers
             for (int kb0 = 0; kb0 < P.n_kb; kb0 += CHUNK_KB) {
-                if (!mbar_wait(&acc_full[abuf], aphase, abort)) { ok = false; break; }
+                if (!mbar_wait(&acc_full[abuf], aphase, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(qw * 32) << 16) +
                                        (uint32_t)(abuf * BN + ch * 128);
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_cons
             tma_prefetch_desc(&p.prob[q].tmB_lo);
         }
         const uint64_t pol_b = l2_policy_evict_last();
-        const uint64_t pol_e = l2_policy_evict_first();
+        const uint64_t pol_e = l2_policy_evict_normal();   // E tiles are shared by the CTAs of other column tiles
         uint32_t issued_phase[STAGES];
         bool issued[STAGES];
         for (int s = 0; s < STAGES; ++s) issued[s] = false;
@@ -417,8 +418,9 @@ __global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_cons
             const int arow = mp * 2 * TC_BM + (int)rank * TC_BM;
             const int brow = ct * BN + (int)rank * (BN / 2);
             for (int kb = 0; kb < P.n_kb; ++kb) {
-                if (!mbar_wait(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
-                if (leader) mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES);
+                if (!mbar_wait(&empty[stage], phase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
+                if (leader)   // test hook as in the one-SM kernel
+                    mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES + (p.stall_inject && kb == 0 ? 16 : 0));
                 const uint32_t fb = mapa_shared(smem_u32(&full[stage]), 0);
                 uint8_t *sa = smem + stage * L::STAGE_BYTES;
                 const int x = kb * BK;
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_cons
                 if (issued[s]) {
                     const long long t0 = clock64();
                     while (!mbar_try_wait(&full[s], issued_phase[s]) &&
-                           clock64() - t0 < WAIT_LIMIT_CYCLES) {
+                           clock64() - t0 < p.wait_limit) {
                     }
                 }
     } else if (warp == 1 && lane == 0 && leader) {
@@ -455,12 +457,12 @@ __global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_cons
         while (ok && it.next(prob, mp, ct)) {
             const TcProblem &P = p.prob[prob];
             for (int kb0 = 0; ok && kb0 < P.n_kb; kb0 += CHUNK_KB) {
-                if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort)) { ok = false; break; }
+                if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * BN);
                 const int kb1 = min(kb0 + CHUNK_KB, P.n_kb);
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                    if (!mbar_wait(&full[stage], phase, abort, p.wait_limit)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a_hi = smem0 + stage * L::STAGE_BYTES;
                     const uint32_t a_lo = a_hi + L::A_BYTES;
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_cons
         }
         umma_commit_pair(done_bar, (uint16_t)0x1);
         const long long t0 = clock64();
-        while (!mbar_try_wait(done_bar, 0) && clock64() - t0 < WAIT_LIMIT_CYCLES) {
+        while (!mbar_try_wait(done_bar, 0) && clock64() - t0 < p.wait_limit) {
         }
     } else if (warp >= 4) {
         // ------------------------------------------------------------ promotion + epilogue (both)
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_cons
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0.f;
             for (int kb0 = 0; kb0 < P.n_kb; kb0 += CHUNK_KB) {
-                if (!mbar_wait(&acc_full[abuf], aphase, abort)) { ok = false; break; }
+                if (!mbar_wait(&acc_full[abuf], aphase, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(qw * 32) << 16) +
                                        (uint32_t)(abuf * BN + ch * 128);

@@ -83,6 +83,8 @@ struct TcParams {
     const uint32_t *sched;   // packed tile list (null: round-robin over prob[0])
     const int *cta_begin;    // [grid+1] offsets into sched
     int n_prob;              // problems in use (prob[0..n_prob-1])
+    long long wait_limit;    // SM cycles a barrier wait may take before the CTA gives up
+    int stall_inject;        // test hook: arm the first stage barrier 16 bytes short of done
     int *status;
     uint32_t idesc;
 };

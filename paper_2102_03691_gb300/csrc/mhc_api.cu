@@ -366,6 +366,7 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         h->tcp.cta_begin = nullptr;
         h->tcp.n_prob = 1;
         h->tcp.status = h->status;
+        h->tcp.wait_limit = 2000000000ll;
         h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, (c.pair ? 2 : 1) * TC_BM, (uint32_t)c.bn);
     }
     h->bins_ready = true;
@@ -404,6 +405,9 @@ mhc_status run_projection(mhc_handle *h, int K) {
     }
     TcConfig c = h->tc;
     TcProblem &P = h->tcp.prob[0];
+    const bool stall = (h->prm.flags & MHC_FLAG_TEST_STALL) != 0;
+    h->tcp.stall_inject = stall ? 1 : 0;
+    h->tcp.wait_limit = stall ? 200000000ll : 2000000000ll;   // 0.1 s when testing the timeout
     P.K = K;
     P.n_col_tiles = (int)((4 * K + c.bn - 1) / c.bn);
     P.n_tiles = mode_tiles(h, c) * P.n_col_tiles;
@@ -839,7 +843,7 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     mhc_status s;
     if ((s = stage_inputs(h, v, W, K, where)) != MHC_OK) return s;
     const bool tuned = !is_tc(h) || h->prm.tile_config != 0 || h->tuned.count(K);
-    if (tuned && !(h->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE))) {
+    if (tuned && !(h->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL))) {
         if (is_tc(h) && h->prm.tile_config == 0 && (s = set_tc_config(h, h->tuned[K])) != MHC_OK) return s;
         return push_graph(h, v, W, K);
     }
@@ -983,9 +987,9 @@ mhc_status mhc_get_info(mhc_handle *h, mhc_info *info) {
 
 mhc_status mhc_set_flags(mhc_handle *h, int32_t flags) {
     if (!h) return MHC_ERR_INVALID_ARG;
-    const int32_t mutable_bits = MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE;
+    const int32_t mutable_bits = MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL;
     if ((flags & ~mutable_bits) != (h->prm.flags & ~mutable_bits))
-        return fail(h, MHC_ERR_INVALID_ARG, "only MHC_FLAG_NO_GRAPH and MHC_FLAG_PROFILE can change");
+        return fail(h, MHC_ERR_INVALID_ARG, "only the NO_GRAPH, PROFILE and TEST_STALL flags can change");
     h->prm.flags = flags;
     return MHC_OK;
 }
@@ -1011,6 +1015,7 @@ mhc_status mhc_reset(mhc_handle *h) {
     if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "no bins");
     MHC_CUDA(h, cudaSetDevice(h->prm.device));
     mhc_status s = reset_accumulators(h);
+    if (s == MHC_OK) MHC_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
     if (s == MHC_OK) MHC_CUDA(h, cudaStreamSynchronize(h->stream));
     return s;
 }
@@ -1100,6 +1105,8 @@ mhc_status group_encode(mhc_group *g) {
         P.n_kb = (int)(h->D_ld / c.bk);
     }
     g->tcp.status = h0->status;
+    g->tcp.wait_limit = 2000000000ll;
+    g->tcp.stall_inject = 0;
     g->tcp.n_prob = (int)g->hs.size();
     g->tcp.idesc = idesc_f16(h0->split == SPLIT_BF16 ? 1u : 0u, (c.pair ? 2 : 1) * TC_BM, (uint32_t)c.bn);
     return MHC_OK;

@@ -23,7 +23,7 @@ PRECISIONS = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
 MEM_HOST, MEM_DEVICE = 0, 1
 F32, F64 = 0, 1
 DOF_MAJOR, MODE_MAJOR = 0, 1
-FLAG_GKMA, FLAG_NO_GRAPH, FLAG_PROFILE = 0x1, 0x2, 0x4
+FLAG_GKMA, FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_TEST_STALL = 0x1, 0x2, 0x4, 0x8
 
 # Every entry point declared in include/mhc.h.
 EXPORTS = (
@@ -378,8 +378,11 @@ class ModalHeatCurrent:
         self._check(self._L.mhc_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in MhcInfo._fields_}
 
-    def set_flags(self, flags: int):
-        """Change the run-time flags (FLAG_NO_GRAPH, FLAG_PROFILE) of the handle."""
+    def set_flags(self, runtime_flags: int):
+        """Set the run-time flags (FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_TEST_STALL); the other
+        bits are kept."""
+        rt = FLAG_NO_GRAPH | FLAG_PROFILE | FLAG_TEST_STALL
+        flags = (self.params.flags & ~rt) | (runtime_flags & rt)
         self._check(self._L.mhc_set_flags(self._h, flags))
         self.params.flags = flags
 
