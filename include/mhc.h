@@ -257,9 +257,17 @@ mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes);
  */
 mhc_status mhc_group_create(mhc_group **g, mhc_handle *const *handles, int32_t n);
 void mhc_group_destroy(mhc_group *g);
-/* v[j], W[j] are the inputs of handle j with K[j] steps (same rules as mhc_push). */
+/* v[j], W[j] are the inputs of handle j with K[j] steps (same rules as mhc_push).  After the
+ * first (autotuning) push, group pushes replay a CUDA graph captured per (K vector, input
+ * pointers, tile shape) unless the first handle has MHC_FLAG_NO_GRAPH, MHC_FLAG_PROFILE or
+ * MHC_FLAG_TEST_STALL set; with MHC_FLAG_PROFILE on the first handle, mhc_kernel_time of that
+ * handle times the grouped tensor-core launches. */
 mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *const *W,
                           const int32_t *K, int32_t where);
+/* HNEMA read-out (as mhc_read_hnema) of every member in one call: kappa and mean_J receive
+ * the members' [B_j][3] arrays one after another (either may be NULL); host outputs cost one
+ * synchronisation for the whole group. */
+mhc_status mhc_group_read_hnema(mhc_group *g, double *kappa, double *mean_J, int32_t where);
 
 /*
  * No-allocation variant of one block's binned modal current.  The paper has no

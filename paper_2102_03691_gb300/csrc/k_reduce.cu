@@ -205,6 +205,16 @@ __global__ void hnema_finalize_kernel(const double *hsum, int n, long long T_s, 
     if (kappa) kappa[q] = m * coef;
 }
 
+__global__ void hnema_finalize_group_kernel(const HnemaGroupArgs a, double *mean, double *kappa) {
+    const int j = blockIdx.y;
+    if (j >= a.n) return;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < a.nb[j]; q += gridDim.x * blockDim.x) {
+        const double m = a.T_s[j] > 0 ? a.hsum[j][q] / (double)a.T_s[j] : 0.0;
+        if (mean) mean[a.off[j] + q] = m;
+        if (kappa) kappa[a.off[j] + q] = m * a.coef[j];
+    }
+}
+
 __global__ void advance_steps_kernel(long long *steps, int K) { *steps += K; }
 
 __global__ void lag_counts_kernel(long long T_s, int L, long long *count) {
@@ -239,6 +249,11 @@ void launch_hnema_finalize(const double *hsum, int B, long long T_s, double coef
                            double *kappa, cudaStream_t s) {
     const int n = B * 3;
     hnema_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(hsum, n, T_s, coef, mean, kappa);
+}
+
+void launch_hnema_finalize_group(const HnemaGroupArgs &a, double *mean, double *kappa,
+                                 cudaStream_t s) {
+    hnema_finalize_group_kernel<<<dim3(4, a.n), 128, 0, s>>>(a, mean, kappa);
 }
 
 void launch_advance_steps(long long *steps, int K, cudaStream_t s) {

@@ -130,6 +130,16 @@ void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coe
 // mean[b][a] = hsum/T_s; kappa[b][a] = mean * coef
 void launch_hnema_finalize(const double *hsum, int B, long long T_s, double coef, double *mean,
                            double *kappa, cudaStream_t s);
+// HNEMA read-out of up to TC_MAX_GROUP systems in one launch, written one after another.
+struct HnemaGroupArgs {
+    const double *hsum[TC_MAX_GROUP];
+    long long T_s[TC_MAX_GROUP];
+    double coef[TC_MAX_GROUP];
+    int nb[TC_MAX_GROUP];     // B_j * 3
+    int off[TC_MAX_GROUP];    // offset of system j in the outputs
+    int n;
+};
+void launch_hnema_finalize_group(const HnemaGroupArgs &a, double *mean, double *kappa, cudaStream_t s);
 // count[l] = max(T_s - l, 0)
 void launch_lag_counts(long long T_s, int L, long long *count, cudaStream_t s);
 

@@ -134,6 +134,17 @@ struct mhc_group {
     bool tuned = false;
     TcParams<TC_MAX_GROUP> tcp{};
     std::map<std::pair<int, std::vector<int>>, GroupSchedule> sched_cache;   // (bn, Ks)
+    // graphs of whole group pushes keyed by (Ks, input pointers, tile shape)
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        uint64_t last_use = 0;
+        int64_t nodes = 0;
+    };
+    std::map<std::tuple<std::vector<int>, std::vector<const void *>, int>, GraphEntry> graphs;
+    uint64_t graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<cudaStream_t> branch;      // side streams: per-system kernels as parallel graph branches
+    std::vector<cudaEvent_t> branch_ev;    // fork/join events used during capture
 };
 
 namespace {
@@ -1265,11 +1276,54 @@ mhc_status mhc_group_create(mhc_group **out, mhc_handle *const *handles, int32_t
 void mhc_group_destroy(mhc_group *g) {
     if (!g) return;
     cudaStreamSynchronize(g->hs[0]->stream);
+    for (auto &kv : g->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    for (cudaStream_t b : g->branch) cudaStreamDestroy(b);
+    for (cudaEvent_t e : g->branch_ev) cudaEventDestroy(e);
     for (auto &kv : g->sched_cache) {
         if (kv.second.sched.p) cudaFree(kv.second.sched.p);
         if (kv.second.cta_begin.p) cudaFree(kv.second.cta_begin.p);
     }
     delete g;
+}
+
+mhc_status mhc_group_read_hnema(mhc_group *g, double *kappa, double *mean_J, int32_t where) {
+    if (!g) return MHC_ERR_INVALID_ARG;
+    mhc_handle *h0 = g->hs[0];
+    if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE) return fail(h0, MHC_ERR_INVALID_ARG, "where");
+    MHC_CUDA(h0, cudaSetDevice(h0->prm.device));
+    HnemaGroupArgs a{};
+    a.n = (int)g->hs.size();
+    int total = 0;
+    for (int j = 0; j < a.n; ++j) {
+        mhc_handle *h = g->hs[j];
+        const double fe = std::sqrt(h->prm.F_e[0] * h->prm.F_e[0] + h->prm.F_e[1] * h->prm.F_e[1] +
+                                    h->prm.F_e[2] * h->prm.F_e[2]);
+        a.hsum[j] = dptr<double>(h, "hsum");
+        a.T_s[j] = h->steps;
+        a.coef[j] = fe > 0 ? WMK_PER_EV_PS_A_K / (h->prm.T_K * h->prm.V_A3 * fe) : 0.0;
+        a.nb[j] = h->B * 3;
+        a.off[j] = total;
+        total += h->B * 3;
+    }
+    double *dk = kappa, *dm = mean_J;
+    if (where == MHC_MEM_HOST) {   // one staging buffer, one copy, one synchronisation
+        mhc_status s;
+        if ((s = dev_alloc(h0, "group_hn", sizeof(double) * 2 * total, false)) != MHC_OK) return s;
+        dm = mean_J ? dptr<double>(h0, "group_hn") : nullptr;
+        dk = kappa ? dptr<double>(h0, "group_hn") + total : nullptr;
+    }
+    launch_hnema_finalize_group(a, dm, dk, h0->stream);
+    h0->launches++;
+    MHC_CUDA(h0, cudaGetLastError());
+    if (where == MHC_MEM_HOST) {
+        if (kappa) MHC_CUDA(h0, cudaMemcpyAsync(kappa, dk, sizeof(double) * total, cudaMemcpyDeviceToHost, h0->stream));
+        if (mean_J) MHC_CUDA(h0, cudaMemcpyAsync(mean_J, dm, sizeof(double) * total, cudaMemcpyDeviceToHost, h0->stream));
+        MHC_CUDA(h0, cudaStreamSynchronize(h0->stream));
+        return check_device_status(h0);
+    }
+    return MHC_OK;
 }
 
 mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *const *W,
@@ -1288,15 +1342,112 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
     }
     MHC_CUDA(h0, cudaSetDevice(h0->prm.device));
     mhc_status s;
-    for (size_t j = 0; j < n; ++j) {
-        const float *vj = v[j], *wj = W[j];
-        if ((s = stage_inputs(g->hs[j], vj, wj, Ks[j], where)) != MHC_OK) return s;
-        if ((s = pack_block(g->hs[j], vj, wj, Ks[j])) != MHC_OK) return s;
+    std::vector<const float *> vs(v, v + n), ws(W, W + n);
+    for (size_t j = 0; j < n; ++j)
+        if ((s = stage_inputs(g->hs[j], vs[j], ws[j], Ks[j], where)) != MHC_OK) return s;
+    const bool tuned = g->tuned || h0->prm.tile_config != 0;
+    const bool profile = (h0->prm.flags & MHC_FLAG_PROFILE) != 0;
+    if (tuned && !(h0->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL))) {
+        // replay (or capture once) the whole group push as one CUDA graph
+        std::vector<const void *> ptrs;
+        for (size_t j = 0; j < n; ++j) {
+            ptrs.push_back(vs[j]);
+            ptrs.push_back(ws[j]);
+        }
+        int cfg = -1;
+        for (int q = 0; q < TC_NUM_CONFIGS; ++q)
+            if (TC_CONFIGS[q].bn == g->tc.bn && TC_CONFIGS[q].bk == g->tc.bk &&
+                TC_CONFIGS[q].stages == g->tc.stages && TC_CONFIGS[q].pair == g->tc.pair)
+                cfg = q;
+        auto key = std::make_tuple(Ks, ptrs, cfg);
+        auto it = g->graphs.find(key);
+        if (it == g->graphs.end()) {
+            if (g->graphs.size() >= 16) {
+                auto lru = g->graphs.begin();
+                for (auto q = g->graphs.begin(); q != g->graphs.end(); ++q)
+                    if (q->second.last_use < lru->second.last_use) lru = q;
+                cudaGraphExecDestroy(lru->second.exec);
+                g->graphs.erase(lru);
+            }
+            GroupSchedule *gs = nullptr;   // build (and upload) the schedule outside the capture
+            if ((s = group_schedule(g, Ks, gs)) != MHC_OK) return s;
+            if (!g->cap_stream) MHC_CUDA(h0, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+            std::vector<int64_t> l0(n);
+            for (size_t j = 0; j < n; ++j) l0[j] = g->hs[j]->launches;
+            if (g->branch.empty()) {
+                g->branch.resize(n);
+                g->branch_ev.resize(2 * n + 2);
+                for (size_t j = 0; j < n; ++j)
+                    MHC_CUDA(h0, cudaStreamCreateWithFlags(&g->branch[j], cudaStreamNonBlocking));
+                for (auto &e : g->branch_ev)
+                    MHC_CUDA(h0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            }
+            cudaStream_t user = h0->stream;
+            // graph: fork -> per-system packs on parallel branches -> join -> grouped launch
+            //        -> fork -> per-system finish kernels on parallel branches -> join
+            auto fork_join = [&](int ev_base, auto &&body) -> mhc_status {
+                MHC_CUDA(h0, cudaEventRecord(g->branch_ev[ev_base], g->cap_stream));
+                mhc_status r = MHC_OK;
+                for (size_t j = 0; j < n && r == MHC_OK; ++j) {
+                    MHC_CUDA(h0, cudaStreamWaitEvent(g->branch[j], g->branch_ev[ev_base], 0));
+                    g->hs[j]->stream = g->branch[j];
+                    r = body(j);
+                    g->hs[j]->stream = g->cap_stream;
+                    MHC_CUDA(h0, cudaEventRecord(g->branch_ev[ev_base + 1 + j], g->branch[j]));
+                    MHC_CUDA(h0, cudaStreamWaitEvent(g->cap_stream, g->branch_ev[ev_base + 1 + j], 0));
+                }
+                return r;
+            };
+            MHC_CUDA(h0, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (size_t j = 0; j < n; ++j) g->hs[j]->stream = g->cap_stream;
+            s = fork_join(0, [&](size_t j) { return pack_block(g->hs[j], vs[j], ws[j], Ks[j]); });
+            if (s == MHC_OK) s = group_launch(g, Ks);
+            if (s == MHC_OK)
+                s = fork_join(0, [&](size_t j) { return finish_kernels(g->hs[j], Ks[j]); });
+            for (size_t j = 0; j < n; ++j) g->hs[j]->stream = user;
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+            if (s != MHC_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s;
+            }
+            if (e != cudaSuccess) return fail(h0, MHC_ERR_CUDA, "capture of a group push failed: %s", cudaGetErrorString(e));
+            mhc_group::GraphEntry ge;
+            e = cudaGraphInstantiate(&ge.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(h0, MHC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+            for (size_t j = 0; j < n; ++j) {
+                ge.nodes += g->hs[j]->launches - l0[j];
+                g->hs[j]->launches = l0[j];
+            }
+            it = g->graphs.emplace(key, ge).first;
+        }
+        it->second.last_use = ++g->graph_clock;
+        MHC_CUDA(h0, cudaGraphLaunch(it->second.exec, h0->stream));
+        h0->launches += it->second.nodes;
+        h0->graph_replays++;
+        for (size_t j = 0; j < n; ++j) count_push(g->hs[j], Ks[j]);
+        return MHC_OK;
     }
+    for (size_t j = 0; j < n; ++j)
+        if ((s = pack_block(g->hs[j], vs[j], ws[j], Ks[j])) != MHC_OK) return s;
     if (!g->tuned && h0->prm.tile_config == 0) {
         if ((s = group_autotune(g, Ks)) != MHC_OK) return s;
     }
+    cudaEvent_t ev1 = nullptr;
+    if (profile) {   // time the grouped launch with the first handle's event pairs
+        if (h0->prof_used == h0->prof_events.size()) {
+            cudaEvent_t a0, a1;
+            MHC_CUDA(h0, cudaEventCreate(&a0));
+            MHC_CUDA(h0, cudaEventCreate(&a1));
+            h0->prof_events.emplace_back(a0, a1);
+        }
+        MHC_CUDA(h0, cudaEventRecord(h0->prof_events[h0->prof_used].first, h0->stream));
+        ev1 = h0->prof_events[h0->prof_used].second;
+        ++h0->prof_used;
+    }
     if ((s = group_launch(g, Ks)) != MHC_OK) return s;
+    if (ev1) MHC_CUDA(h0, cudaEventRecord(ev1, h0->stream));
     for (size_t j = 0; j < n; ++j)
         if ((s = finish_block(g->hs[j], Ks[j])) != MHC_OK) return s;
     return MHC_OK;

@@ -34,7 +34,7 @@ EXPORTS = (
     "mhc_kernel_time",
     "mhc_reset",
     "mhc_state_size", "mhc_get_state", "mhc_set_state", "mhc_group_create",
-    "mhc_group_destroy", "mhc_group_push", "mhc_binned_current_noalloc",
+    "mhc_group_destroy", "mhc_group_push", "mhc_group_read_hnema", "mhc_binned_current_noalloc",
 )
 
 
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_group_destroy.restype = None
     L.mhc_group_push.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                  ctypes.POINTER(i32), i32]
+    L.mhc_group_read_hnema.argtypes = [vp, vp, vp, i32]
     L.mhc_binned_current_noalloc.argtypes = [i32, i32, vp, i64, vp, i32, vp, vp, vp, i32, vp, vp,
                                              i32, vp]
     for name in EXPORTS:
@@ -155,6 +156,19 @@ class ModalHeatCurrentGroup:
             raise MhcError(st, self._L.mhc_last_error(self.members[0]._h).decode())
         for m, k in zip(self.members, ks):
             m._lastK = k
+
+    def read_hnema(self, kappa=None, mean=None):
+        """All members' HNEMA kappa (and mean current) in one call: numpy arrays (host, one
+        synchronisation) or CUDA tensors (device, asynchronous), concatenated [sum B_j * 3]."""
+        n = sum(m.B * 3 for m in self.members)
+        if kappa is None:
+            kappa = np.empty(n)
+        pk, where, kk = _ptr(kappa, np.float64)
+        pm = None if mean is None else _ptr(mean, np.float64)[0]
+        st = self._L.mhc_group_read_hnema(self._g, pk, pm, where)
+        if st != MHC_OK:
+            raise MhcError(st, self._L.mhc_last_error(self.members[0]._h).decode())
+        return kk
 
     def close(self):
         if getattr(self, "_g", None):

@@ -103,3 +103,33 @@ def test_cnt_batch_16_systems_full_size_sampled():
         empty = np.abs(o["Jb"]).max(axis=0) == 0
         assert np.all(Jb[:, empty] == 0)
     grp.close()
+
+
+def test_group_graph_replay_matches_direct():
+    # group pushes after the first replay one captured CUDA graph covering every system
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import FLAG_NO_GRAPH, ModalHeatCurrentGroup
+    sizes = [160, 80, 240]
+    K, L = 32, 8
+    systems = [system(N, 500 + j) for j, N in enumerate(sizes)]
+    blocks = [[s["tr"].next_block(K) for _ in range(4)] for s in systems]
+    results = []
+    for flags in (FLAG_NO_GRAPH, 0):
+        hs = [handle(s, K, L) for s in systems]
+        hs[0].set_flags(flags)
+        grp = ModalHeatCurrentGroup(hs)
+        out = []
+        for step in range(4):
+            grp.push([bl[step][0] for bl in blocks], [bl[step][1] for bl in blocks])
+            out.append([h.read_binned_current().copy() for h in hs])
+        kap_all = grp.read_hnema()
+        kap_one = np.concatenate([h.read_hnema()[1].ravel() for h in hs])
+        np.testing.assert_array_equal(kap_all, kap_one)
+        results.append((out, [h.read_corr()[0] for h in hs], hs[0].info()["graph_replays"]))
+        grp.close()
+    for a, b in zip(results[0][0], results[1][0]):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+    for x, y in zip(results[0][1], results[1][1]):
+        np.testing.assert_array_equal(x, y)
+    assert results[0][2] == 0 and results[1][2] == 3
