@@ -3,8 +3,9 @@
 Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of bench.py
 may import this package.  The CUDA library never calls it and shares no code
 with it.  ``mhc_oracle.c`` holds the plain FP64 loops (Eqs. 10, 13, 16, 17,
-19 and frequency binning); ``brute.py`` restates the same definitions with
-per-atom 3-vectors in scalar Python for tiny systems.
+19 and frequency binning; the SHC correlation and spectrum of Eqs. 20-23);
+``brute.py`` restates the same definitions with per-atom 3-vectors in scalar
+Python for tiny systems.
 
 This module compiles ``mhc_oracle.c`` with gcc on first use (or through
 ``build()``) and wraps it with ctypes and numpy.
@@ -59,6 +60,8 @@ def lib():
             L.orc_kappa_window.argtypes = [_i32, _i32, _p, _dbl, _dbl, _dbl, _p]
             L.orc_kappa_window.restype = _i32
             L.orc_hnema.argtypes = [_i64, _i32, _p, _dbl, _dbl, _p, _p, _p]
+            L.orc_shc_corr.argtypes = [_i64, _i64, _p, _p, _i32, _p, _p]
+            L.orc_shc_kappa.argtypes = [_i32, _p, _p, _dbl, _dbl, _dbl, _dbl, _i32, _i32, _p, _p]
             L.orc_orthonormality.argtypes = [_i64, _i64, _p]
             L.orc_orthonormality.restype = _dbl
             _lib = L
@@ -157,3 +160,27 @@ def orthonormality(E: np.ndarray) -> float:
     Et = np.ascontiguousarray(np.asarray(E, dtype=np.float64).T)
     M, D = Et.shape
     return float(lib().orc_orthonormality(D, M, _ptr(Et)))
+
+
+def shc_corr(v, W, nc: int):
+    """SHC correlation sums Ksum [9][nc] (pair 3a+b) and origin counts [nc] (Eq. 20-21)."""
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    T, N, _ = v.shape
+    W = np.ascontiguousarray(W, dtype=np.float32).reshape(T, N, 9)
+    K = np.empty((9, nc))
+    cnt = np.empty(nc, dtype=np.int64)
+    lib().orc_shc_corr(N, T, _ptr(v), _ptr(W), nc, _ptr(K), _ptr(cnt))
+    return K, cnt
+
+
+def shc_kappa(Ksum, count, dt_ps: float, T_K: float, V_A3: float, Fe: float, f_THz,
+              window: int = 0):
+    """SHC spectral conductivity kappa [9][n_freq] in W/(m K THz) (Eq. 22-23)."""
+    Ksum = np.ascontiguousarray(Ksum, dtype=np.float64)
+    nc = Ksum.shape[1]
+    count = np.ascontiguousarray(count, dtype=np.int64)
+    f = np.ascontiguousarray(f_THz, dtype=np.float64)
+    out = np.empty((9, f.shape[0]))
+    lib().orc_shc_kappa(nc, _ptr(Ksum), _ptr(count), dt_ps, T_K, V_A3, Fe, window, f.shape[0],
+                        _ptr(f), _ptr(out))
+    return out

@@ -86,3 +86,25 @@ def run(E, mass, v, W, bin_of_mode, B, L=0):
                         C[b][mu][nu][l] = sum(pairs) / len(pairs) if pairs else 0.0
         out["C"] = C
     return out
+
+
+def shc(v, W, nc):
+    """Eq. 21 with per-atom tensors: K^{ab}(l) = < sum_i W_i^{ab}(t - l) v_i^b(t) > over the
+    origins t - l >= 0 (not summed over b; summing over b gives K^a)."""
+    T = len(v)
+    N = len(v[0])
+    out = [[0.0] * nc for _ in range(9)]
+    for l in range(nc):
+        n = 0
+        acc = [0.0] * 9
+        for t in range(l, T):
+            n += 1
+            for i in range(N):
+                Wi = [[float(W[t - l][i][3 * a + b]) for b in range(3)] for a in range(3)]
+                vi = [float(v[t][i][b]) for b in range(3)]
+                for a in range(3):
+                    for b in range(3):
+                        acc[3 * a + b] += Wi[a][b] * vi[b]
+        for c in range(9):
+            out[c][l] = acc[c] / n if n else 0.0
+    return out

@@ -15,6 +15,9 @@
  *   binning  J_b^a     = sum_{n in b} J_n^a   (frequency bins, Sec. III.A)
  *   Eq. 17   kappa_n^{mu nu}(tau) = (k_B T^2 V)^{-1} int_0^tau <J_n^mu(t') J^nu(0)> dt'
  *   Eq. 19   <J_n^mu>/(T V) = sum_nu kappa_n^{mu nu} F_e^nu
+ *   Eq. 21   K(t) = sum_i <W_i(0) . v_i(t)>                     (SHC correlation)
+ *   Eq. 22   Ktilde(omega) = int K(t) e^{i omega t} dt
+ *   Eq. 23   kappa(omega) = 2 Ktilde(omega) / (V T F_e)
  *
  * Readings where the paper is silent (each stated where it is used):
  *   - e is real (Gamma point), so e* = e in Eq. 13.
@@ -257,4 +260,60 @@ double orc_orthonormality(int64_t D, int64_t M, const double *Et)
             if (r > worst) worst = r;
         }
     return worst;
+}
+
+/*
+ * SHC correlation sums (Eq. 20-21), resolved by the tensor pair (a, b):
+ *   Ksum[3a+b][l] = sum_{t=l}^{T-1} sum_i W_i^{ab}(t - l) v_i^b(t)
+ *   count[l]      = max(T - l, 0)
+ * K^a(l) of Eq. 21 is sum_b Ksum[3a+b][l] / count[l]; at l = 0 it is the time average
+ * of the total heat current of Eq. 10.  v is [T][N][3], W is [T][N][9].
+ */
+void orc_shc_corr(int64_t N, int64_t T, const float *v, const float *W, int32_t nc,
+                  double *Ksum, int64_t *count)
+{
+    for (int32_t l = 0; l < nc; ++l) count[l] = T > l ? T - l : 0;
+#pragma omp parallel for schedule(static)
+    for (int32_t l = 0; l < nc; ++l)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int64_t t = l; t < T; ++t)
+                    for (int64_t i = 0; i < N; ++i)
+                        s += (double)W[((t - l) * N + i) * 9 + 3 * a + b] *
+                             (double)v[(t * N + i) * 3 + b];
+                Ksum[(int64_t)(3 * a + b) * nc + l] = s;
+            }
+}
+
+/*
+ * SHC spectrum (Eq. 22-23).  Reading: K is computed for t >= 0 only and extended
+ * evenly, K(-t) = K(t), so Ktilde(omega) = 2 int_0^{t_c} w(t) K(t) cos(omega t) dt with
+ * t_c = (nc - 1) dt, the trapezoid rule on the lags, and w = 1 (window 0) or the Hann
+ * window w = (1 + cos(pi t / t_c)) / 2 (window 1).  omega = 2 pi f with f in THz.
+ *   kappa[c][k] = 2 Ktilde_c(2 pi f_k) / (V T |F_e|)   in W/(m K) per THz
+ * for every tensor pair c = 3a+b (sum over b gives the a component of Eq. 23).
+ */
+void orc_shc_kappa(int32_t nc, const double *Ksum, const int64_t *count, double dt_ps,
+                   double T_K, double V_A3, double Fe, int32_t window, int32_t n_freq,
+                   const double *f_THz, double *kappa)
+{
+    const double PI = 3.14159265358979323846;
+    const double tc = (nc - 1) * dt_ps;
+    for (int c = 0; c < 9; ++c)
+        for (int32_t k = 0; k < n_freq; ++k) {
+            const double omega = 2.0 * PI * f_THz[k];
+            double s = 0.0;
+            for (int32_t l = 0; l < nc; ++l) {
+                const double K = count[l] > 0 ? Ksum[(int64_t)c * nc + l] / (double)count[l] : 0.0;
+                const double t = l * dt_ps;
+                double w = 1.0;
+                if (window == 1 && tc > 0) w = 0.5 * (1.0 + cos(PI * t / tc));
+                const double trap = (l == 0 || l == nc - 1) ? 0.5 : 1.0;
+                s += trap * w * K * cos(omega * t);
+            }
+            const double Kt = 2.0 * s * dt_ps;   /* eV A */
+            kappa[(int64_t)c * n_freq + k] =
+                Fe > 0 ? 2.0 * Kt / (V_A3 * T_K * Fe) * ORC_WMK_PER_EV_PS_A_K : 0.0;
+        }
 }

@@ -274,3 +274,28 @@ def test_gkma_si_n512_full_run(precision):
     assert np.all(err <= TOL[precision])
     assert np.all(errC <= TOL[precision])
     assert np.all(errK <= TOL[precision])
+
+
+def test_orthonormality_check_fp64_on_gpu():
+    # max |E^T E - I| in FP64 on the GPU: ~1e-15 for a QR basis; perturbing one entry by d
+    # changes row/column n of E^T E by d*E[r,m] (m != n) and the diagonal by 2 d E[r,n] + d^2
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import ModalHeatCurrent
+    N = 40
+    D = 3 * N
+    E = synth.eigvecs(D, D, 109)
+    mass = synth.masses(N, 28.085)
+    for probe in (0, 17):        # full check, and 17 probe modes
+        h = ModalHeatCurrent(precision="fp16x3", k_max=4, ortho_probe=probe)
+        h.set_modes(E, mass, None)
+        assert h.check_orthonormality(1e-12) < 1e-13
+        h.close()
+    r, n, d = 5, 0, 1e-3          # mode 0 is probe 0 in both settings
+    E2 = E.copy()
+    E2[r, n] += d
+    expect = max(np.abs(d * np.delete(E[r], n)).max(), abs(2 * d * E[r, n] + d * d))
+    h = ModalHeatCurrent(precision="fp16x3", k_max=4, ortho_probe=0)
+    with pytest.warns(UserWarning):
+        h.set_modes(E2, mass, None)
+    assert abs(h.check_orthonormality(1e-6) - expect) < 1e-13
+    h.close()

@@ -313,6 +313,10 @@ MUTATIONS = {
                              "s += Jb[((t - l) * B + b) * 3 + mu] * J[t * 3 + nu];"),
     "trapezoid_half_dropped": ("acc += 0.5 * (prev + C) * dt_ps;", "acc += (prev + C) * dt_ps;"),
     "last_bin_open": ("if (b >= B) b = B - 1;", "if (b >= B) b = -1;"),
+    "shc_lag_on_velocity": ("s += (double)W[((t - l) * N + i) * 9 + 3 * a + b] *\n                             (double)v[(t * N + i) * 3 + b];",
+                            "s += (double)W[(t * N + i) * 9 + 3 * a + b] *\n                             (double)v[((t - l) * N + i) * 3 + b];"),
+    "shc_trapezoid_dropped": ("const double trap = (l == 0 || l == nc - 1) ? 0.5 : 1.0;",
+                              "const double trap = 1.0;"),
 }
 
 
@@ -332,14 +336,17 @@ def _pins_pass(L):
     """Run a subset of the pins above against library handle L; True if all pass."""
     real = oracle.lib()
     for fn in ("orc_bins_uniform", "orc_modal_current", "orc_gkma_corr", "orc_gk_kappa",
-               "orc_hnema", "orc_kappa_window", "orc_orthonormality"):
+               "orc_hnema", "orc_kappa_window", "orc_orthonormality", "orc_shc_corr",
+               "orc_shc_kappa"):
         getattr(L, fn).argtypes = getattr(real, fn).argtypes
         getattr(L, fn).restype = getattr(real, fn).restype
     checks = [test_golden_one_atom_identity_basis, test_golden_two_atoms_mixed_basis,
               test_bins_edges_and_exclusions, test_parseval_and_inverse_transform,
               test_identity_basis_direction_decomposition,
               test_constant_input_correlation_closed_form,
-              lambda: test_oracle_matches_scalar_brute_force(3, 7, 6, 4)]
+              lambda: test_oracle_matches_scalar_brute_force(3, 7, 6, 4),
+              lambda: test_shc_matches_scalar_brute_force(3, 7, 4),
+              test_shc_spectrum_constant_input_closed_form]
     oracle._lib = L
     try:
         for c in checks:
@@ -359,3 +366,77 @@ def test_planted_mistake_is_caught(tmp_path, name):
     oracle.lib()
     assert _pins_pass(oracle.lib()), "pins must pass on the unmodified oracle"
     assert not _pins_pass(_compile_mutant(tmp_path, name)), f"mutation {name} not detected"
+
+
+# ---------------------------------------------------------------- SHC (Eq. 20-23)
+def test_shc_lag_zero_is_total_heat_current():
+    # Eq. 21 reduces to the heat current of Eq. 10 at t = 0 (Sec. II.C)
+    N, T = 9, 12
+    _, mass, v, W = tiny_system(N, T=T, seed=31)
+    K, cnt = oracle.shc_corr(v, W, 5)
+    J = np.einsum("tiab,tib->ta", W.astype(np.float64).reshape(T, N, 3, 3), v.astype(np.float64))
+    np.testing.assert_allclose(K.reshape(3, 3, 5)[:, :, 0].sum(axis=1), J.sum(axis=0),
+                               rtol=1e-12, atol=1e-11)
+    assert cnt.tolist() == [12, 11, 10, 9, 8]
+
+
+@pytest.mark.parametrize("N,T,nc", [(1, 4, 3), (3, 7, 4), (4, 9, 9)])
+def test_shc_matches_scalar_brute_force(N, T, nc):
+    _, mass, v, W = tiny_system(N, T=T, seed=40 + N)
+    K, cnt = oracle.shc_corr(v, W, nc)
+    ref = np.array(brute.shc(v, W, nc))
+    np.testing.assert_allclose(K / np.maximum(cnt, 1), ref, rtol=1e-12, atol=1e-10)
+
+
+def test_shc_correlation_matches_fft():
+    # direct lag sums vs FFT cross-correlation per atom and tensor pair
+    N, T, nc = 5, 64, 20
+    _, mass, v, W = tiny_system(N, T=T, seed=33)
+    K, _ = oracle.shc_corr(v, W, nc)
+    Wd = W.astype(np.float64).reshape(T, N, 3, 3)
+    vd = v.astype(np.float64)
+    ref = np.zeros((3, 3, nc))
+    nfft = 2 * T
+    for a in range(3):
+        for b in range(3):
+            fv = np.fft.rfft(vd[:, :, b], nfft, axis=0)
+            fw = np.fft.rfft(Wd[:, :, a, b], nfft, axis=0)
+            ref[a, b] = np.fft.irfft(fv * np.conj(fw), nfft, axis=0)[:nc].sum(axis=1)
+    np.testing.assert_allclose(K.reshape(3, 3, nc), ref, rtol=1e-9, atol=1e-8)
+
+
+def test_shc_spectrum_constant_input_closed_form():
+    # K(l) = K constant: the trapezoid cosine sum has the closed form
+    #   sum_{l=0}^{m} c_l cos(l th) = sin(m th) cot(th/2) / 2  (c_0 = c_m = 1/2, else 1),
+    # so Ktilde = dt K sin(m th) cot(th/2) with th = omega dt, and 2 m dt K at omega = 0.
+    nc, dt, TK, V, Fe = 30, 0.002, 300.0, 1000.0, 1e-4
+    m = nc - 1
+    Kc = np.tile(np.linspace(-2.0, 3.0, 9)[:, None], (1, nc)) * 7.0
+    cnt = np.full(nc, 7, dtype=np.int64)
+    f = np.array([0.0, 1.3, 17.0, 101.0])
+    kap = oracle.shc_kappa(Kc, cnt, dt, TK, V, Fe, f, window=0)
+    sc = pytest.importorskip("scipy.constants")
+    wmk = sc.e / (1e-12 * 1e-10)
+    Kv = Kc[:, 0] / 7.0
+    th = 2 * np.pi * f * dt
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kt = np.where(th > 0, dt * np.sin(m * th) / np.tan(th / 2), 2 * m * dt)
+    expect = 2 * np.outer(Kv, kt) / (V * TK * Fe) * wmk
+    np.testing.assert_allclose(kap, expect, rtol=1e-9, atol=1e-9 * np.abs(expect).max())
+
+
+def test_shc_spectrum_sum_rule():
+    # integral of kappa(f) over [0, 1/(2 dt)] recovers K(0)/(V T F_e) (discrete Fourier
+    # inversion of the even cosine series), for any K and either window
+    nc, dt, TK, V, Fe = 40, 0.002, 300.0, 500.0, 2e-4
+    rng = np.random.default_rng(5)
+    Ks = rng.standard_normal((9, nc)) * 50.0
+    cnt = np.full(nc, 1, dtype=np.int64)
+    f = np.linspace(0.0, 1.0 / (2 * dt), 20001)
+    sc = pytest.importorskip("scipy.constants")
+    wmk = sc.e / (1e-12 * 1e-10)
+    for window in (0, 1):
+        kap = oracle.shc_kappa(Ks, cnt, dt, TK, V, Fe, f, window=window)
+        total = np.trapezoid(kap, f, axis=1)
+        np.testing.assert_allclose(total, Ks[:, 0] / (V * TK * Fe) * wmk, rtol=1e-6,
+                                   atol=1e-9 * np.abs(Ks[:, 0]).max() / (V * TK * Fe) * wmk)
