@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="gkma_si_n8000",
-                    choices=sorted(synth.WORKLOADS) + ["cnt_group16"])
+                    choices=sorted(synth.WORKLOADS) + ["cnt_group16", "shc_si_n8000"])
     ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "bf16x3", "fp32"])
     ap.add_argument("--fp32-steps", type=int, default=12)
     ap.add_argument("--e2e-steps", type=int, default=200)
@@ -383,9 +383,100 @@ def run_group(args):
     }), flush=True)
     grp.close()
 
+
+# ----------------------------------------------------------------------------- SHC
+def run_shc(args):
+    """SHC correlation (Eq. 20-21) on the Si-8000 shape: 250 lags (500 fs at 2 fs), one bench
+    step = one block of K = 256 samples + the spectrum read-out (Eq. 22-23).  Unit: atom.lag.steps/s."""
+    world, rank, local = dist_init(args)
+    import torch
+    from paper_2102_03691_gb300.mhc import SpectralHeatCurrent
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, nc, K, P = 8000, 250, 256, 8
+    mass = synth.masses(N, isotopes=synth.SI_ISOTOPES, seed=20210211 + rank)
+    V = N * 20.02
+    tr = synth.Trajectory(mass, drive_g=synth.drive_coupling(150.0, 300.0, V, 1e-5, mass),
+                          seed=20210211 + 1000 * rank)
+    host_pool = [tuple(torch.from_numpy(a).pin_memory() for a in tr.next_block(K)) for _ in range(P)]
+    dev_pool = [(a.to(dev), b.to(dev)) for a, b in host_pool]
+    s = SpectralHeatCurrent(N, nc, k_max=K, dt_ps=0.002, T_K=300.0, V_A3=V, F_e=(1e-5, 0.0, 0.0),
+                            device=local)
+    f = np.linspace(0.0, 60.0, 241)
+    out = torch.empty((9, f.size), dtype=torch.float64, device=dev)
+    unit = "atom·lag·steps/s"
+
+    def step(i, host=False):
+        a, b = (host_pool if host else dev_pool)[i % P]
+        s.push(a, b)
+        return s.read_kappa(f, 1) if host else s.read_kappa(f, 1, out=out)
+
+    for i in range(max(3, args.warmup)):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(None)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        step(i)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    el_max, units = aggregate(e0.elapsed_time(e1) / 1e3, float(N) * nc * K * args.steps, world)
+    n_e2e = max(3, min(args.e2e_steps, args.steps))
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        step(i, host=True)
+    e2e_max, e2e_units = aggregate(time.perf_counter() - t0, float(N) * nc * K * n_e2e, world)
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        S = 384
+        v, W = tr.next_block(S)
+        t = time.perf_counter()
+        oracle.shc_corr(v, W, min(nc, S))
+        el = time.perf_counter() - t
+        cpu = {"value": float(N) * min(nc, S) * S / el, "unit": unit, "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"{S} samples x {min(nc, S)} lags x {N} atoms, {el:.1f} s"}
+    value = units / el_max
+    flops_step = 2.0 * 9 * N * nc * K
+    props = torch.cuda.get_device_properties(dev)
+    peaks, _ = measured_peaks()
+    fp32_peak = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    print(json.dumps({
+        "metric": "SHC correlation atom·lag·steps/s", "value": value, "unit": unit,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FP64 lag sums)", "data": "synthetic",
+        "config": {"workload": "shc_si_n8000", "N_atoms": N, "lags": nc, "K_steps_per_block": K,
+                   "l2": "inputs larger than L2 (145 MB virial ring + 8-block pool)"},
+        "roofline": {"bound": "alu", "achieved": flops_step / (el_max / args.steps) / 1e12 * world,
+                     "unit": "TFLOP/s", "peak": fp32_peak,
+                     "frac": flops_step / (el_max / args.steps) / 1e12 * world / fp32_peak,
+                     "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x max SM clock",
+                     "note": "whole step (correlation, FP64 tile reduction, spectrum) in FP32 FMA flops"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_units / e2e_max, "unit": unit, "h2d_bytes_per_step": 48 * N * K,
+                "d2h_bytes_per_step": 8 * 9 * f.size, "steps": n_e2e},
+        "clocks": clk, "gpu_launches": 3 * args.steps * world,
+    }), flush=True)
+    s.close()
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
+    if args.workload == "shc_si_n8000":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the SHC workload is measured "
+                              "on the GPU arm only; its CPU baseline is in the GPU line"}))
+            return
+        return run_shc(args)
     if args.workload == "cnt_group16":
         if args.impl == "reference":
             n = max(synth.cnt_group_sizes())

@@ -270,6 +270,32 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
 mhc_status mhc_group_read_hnema(mhc_group *g, double *kappa, double *mean_J, int32_t where);
 
 /*
+ * Spectral heat current (SHC, Sec. II.C): the virial-velocity correlation of Eq. 20-21,
+ *   Ksum[3a+b][l] = sum_{t >= l} sum_i W_i^{ab}(t - l) v_i^b(t),   count[l] = T_s - l,
+ * accumulated at run time (no eigenvectors needed), and the spectrum of Eq. 22-23,
+ *   kappa[3a+b][k] = 2 Ktilde(2 pi f_k) / (V T |F_e|)   in W/(m K) per THz,
+ *   Ktilde(omega) = 2 dt sum_l c_l w_l K(l) cos(omega l dt)  (K extended evenly to t < 0,
+ *   trapezoid weights c_l, window w = 1 or Hann (1 + cos(pi l / (L-1))) / 2).
+ * Summing a tensor pair over b gives the a component of Eq. 21 / 23; at lag 0 it is the
+ * time average of the total heat current (Eq. 10).  v, W as for mhc_push.
+ *   n_lags  L correlation lags, L <= 4096 (the paper uses 250 lags of 2 fs); k_max <= 1024.
+ * Errors as for the modal handle; messages through mhc_shc_last_error.
+ */
+typedef struct mhc_shc mhc_shc;
+mhc_status mhc_shc_create(mhc_shc **s, int32_t device, void *stream, int64_t n_atoms,
+                          int32_t n_lags, int32_t k_max, double dt_ps, double T_K, double V_A3,
+                          const double *F_e);
+void mhc_shc_destroy(mhc_shc *s);
+const char *mhc_shc_last_error(const mhc_shc *s);
+/* One block of K samples (host or device memory). */
+mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, int32_t where);
+/* Raw sums Ksum [9][L] (float64) and origin counts [L] (int64); either may be NULL. */
+mhc_status mhc_shc_read_corr(mhc_shc *s, double *Ksum, int64_t *count, int32_t where);
+/* kappa [9][n_freq] for the host array of frequencies f_THz; window 0 (none) or 1 (Hann). */
+mhc_status mhc_shc_read_kappa(mhc_shc *s, const double *f_THz, int32_t n_freq, int32_t window,
+                              double *kappa, int32_t where);
+
+/*
  * No-allocation variant of one block's binned modal current.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device memory,
  * e.g. an MD engine calling from inside its time-step loop (where cudaMalloc would

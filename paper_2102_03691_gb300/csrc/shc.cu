@@ -1,0 +1,341 @@
+// Spectral heat current (SHC, Eqs. 20-23): the virial-velocity correlation
+//   Ksum^{ab}(l) += sum_{t in block} sum_i W_i^{ab}(t - l) v_i^b(t),  t - l >= 0,
+// accumulated at run time over blocks of K samples with a ring of past virials, and the
+// spectrum kappa(omega) = 2 Ktilde(omega) / (V T |F_e|) on read.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mhc.h"
+#include "common.cuh"
+
+namespace {
+
+constexpr int SHC_LAGS = 256;      // lags per CTA (lag tile)
+constexpr int SHC_ATILE = 2;       // atoms per CTA
+constexpr int SHC_THREADS = 256;   // one thread per lag of the tile
+constexpr double WMK = 1602.176634;
+
+// One CTA: SHC_ATILE atoms x SHC_LAGS lags [L0, L0 + 256).  Warp w owns lags L0 + 32w + lane
+// and walks the shifted time tau = t - l shared by the warp, so W(tau) is a broadcast and
+// v(tau + l) is a conflict-free vector load.  Shared memory:
+//   sW[a][j][12]  W_i^{ab} of times tw0 + j, tw0 = t0 - L0 - 255 (zero before t = 0)
+//   sv[a][k][4]   v_i of block step k - 32 (zero outside the block)
+__global__ void __launch_bounds__(SHC_THREADS) shc_corr_kernel(const float *__restrict__ v,
+                                                               const float *__restrict__ Wring,
+                                                               int R, int N, int K, int nc,
+                                                               long long t0, float *partials,
+                                                               int nc_pad) {
+    extern __shared__ float4 smem4[];
+    const int L0 = blockIdx.y * SHC_LAGS;
+    const int atom0 = blockIdx.x * SHC_ATILE;
+    const int nw = K + SHC_LAGS - 1;    // W window entries
+    const int nv = K + 64;              // v entries (32 zeros on each side)
+    float4 *sW = smem4;                               // [ATILE][nw][3]
+    float4 *sv = smem4 + SHC_ATILE * nw * 3;          // [ATILE][nv]
+    const long long tw0 = t0 - L0 - (SHC_LAGS - 1);
+    for (int q = threadIdx.x; q < SHC_ATILE * nw; q += SHC_THREADS) {
+        const int a = q / nw, j = q - a * nw;
+        const int i = atom0 + a;
+        const long long tt = tw0 + j;
+        float w[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (i < N && tt >= 0) {
+            const float *src = Wring + ((tt % R) * (long long)N + i) * 9;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) w[c] = src[c];
+        }
+        float4 *d = sW + ((size_t)a * nw + j) * 3;
+        d[0] = make_float4(w[0], w[1], w[2], w[3]);
+        d[1] = make_float4(w[4], w[5], w[6], w[7]);
+        d[2] = make_float4(w[8], 0.f, 0.f, 0.f);
+    }
+    for (int q = threadIdx.x; q < SHC_ATILE * nv; q += SHC_THREADS) {
+        const int a = q / nv, k = q - a * nv - 32;
+        const int i = atom0 + a;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < N && k >= 0 && k < K) {
+            const float *src = v + ((long long)k * N + i) * 3;
+            x = make_float4(src[0], src[1], src[2], 0.f);
+        }
+        sv[(size_t)a * nv + k + 32] = x;
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lam = warp * 32 + lane;   // lag within the tile
+    float acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
+    for (int a = 0; a < SHC_ATILE; ++a) {
+        const float4 *wa = sW + (size_t)a * nw * 3;
+        const float4 *va = sv + (size_t)a * nv;
+        // tau_rel = i - 32 warp - 31: step k = tau_rel + lam = i - 31 + lane
+        for (int it = 0; it < K + 31; ++it) {
+            const int j = it - warp * 32 - 31 + (SHC_LAGS - 1);   // window index of W(tau)
+            const float4 w0 = wa[j * 3], w1 = wa[j * 3 + 1], w2 = wa[j * 3 + 2];
+            const float4 x = va[it - 31 + lane + 32];
+            // W^{ab} v^b, row-major ab: w0 = (xx, xy, xz, yx), w1 = (yy, yz, zx, zy), w2.x = zz
+            acc[0] = fmaf(w0.x, x.x, acc[0]);
+            acc[1] = fmaf(w0.y, x.y, acc[1]);
+            acc[2] = fmaf(w0.z, x.z, acc[2]);
+            acc[3] = fmaf(w0.w, x.x, acc[3]);
+            acc[4] = fmaf(w1.x, x.y, acc[4]);
+            acc[5] = fmaf(w1.y, x.z, acc[5]);
+            acc[6] = fmaf(w1.z, x.x, acc[6]);
+            acc[7] = fmaf(w1.w, x.y, acc[7]);
+            acc[8] = fmaf(w2.x, x.z, acc[8]);
+        }
+    }
+    const int l = L0 + lam;
+    if (l < nc) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c)
+            partials[((size_t)blockIdx.x * 9 + c) * nc_pad + l] = acc[c];
+    }
+}
+
+// Ksum[c][l] += sum over atom tiles of partials (FP64).  One CTA per (pair c, 32 lags):
+// warp w sums tiles w, w + 32, ... in order, then warp 0 adds the 32 warp sums in order
+// (a fixed tree: deterministic).
+constexpr int RED_WARPS = 32;
+__global__ void __launch_bounds__(RED_WARPS * 32) shc_reduce_kernel(const float *__restrict__ partials,
+                                                                   int n_tiles, int nc, int nc_pad,
+                                                                   double *Ksum) {
+    __shared__ double part[RED_WARPS][33];
+    const int c = blockIdx.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int l = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (l < nc)
+        for (int t = w; t < n_tiles; t += RED_WARPS)
+            s += (double)partials[((size_t)t * 9 + c) * nc_pad + l];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && l < nc) {
+        double tot = 0.0;
+        for (int q = 0; q < RED_WARPS; ++q) tot += part[q][lane];
+        Ksum[(size_t)c * nc + l] += tot;
+    }
+}
+
+// kappa[c][k] = 2 Ktilde_c(2 pi f_k) / (V T |F_e|), Ktilde = 2 dt sum_l trap_l w_l K_l cos(omega l dt).
+// One CTA per tensor pair c: the per-lag coefficients trap_l w_l K_l go to shared memory once;
+// each thread takes frequencies and runs the Chebyshev recurrence
+//   cos((l+1) x) = 2 cos(x) cos(l x) - cos((l-1) x),  x = omega dt,
+// so the lag sum costs FP64 FMAs only (one cos per frequency).
+constexpr int KAPPA_MAX_LAGS = 4096;
+__global__ void __launch_bounds__(256) shc_kappa_kernel(const double *Ksum, int nc, long long T_s,
+                                                        double dt, double coef, int window,
+                                                        const double *f, int n_freq, double *kappa) {
+    __shared__ double cl[KAPPA_MAX_LAGS];
+    const int c = blockIdx.x;
+    const double PI = 3.14159265358979323846;
+    for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+        const long long cnt = T_s - l;
+        const double Kl = cnt > 0 ? Ksum[(size_t)c * nc + l] / (double)cnt : 0.0;
+        const double w = (window == 1 && nc > 1) ? 0.5 * (1.0 + cos(PI * l / (double)(nc - 1))) : 1.0;
+        const double trap = (l == 0 || l == nc - 1) ? 0.5 : 1.0;
+        cl[l] = trap * w * Kl;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_freq; k += blockDim.x) {
+        const double x = 2.0 * PI * f[k] * dt;
+        const double c1 = cos(x);
+        double cprev = c1, ccur = 1.0;   // cos(-x), cos(0)
+        double s = 0.0;
+        for (int l = 0; l < nc; ++l) {
+            s = fma(cl[l], ccur, s);
+            const double cnext = 2.0 * c1 * ccur - cprev;
+            cprev = ccur;
+            ccur = cnext;
+        }
+        kappa[(size_t)c * n_freq + k] = coef * 2.0 * (2.0 * s * dt);
+    }
+}
+
+}  // namespace
+
+struct mhc_shc {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t N = 0;
+    int nc = 0, nc_pad = 0, k_max = 0, R = 0, n_tiles = 0;
+    double dt = 0, T = 0, V = 0, Fe = 0;
+    long long steps = 0;
+    float *Wring = nullptr, *partials = nullptr, *v_stage = nullptr, *W_stage = nullptr;
+    double *Ksum = nullptr, *out = nullptr;
+    long long *counts = nullptr;
+    size_t out_cap = 0;
+    std::string err;
+};
+
+namespace {
+thread_local std::string g_shc_create_error;
+
+mhc_status sfail(mhc_shc *s, mhc_status st, const char *fmt, ...) {
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    if (s) s->err = msg;
+    else g_shc_create_error = msg;
+    return st;
+}
+
+#define SHC_CUDA(s, call)                                                                         \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return sfail((s), e_ == cudaErrorMemoryAllocation ? MHC_ERR_OOM : MHC_ERR_CUDA,       \
+                         "%s failed: %s", #call, cudaGetErrorString(e_));                        \
+    } while (0)
+
+size_t shc_smem(int K) {
+    return ((size_t)SHC_ATILE * (K + SHC_LAGS - 1) * 3 + (size_t)SHC_ATILE * (K + 64)) * sizeof(float4);
+}
+}  // namespace
+
+extern "C" {
+
+mhc_status mhc_shc_create(mhc_shc **out, int32_t device, void *stream, int64_t n_atoms,
+                          int32_t n_lags, int32_t k_max, double dt_ps, double T_K, double V_A3,
+                          const double *F_e) {
+    if (!out) return MHC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_atoms < 1 || n_lags < 1 || n_lags > KAPPA_MAX_LAGS || k_max < 1 || k_max > 1024 ||
+        !(dt_ps > 0) || !(T_K > 0) ||
+        !(V_A3 > 0) || !F_e)
+        return sfail(nullptr, MHC_ERR_INVALID_ARG,
+                     "need n_atoms, n_lags >= 1, 1 <= k_max <= 1024, positive dt, T, V and F_e");
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return sfail(nullptr, MHC_ERR_CUDA, "no CUDA device %d", device);
+    if (!(prop.major == 10 && prop.minor == 3))
+        return sfail(nullptr, MHC_ERR_UNSUPPORTED, "built for sm_103a only");
+    auto *s = new mhc_shc();
+    s->device = device;
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->N = n_atoms;
+    s->nc = n_lags;
+    s->nc_pad = (n_lags + SHC_LAGS - 1) / SHC_LAGS * SHC_LAGS;
+    s->k_max = k_max;
+    s->R = k_max + s->nc_pad;   // holds every time the last lag tile reads
+    s->n_tiles = (int)((n_atoms + SHC_ATILE - 1) / SHC_ATILE);
+    s->dt = dt_ps;
+    s->T = T_K;
+    s->V = V_A3;
+    s->Fe = std::sqrt(F_e[0] * F_e[0] + F_e[1] * F_e[1] + F_e[2] * F_e[2]);
+    auto fail_free = [&](cudaError_t er) {
+        mhc_shc_destroy(s);
+        return sfail(nullptr, er == cudaErrorMemoryAllocation ? MHC_ERR_OOM : MHC_ERR_CUDA,
+                     "allocation: %s", cudaGetErrorString(er));
+    };
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMalloc(&s->Wring, sizeof(float) * (size_t)s->R * n_atoms * 9)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMalloc(&s->partials, sizeof(float) * (size_t)s->n_tiles * 9 * s->nc_pad)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMalloc(&s->Ksum, sizeof(double) * 9 * n_lags)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMalloc(&s->counts, sizeof(long long) * n_lags)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMalloc(&s->v_stage, sizeof(float) * (size_t)k_max * n_atoms * 3)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMalloc(&s->W_stage, sizeof(float) * (size_t)k_max * n_atoms * 9)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMemsetAsync(s->Wring, 0, sizeof(float) * (size_t)s->R * n_atoms * 9, s->stream)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMemsetAsync(s->Ksum, 0, sizeof(double) * 9 * n_lags, s->stream)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaFuncSetAttribute(shc_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)shc_smem(k_max))) != cudaSuccess)
+        return fail_free(e);
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return fail_free(e);
+    *out = s;
+    return MHC_OK;
+}
+
+void mhc_shc_destroy(mhc_shc *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    cudaFree(s->Wring);
+    cudaFree(s->partials);
+    cudaFree(s->Ksum);
+    cudaFree(s->counts);
+    cudaFree(s->v_stage);
+    cudaFree(s->W_stage);
+    cudaFree(s->out);
+    delete s;
+}
+
+const char *mhc_shc_last_error(const mhc_shc *s) { return s ? s->err.c_str() : g_shc_create_error.c_str(); }
+
+mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, int32_t where) {
+    if (!s) return MHC_ERR_INVALID_ARG;
+    if (!v || !W || K < 1 || K > s->k_max || (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE))
+        return sfail(s, MHC_ERR_INVALID_ARG, "bad inputs or K=%d outside [1, %d]", K, s->k_max);
+    SHC_CUDA(s, cudaSetDevice(s->device));
+    const size_t nv = (size_t)K * s->N * 3, nwf = (size_t)K * s->N * 9;
+    if (where == MHC_MEM_HOST) {
+        SHC_CUDA(s, cudaMemcpyAsync(s->v_stage, v, nv * 4, cudaMemcpyHostToDevice, s->stream));
+        v = s->v_stage;
+    }
+    // this block's virials into the ring at rows (t0 + k) mod R (at most two segments)
+    const size_t row = (size_t)s->N * 9 * sizeof(float);
+    const cudaMemcpyKind kind = where == MHC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const int r0 = (int)(s->steps % s->R);
+    const int first = std::min(K, s->R - r0);
+    SHC_CUDA(s, cudaMemcpyAsync((char *)s->Wring + r0 * row, W, first * row, kind, s->stream));
+    if (first < K)
+        SHC_CUDA(s, cudaMemcpyAsync(s->Wring, (const char *)W + first * row, (K - first) * row, kind, s->stream));
+    (void)nwf;
+    dim3 grid(s->n_tiles, s->nc_pad / SHC_LAGS);
+    shc_corr_kernel<<<grid, SHC_THREADS, shc_smem(K), s->stream>>>(v, s->Wring, s->R, (int)s->N, K,
+                                                                   s->nc, s->steps, s->partials,
+                                                                   s->nc_pad);
+    shc_reduce_kernel<<<dim3((s->nc + 31) / 32, 9), RED_WARPS * 32, 0, s->stream>>>(
+        s->partials, s->n_tiles, s->nc, s->nc_pad, s->Ksum);
+    SHC_CUDA(s, cudaGetLastError());
+    s->steps += K;
+    return MHC_OK;
+}
+
+mhc_status mhc_shc_read_corr(mhc_shc *s, double *Ksum, int64_t *count, int32_t where) {
+    if (!s) return MHC_ERR_INVALID_ARG;
+    const cudaMemcpyKind kind = where == MHC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (Ksum) SHC_CUDA(s, cudaMemcpyAsync(Ksum, s->Ksum, sizeof(double) * 9 * s->nc, kind, s->stream));
+    if (count) {
+        std::vector<long long> c(s->nc);
+        for (int l = 0; l < s->nc; ++l) c[l] = s->steps > l ? s->steps - l : 0;
+        if (where == MHC_MEM_HOST) std::memcpy(count, c.data(), sizeof(long long) * s->nc);
+        else SHC_CUDA(s, cudaMemcpy(count, c.data(), sizeof(long long) * s->nc, cudaMemcpyHostToDevice));
+    }
+    if (where == MHC_MEM_HOST) SHC_CUDA(s, cudaStreamSynchronize(s->stream));
+    return MHC_OK;
+}
+
+mhc_status mhc_shc_read_kappa(mhc_shc *s, const double *f_THz, int32_t n_freq, int32_t window,
+                              double *kappa, int32_t where) {
+    if (!s) return MHC_ERR_INVALID_ARG;
+    if (!f_THz || !kappa || n_freq < 1 || (window != 0 && window != 1))
+        return sfail(s, MHC_ERR_INVALID_ARG, "need frequencies, an output, window 0 or 1");
+    SHC_CUDA(s, cudaSetDevice(s->device));
+    const size_t need = sizeof(double) * (size_t)n_freq * 10;
+    if (s->out_cap < need) {
+        cudaStreamSynchronize(s->stream);
+        cudaFree(s->out);
+        s->out = nullptr;
+        SHC_CUDA(s, cudaMalloc(&s->out, need));
+        s->out_cap = need;
+    }
+    double *df = s->out + (size_t)n_freq * 9;
+    SHC_CUDA(s, cudaMemcpyAsync(df, f_THz, sizeof(double) * n_freq, cudaMemcpyHostToDevice, s->stream));
+    const double coef = s->Fe > 0 ? WMK / (s->V * s->T * s->Fe) : 0.0;
+    shc_kappa_kernel<<<9, 256, 0, s->stream>>>(s->Ksum, s->nc, s->steps, s->dt, coef, window, df,
+                                                n_freq, s->out);
+    SHC_CUDA(s, cudaGetLastError());
+    const cudaMemcpyKind kind = where == MHC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    SHC_CUDA(s, cudaMemcpyAsync(kappa, s->out, sizeof(double) * 9 * n_freq, kind, s->stream));
+    if (where == MHC_MEM_HOST) SHC_CUDA(s, cudaStreamSynchronize(s->stream));
+    return MHC_OK;
+}
+
+}  // extern "C"

@@ -35,6 +35,8 @@ EXPORTS = (
     "mhc_reset",
     "mhc_state_size", "mhc_get_state", "mhc_set_state", "mhc_group_create",
     "mhc_group_destroy", "mhc_group_push", "mhc_group_read_hnema", "mhc_binned_current_noalloc",
+    "mhc_shc_create", "mhc_shc_destroy", "mhc_shc_last_error", "mhc_shc_push", "mhc_shc_read_corr",
+    "mhc_shc_read_kappa",
 )
 
 
@@ -112,11 +114,20 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_group_push.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                  ctypes.POINTER(i32), i32]
     L.mhc_group_read_hnema.argtypes = [vp, vp, vp, i32]
+    L.mhc_shc_create.argtypes = [ctypes.POINTER(vp), i32, vp, i64, i32, i32, dbl, dbl, dbl, vp]
+    L.mhc_shc_destroy.argtypes = [vp]
+    L.mhc_shc_destroy.restype = None
+    L.mhc_shc_last_error.argtypes = [vp]
+    L.mhc_shc_last_error.restype = ctypes.c_char_p
+    L.mhc_shc_push.argtypes = [vp, vp, vp, i32, i32]
+    L.mhc_shc_read_corr.argtypes = [vp, vp, vp, i32]
+    L.mhc_shc_read_kappa.argtypes = [vp, vp, i32, i32, vp, i32]
     L.mhc_binned_current_noalloc.argtypes = [i32, i32, vp, i64, vp, i32, vp, vp, vp, i32, vp, vp,
                                              i32, vp]
     for name in EXPORTS:
         if name not in ("mhc_default_params", "mhc_destroy", "mhc_last_error",
-                        "mhc_status_string", "mhc_group_destroy"):
+                        "mhc_status_string", "mhc_group_destroy", "mhc_shc_destroy",
+                        "mhc_shc_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -174,6 +185,64 @@ class ModalHeatCurrentGroup:
         if getattr(self, "_g", None):
             self._L.mhc_group_destroy(self._g)
             self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SpectralHeatCurrent:
+    """mhc_shc_*: run-time SHC correlation K^{ab}(l) (Eq. 20-21) and spectrum (Eq. 22-23)."""
+
+    def __init__(self, n_atoms: int, n_lags: int, k_max: int = 256, dt_ps: float = 0.002,
+                 T_K: float = 300.0, V_A3: float = 1.0, F_e=(1e-5, 0.0, 0.0), device: int = 0,
+                 stream=None):
+        self._L = load()
+        fe = (ctypes.c_double * 3)(*F_e)
+        st_ptr = stream if isinstance(stream, ctypes.c_void_p) else (
+            ctypes.c_void_p(stream) if stream is not None else _current_stream(device))
+        s = ctypes.c_void_p()
+        st = self._L.mhc_shc_create(ctypes.byref(s), device, st_ptr, n_atoms, n_lags, k_max, dt_ps,
+                                    T_K, V_A3, fe)
+        if st != MHC_OK:
+            raise MhcError(st, self._L.mhc_shc_last_error(None).decode())
+        self._s = s
+        self.N, self.n_lags = n_atoms, n_lags
+
+    def _check(self, st):
+        if st != MHC_OK:
+            raise MhcError(st, self._L.mhc_shc_last_error(self._s).decode())
+
+    def push(self, v, W):
+        pv, wv, kv = _ptr(v, np.float32)
+        pw, ww, kw = _ptr(W, np.float32)
+        if wv != ww:
+            raise ValueError("v and W must be in the same memory space")
+        self._keep = (kv, kw)
+        self._check(self._L.mhc_shc_push(self._s, pv, pw, int(kv.shape[0]), wv))
+
+    def read_corr(self):
+        K = np.empty((9, self.n_lags))
+        cnt = np.empty(self.n_lags, np.int64)
+        self._check(self._L.mhc_shc_read_corr(self._s, K.ctypes.data_as(ctypes.c_void_p),
+                                              cnt.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
+        return K, cnt
+
+    def read_kappa(self, f_THz, window: int = 0, out=None):
+        f = np.ascontiguousarray(f_THz, dtype=np.float64)
+        if out is None:
+            out = np.empty((9, f.shape[0]))
+        p, where, keep = _ptr(out, np.float64)
+        self._check(self._L.mhc_shc_read_kappa(self._s, f.ctypes.data_as(ctypes.c_void_p),
+                                               f.shape[0], window, p, where))
+        return keep
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._L.mhc_shc_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:
