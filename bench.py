@@ -159,8 +159,9 @@ def measured_peaks():
 
 
 def tc_source_hash() -> str:
+    """Hash of the projection kernel's own sources (the device code and its PTX wrappers)."""
     h = hashlib.sha256()
-    for name in ("k_tc.cu", "common.cuh", "kernels.h"):
+    for name in ("k_tc.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2102_03691_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
