@@ -3,7 +3,7 @@
 Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of bench.py
 may import this package.  The CUDA library never calls it and shares no code
 with it.  ``mhc_oracle.c`` holds the plain FP64 loops (Eqs. 10, 13, 16, 17,
-19 and frequency binning; the SHC correlation and spectrum of Eqs. 20-23);
+19 and frequency binning; the direction split of Sec. II.A; the SHC correlation and spectrum of Eqs. 20-23);
 ``brute.py`` restates the same definitions with per-atom 3-vectors in scalar
 Python for tiny systems.
 
@@ -55,6 +55,8 @@ def lib():
             L.orc_bins_uniform.argtypes = [_i64, _p, _dbl, _dbl, _i32, _p]
             L.orc_modal_current.argtypes = [_i64, _i64, _p, _p, _i64, _p, _p, _p, _i32,
                                             _p, _p, _p, _p]
+            L.orc_modal_current_dir.argtypes = [_i64, _i64, _p, _p, _i64, _p, _p, _p, _i32,
+                                                _p, _p, _p]
             L.orc_gkma_corr.argtypes = [_i64, _i32, _p, _p, _i32, _p, _p]
             L.orc_gk_kappa.argtypes = [_i32, _i32, _p, _p, _dbl, _dbl, _dbl, _p]
             L.orc_kappa_window.argtypes = [_i32, _i32, _p, _dbl, _dbl, _dbl, _p]
@@ -113,6 +115,33 @@ def modal_current(E: np.ndarray, mass, v, W, bin_of_mode, B: int,
     if want_modes:
         out["xdot"] = xd
         out["Jn"] = Jn
+    return out
+
+
+def modal_current_dir(E: np.ndarray, mass, v, W, bin_of_mode, B: int,
+                      want_modes: bool = False):
+    """Direction-resolved currents (Sec. II.A split by the velocity component b).
+    Returns dict with Jbd [T][3][B][3] (index [t][b][bin][a]), Jd [T][3][3] ([t][b][a],
+    J^{ab} = sum_i W_i^{ab} v_i^b) and, when want_modes, Jnd [T][M][3][3] ([t][n][b][a])."""
+    E = np.asarray(E, dtype=np.float64)
+    D, M = E.shape
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    N = mass.shape[0]
+    if D != 3 * N:
+        raise ValueError("E must have 3N rows")
+    Et = np.ascontiguousarray(E.T)
+    v = np.ascontiguousarray(v, dtype=np.float32).reshape(-1, N, 3)
+    W = np.ascontiguousarray(W, dtype=np.float32).reshape(-1, N, 9)
+    T = v.shape[0]
+    bins = np.ascontiguousarray(bin_of_mode, dtype=np.int32)
+    Jbd = np.empty((T, 3, B, 3))
+    Jd = np.empty((T, 3, 3))
+    Jnd = np.empty((T, M, 3, 3)) if want_modes else None
+    lib().orc_modal_current_dir(N, M, _ptr(Et), _ptr(mass), T, _ptr(v), _ptr(W), _ptr(bins), B,
+                                _ptr(Jbd), _ptr(Jd), _ptr(Jnd))
+    out = {"Jbd": Jbd, "Jd": Jd}
+    if want_modes:
+        out["Jnd"] = Jnd
     return out
 
 

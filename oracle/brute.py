@@ -88,6 +88,47 @@ def run(E, mass, v, W, bin_of_mode, B, L=0):
     return out
 
 
+def step_dir(e, mass, v, W):
+    """Direction-resolved step: J_n^{ab} = Xdot_n sum_i W_i^{ab} e^b_{i,n} / sqrt(m_i), i.e. the
+    heat current of the modal atomic velocities v_{i,n} = Xdot_n e_{i,n}/sqrt(m_i) (Eq. 14)
+    restricted to their b-th component.  Returns Jn[n][b][a]."""
+    N = len(mass)
+    M = len(e[0])
+    out = []
+    for n in range(M):
+        x = sum(math.sqrt(mass[i]) * dot(e[i][n], v[i]) for i in range(N))
+        jn = [[0.0, 0.0, 0.0] for _ in range(3)]
+        for i in range(N):
+            # modal velocity of atom i, component b only
+            for b in range(3):
+                vb = x * e[i][n][b] / math.sqrt(mass[i])
+                for a in range(3):
+                    jn[b][a] += W[i][a][b] * vb
+        out.append(jn)
+    return out
+
+
+def run_dir(E, mass, v, W, bin_of_mode, B):
+    """Binned direction-resolved current Jbd[t][b][bin][a]."""
+    N = len(mass)
+    M = len(E[0])
+    e = [[[float(E[3 * i + b][n]) for b in range(3)] for n in range(M)] for i in range(N)]
+    out = []
+    for t in range(len(v)):
+        vt = [[float(v[t][i][b]) for b in range(3)] for i in range(N)]
+        Wt = [[[float(W[t][i][3 * a + b]) for b in range(3)] for a in range(3)] for i in range(N)]
+        jn = step_dir(e, [float(m) for m in mass], vt, Wt)
+        jb = [[[0.0, 0.0, 0.0] for _ in range(B)] for _ in range(3)]
+        for n in range(M):
+            bn = int(bin_of_mode[n])
+            if 0 <= bn < B:
+                for b in range(3):
+                    for a in range(3):
+                        jb[b][bn][a] += jn[n][b][a]
+        out.append(jb)
+    return out
+
+
 def shc(v, W, nc):
     """Eq. 21 with per-atom tensors: K^{ab}(l) = < sum_i W_i^{ab}(t - l) v_i^b(t) > over the
     origins t - l >= 0 (not summed over b; summing over b gives K^a)."""

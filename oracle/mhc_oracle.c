@@ -161,6 +161,66 @@ void orc_modal_current(int64_t N, int64_t M, const double *Et, const double *mas
 }
 
 /*
+ * Direction-resolved modal heat current (Sec. II.A: the heat current along a splits
+ * into the contributions of the atoms' motion along each Cartesian direction b; the
+ * closing paragraph of Sec. II.C applies this split to every method's spectral result).
+ * With the modal atomic velocity of Eq. 14, v_{i,n} = Xdot_n e_{i,n} / sqrt(m_i):
+ *   J_n^{ab}(t) = Xdot_n(t) sum_i m_i^{-1/2} W_i^{ab}(t) e^b_{i,n}        (no sum over b)
+ * so that sum_b J_n^{ab} is the J_n^a of Eq. 16.
+ *   Jbd  [T][3 (b)][B][3 (a)]   binned, modes in ascending n within each bin
+ *   Jd   [T][3 (b)][3 (a)]      J^{ab} = sum_i W_i^{ab} v_i^b (optional, may be NULL)
+ *   Jnd  [T][M][3 (b)][3 (a)]   per mode (optional, may be NULL)
+ */
+void orc_modal_current_dir(int64_t N, int64_t M, const double *Et, const double *mass,
+                           int64_t T, const float *v, const float *W,
+                           const int32_t *bin_of_mode, int32_t B,
+                           double *Jbd, double *Jd, double *Jnd)
+{
+    const int64_t D = 3 * N;
+    double *jn = (double *)malloc(sizeof(double) * (size_t)M * 9);
+    for (int64_t t = 0; t < T; ++t) {
+        const float *vt = v + t * N * 3;
+        const float *Wt = W + t * N * 9;
+        if (Jd) {
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    double s = 0.0;
+                    for (int64_t i = 0; i < N; ++i)
+                        s += (double)Wt[i * 9 + 3 * a + b] * (double)vt[i * 3 + b];
+                    Jd[t * 9 + 3 * b + a] = s;
+                }
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < M; ++n) {
+            const double *e = Et + n * D;
+            double x = 0.0;   /* Eq. 13 */
+            for (int64_t i = 0; i < N; ++i) {
+                double ev = 0.0;
+                for (int b = 0; b < 3; ++b) ev += e[3 * i + b] * (double)vt[i * 3 + b];
+                x += sqrt(mass[i]) * ev;
+            }
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    double y = 0.0;   /* only the b-th velocity component of the modal motion */
+                    for (int64_t i = 0; i < N; ++i)
+                        y += (double)Wt[i * 9 + 3 * a + b] * e[3 * i + b] / sqrt(mass[i]);
+                    jn[n * 9 + 3 * b + a] = x * y;
+                }
+        }
+        if (Jnd) memcpy(Jnd + t * M * 9, jn, sizeof(double) * (size_t)M * 9);
+        double *jb = Jbd + t * 3 * (int64_t)B * 3;
+        for (int64_t k = 0; k < 9 * (int64_t)B; ++k) jb[k] = 0.0;
+        for (int64_t n = 0; n < M; ++n) {
+            const int32_t bn = bin_of_mode[n];
+            if (bn < 0 || bn >= B) continue;
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) jb[((int64_t)b * B + bn) * 3 + a] += jn[n * 9 + 3 * b + a];
+        }
+    }
+    free(jn);
+}
+
+/*
  * GKMA correlation sums (Eq. 17 integrand, reading: the modal current is lagged,
  * the total current sits at the time origin, all origins with t - lag >= 0):
  *   Csum[b][mu][nu][l] = sum_{t=l}^{T-1} Jb[t][b][mu] * J[t-l][nu]

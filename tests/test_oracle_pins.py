@@ -161,6 +161,76 @@ def test_identity_basis_direction_decomposition():
     np.testing.assert_allclose(r["Jn"], expect, rtol=1e-13, atol=1e-13)
 
 
+# ---------------------------------------------------------------- direction split (Sec. II.A)
+def test_golden_direction_split_rotated_basis():
+    ex = golden("one_atom_rotated_basis_direction_split")
+    r = oracle.modal_current_dir(np.array(ex["E_dof_major"], float), ex["mass"],
+                                 np.array(ex["v"], np.float32), np.array(ex["W"], np.float32),
+                                 [0, 0, 0], 1, want_modes=True)
+    np.testing.assert_allclose(r["Jnd"], ex["Jnd"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r["Jd"], ex["Jd"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r["Jbd"][:, :, 0, :], np.array(ex["Jnd"]).sum(axis=1), atol=1e-12)
+
+
+def test_golden_direction_split_two_atoms():
+    ex = golden("two_atoms_mixed_basis_two_steps")
+    r = oracle.modal_current_dir(np.array(ex["E_dof_major"], float), ex["mass"],
+                                 np.array(ex["v"], np.float32), np.array(ex["W"], np.float32),
+                                 ex["bins"]["bin_of_mode"], ex["bins"]["B"])
+    np.testing.assert_allclose(r["Jbd"], ex["Jbd"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r["Jd"], ex["Jd"], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,M,T", [(1, 3, 2), (2, 5, 3), (4, 12, 2)])
+def test_direction_split_matches_scalar_brute_force(N, M, T):
+    E, mass, v, W = tiny_system(N, M, T=T, seed=30 + N)
+    bins = np.arange(M) % 2
+    r = oracle.modal_current_dir(E, mass, v, W, bins, 2)
+    ref = np.array(brute.run_dir(E, mass, v, W, bins, 2))
+    np.testing.assert_allclose(r["Jbd"], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_direction_split_completeness_per_direction():
+    # With all 3N orthonormal modes, sum_n e^b_{i,n} e^b'_{j,n} = delta_ij delta_bb', so the
+    # modes of each direction b add up to J^{ab} = sum_i W_i^{ab} v_i^b.
+    N = 12
+    E, mass, v, W = tiny_system(N, T=3, seed=41)
+    ref = np.einsum("tiab,tib->tba", W.astype(np.float64).reshape(3, N, 3, 3), v.astype(np.float64))
+    r = oracle.modal_current_dir(E, mass, v, W, np.zeros(3 * N, np.int32), 1, want_modes=True)
+    np.testing.assert_allclose(r["Jd"], ref, rtol=1e-12, atol=1e-10)
+    np.testing.assert_allclose(r["Jnd"].sum(axis=1), ref, rtol=1e-10, atol=1e-9)
+    np.testing.assert_allclose(r["Jbd"][:, :, 0, :], ref, rtol=1e-10, atol=1e-9)
+
+
+def test_direction_split_adds_up_to_eq16():
+    N = 5
+    E, mass, v, W = tiny_system(N, 11, T=3, seed=43)
+    bins = np.array([0, 1, 2] * 4)[:11]
+    rd = oracle.modal_current_dir(E, mass, v, W, bins, 3, want_modes=True)
+    r = oracle.modal_current(E, mass, v, W, bins, 3, want_modes=True)
+    np.testing.assert_allclose(rd["Jnd"].sum(axis=2), r["Jn"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(rd["Jbd"].sum(axis=1), r["Jb"], rtol=1e-12, atol=1e-12)
+
+
+def test_direction_split_planar_modes():
+    # A basis of in-plane (x, y only) and out-of-plane (z only) modes, as for flat graphene:
+    # in-plane modes carry nothing along beta = z, out-of-plane modes nothing along x, y.
+    N = 6
+    rng = np.random.default_rng(44)
+    Qxy, _ = np.linalg.qr(rng.standard_normal((2 * N, 2 * N)))
+    Qz, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    E = np.zeros((3 * N, 3 * N))
+    xy = np.array([3 * i + b for i in range(N) for b in (0, 1)])
+    z = np.array([3 * i + 2 for i in range(N)])
+    E[np.ix_(xy, np.arange(2 * N))] = Qxy
+    E[np.ix_(z, np.arange(2 * N, 3 * N))] = Qz
+    _, mass, v, W = tiny_system(N, T=2, seed=44)
+    r = oracle.modal_current_dir(E, mass, v, W, np.zeros(3 * N, np.int32), 1, want_modes=True)
+    assert np.all(r["Jnd"][:, :2 * N, 2, :] == 0)
+    assert np.all(r["Jnd"][:, 2 * N:, :2, :] == 0)
+    assert np.abs(r["Jnd"][:, :2 * N, :2, :]).max() > 0
+
+
 def test_mode_permutation_and_sign_flips():
     N = 6
     E, mass, v, W = tiny_system(N, T=2, seed=9)
@@ -305,8 +375,8 @@ def test_drive_coupling_gives_target_mean_current():
 
 # ---------------------------------------------------------------- planted mistakes
 MUTATIONS = {
-    "W_transposed": ("(double)Wt[i * 9 + 3 * a + b] * e[3 * i + b]",
-                     "(double)Wt[i * 9 + 3 * b + a] * e[3 * i + b]"),
+    "W_transposed": ("we += (double)Wt[i * 9 + 3 * a + b] * e[3 * i + b];",
+                     "we += (double)Wt[i * 9 + 3 * b + a] * e[3 * i + b];"),
     "mass_weight_dropped": ("x += sqm[i] * ev;", "x += ev;"),
     "inverse_mass_as_mass": ("y[a] += isqm[i] * we;", "y[a] += sqm[i] * we;"),
     "lag_on_total_current": ("s += Jb[(t * B + b) * 3 + mu] * J[(t - l) * 3 + nu];",
@@ -315,6 +385,10 @@ MUTATIONS = {
     "last_bin_open": ("if (b >= B) b = B - 1;", "if (b >= B) b = -1;"),
     "shc_lag_on_velocity": ("s += (double)W[((t - l) * N + i) * 9 + 3 * a + b] *\n                             (double)v[(t * N + i) * 3 + b];",
                             "s += (double)W[(t * N + i) * 9 + 3 * a + b] *\n                             (double)v[((t - l) * N + i) * 3 + b];"),
+    "dir_wrong_eigvec_component": ("y += (double)Wt[i * 9 + 3 * a + b] * e[3 * i + b] / sqrt(mass[i]);",
+                                   "y += (double)Wt[i * 9 + 3 * a + b] * e[3 * i + a] / sqrt(mass[i]);"),
+    "dir_bin_layout_swapped": ("jb[((int64_t)b * B + bn) * 3 + a] += jn[n * 9 + 3 * b + a];",
+                               "jb[((int64_t)b * B + bn) * 3 + a] += jn[n * 9 + 3 * a + b];"),
     "shc_trapezoid_dropped": ("const double trap = (l == 0 || l == nc - 1) ? 0.5 : 1.0;",
                               "const double trap = 1.0;"),
 }
@@ -337,7 +411,7 @@ def _pins_pass(L):
     real = oracle.lib()
     for fn in ("orc_bins_uniform", "orc_modal_current", "orc_gkma_corr", "orc_gk_kappa",
                "orc_hnema", "orc_kappa_window", "orc_orthonormality", "orc_shc_corr",
-               "orc_shc_kappa"):
+               "orc_shc_kappa", "orc_modal_current_dir"):
         getattr(L, fn).argtypes = getattr(real, fn).argtypes
         getattr(L, fn).restype = getattr(real, fn).restype
     checks = [test_golden_one_atom_identity_basis, test_golden_two_atoms_mixed_basis,
@@ -346,7 +420,8 @@ def _pins_pass(L):
               test_constant_input_correlation_closed_form,
               lambda: test_oracle_matches_scalar_brute_force(3, 7, 6, 4),
               lambda: test_shc_matches_scalar_brute_force(3, 7, 4),
-              test_shc_spectrum_constant_input_closed_form]
+              test_shc_spectrum_constant_input_closed_form,
+              test_golden_direction_split_rotated_basis, test_golden_direction_split_two_atoms]
     oracle._lib = L
     try:
         for c in checks:
