@@ -81,6 +81,18 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
                                       copies deliver, so its bounded waits (0.1 s with this flag)
                                       give up and the next sync/read returns MHC_ERR_TIMEOUT; no
                                       memory is touched out of bounds.  Implies direct launches. */
+#define MHC_FLAG_DIRECTION 0x10    /* direction-resolved split (Sec. II.A: the current along a is the
+                                      sum of the contributions of the atoms' motion along each
+                                      direction b; Sec. II.C applies the split to every method's
+                                      spectral result).  Per mode, with the modal velocity of Eq. 14,
+                                        J_n^{ab} = Xdot_n sum_i m_i^{-1/2} W_i^{ab} e^b_{i,n},
+                                      sum_b J_n^{ab} = J_n^a of Eq. 16.  Every per-bin output then
+                                      has 3 B rows, row b * B + bin (b = direction of the motion):
+                                      binned current [K][3][B][3], HNEMA [3][B][3], GKMA sums
+                                      [3][B][3][3][L], each correlated with the total J (Eq. 17).
+                                      Same tensor work as without the split.  Tensor-core
+                                      precisions take tile_config 0 (autotuned among 3, 4), 3 or 4;
+                                      set at mhc_create, not with mhc_set_flags; not for groups. */
 
 typedef struct {
     int32_t device;      /* CUDA device ordinal */

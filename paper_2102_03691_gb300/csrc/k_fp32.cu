@@ -18,8 +18,8 @@ constexpr int SG_THREADS = 256;
 // columns ty*4+{0..3}, 64+ty*4+{0..3}); shared tiles stored d-major.
 __global__ void __launch_bounds__(SG_THREADS) sgemm_tn_kernel(const float *__restrict__ Et,
                                                               const float *__restrict__ Bt,
-                                                              float *__restrict__ R, int D_ld,
-                                                              int Mp, int C) {
+                                                              float *__restrict__ R, int Dk,
+                                                              int D_ld, int Mp, int C) {
     __shared__ __align__(16) float As[SG_BK][SG_BM];
     __shared__ __align__(16) float Bs[SG_BK][SG_BN];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -40,14 +40,14 @@ __global__ void __launch_bounds__(SG_THREADS) sgemm_tn_kernel(const float *__res
     float4 ra1 = *reinterpret_cast<const float4 *>(ga + 4);
     float4 rb0 = *reinterpret_cast<const float4 *>(gb);
     float4 rb1 = *reinterpret_cast<const float4 *>(gb + 4);
-    for (int d0 = 0; d0 < D_ld; d0 += SG_BK) {
+    for (int d0 = 0; d0 < Dk; d0 += SG_BK) {
         __syncthreads();
         As[lk + 0][lrow] = ra0.x; As[lk + 1][lrow] = ra0.y; As[lk + 2][lrow] = ra0.z; As[lk + 3][lrow] = ra0.w;
         As[lk + 4][lrow] = ra1.x; As[lk + 5][lrow] = ra1.y; As[lk + 6][lrow] = ra1.z; As[lk + 7][lrow] = ra1.w;
         Bs[lk + 0][lrow] = rb0.x; Bs[lk + 1][lrow] = rb0.y; Bs[lk + 2][lrow] = rb0.z; Bs[lk + 3][lrow] = rb0.w;
         Bs[lk + 4][lrow] = rb1.x; Bs[lk + 5][lrow] = rb1.y; Bs[lk + 6][lrow] = rb1.z; Bs[lk + 7][lrow] = rb1.w;
         __syncthreads();
-        if (d0 + SG_BK < D_ld) {   // prefetch the next slab into registers
+        if (d0 + SG_BK < Dk) {   // prefetch the next slab into registers
             ra0 = *reinterpret_cast<const float4 *>(ga + d0 + SG_BK);
             ra1 = *reinterpret_cast<const float4 *>(ga + d0 + SG_BK + 4);
             rb0 = *reinterpret_cast<const float4 *>(gb + d0 + SG_BK);
@@ -100,12 +100,45 @@ __global__ void __launch_bounds__(128) fp32_bin_epilogue_kernel(const float *__r
     }
 }
 
+// Direction-resolved variant: the three products R_b of the direction segments of d.
+__global__ void __launch_bounds__(128) fp32_dir_epilogue_kernel(const float *__restrict__ R,
+                                                                size_t rstride, int Mp, int K,
+                                                                const int *mode_bin,
+                                                                const int *mode_slot,
+                                                                float *partials, int n_slots) {
+    const int n = blockIdx.x * 128 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int bin = mode_bin[n];
+    const int slot = mode_slot[n];
+    const uint32_t take = seg_scan_masks(bin, lane);
+    const int k0 = blockIdx.y * EPI_STEPS;
+    for (int k = k0; k < min(K, k0 + EPI_STEPS); ++k) {
+        const size_t xo = (size_t)(4 * k) * Mp + n;
+        const float x = (R[xo] + R[rstride + xo]) + R[2 * rstride + xo];   // Eq. 13 over all d
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float y = R[b * rstride + (size_t)(4 * k + 1 + a) * Mp + n];
+                const float s = seg_scan(x * y, take);
+                if (slot >= 0) partials[((size_t)k * 3 + a) * (3 * (size_t)n_slots) + (size_t)b * n_slots + slot] = s;
+            }
+    }
+}
+
 }  // namespace
 
-void launch_sgemm(const float *Et32, const float *Bt32, float *R, int D_ld, int Mp, int C,
+void launch_sgemm(const float *Et32, const float *Bt32, float *R, int Dk, int ld, int Mp, int C,
                   cudaStream_t s) {
     dim3 grid(Mp / SG_BM, (C + SG_BN - 1) / SG_BN);
-    sgemm_tn_kernel<<<grid, SG_THREADS, 0, s>>>(Et32, Bt32, R, D_ld, Mp, C);
+    sgemm_tn_kernel<<<grid, SG_THREADS, 0, s>>>(Et32, Bt32, R, Dk, ld, Mp, C);
+}
+
+void launch_fp32_dir_epilogue(const float *R, size_t rstride, int Mp, int K, const int *mode_bin,
+                              const int *mode_slot, float *partials, int n_slots, cudaStream_t s) {
+    dim3 grid(Mp / 128, (K + EPI_STEPS - 1) / EPI_STEPS);
+    fp32_dir_epilogue_kernel<<<grid, 128, 0, s>>>(R, rstride, Mp, K, mode_bin, mode_slot, partials,
+                                                  n_slots);
 }
 
 void launch_fp32_bin_epilogue(const float *R, int Mp, int K, const int *mode_bin,

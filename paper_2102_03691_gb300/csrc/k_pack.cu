@@ -115,18 +115,21 @@ __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
     // Phase 2, one thread per atom: the four scaled rows of step k,
     //   Bt[4k][3i+b] = sqrt(m_i) v_i^b,  Bt[4k+1+a][3i+b] = W_i^{ab} / sqrt(m_i),
     // split into hi/lo (inputs re-read from L2).
+    // (direction-major columns b*npad + i when npad > 0)
     const float mul[4] = {s_mul[0], s_mul[1], s_mul[2], s_mul[3]};
     const size_t r0 = (size_t)(4 * k) * a.D_ld;
     const size_t ld = (size_t)a.D_ld;
+    const size_t cs_i = a.npad ? 1 : 3, cs_b = a.npad ? (size_t)a.npad : 1;
     for (int i = threadIdx.x; i < a.N; i += PACK_THREADS) {
         const float sm = a.sqm[i], ism = a.isqm[i];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) store_split(a, r0 + 3 * i + b, (sm * v[(size_t)i * 3 + b]) * mul[0]);
+        for (int b = 0; b < 3; ++b)
+            store_split(a, r0 + cs_i * i + cs_b * b, (sm * v[(size_t)i * 3 + b]) * mul[0]);
 #pragma unroll
         for (int al = 0; al < 3; ++al)
 #pragma unroll
             for (int b = 0; b < 3; ++b)
-                store_split(a, r0 + (1 + al) * ld + 3 * i + b,
+                store_split(a, r0 + (1 + al) * ld + cs_i * i + cs_b * b,
                             (W[(size_t)i * 9 + 3 * al + b] * ism) * mul[1 + al]);
     }
 }

@@ -34,10 +34,18 @@ __global__ void max_abs_kernel(const T *E, int layout, int64_t ld, int64_t D, in
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
+// Source dof of stored column c: c itself, or 3i+b for the direction-major column
+// c = b*npad + i (-1 for the zero padding of each direction segment).
+__device__ __forceinline__ int64_t source_dof(int64_t c, int64_t D, int64_t npad) {
+    if (npad == 0) return c < D ? c : -1;
+    const int64_t b = c / npad, i = c - b * npad;
+    return (b < 3 && i < D / 3) ? 3 * i + b : -1;
+}
+
 template <typename T, int SPLIT>
 __global__ void prepare_kernel(const T *E, int layout, int64_t ld, int64_t D, int64_t M_eff,
                                const int *perm, int e_exp, void *Et_hi, void *Et_lo,
-                               float *Et32, int64_t D_ld) {
+                               float *Et32, int64_t D_ld, int64_t npad) {
     __shared__ double tile[32][33];
     const int64_t d0 = (int64_t)blockIdx.x * 32, n0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
@@ -45,16 +53,16 @@ __global__ void prepare_kernel(const T *E, int layout, int64_t ld, int64_t D, in
     if (layout == 0) {
         // rows of E are dofs: read E[d][perm[n]] with n along tx
         for (int r = ty; r < 32; r += 8) {
-            const int64_t d = d0 + r, n = n0 + tx;
+            const int64_t d = source_dof(d0 + r, D, npad), n = n0 + tx;
             double x = 0.0;
-            if (d < D && n < M_eff) x = load_e(E, 0, ld, d, (int64_t)perm[n]);
+            if (d >= 0 && n < M_eff) x = load_e(E, 0, ld, d, (int64_t)perm[n]);
             tile[tx][r] = x;   // tile[n_local][d_local]
         }
     } else {
         for (int r = ty; r < 32; r += 8) {
-            const int64_t n = n0 + r, d = d0 + tx;
+            const int64_t n = n0 + r, d = source_dof(d0 + tx, D, npad);
             double x = 0.0;
-            if (d < D && n < M_eff) x = load_e(E, 1, ld, d, (int64_t)perm[n]);
+            if (d >= 0 && n < M_eff) x = load_e(E, 1, ld, d, (int64_t)perm[n]);
             tile[r][tx] = x;
         }
     }
@@ -127,11 +135,12 @@ void launch_max_abs(const void *E, int dtype, int layout, int64_t ld, int64_t D,
 
 void launch_prepare_modes(const void *E, int dtype, int layout, int64_t ld, int64_t D,
                           int64_t M_eff, const int *perm, int e_exp, int split, void *Et_hi,
-                          void *Et_lo, float *Et32, int64_t D_ld, int64_t M_pad, cudaStream_t s) {
+                          void *Et_lo, float *Et32, int64_t D_ld, int64_t M_pad, int64_t npad,
+                          cudaStream_t s) {
     dim3 block(32, 8), grid((unsigned)(D_ld / 32), (unsigned)(M_pad / 32));
 #define MHC_PREP(T, S)                                                                         \
     prepare_kernel<T, S><<<grid, block, 0, s>>>((const T *)E, layout, ld, D, M_eff, perm, e_exp, \
-                                                Et_hi, Et_lo, Et32, D_ld)
+                                                Et_hi, Et_lo, Et32, D_ld, npad)
     if (dtype == 1) {
         if (split == SPLIT_BF16) MHC_PREP(double, SPLIT_BF16);
         else if (split == SPLIT_FP16) MHC_PREP(double, SPLIT_FP16);

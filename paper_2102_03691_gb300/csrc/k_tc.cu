@@ -42,7 +42,9 @@ struct TcLayout {
     static constexpr int TILE_BYTES = STAGES * STAGE_BYTES;
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM_BYTES = TILE_BYTES + BAR_BYTES + 1024;   // + alignment slack
-    static constexpr uint32_t TMEM_COLS = 2 * BN;                       // two chunk accumulators
+    // two chunk accumulators; 128-column tiles also keep 2 x 96 columns for the parked
+    // bracket sums of the direction-resolved split (the allocation is a power of two)
+    static constexpr uint32_t TMEM_COLS = BN == 128 ? 512 : 2 * BN;
     static constexpr uint32_t SWIZZLE_CODE = BK == 64 ? 2u : 4u;        // 128 B or 64 B rows
     static constexpr uint32_t SBO = 8 * BK * 2;                         // 8-row core group
     static_assert(BK == 64 || BK == 32, "BK");
@@ -85,6 +87,45 @@ struct TileIter {
 };
 
 constexpr int PROMOTE_D = 128;   // d elements per TMEM chunk accumulator
+
+// Direction-resolved split (one-SM 128-column tiles).  The d axis is stored direction-major
+// (segment b holds the dofs 3i+b), so every chunk lies inside one segment.  The epilogue keeps
+// Xdot (columns 4s) accumulating over all segments; at the end of segment b < 2 it parks the
+// finished bracket sums Y^{a b} (columns 4s+1+a of 32 steps: 96 values a lane) in TMEM
+// columns PARK_COL + 96 b and restarts them from zero.
+constexpr uint32_t PARK_COL = 256;
+
+__device__ __forceinline__ void park_y(float (&acc)[128], uint32_t taddr) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        uint32_t r[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int j = 16 * c + q;   // j = 3 s + a
+            r[q] = __float_as_uint(acc[4 * (j / 3) + 1 + j % 3]);
+        }
+        tmem_st_32x32b_x16(taddr + (uint32_t)(16 * c), r);
+    }
+    tmem_st_wait();
+#pragma unroll
+    for (int s = 0; s < 32; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[4 * s + 1 + a] = 0.f;
+}
+
+__device__ __forceinline__ void unpark_y(float (&acc)[128], uint32_t taddr) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        uint32_t r[16];
+        tmem_ld_32x32b_x16(taddr + (uint32_t)(16 * c), r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int j = 16 * c + q;
+            acc[4 * (j / 3) + 1 + j % 3] = __uint_as_float(r[q]);
+        }
+    }
+}
 
 template <int BN, int BK, int STAGES, int NPROB>
 __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_constant__ TcParams<NPROB> p) {
@@ -260,10 +301,47 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
                 tc_fence_before();
                 mbar_arrive(&acc_empty[abuf]);
                 if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+                if constexpr (BN == 128) {
+                    const int kn = kb0 + CHUNK_KB;
+                    if (P.dir_seg_kb && kn % P.dir_seg_kb == 0 && kn < P.n_kb)
+                        park_y(acc, tmem_base + ((uint32_t)(qw * 32) << 16) + PARK_COL +
+                                        (uint32_t)(96 * (kn / P.dir_seg_kb - 1)));
+                }
             }
             if (!ok) break;
             // Eq. 16 product and the bin-run sums of this warp's 32 steps
             const int kbase = ct * (BN / 4) + ch * 32;
+            if constexpr (BN == 128) {
+                if (P.dir_seg_kb) {
+                    // direction-resolved: J_n^{ab}(k) = Xdot_n(k) Y_n^{ab}(k), direction 2 from
+                    // the registers, directions 1 and 0 from their parked columns
+                    const size_t row = 3 * (size_t)P.n_slots;
+                    for (int b = 2; b >= 0; --b) {
+                        if (b < 2)
+                            unpark_y(acc, tmem_base + ((uint32_t)(qw * 32) << 16) + PARK_COL +
+                                              (uint32_t)(96 * b));
+                        // opaque per pass: keeps the 128 scale loads from being hoisted out of
+                        // the direction loop (they would not fit in registers beside acc)
+                        const float *csb = P.col_scale;
+                        asm volatile("" : "+l"(csb));
+#pragma unroll
+                        for (int s4 = 0; s4 < 32; ++s4) {
+                            const int k = kbase + s4;
+                            if (k >= P.K) break;   // warp-uniform
+                            const float *cs = csb + 4 * k;
+                            const float x = acc[4 * s4] * __ldg(cs);
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                const float y = acc[4 * s4 + 1 + a] * __ldg(cs + 1 + a);
+                                const float v = seg_scan(x * y, take);
+                                if (slot >= 0)
+                                    P.partials[((size_t)k * 3 + a) * row + (size_t)b * P.n_slots + slot] = v;
+                            }
+                        }
+                    }
+                    continue;
+                }
+            }
 #pragma unroll
             for (int s4 = 0; s4 < 32; ++s4) {
                 const int k = kbase + s4;

@@ -24,6 +24,8 @@ __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt, uint32_t M, ui
 //   Bt[4k+1+a][d]   = W_i^{ab} / sqrt(m_i)       (Eq. 16 bracket weights)
 // (d = 3i+b), split into hi/lo 16-bit parts after a per-row power-of-two scale
 // 2^s (FP16), and the FP64 total current J(t0+k) of Eq. 10.
+// With npad > 0 the d axis is stored direction-major: column b*npad + i holds dof 3i+b
+// (columns npad*b + [N, npad) stay zero), the layout of the direction-resolved split.
 struct PackArgs {
     const float *v;        // [K][N][3]
     const float *W;        // [K][N][9]
@@ -38,6 +40,7 @@ struct PackArgs {
     double *Jtot;          // [K][3]
     double *Jring;         // [R][3] ring of past J (GKMA) or null
     int R;
+    int npad;              // 0: column 3i+b; > 0: column b*npad + i
 };
 void launch_pack(const PackArgs &a, cudaStream_t s);
 
@@ -46,21 +49,29 @@ void launch_pack(const PackArgs &a, cudaStream_t s);
 void launch_max_abs(const void *E, int dtype, int layout, int64_t ld, int64_t D, int64_t M,
                     unsigned *out_bits, cudaStream_t s);
 // Gather the kept modes in bin order (perm), transpose to mode-major and split:
-//   Et[n'][d] = E[d, perm[n']] * 2^e_exp   (zero for n' >= M_eff or d >= D)
+//   Et[n'][c] = E[d(c), perm[n']] * 2^e_exp   (zero for n' >= M_eff or d(c) >= D)
+// with d(c) = c (npad == 0) or, direction-major, d(b*npad + i) = 3i+b for i < D/3.
 void launch_prepare_modes(const void *E, int dtype, int layout, int64_t ld, int64_t D,
                           int64_t M_eff, const int *perm, int e_exp, int split, void *Et_hi,
-                          void *Et_lo, float *Et32, int64_t D_ld, int64_t M_pad, cudaStream_t s);
+                          void *Et_lo, float *Et32, int64_t D_ld, int64_t M_pad, int64_t npad,
+                          cudaStream_t s);
 // FP64 basis check: max over probe modes p and all modes m of |sum_d E[d,p]E[d,m] - delta|
 void launch_orthonormality(const void *E, int dtype, int layout, int64_t ld, int64_t D,
                            int64_t M, const int *probe, int n_probe,
                            unsigned long long *out_bits, cudaStream_t s);
 
 // ---------------------------------------------------------------- FP32 path
-// R[c][n] = sum_d Bt32[c][d] Et32[n][d] for c < C (rows of the block), n < Mp.
-void launch_sgemm(const float *Et32, const float *Bt32, float *R, int D_ld, int Mp, int C,
+// R[c][n] = sum_{d < Dk} Bt32[c][d] Et32[n][d] for c < C (rows of the block), n < Mp;
+// both operands have row pitch ld (Dk a multiple of 16).
+void launch_sgemm(const float *Et32, const float *Bt32, float *R, int Dk, int ld, int Mp, int C,
                   cudaStream_t s);
 // J_n^a(k) = R[4k][n] R[4k+1+a][n]; segmented bin sums into partials[k][a][slot].
 void launch_fp32_bin_epilogue(const float *R, int Mp, int K, const int *mode_bin,
+                              const int *mode_slot, float *partials, int n_slots, cudaStream_t s);
+// Direction-resolved epilogue over the three per-direction products R_b = R + b*rstride:
+// Xdot = sum_b R_b[4k][n], J_n^{ab}(k) = Xdot R_b[4k+1+a][n]; bin-run sums into
+// partials[k][a][b*n_slots + slot].
+void launch_fp32_dir_epilogue(const float *R, size_t rstride, int Mp, int K, const int *mode_bin,
                               const int *mode_slot, float *partials, int n_slots, cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core path
@@ -73,8 +84,11 @@ struct TcProblem {   // 128-byte aligned through CUtensorMap
     const int *mode_bin;          // [M_pad] bin of each stored mode, -1 for padding
     const int *mode_slot;         // [M_pad] partial-sum slot of run tails, else -1
     const float *col_scale;       // [4K]
-    float *partials;              // [K][3][n_slots]
+    float *partials;              // [K][3][n_slots] ([K][3][3 n_slots] with the direction split)
     int n_slots, n_kb, K, n_col_tiles, n_tiles;
+    // Direction-resolved split (one-SM tiles of 128 columns only): k-blocks per direction
+    // segment of the direction-major d axis, 0 when off.
+    int dir_seg_kb;
 };
 
 template <int NPROB>

@@ -82,6 +82,10 @@ struct mhc_handle {
     // modes
     bool modes_ready = false, bins_ready = false;
     int64_t N = 0, D = 0, M_in = 0, M_eff = 0, D_ld = 0, M_pad = 0;
+    // direction-resolved split (MHC_FLAG_DIRECTION): d stored direction-major in three
+    // segments of N_pad columns; every per-bin output has 3 B rows, row = b * B + bin
+    bool dir = false;
+    int64_t N_pad = 0;
     std::vector<double> freq, mass;
     std::vector<int> perm;          // stored (bin-sorted) mode -> input mode
     int e_exp = 0;
@@ -208,6 +212,15 @@ void dev_free(mhc_handle *h, const char *name) {
 
 bool is_tc(const mhc_handle *h) { return h->split != SPLIT_FP32; }
 
+// Rows of the per-bin outputs: B, or 3 B (direction b, bin) with the direction split.
+int64_t n_out_bins(const mhc_handle *h) { return (int64_t)h->B * (h->dir ? 3 : 1); }
+
+// Partial-sum slots per step component (one set per direction with the split).
+int64_t slot_stride(const mhc_handle *h) { return h->n_slots * (h->dir ? 3 : 1); }
+
+// The direction split parks its bracket sums in TMEM beside one-SM 128-column tiles.
+bool dir_config_ok(const TcConfig &c) { return c.bn == 128 && !c.pair; }
+
 void drop_graphs(mhc_handle *h) {
     for (auto &kv : h->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -227,7 +240,7 @@ mhc_status check_device_status(mhc_handle *h) {
 mhc_status reset_accumulators(mhc_handle *h) {
     h->steps = 0;
     h->K_last = 0;
-    const int64_t B = std::max<int32_t>(h->B, 1), L = std::max<int32_t>(h->prm.n_lags, 0);
+    const int64_t B = std::max<int64_t>(n_out_bins(h), 1), L = std::max<int32_t>(h->prm.n_lags, 0);
     mhc_status s;
     if ((s = dev_alloc(h, "hsum", sizeof(double) * B * 3)) != MHC_OK) return s;
     if ((s = dev_alloc(h, "Jsum", sizeof(double) * 3)) != MHC_OK) return s;
@@ -327,20 +340,29 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         sbeg[b] = s;
     }
     sbeg[B] = (int)slot_bin.size();
+    if (h->dir) {
+        // output row b*B + bin reads slots b*n_slots + [sbeg[bin], sbeg[bin+1])
+        std::vector<int> sd(3 * (size_t)B + 1);
+        for (int b = 0; b < 3; ++b)
+            for (int q = 0; q < B; ++q) sd[(size_t)b * B + q] = b * (int)h->n_slots + sbeg[q];
+        sd[3 * (size_t)B] = 2 * (int)h->n_slots + sbeg[B];
+        sbeg.swap(sd);
+    }
+    const int64_t nbo = n_out_bins(h);
 
     mhc_status s;
     const int K = h->prm.k_max;
     if ((s = dev_alloc(h, "mode_bin", sizeof(int) * h->M_pad, false)) != MHC_OK) return s;
     if ((s = dev_alloc(h, "mode_slot", sizeof(int) * h->M_pad, false)) != MHC_OK) return s;
-    if ((s = dev_alloc(h, "slot_begin", sizeof(int) * (B + 1), false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "slot_begin", sizeof(int) * (nbo + 1), false)) != MHC_OK) return s;
     if ((s = dev_alloc(h, "perm", sizeof(int) * std::max<int64_t>(h->M_eff, 1), false)) != MHC_OK) return s;
-    if ((s = dev_alloc(h, "partials", sizeof(float) * K * 3 * h->n_slots)) != MHC_OK) return s;
-    if ((s = dev_alloc(h, "Jb", sizeof(float) * K * B * 3)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "partials", sizeof(float) * K * 3 * slot_stride(h))) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "Jb", sizeof(float) * K * nbo * 3)) != MHC_OK) return s;
     MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "mode_bin"), mbin.data(), sizeof(int) * h->M_pad,
                                 cudaMemcpyHostToDevice, h->stream));
     MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "mode_slot"), mslot.data(), sizeof(int) * h->M_pad,
                                 cudaMemcpyHostToDevice, h->stream));
-    MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "slot_begin"), sbeg.data(), sizeof(int) * (B + 1),
+    MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "slot_begin"), sbeg.data(), sizeof(int) * (nbo + 1),
                                 cudaMemcpyHostToDevice, h->stream));
     if (h->M_eff > 0)
         MHC_CUDA(h, cudaMemcpyAsync(dptr<int>(h, "perm"), h->perm.data(), sizeof(int) * h->M_eff,
@@ -354,12 +376,14 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         if ((s = dev_alloc(h, "Et_lo", ecount * 2, false)) != MHC_OK) return s;
     } else {
         if ((s = dev_alloc(h, "Et32", ecount * 4, false)) != MHC_OK) return s;
-        if ((s = dev_alloc(h, "R", sizeof(float) * h->B_rows * h->M_pad, false)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "R", sizeof(float) * h->B_rows * h->M_pad * (h->dir ? 3 : 1), false)) != MHC_OK)
+            return s;
     }
-    launch_prepare_modes(dptr<float>(h, "Eraw"), MHC_F32, MHC_MODE_MAJOR, h->D_ld, h->D, h->M_eff,
-                         dptr<int>(h, "perm"), h->e_exp, h->split, dptr<void>(h, "Et_hi"),
-                         dptr<void>(h, "Et_lo"), dptr<float>(h, "Et32"), h->D_ld, h->M_pad,
-                         h->stream);
+    // Eraw is already in the stored column order (direction-major with the split)
+    launch_prepare_modes(dptr<float>(h, "Eraw"), MHC_F32, MHC_MODE_MAJOR, h->D_ld,
+                         h->dir ? h->D_ld : h->D, h->M_eff, dptr<int>(h, "perm"), h->e_exp,
+                         h->split, dptr<void>(h, "Et_hi"), dptr<void>(h, "Et_lo"),
+                         dptr<float>(h, "Et32"), h->D_ld, h->M_pad, 0, h->stream);
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
 
@@ -373,6 +397,7 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         P.partials = dptr<float>(h, "partials");
         P.n_slots = (int)h->n_slots;
         P.n_kb = (int)(h->D_ld / c.bk);
+        P.dir_seg_kb = h->dir ? (int)(h->N_pad / c.bk) : 0;
         h->tcp.sched = nullptr;
         h->tcp.cta_begin = nullptr;
         h->tcp.n_prob = 1;
@@ -386,12 +411,15 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
 
 mhc_status set_tc_config(mhc_handle *h, const TcConfig &c) {
     if (!tc_config_supported(c)) return fail(h, MHC_ERR_INVALID_ARG, "unsupported tile configuration");
+    if (h->dir && !dir_config_ok(c))
+        return fail(h, MHC_ERR_INVALID_ARG, "the direction split needs a one-SM 128-column tile (tile_config 3 or 4)");
     const bool remap = h->bins_ready && (c.bn != h->tc.bn || c.bk != h->tc.bk || c.pair != h->tc.pair);
     h->tc = c;
     if (remap) {
         TcProblem &P = h->tcp.prob[0];
         if (encode_maps(h, c, P)) return fail(h, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         P.n_kb = (int)(h->D_ld / c.bk);
+        P.dir_seg_kb = h->dir ? (int)(h->N_pad / c.bk) : 0;
         h->tcp.idesc = idesc_f16(h->split == SPLIT_BF16 ? 1u : 0u, (c.pair ? 2 : 1) * TC_BM, (uint32_t)c.bn);
     }
     return MHC_OK;
@@ -401,12 +429,26 @@ mhc_status set_tc_config(mhc_handle *h, const TcConfig &c) {
 mhc_status run_projection(mhc_handle *h, int K) {
     if (h->M_eff == 0) {
         MHC_CUDA(h, cudaMemsetAsync(dptr<float>(h, "partials"), 0,
-                                    sizeof(float) * K * 3 * h->n_slots, h->stream));
+                                    sizeof(float) * K * 3 * slot_stride(h), h->stream));
+        return MHC_OK;
+    }
+    if (!is_tc(h) && h->dir) {
+        // one product per direction segment of d, then Xdot = sum over segments
+        const size_t rstride = (size_t)h->B_rows * h->M_pad;
+        for (int b = 0; b < 3; ++b)
+            launch_sgemm(dptr<float>(h, "Et32") + b * h->N_pad, dptr<float>(h, "Bt32") + b * h->N_pad,
+                         dptr<float>(h, "R") + b * rstride, (int)h->N_pad, (int)h->D_ld,
+                         (int)h->M_pad, 4 * K, h->stream);
+        launch_fp32_dir_epilogue(dptr<float>(h, "R"), rstride, (int)h->M_pad, K,
+                                 dptr<int>(h, "mode_bin"), dptr<int>(h, "mode_slot"),
+                                 dptr<float>(h, "partials"), (int)h->n_slots, h->stream);
+        h->launches += 4;
+        MHC_CUDA(h, cudaGetLastError());
         return MHC_OK;
     }
     if (!is_tc(h)) {
         launch_sgemm(dptr<float>(h, "Et32"), dptr<float>(h, "Bt32"), dptr<float>(h, "R"),
-                     (int)h->D_ld, (int)h->M_pad, 4 * K, h->stream);
+                     (int)h->D_ld, (int)h->D_ld, (int)h->M_pad, 4 * K, h->stream);
         launch_fp32_bin_epilogue(dptr<float>(h, "R"), (int)h->M_pad, K, dptr<int>(h, "mode_bin"),
                                  dptr<int>(h, "mode_slot"), dptr<float>(h, "partials"),
                                  (int)h->n_slots, h->stream);
@@ -438,6 +480,7 @@ mhc_status autotune(mhc_handle *h, int K) {
     float best = 1e30f;
     TcConfig best_c = h->tc;
     for (const TcConfig &c : TC_CONFIGS) {
+        if (h->dir && !dir_config_ok(c)) continue;
         mhc_status s = set_tc_config(h, c);
         if (s != MHC_OK) return s;
         if ((s = run_projection(h, K)) != MHC_OK) return s;   // warm-up
@@ -489,6 +532,7 @@ mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
     a.Jtot = dptr<double>(h, "Jtot");
     a.Jring = (h->prm.flags & MHC_FLAG_GKMA) ? dptr<double>(h, "Jring") : nullptr;
     a.R = h->R_ring;
+    a.npad = h->dir ? (int)h->N_pad : 0;
     launch_pack(a, h->stream);
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
@@ -497,13 +541,13 @@ mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
 
 // Kernels that close a push: bin finish + HNEMA sums, GKMA lag correlation, step counter.
 mhc_status finish_kernels(mhc_handle *h, int K) {
-    launch_bin_finish(dptr<float>(h, "partials"), (int)h->n_slots, dptr<int>(h, "slot_begin"), h->B,
-                      K, dptr<float>(h, "Jb"), dptr<double>(h, "hsum"), dptr<double>(h, "Jtot"),
-                      dptr<double>(h, "Jsum"), h->stream);
+    launch_bin_finish(dptr<float>(h, "partials"), (int)slot_stride(h), dptr<int>(h, "slot_begin"),
+                      (int)n_out_bins(h), K, dptr<float>(h, "Jb"), dptr<double>(h, "hsum"),
+                      dptr<double>(h, "Jtot"), dptr<double>(h, "Jsum"), h->stream);
     h->launches++;
     if (h->prm.flags & MHC_FLAG_GKMA) {
         launch_lag_corr(dptr<float>(h, "Jb"), dptr<double>(h, "Jring"), h->R_ring,
-                        dptr<double>(h, "Csum"), K, h->B, h->prm.n_lags, h->steps,
+                        dptr<double>(h, "Csum"), K, (int)n_out_bins(h), h->prm.n_lags, h->steps,
                         dptr<long long>(h, "steps_dev"), h->stream);
         h->launches++;
     }
@@ -641,6 +685,10 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
         return fail(nullptr, MHC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
     if (p->tile_config < 0 || p->tile_config > TC_NUM_CONFIGS)
         return fail(nullptr, MHC_ERR_INVALID_ARG, "tile_config must be in [0, %d]", TC_NUM_CONFIGS);
+    if ((p->flags & MHC_FLAG_DIRECTION) && p->tile_config > 0 &&
+        !dir_config_ok(TC_CONFIGS[p->tile_config - 1]))
+        return fail(nullptr, MHC_ERR_INVALID_ARG,
+                    "MHC_FLAG_DIRECTION needs tile_config 0, 3 or 4 (one-SM 128-column tiles)");
     if (!(p->dt_ps > 0) || !(p->T_K > 0) || !(p->V_A3 > 0))
         return fail(nullptr, MHC_ERR_INVALID_ARG, "dt_ps, T_K and V_A3 must be positive");
     int ndev = 0;
@@ -664,7 +712,9 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
     h->cc_minor = prop.minor;
     h->split = p->precision == MHC_PREC_FP32 ? SPLIT_FP32
                : p->precision == MHC_PREC_BF16X3 ? SPLIT_BF16 : SPLIT_FP16;
+    h->dir = (p->flags & MHC_FLAG_DIRECTION) != 0;
     if (p->tile_config > 0) h->tc = TC_CONFIGS[p->tile_config - 1];
+    else if (h->dir) h->tc = TC_CONFIGS[2];
     if ((e = cudaSetDevice(p->device)) != cudaSuccess) {
         delete h;
         return fail(nullptr, MHC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -718,7 +768,10 @@ mhc_status mhc_set_modes(mhc_handle *h, int64_t n_atoms, int64_t n_modes, const 
     h->N = n_atoms;
     h->D = D;
     h->M_in = n_modes;
-    h->D_ld = round_up(D, 64);
+    // direction split: three segments of N_pad columns, N_pad a multiple of the 128-element
+    // promotion chunk so that no chunk straddles two directions
+    h->N_pad = h->dir ? round_up(n_atoms, 128) : 0;
+    h->D_ld = h->dir ? 3 * h->N_pad : round_up(D, 64);
     h->mass.assign(mass_amu, mass_amu + n_atoms);
     if (freq_THz) h->freq.assign(freq_THz, freq_THz + n_modes);
     else h->freq.clear();
@@ -784,7 +837,7 @@ mhc_status mhc_set_modes(mhc_handle *h, int64_t n_atoms, int64_t n_modes, const 
     const int64_t Mraw = round_up(n_modes, 32);
     if ((s = dev_alloc(h, "Eraw", sizeof(float) * Mraw * h->D_ld, false)) != MHC_OK) return s;
     launch_prepare_modes(Edev, dtype, layout, ld, D, n_modes, dptr<int>(h, "perm"), 0, SPLIT_FP32,
-                         nullptr, nullptr, dptr<float>(h, "Eraw"), h->D_ld, Mraw, h->stream);
+                         nullptr, nullptr, dptr<float>(h, "Eraw"), h->D_ld, Mraw, h->N_pad, h->stream);
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
     MHC_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -894,7 +947,7 @@ mhc_status mhc_sync(mhc_handle *h) {
 mhc_status mhc_read_binned_current(mhc_handle *h, float *out, int32_t where) {
     if (!h || !out) return h ? fail(h, MHC_ERR_INVALID_ARG, "null output") : MHC_ERR_INVALID_ARG;
     if (h->K_last == 0) return fail(h, MHC_ERR_INVALID_ARG, "nothing pushed yet");
-    return copy_out(h, out, dptr<float>(h, "Jb"), sizeof(float) * h->K_last * h->B * 3, where);
+    return copy_out(h, out, dptr<float>(h, "Jb"), sizeof(float) * h->K_last * n_out_bins(h) * 3, where);
 }
 
 mhc_status mhc_read_total_current(mhc_handle *h, double *out, int32_t where) {
@@ -907,13 +960,13 @@ mhc_status mhc_read_hnema(mhc_handle *h, double *kappa, double *mean_J, int32_t 
     if (!h) return MHC_ERR_INVALID_ARG;
     if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "no bins");
     mhc_status s;
-    const size_t n = (size_t)h->B * 3;
+    const size_t n = (size_t)n_out_bins(h) * 3;
     if ((s = dev_alloc(h, "hn_out", sizeof(double) * 2 * n, false)) != MHC_OK) return s;
     const double fe = std::sqrt(h->prm.F_e[0] * h->prm.F_e[0] + h->prm.F_e[1] * h->prm.F_e[1] +
                                 h->prm.F_e[2] * h->prm.F_e[2]);
     const double coef = fe > 0 ? WMK_PER_EV_PS_A_K / (h->prm.T_K * h->prm.V_A3 * fe) : 0.0;
     double *dm = dptr<double>(h, "hn_out"), *dk = dm + n;
-    launch_hnema_finalize(dptr<double>(h, "hsum"), h->B, h->steps, coef, dm, dk, h->stream);
+    launch_hnema_finalize(dptr<double>(h, "hsum"), (int)n_out_bins(h), h->steps, coef, dm, dk, h->stream);
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
     if (kappa && (s = copy_out(h, kappa, dk, sizeof(double) * n, where)) != MHC_OK) return s;
@@ -928,7 +981,7 @@ mhc_status mhc_read_corr(mhc_handle *h, double *corr_sum, int64_t *count, int32_
     const int L = h->prm.n_lags;
     mhc_status s;
     if (corr_sum && (s = copy_out(h, corr_sum, dptr<double>(h, "Csum"),
-                                  sizeof(double) * h->B * 9 * L, where)) != MHC_OK)
+                                  sizeof(double) * n_out_bins(h) * 9 * L, where)) != MHC_OK)
         return s;
     if (count) {
         if ((s = dev_alloc(h, "counts", sizeof(long long) * L, false)) != MHC_OK) return s;
@@ -946,12 +999,12 @@ mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, do
     if (!(h->prm.flags & MHC_FLAG_GKMA) || !h->bins_ready)
         return fail(h, MHC_ERR_INVALID_ARG, "GKMA is not enabled or no bins");
     const int L = h->prm.n_lags;
-    const size_t rows = (size_t)h->B * 9;
+    const size_t rows = (size_t)n_out_bins(h) * 9;
     mhc_status s;
     if ((s = dev_alloc(h, "gk_out", sizeof(double) * rows * (L + 1), false)) != MHC_OK) return s;
     double *dk = dptr<double>(h, "gk_out"), *dw = dk + rows * L;
     const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
-    launch_gk_kappa(dptr<double>(h, "Csum"), h->B, L, h->steps, coef * h->prm.dt_ps, tau_lo, tau_hi,
+    launch_gk_kappa(dptr<double>(h, "Csum"), (int)n_out_bins(h), L, h->steps, coef * h->prm.dt_ps, tau_lo, tau_hi,
                     h->prm.dt_ps, dk, dw, h->stream);
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
@@ -1031,10 +1084,12 @@ mhc_status mhc_reset(mhc_handle *h) {
     return s;
 }
 
-// Blob: header {magic, B, L, k_max, R_ring, steps} then hsum[B*3], Jsum[3], Csum[B*9*L], Jring[R*3].
+// Blob: header {magic, rows, L, k_max, R_ring, kind, steps, M_eff} then hsum[rows*3], Jsum[3],
+// Csum[rows*9*L], Jring[R*3]; rows = B (3 B with the direction split), kind = GKMA bit 0,
+// direction split bit 1.
 struct StateHeader {
     uint32_t magic;
-    int32_t B, L, k_max, R_ring, gkma;
+    int32_t B, L, k_max, R_ring, kind;
     int64_t steps, M_eff;
 };
 
@@ -1042,8 +1097,9 @@ mhc_status mhc_state_size(mhc_handle *h, size_t *bytes) {
     if (!h || !bytes) return MHC_ERR_INVALID_ARG;
     if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "no bins");
     const bool g = h->prm.flags & MHC_FLAG_GKMA;
-    *bytes = sizeof(StateHeader) + sizeof(double) * (h->B * 3 + 3) +
-             (g ? sizeof(double) * ((size_t)h->B * 9 * h->prm.n_lags + (size_t)h->R_ring * 3) : 0);
+    const size_t nb = (size_t)n_out_bins(h);
+    *bytes = sizeof(StateHeader) + sizeof(double) * (nb * 3 + 3) +
+             (g ? sizeof(double) * (nb * 9 * h->prm.n_lags + (size_t)h->R_ring * 3) : 0);
     return MHC_OK;
 }
 
@@ -1055,14 +1111,16 @@ mhc_status mhc_get_state(mhc_handle *h, void *blob, size_t bytes) {
     if ((s = mhc_sync(h)) != MHC_OK) return s;
     auto *hd = static_cast<StateHeader *>(blob);
     const bool g = h->prm.flags & MHC_FLAG_GKMA;
-    *hd = StateHeader{STATE_MAGIC, h->B, h->prm.n_lags, h->prm.k_max, h->R_ring, g ? 1 : 0, h->steps, h->M_eff};
+    const size_t nb = (size_t)n_out_bins(h);
+    *hd = StateHeader{STATE_MAGIC, (int32_t)nb, h->prm.n_lags, h->prm.k_max, h->R_ring,
+                      (g ? 1 : 0) | (h->dir ? 2 : 0), h->steps, h->M_eff};
     char *p = static_cast<char *>(blob) + sizeof(StateHeader);
-    MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "hsum"), sizeof(double) * h->B * 3, cudaMemcpyDeviceToHost));
-    p += sizeof(double) * h->B * 3;
+    MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "hsum"), sizeof(double) * nb * 3, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * nb * 3;
     MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Jsum"), sizeof(double) * 3, cudaMemcpyDeviceToHost));
     p += sizeof(double) * 3;
     if (g) {
-        const size_t nc = (size_t)h->B * 9 * h->prm.n_lags;
+        const size_t nc = nb * 9 * h->prm.n_lags;
         MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Csum"), sizeof(double) * nc, cudaMemcpyDeviceToHost));
         p += sizeof(double) * nc;
         MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Jring"), sizeof(double) * h->R_ring * 3, cudaMemcpyDeviceToHost));
@@ -1077,17 +1135,19 @@ mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes) {
     if (!blob || bytes < need) return fail(h, MHC_ERR_STATE, "state blob too small");
     const auto *hd = static_cast<const StateHeader *>(blob);
     const bool g = h->prm.flags & MHC_FLAG_GKMA;
-    if (hd->magic != STATE_MAGIC || hd->B != h->B || hd->L != h->prm.n_lags || hd->k_max != h->prm.k_max ||
-        hd->R_ring != h->R_ring || hd->gkma != (g ? 1 : 0) || hd->M_eff != h->M_eff || hd->steps < 0)
+    const size_t nb = (size_t)n_out_bins(h);
+    if (hd->magic != STATE_MAGIC || hd->B != (int32_t)nb || hd->L != h->prm.n_lags ||
+        hd->k_max != h->prm.k_max || hd->R_ring != h->R_ring ||
+        hd->kind != ((g ? 1 : 0) | (h->dir ? 2 : 0)) || hd->M_eff != h->M_eff || hd->steps < 0)
         return fail(h, MHC_ERR_STATE, "state blob does not match this handle's modes/bins/lags/k_max");
     MHC_CUDA(h, cudaStreamSynchronize(h->stream));
     const char *p = static_cast<const char *>(blob) + sizeof(StateHeader);
-    MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "hsum"), p, sizeof(double) * h->B * 3, cudaMemcpyHostToDevice));
-    p += sizeof(double) * h->B * 3;
+    MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "hsum"), p, sizeof(double) * nb * 3, cudaMemcpyHostToDevice));
+    p += sizeof(double) * nb * 3;
     MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Jsum"), p, sizeof(double) * 3, cudaMemcpyHostToDevice));
     p += sizeof(double) * 3;
     if (g) {
-        const size_t nc = (size_t)h->B * 9 * h->prm.n_lags;
+        const size_t nc = nb * 9 * h->prm.n_lags;
         MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Csum"), p, sizeof(double) * nc, cudaMemcpyHostToDevice));
         p += sizeof(double) * nc;
         MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Jring"), p, sizeof(double) * h->R_ring * 3, cudaMemcpyHostToDevice));
@@ -1256,6 +1316,7 @@ mhc_status mhc_group_create(mhc_group **out, mhc_handle *const *handles, int32_t
         if (!h) return fail(h0, MHC_ERR_INVALID_ARG, "handle %d is null", j);
         if (!h->bins_ready) return fail(h0, MHC_ERR_INVALID_ARG, "handle %d has no modes/bins", j);
         if (!is_tc(h)) return fail(h0, MHC_ERR_UNSUPPORTED, "grouped launches need a tensor-core precision");
+        if (h->dir) return fail(h0, MHC_ERR_UNSUPPORTED, "grouped launches do not take the direction split");
         if (h->prm.device != h0->prm.device || h->stream != h0->stream || h->split != h0->split)
             return fail(h0, MHC_ERR_INVALID_ARG, "handle %d differs in device, stream or precision", j);
         for (int q = 0; q < j; ++q)

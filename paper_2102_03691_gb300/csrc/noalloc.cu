@@ -150,7 +150,7 @@ extern "C" mhc_status mhc_binned_current_noalloc(int32_t n_atoms, int32_t n_mode
                                             reinterpret_cast<float *>(s + o_sqm),
                                             reinterpret_cast<float *>(s + o_isqm), status);
     launch_prepare_modes(E, MHC_F32, MHC_MODE_MAJOR, ld, D, M, perm, 0, SPLIT_FP32, nullptr,
-                         nullptr, Et32, D_ld, M_pad, st);
+                         nullptr, Et32, D_ld, M_pad, 0, st);
     PackArgs a{};
     a.v = v;
     a.W = W;
@@ -164,7 +164,8 @@ extern "C" mhc_status mhc_binned_current_noalloc(int32_t n_atoms, int32_t n_mode
     a.col_scale = reinterpret_cast<float *>(s + o_cs);
     a.Jtot = J;
     launch_pack(a, st);
-    launch_sgemm(Et32, Bt32, reinterpret_cast<float *>(s + o_R), (int)D_ld, (int)M_pad, 4 * K, st);
+    launch_sgemm(Et32, Bt32, reinterpret_cast<float *>(s + o_R), (int)D_ld, (int)D_ld, (int)M_pad,
+                 4 * K, st);
     launch_fp32_bin_epilogue(reinterpret_cast<float *>(s + o_R), (int)M_pad, K, mode_bin, mode_slot,
                              partials, (int)M_pad, st);
     launch_bin_finish(partials, (int)M_pad, slot_begin, n_bins, K, Jb, hsum, J, jsum, st);

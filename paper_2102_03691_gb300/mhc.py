@@ -24,6 +24,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 F32, F64 = 0, 1
 DOF_MAJOR, MODE_MAJOR = 0, 1
 FLAG_GKMA, FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_TEST_STALL = 0x1, 0x2, 0x4, 0x8
+FLAG_DIRECTION = 0x10
 
 # Every entry point declared in include/mhc.h.
 EXPORTS = (
@@ -299,12 +300,17 @@ def _current_stream(device: int):
 
 
 class ModalHeatCurrent:
-    """One system: eigenvectors, bins and the GKMA / HNEMA accumulators (see include/mhc.h)."""
+    """One system: eigenvectors, bins and the GKMA / HNEMA accumulators (see include/mhc.h).
+
+    With direction=True (MHC_FLAG_DIRECTION) every per-bin result gains a leading axis for the
+    direction b of the atoms' motion: binned current [K][3][B][3], HNEMA [3][B][3], GKMA
+    [3][B][3][3][L]; summing that axis gives the results without the split."""
 
     def __init__(self, precision: str = "bf16x3", k_max: int = 256, n_lags: int = 0,
                  gkma: bool | None = None, dt_ps: float = 0.01, T_K: float = 300.0,
                  V_A3: float = 1.0, F_e=(1e-5, 0.0, 0.0), device: int = 0, stream=None,
-                 tile_config: int = 0, ortho_probe: int = -1, flags: int = 0):
+                 tile_config: int = 0, ortho_probe: int = -1, flags: int = 0,
+                 direction: bool = False):
         self._L = load()
         p = MhcParams()
         self._L.mhc_default_params(ctypes.byref(p))
@@ -315,7 +321,7 @@ class ModalHeatCurrent:
         p.n_lags = n_lags
         p.precision = PRECISIONS[precision]
         gk = (n_lags > 0) if gkma is None else gkma
-        p.flags = flags | (FLAG_GKMA if gk else 0)
+        p.flags = flags | (FLAG_GKMA if gk else 0) | (FLAG_DIRECTION if direction else 0)
         p.tile_config = tile_config
         p.ortho_probe = ortho_probe
         p.dt_ps, p.T_K, p.V_A3 = dt_ps, T_K, V_A3
@@ -331,6 +337,7 @@ class ModalHeatCurrent:
         self.B = 0
         self.N = 0
         self._lastK = 0
+        self.direction = bool(p.flags & FLAG_DIRECTION)
 
     # ------------------------------------------------------------------ plumbing
     def _check(self, st: int):
@@ -406,9 +413,13 @@ class ModalHeatCurrent:
         self._check(self._L.mhc_sync(self._h))
 
     # ------------------------------------------------------------------ reads
+    def _rows(self):
+        """Leading shape of a per-bin result: (B,) or (3, B) with the direction split."""
+        return (3, self.B) if self.direction else (self.B,)
+
     def read_binned_current(self, out=None):
         if out is None:
-            out = np.empty((self._lastK, self.B, 3), np.float32)
+            out = np.empty((self._lastK, *self._rows(), 3), np.float32)
         p, where, keep = _ptr(out, np.float32)
         self._check(self._L.mhc_read_binned_current(self._h, p, where))
         return keep
@@ -421,8 +432,8 @@ class ModalHeatCurrent:
         return keep
 
     def read_hnema(self):
-        kap = np.empty((self.B, 3))
-        mean = np.empty((self.B, 3))
+        kap = np.empty((*self._rows(), 3))
+        mean = np.empty((*self._rows(), 3))
         self._check(self._L.mhc_read_hnema(self._h, kap.ctypes.data_as(ctypes.c_void_p),
                                            mean.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
         return mean, kap
@@ -434,7 +445,7 @@ class ModalHeatCurrent:
 
     def read_corr(self):
         L_ = self.params.n_lags
-        C = np.empty((self.B, 3, 3, L_))
+        C = np.empty((*self._rows(), 3, 3, L_))
         cnt = np.empty(L_, np.int64)
         self._check(self._L.mhc_read_corr(self._h, C.ctypes.data_as(ctypes.c_void_p),
                                           cnt.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
@@ -442,8 +453,8 @@ class ModalHeatCurrent:
 
     def read_kappa_gk(self, tau_lo: float, tau_hi: float):
         L_ = self.params.n_lags
-        kt = np.empty((self.B, 3, 3, L_))
-        kw = np.empty((self.B, 3, 3))
+        kt = np.empty((*self._rows(), 3, 3, L_))
+        kw = np.empty((*self._rows(), 3, 3))
         self._check(self._L.mhc_read_kappa_gk(self._h, kt.ctypes.data_as(ctypes.c_void_p), tau_lo,
                                               tau_hi, kw.ctypes.data_as(ctypes.c_void_p),
                                               MEM_HOST))
