@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--basis", default="qr", choices=["qr", "gaussian"],
                     help="qr: orthonormal E from a seeded QR; gaussian: seeded N(0, 1/3N) "
                          "entries (same sizes and work, for tools that cannot load torch.linalg)")
+    ap.add_argument("--direction", action="store_true",
+                    help="direction-resolved split J_n^{ab} (every per-bin output x 3, same "
+                         "tensor work; one-SM 128-column tiles)")
     return ap.parse_args()
 
 
@@ -263,7 +266,8 @@ def config_dict(w, args, precision):
     return {"workload": args.workload, "N_atoms": w["N"], "M_modes": w["M"], "K_steps_per_block": w["K"],
             "bins": w["B"], "lags": w["L"], "gkma": bool(w["gkma"]), "precision": precision,
             "l2": "inputs larger than L2 (eigenvectors streamed every step; 8-block input pool)",
-            "basis": getattr(args, "basis", "qr")}
+            "basis": getattr(args, "basis", "qr"),
+            "direction_split": bool(getattr(args, "direction", False))}
 
 
 
@@ -402,7 +406,7 @@ def run_shc(args):
     host_pool = [tuple(torch.from_numpy(a).pin_memory() for a in tr.next_block(K)) for _ in range(P)]
     dev_pool = [(a.to(dev), b.to(dev)) for a, b in host_pool]
     s = SpectralHeatCurrent(N, nc, k_max=K, dt_ps=0.002, T_K=300.0, V_A3=V, F_e=(1e-5, 0.0, 0.0),
-                            device=local)
+                            device=local, precision=args.precision)
     f = np.linspace(0.0, 60.0, 241)
     out = torch.empty((9, f.size), dtype=torch.float64, device=dev)
     unit = "atom·lag·steps/s"
@@ -433,6 +437,14 @@ def run_shc(args):
     for i in range(n_e2e):
         step(i, host=True)
     e2e_max, e2e_units = aggregate(time.perf_counter() - t0, float(N) * nc * K * n_e2e, world)
+    # the correlation kernel alone (CUDA events around each launch on the handle's stream)
+    s.set_profile(True)
+    n_prof = max(3, min(args.steps, 200))
+    for i in range(n_prof):
+        step(i)
+    torch.cuda.synchronize()
+    kms, kn = s.kernel_time()
+    s.set_profile(False)
     if rank != 0:
         return
     cpu = None
@@ -446,26 +458,49 @@ def run_shc(args):
         cpu = {"value": float(N) * min(nc, S) * S / el, "unit": unit, "cores": oracle.num_threads(),
                "kind": "oracle", "sample": f"{S} samples x {min(nc, S)} lags x {N} atoms, {el:.1f} s"}
     value = units / el_max
-    flops_step = 2.0 * 9 * N * nc * K
+    flops_step = 2.0 * 9 * N * nc * K            # Eq. 21 by its definition: 9 products per atom, lag, step
     props = torch.cuda.get_device_properties(dev)
-    peaks, _ = measured_peaks()
+    peaks, peak_src = measured_peaks()
     fp32_peak = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    k_launch_s = kms / 1e3 / kn if kn else None
+    if args.precision == "fp32":
+        roof = {"bound": "alu", "kernel": "shc_corr_kernel (FP32 CUDA cores)",
+                "achieved": flops_step / k_launch_s / 1e12, "unit": "TFLOP/s", "peak": fp32_peak,
+                "peak_source": "derived: SMs x 128 FP32 FMA/clk x 2 flop x max SM clock"}
+    else:
+        # 128 x 128 tiles touching the band 0 <= t - tau < nc of a block at t0 = multiple of K
+        t0s, Tt = 4 * K, 128
+        pairs = 0
+        for q in range((K + Tt - 1) // Tt):
+            tmin, tmax = t0s + q * Tt, t0s + min((q + 1) * Tt, K) - 1
+            pairs += tmax // Tt - max(0, (tmin - nc + 1) // Tt) + 1
+        n_pad = (N + 127) // 128 * 128
+        executed = 3 * 2.0 * Tt * Tt * n_pad * 9 * pairs
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        roof = {"bound": "tensor", "kernel": "shc_tc_kernel (banded contraction, split 16-bit)",
+                "achieved": flops_step / k_launch_s / 1e12, "unit": "TFLOP/s", "peak": peak,
+                "peak_source": f"{peak_src} bf16 dense, sustained; fp16 has the same dense rate",
+                "executed_tflops": executed / k_launch_s / 1e12,
+                "executed_frac": executed / k_launch_s / 1e12 / peak,
+                "note": "achieved counts the 2*9*N*nc*K flops of the definition; the tensor cores "
+                        f"execute {executed / flops_step:.2f}x that (3 split products, 128 x 128 tiles "
+                        "over the band)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel_ms_per_launch"] = 1e3 * k_launch_s
+    roof["flops_per_launch"] = flops_step
+    roof["traffic"] = None
     print(json.dumps({
         "metric": "SHC correlation atom·lag·steps/s", "value": value, "unit": unit,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (FP64 lag sums)", "data": "synthetic",
+        "vs_baseline": None, "dtype": args.precision + " (FP64 lag sums)", "data": "synthetic",
         "config": {"workload": "shc_si_n8000", "N_atoms": N, "lags": nc, "K_steps_per_block": K,
                    "l2": "inputs larger than L2 (145 MB virial ring + 8-block pool)"},
-        "roofline": {"bound": "alu", "achieved": flops_step / (el_max / args.steps) / 1e12 * world,
-                     "unit": "TFLOP/s", "peak": fp32_peak,
-                     "frac": flops_step / (el_max / args.steps) / 1e12 * world / fp32_peak,
-                     "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x max SM clock",
-                     "note": "whole step (correlation, FP64 tile reduction, spectrum) in FP32 FMA flops"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_units / e2e_max, "unit": unit, "h2d_bytes_per_step": 48 * N * K,
                 "d2h_bytes_per_step": 8 * 9 * f.size, "steps": n_e2e},
-        "clocks": clk, "gpu_launches": 3 * args.steps * world,
+        "clocks": clk, "gpu_launches": (3 if args.precision == "fp32" else 4) * args.steps * world,
     }), flush=True)
     s.close()
 
@@ -525,13 +560,14 @@ def main():
     def make(precision):
         h = ModalHeatCurrent(precision=precision, k_max=K, n_lags=L, dt_ps=w["dt_ps"],
                              T_K=w["T_K"], V_A3=V, F_e=w["Fe"], device=local,
-                             tile_config=args.tile_config)
+                             tile_config=args.tile_config, direction=args.direction)
         h.set_modes(E, mass, f)
         h.set_bins_uniform(w["f"][0], w["f"][1], B)
         return h
 
     h = make(args.precision)
-    kap_w = torch.empty(B * 9 if L else B * 3, dtype=torch.float64, device=dev)
+    rows = B * (3 if args.direction else 1)
+    kap_w = torch.empty(rows * 9 if L else rows * 3, dtype=torch.float64, device=dev)
 
     def step(hh, i, host=False):
         v, W = (host_pool if host else dev_pool)[i % POOL]
@@ -599,7 +635,7 @@ def main():
     e2e_el = time.perf_counter() - t0
     e2e_max, e2e_units = aggregate(e2e_el, float(M) * N * K * n_e2e, world)
     h2d = 4 * K * N * 12
-    d2h = 8 * (B * 9 if L else B * 3)
+    d2h = 8 * (rows * 9 if L else rows * 3)
 
     # ---- FP32 CUDA-core path on the same workload (comparison)
     fp32 = None

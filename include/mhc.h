@@ -291,7 +291,13 @@ mhc_status mhc_group_read_hnema(mhc_group *g, double *kappa, double *mean_J, int
  * Summing a tensor pair over b gives the a component of Eq. 21 / 23; at lag 0 it is the
  * time average of the total heat current (Eq. 10).  v, W as for mhc_push.
  *   n_lags  L correlation lags, L <= 4096 (the paper uses 250 lags of 2 fs); k_max <= 1024.
- * Errors as for the modal handle; messages through mhc_shc_last_error.
+ * Arithmetic (mhc_shc_set_precision, default MHC_PREC_FP16X3): the tensor-core precisions
+ * compute each block as a banded contraction over the atoms, G_b[(a,tau)][t] =
+ * sum_i W_i^{ab}(tau) v_i^b(t), in 128 x 128 tiles with split 16-bit operands (one
+ * power-of-two scale per row) and FP32 accumulation, whose diagonals t - tau = l are the
+ * lag sums; MHC_PREC_FP32 runs FP32 FMAs on the CUDA cores.  Lag sums are FP64 in both.
+ * Errors as for the modal handle; messages through mhc_shc_last_error.  A kernel that waited
+ * too long on a barrier is reported as MHC_ERR_TIMEOUT by the next host read.
  */
 typedef struct mhc_shc mhc_shc;
 mhc_status mhc_shc_create(mhc_shc **s, int32_t device, void *stream, int64_t n_atoms,
@@ -299,6 +305,14 @@ mhc_status mhc_shc_create(mhc_shc **s, int32_t device, void *stream, int64_t n_a
                           const double *F_e);
 void mhc_shc_destroy(mhc_shc *s);
 const char *mhc_shc_last_error(const mhc_shc *s);
+/* Select the arithmetic (mhc_precision) before the first push; INVALID_ARG afterwards.
+ * Reallocates the handle's ring buffers. */
+mhc_status mhc_shc_set_precision(mhc_shc *s, int32_t precision);
+/* CUDA-event timing of the correlation kernel of each push while on != 0 (restarts the
+ * count); mhc_shc_kernel_time returns the total ms and launches since the last call and
+ * resets them.  INVALID_ARG when profiling is off. */
+mhc_status mhc_shc_set_profile(mhc_shc *s, int32_t on);
+mhc_status mhc_shc_kernel_time(mhc_shc *s, double *ms, int64_t *launches);
 /* One block of K samples (host or device memory). */
 mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, int32_t where);
 /* Raw sums Ksum [9][L] (float64) and origin counts [L] (int64); either may be NULL. */

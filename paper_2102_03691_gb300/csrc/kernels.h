@@ -127,6 +127,36 @@ __host__ __device__ inline uint32_t tc_tile_id(int prob, int mt, int ct) {
     return ((uint32_t)prob << 28) | ((uint32_t)ct << 20) | (uint32_t)mt;
 }
 
+// ---------------------------------------------------------------- SHC on the tensor cores
+// Tile pairs (tau tile p, step tile q) of one block, 128 x 128 each; see k_shc_tc.cu.
+constexpr int SHC_TC_MAX_PAIRS = 288;
+constexpr int SHC_TC_TILE = 128;
+struct ShcTcParams {
+    CUtensorMap tmA_hi, tmA_lo;   // virial ring [9 R][N_pad]: row (3a+b) R + slot, 16-bit hi/lo
+    CUtensorMap tmB_hi, tmB_lo;   // velocities [3 Kpad][N_pad]: row b Kpad + k
+    const float *scaleA;          // [9 R] 2^-s of each virial row
+    const float *scaleB;          // [3 Kpad] 2^-s of each velocity row
+    float *partials;              // [units][256] diagonal sums of each unit's tile
+    long long t0;                 // first sample of the block
+    int R, nR, Kpad, K, nc;
+    int n_pairs, splits, kb_per_split, n_kb;
+    long long wait_limit;
+    int *status;
+    uint32_t idesc;
+    int p_tile[SHC_TC_MAX_PAIRS]; // tau tile index (tau0 = 128 p, p >= 0)
+    int q_tile[SHC_TC_MAX_PAIRS]; // step tile index in the block (k0 = 128 q)
+};
+// Split/scale one block into the operands: velocities of step k to rows b Kpad + k and the
+// virials to ring rows (3a+b) R + (t0+k) mod R, with one power-of-two scale per row.
+void launch_shc_tc_pack(const float *v, const float *W, int N, int N_pad, int K, int Kpad, int R,
+                        long long t0, int split, void *A_hi, void *A_lo, void *B_hi, void *B_lo,
+                        float *scaleA, float *scaleB, cudaStream_t s);
+// One CTA per unit (pair c = 3a+b, tile pair, atom split): 9 n_pairs splits CTAs.
+cudaError_t launch_shc_tc(const ShcTcParams &p, cudaStream_t s);
+size_t shc_tc_smem_bytes();
+// Ksum[c][l] += sum over the units of pair c, in order, of their diagonal sums at lag l (FP64).
+void launch_shc_tc_reduce(const ShcTcParams &p, double *Ksum, cudaStream_t s);
+
 // ---------------------------------------------------------------- K3 .. K5
 // Jb[k][b][a] = sum of partial slots of bin b; HNEMA sums += sum_k Jb (FP64);
 // Jsum[a] += sum_k Jtot[k][a].

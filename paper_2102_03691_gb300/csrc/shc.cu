@@ -2,6 +2,8 @@
 //   Ksum^{ab}(l) += sum_{t in block} sum_i W_i^{ab}(t - l) v_i^b(t),  t - l >= 0,
 // accumulated at run time over blocks of K samples with a ring of past virials, and the
 // spectrum kappa(omega) = 2 Ktilde(omega) / (V T |F_e|) on read.
+// Two paths: the tensor-core banded contraction of k_shc_tc.cu (FP16x3 / BF16x3, default)
+// and the FP32 CUDA-core kernel below (MHC_PREC_FP32).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -13,6 +15,7 @@
 
 #include "../../include/mhc.h"
 #include "common.cuh"
+#include "kernels.h"
 
 namespace {
 
@@ -164,7 +167,8 @@ struct mhc_shc {
     int device = 0;
     cudaStream_t stream = nullptr;
     int64_t N = 0;
-    int nc = 0, nc_pad = 0, k_max = 0, R = 0, n_tiles = 0;
+    int nc = 0, nc_pad = 0, k_max = 0, R = 0, n_tiles = 0, sm_count = 0;
+    int precision = MHC_PREC_FP16X3;
     double dt = 0, T = 0, V = 0, Fe = 0;
     long long steps = 0;
     float *Wring = nullptr, *partials = nullptr, *v_stage = nullptr, *W_stage = nullptr;
@@ -172,6 +176,17 @@ struct mhc_shc {
     long long *counts = nullptr;
     size_t out_cap = 0;
     std::string err;
+    // tensor-core path: 16-bit virial ring [9 R_tc][N_pad], velocities [3 Kpad][N_pad]
+    int64_t N_pad = 0;
+    int R_tc = 0, Kpad = 0;
+    void *A_hi = nullptr, *A_lo = nullptr, *B_hi = nullptr, *B_lo = nullptr;
+    float *scaleA = nullptr, *scaleB = nullptr, *tc_partials = nullptr;
+    mhc::ShcTcParams tcp{};
+    int *status = nullptr;   // sticky device status (a bounded wait that gave up)
+    // optional CUDA-event timing of the correlation kernel
+    bool profile = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+    size_t prof_used = 0;
 };
 
 namespace {
@@ -198,6 +213,98 @@ mhc_status sfail(mhc_shc *s, mhc_status st, const char *fmt, ...) {
 
 size_t shc_smem(int K) {
     return ((size_t)SHC_ATILE * (K + SHC_LAGS - 1) * 3 + (size_t)SHC_ATILE * (K + 64)) * sizeof(float4);
+}
+
+bool shc_is_tc(const mhc_shc *s) { return s->precision != MHC_PREC_FP32; }
+
+void free_path(mhc_shc *s) {
+    for (void **q : {(void **)&s->Wring, (void **)&s->partials, &s->A_hi, &s->A_lo, &s->B_hi,
+                     &s->B_lo, (void **)&s->scaleA, (void **)&s->scaleB, (void **)&s->tc_partials}) {
+        cudaFree(*q);
+        *q = nullptr;
+    }
+}
+
+// Buffers of the selected path (zeroed: the rings start empty, padding atoms stay zero).
+cudaError_t alloc_path(mhc_shc *s) {
+    free_path(s);
+    cudaError_t e;
+    auto get = [&](void **q, size_t bytes) {
+        if ((e = cudaMalloc(q, bytes)) != cudaSuccess) return false;
+        return (e = cudaMemsetAsync(*q, 0, bytes, s->stream)) == cudaSuccess;
+    };
+    if (!shc_is_tc(s)) {
+        if (!get((void **)&s->Wring, sizeof(float) * (size_t)s->R * s->N * 9)) return e;
+        if (!get((void **)&s->partials, sizeof(float) * (size_t)s->n_tiles * 9 * s->nc_pad)) return e;
+        return cudaFuncSetAttribute(shc_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)shc_smem(s->k_max));
+    }
+    const size_t a = (size_t)9 * s->R_tc * s->N_pad * 2, b = (size_t)3 * s->Kpad * s->N_pad * 2;
+    const size_t units = std::max<size_t>((size_t)9 * mhc::SHC_TC_MAX_PAIRS, (size_t)s->sm_count);
+    if (!get(&s->A_hi, a) || !get(&s->A_lo, a) || !get(&s->B_hi, b) || !get(&s->B_lo, b) ||
+        !get((void **)&s->scaleA, sizeof(float) * 9 * s->R_tc) ||
+        !get((void **)&s->scaleB, sizeof(float) * 3 * s->Kpad) ||
+        !get((void **)&s->tc_partials, sizeof(float) * units * 256))
+        return e;
+    mhc::ShcTcParams &P = s->tcp;
+    const uint32_t T = mhc::SHC_TC_TILE;
+    if (mhc::tc_make_tmap(&P.tmA_hi, s->A_hi, (uint64_t)9 * s->R_tc, s->N_pad, s->N_pad, T, 64) ||
+        mhc::tc_make_tmap(&P.tmA_lo, s->A_lo, (uint64_t)9 * s->R_tc, s->N_pad, s->N_pad, T, 64) ||
+        mhc::tc_make_tmap(&P.tmB_hi, s->B_hi, (uint64_t)3 * s->Kpad, s->N_pad, s->N_pad, T, 64) ||
+        mhc::tc_make_tmap(&P.tmB_lo, s->B_lo, (uint64_t)3 * s->Kpad, s->N_pad, s->N_pad, T, 64))
+        return cudaErrorInvalidValue;
+    P.scaleA = s->scaleA;
+    P.scaleB = s->scaleB;
+    P.partials = s->tc_partials;
+    P.R = s->R_tc;
+    P.nR = s->R_tc / (int)T;
+    P.Kpad = s->Kpad;
+    P.nc = s->nc;
+    P.n_kb = (int)(s->N_pad / 64);
+    P.wait_limit = 2000000000ll;
+    P.status = s->status;
+    P.idesc = mhc::idesc_f16(s->precision == MHC_PREC_BF16X3 ? 1u : 0u, T, T);
+    return cudaSuccess;
+}
+
+mhc_status shc_check_status(mhc_shc *s) {
+    int st = 0;
+    if (cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return sfail(s, MHC_ERR_CUDA, "reading the device status failed");
+    if (st == mhc::DEV_TIMEOUT) return sfail(s, MHC_ERR_TIMEOUT, "a tensor-core SHC kernel gave up waiting on a barrier");
+    if (st != 0) return sfail(s, MHC_ERR_STATE, "device status word %d", st);
+    return MHC_OK;
+}
+
+long long floor_div(long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Tile pairs of the block [t0, t0 + K) that touch the band 0 <= t - tau < nc, tau >= 0,
+// and the split of the atom axis that fills the SMs.
+bool plan_tiles(mhc_shc *s, int K) {
+    mhc::ShcTcParams &P = s->tcp;
+    const long long T = mhc::SHC_TC_TILE, t0 = s->steps;
+    int n = 0;
+    for (int q = 0; q * T < K; ++q) {
+        const long long tmin = t0 + q * T, tmax = t0 + std::min<long long>((q + 1) * T, K) - 1;
+        const long long p0 = std::max<long long>(0, floor_div(tmin - s->nc + 1, T));
+        for (long long pp = p0; pp <= tmax / T; ++pp) {
+            if (n == mhc::SHC_TC_MAX_PAIRS) return false;
+            P.p_tile[n] = (int)pp;
+            P.q_tile[n] = q;
+            ++n;
+        }
+    }
+    P.n_pairs = n;
+    P.t0 = t0;
+    P.K = K;
+    const int chunks = (int)(s->N_pad / 128);
+    int splits = std::max(1, s->sm_count / (9 * n));
+    splits = std::min(splits, chunks);
+    const int per = (chunks + splits - 1) / splits;   // chunks per split
+    P.kb_per_split = 2 * per;
+    P.splits = (chunks + per - 1) / per;
+    return true;
 }
 }  // namespace
 
@@ -227,6 +334,10 @@ mhc_status mhc_shc_create(mhc_shc **out, int32_t device, void *stream, int64_t n
     s->k_max = k_max;
     s->R = k_max + s->nc_pad;   // holds every time the last lag tile reads
     s->n_tiles = (int)((n_atoms + SHC_ATILE - 1) / SHC_ATILE);
+    s->sm_count = prop.multiProcessorCount;
+    s->N_pad = (n_atoms + 127) / 128 * 128;
+    s->Kpad = (k_max + 127) / 128 * 128;
+    s->R_tc = (k_max + n_lags + 127) / 128 * 128;   // >= K + nc - 1 live samples, whole tiles
     s->dt = dt_ps;
     s->T = T_K;
     s->V = V_A3;
@@ -237,17 +348,14 @@ mhc_status mhc_shc_create(mhc_shc **out, int32_t device, void *stream, int64_t n
                      "allocation: %s", cudaGetErrorString(er));
     };
     if ((e = cudaSetDevice(device)) != cudaSuccess) return fail_free(e);
-    if ((e = cudaMalloc(&s->Wring, sizeof(float) * (size_t)s->R * n_atoms * 9)) != cudaSuccess) return fail_free(e);
-    if ((e = cudaMalloc(&s->partials, sizeof(float) * (size_t)s->n_tiles * 9 * s->nc_pad)) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMalloc(&s->status, sizeof(int))) != cudaSuccess) return fail_free(e);
+    if ((e = cudaMemsetAsync(s->status, 0, sizeof(int), s->stream)) != cudaSuccess) return fail_free(e);
+    if ((e = alloc_path(s)) != cudaSuccess) return fail_free(e);
     if ((e = cudaMalloc(&s->Ksum, sizeof(double) * 9 * n_lags)) != cudaSuccess) return fail_free(e);
     if ((e = cudaMalloc(&s->counts, sizeof(long long) * n_lags)) != cudaSuccess) return fail_free(e);
     if ((e = cudaMalloc(&s->v_stage, sizeof(float) * (size_t)k_max * n_atoms * 3)) != cudaSuccess) return fail_free(e);
     if ((e = cudaMalloc(&s->W_stage, sizeof(float) * (size_t)k_max * n_atoms * 9)) != cudaSuccess) return fail_free(e);
-    if ((e = cudaMemsetAsync(s->Wring, 0, sizeof(float) * (size_t)s->R * n_atoms * 9, s->stream)) != cudaSuccess) return fail_free(e);
     if ((e = cudaMemsetAsync(s->Ksum, 0, sizeof(double) * 9 * n_lags, s->stream)) != cudaSuccess) return fail_free(e);
-    if ((e = cudaFuncSetAttribute(shc_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)shc_smem(k_max))) != cudaSuccess)
-        return fail_free(e);
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return fail_free(e);
     *out = s;
     return MHC_OK;
@@ -256,8 +364,12 @@ mhc_status mhc_shc_create(mhc_shc **out, int32_t device, void *stream, int64_t n
 void mhc_shc_destroy(mhc_shc *s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
-    cudaFree(s->Wring);
-    cudaFree(s->partials);
+    free_path(s);
+    for (auto &e : s->prof_events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    cudaFree(s->status);
     cudaFree(s->Ksum);
     cudaFree(s->counts);
     cudaFree(s->v_stage);
@@ -267,6 +379,20 @@ void mhc_shc_destroy(mhc_shc *s) {
 }
 
 const char *mhc_shc_last_error(const mhc_shc *s) { return s ? s->err.c_str() : g_shc_create_error.c_str(); }
+
+mhc_status mhc_shc_set_precision(mhc_shc *s, int32_t precision) {
+    if (!s) return MHC_ERR_INVALID_ARG;
+    if (precision < MHC_PREC_FP32 || precision > MHC_PREC_FP16X3)
+        return sfail(s, MHC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (s->steps != 0) return sfail(s, MHC_ERR_INVALID_ARG, "the precision can only change before the first push");
+    if (precision == s->precision) return MHC_OK;
+    SHC_CUDA(s, cudaSetDevice(s->device));
+    SHC_CUDA(s, cudaStreamSynchronize(s->stream));
+    s->precision = precision;
+    SHC_CUDA(s, alloc_path(s));
+    SHC_CUDA(s, cudaStreamSynchronize(s->stream));
+    return MHC_OK;
+}
 
 mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, int32_t where) {
     if (!s) return MHC_ERR_INVALID_ARG;
@@ -278,6 +404,33 @@ mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, i
         SHC_CUDA(s, cudaMemcpyAsync(s->v_stage, v, nv * 4, cudaMemcpyHostToDevice, s->stream));
         v = s->v_stage;
     }
+    if (shc_is_tc(s)) {
+        if (where == MHC_MEM_HOST) {
+            SHC_CUDA(s, cudaMemcpyAsync(s->W_stage, W, nwf * 4, cudaMemcpyHostToDevice, s->stream));
+            W = s->W_stage;
+        }
+        if (!plan_tiles(s, K)) return sfail(s, MHC_ERR_UNSUPPORTED, "too many tile pairs for K=%d", K);
+        mhc::launch_shc_tc_pack(v, W, (int)s->N, (int)s->N_pad, K, s->Kpad, s->R_tc, s->steps,
+                                s->precision == MHC_PREC_BF16X3 ? mhc::SPLIT_BF16 : mhc::SPLIT_FP16,
+                                s->A_hi, s->A_lo, s->B_hi, s->B_lo, s->scaleA, s->scaleB, s->stream);
+        cudaEvent_t ev1 = nullptr;
+        if (s->profile) {
+            if (s->prof_used == s->prof_events.size()) {
+                cudaEvent_t a0, a1;
+                SHC_CUDA(s, cudaEventCreate(&a0));
+                SHC_CUDA(s, cudaEventCreate(&a1));
+                s->prof_events.emplace_back(a0, a1);
+            }
+            SHC_CUDA(s, cudaEventRecord(s->prof_events[s->prof_used].first, s->stream));
+            ev1 = s->prof_events[s->prof_used++].second;
+        }
+        SHC_CUDA(s, mhc::launch_shc_tc(s->tcp, s->stream));
+        if (ev1) SHC_CUDA(s, cudaEventRecord(ev1, s->stream));
+        mhc::launch_shc_tc_reduce(s->tcp, s->Ksum, s->stream);
+        SHC_CUDA(s, cudaGetLastError());
+        s->steps += K;
+        return MHC_OK;
+    }
     // this block's virials into the ring at rows (t0 + k) mod R (at most two segments)
     const size_t row = (size_t)s->N * 9 * sizeof(float);
     const cudaMemcpyKind kind = where == MHC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -288,13 +441,48 @@ mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, i
         SHC_CUDA(s, cudaMemcpyAsync(s->Wring, (const char *)W + first * row, (K - first) * row, kind, s->stream));
     (void)nwf;
     dim3 grid(s->n_tiles, s->nc_pad / SHC_LAGS);
+    cudaEvent_t ev1 = nullptr;
+    if (s->profile) {
+        if (s->prof_used == s->prof_events.size()) {
+            cudaEvent_t a0, a1;
+            SHC_CUDA(s, cudaEventCreate(&a0));
+            SHC_CUDA(s, cudaEventCreate(&a1));
+            s->prof_events.emplace_back(a0, a1);
+        }
+        SHC_CUDA(s, cudaEventRecord(s->prof_events[s->prof_used].first, s->stream));
+        ev1 = s->prof_events[s->prof_used++].second;
+    }
     shc_corr_kernel<<<grid, SHC_THREADS, shc_smem(K), s->stream>>>(v, s->Wring, s->R, (int)s->N, K,
                                                                    s->nc, s->steps, s->partials,
                                                                    s->nc_pad);
+    if (ev1) SHC_CUDA(s, cudaEventRecord(ev1, s->stream));
     shc_reduce_kernel<<<dim3((s->nc + 31) / 32, 9), RED_WARPS * 32, 0, s->stream>>>(
         s->partials, s->n_tiles, s->nc, s->nc_pad, s->Ksum);
     SHC_CUDA(s, cudaGetLastError());
     s->steps += K;
+    return MHC_OK;
+}
+
+mhc_status mhc_shc_set_profile(mhc_shc *s, int32_t on) {
+    if (!s) return MHC_ERR_INVALID_ARG;
+    s->profile = on != 0;
+    s->prof_used = 0;
+    return MHC_OK;
+}
+
+mhc_status mhc_shc_kernel_time(mhc_shc *s, double *ms, int64_t *launches) {
+    if (!s) return MHC_ERR_INVALID_ARG;
+    if (!s->profile) return sfail(s, MHC_ERR_INVALID_ARG, "profiling is off (mhc_shc_set_profile)");
+    SHC_CUDA(s, cudaStreamSynchronize(s->stream));
+    double total = 0.0;
+    for (size_t q = 0; q < s->prof_used; ++q) {
+        float t = 0.f;
+        SHC_CUDA(s, cudaEventElapsedTime(&t, s->prof_events[q].first, s->prof_events[q].second));
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = (int64_t)s->prof_used;
+    s->prof_used = 0;
     return MHC_OK;
 }
 
@@ -308,7 +496,7 @@ mhc_status mhc_shc_read_corr(mhc_shc *s, double *Ksum, int64_t *count, int32_t w
         if (where == MHC_MEM_HOST) std::memcpy(count, c.data(), sizeof(long long) * s->nc);
         else SHC_CUDA(s, cudaMemcpy(count, c.data(), sizeof(long long) * s->nc, cudaMemcpyHostToDevice));
     }
-    if (where == MHC_MEM_HOST) SHC_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (where == MHC_MEM_HOST) return shc_check_status(s);
     return MHC_OK;
 }
 
@@ -334,7 +522,7 @@ mhc_status mhc_shc_read_kappa(mhc_shc *s, const double *f_THz, int32_t n_freq, i
     SHC_CUDA(s, cudaGetLastError());
     const cudaMemcpyKind kind = where == MHC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     SHC_CUDA(s, cudaMemcpyAsync(kappa, s->out, sizeof(double) * 9 * n_freq, kind, s->stream));
-    if (where == MHC_MEM_HOST) SHC_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (where == MHC_MEM_HOST) return shc_check_status(s);
     return MHC_OK;
 }
 

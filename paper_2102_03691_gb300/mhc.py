@@ -37,7 +37,7 @@ EXPORTS = (
     "mhc_state_size", "mhc_get_state", "mhc_set_state", "mhc_group_create",
     "mhc_group_destroy", "mhc_group_push", "mhc_group_read_hnema", "mhc_binned_current_noalloc",
     "mhc_shc_create", "mhc_shc_destroy", "mhc_shc_last_error", "mhc_shc_push", "mhc_shc_read_corr",
-    "mhc_shc_read_kappa",
+    "mhc_shc_read_kappa", "mhc_shc_set_precision", "mhc_shc_set_profile", "mhc_shc_kernel_time",
 )
 
 
@@ -123,6 +123,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_shc_push.argtypes = [vp, vp, vp, i32, i32]
     L.mhc_shc_read_corr.argtypes = [vp, vp, vp, i32]
     L.mhc_shc_read_kappa.argtypes = [vp, vp, i32, i32, vp, i32]
+    L.mhc_shc_set_precision.argtypes = [vp, i32]
+    L.mhc_shc_set_profile.argtypes = [vp, i32]
+    L.mhc_shc_kernel_time.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
     L.mhc_binned_current_noalloc.argtypes = [i32, i32, vp, i64, vp, i32, vp, vp, vp, i32, vp, vp,
                                              i32, vp]
     for name in EXPORTS:
@@ -199,7 +202,7 @@ class SpectralHeatCurrent:
 
     def __init__(self, n_atoms: int, n_lags: int, k_max: int = 256, dt_ps: float = 0.002,
                  T_K: float = 300.0, V_A3: float = 1.0, F_e=(1e-5, 0.0, 0.0), device: int = 0,
-                 stream=None):
+                 stream=None, precision: str = "fp16x3"):
         self._L = load()
         fe = (ctypes.c_double * 3)(*F_e)
         st_ptr = stream if isinstance(stream, ctypes.c_void_p) else (
@@ -211,6 +214,8 @@ class SpectralHeatCurrent:
             raise MhcError(st, self._L.mhc_shc_last_error(None).decode())
         self._s = s
         self.N, self.n_lags = n_atoms, n_lags
+        if precision != "fp16x3":
+            self._check(self._L.mhc_shc_set_precision(s, PRECISIONS[precision]))
 
     def _check(self, st):
         if st != MHC_OK:
@@ -223,6 +228,16 @@ class SpectralHeatCurrent:
             raise ValueError("v and W must be in the same memory space")
         self._keep = (kv, kw)
         self._check(self._L.mhc_shc_push(self._s, pv, pw, int(kv.shape[0]), wv))
+
+    def set_profile(self, on: bool):
+        self._check(self._L.mhc_shc_set_profile(self._s, 1 if on else 0))
+
+    def kernel_time(self):
+        """(total ms, launches) of the correlation kernel since the last call (profiling on)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self._L.mhc_shc_kernel_time(self._s, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def read_corr(self):
         K = np.empty((9, self.n_lags))

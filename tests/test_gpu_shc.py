@@ -15,15 +15,20 @@ def need_gpu():
         pytest.skip("no CUDA device")
 
 
-def run(N, T, nc, K, seed, device_inputs=True, drive=0.0):
+# BF16x3 keeps ~16 significand bits per operand pair (see test_gpu_parity.py)
+TOL = {"fp32": REL_TOL, "fp16x3": REL_TOL, "bf16x3": 6e-5}
+
+
+def run(N, T, nc, K, seed, device_inputs=True, drive=0.0, precision="fp16x3", blocks=None):
     from paper_2102_03691_gb300.mhc import SpectralHeatCurrent
     mass = synth.masses(N, isotopes=synth.SI_ISOTOPES, seed=seed)
     tr = synth.Trajectory(mass, drive_g=drive, seed=seed)
     v, W = tr.next_block(T)
     s = SpectralHeatCurrent(N, nc, k_max=K, dt_ps=0.002, T_K=300.0, V_A3=N * 20.02,
-                            F_e=(1e-4, 0.0, 0.0))
-    for t0 in range(0, T, K):
-        a, b = np.ascontiguousarray(v[t0:t0 + K]), np.ascontiguousarray(W[t0:t0 + K])
+                            F_e=(1e-4, 0.0, 0.0), precision=precision)
+    starts = list(range(0, T, K)) if blocks is None else blocks
+    for t0, t1 in zip(starts, starts[1:] + [T]):
+        a, b = np.ascontiguousarray(v[t0:t1]), np.ascontiguousarray(W[t0:t1])
         if device_inputs:
             a, b = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
         s.push(a, b)
@@ -44,6 +49,40 @@ def test_shc_corr_and_kappa_match_oracle(N, T, nc, K):
         ko = oracle.shc_kappa(Ko, cnto, 0.002, 300.0, N * 20.02, 1e-4, f, window)
         assert np.all(spectrum_rel_err(kg.T, ko.T) <= REL_TOL)
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "fp16x3"])
+def test_shc_precisions_ragged_blocks(precision):
+    # 150 atoms (two 128-atom chunks, the second ragged), 140 lags over blocks of uneven
+    # length (37, 100, 5, 128, 30: the tau tiles start off the block boundaries and the
+    # last step tile of each block is ragged), so the virial ring wraps
+    need_gpu()
+    starts = [0, 37, 137, 142, 270]
+    s, v, W = run(150, 300, 140, 128, seed=620, drive=1e-3, precision=precision, blocks=starts)
+    Kg, cnt = s.read_corr()
+    Ko, cnto = oracle.shc_corr(v, W, 140)
+    np.testing.assert_array_equal(cnt, cnto)
+    err = series_rel_err(Kg.T, Ko.T)
+    print(f"shc {precision}: max {err.max():.3e}")
+    assert np.all(err <= TOL[precision])
+    s.close()
+
+
+def test_shc_tensor_path_is_deterministic_and_profiled():
+    need_gpu()
+    s1, v, W = run(300, 200, 64, 100, seed=630)
+    s2, _, _ = run(300, 200, 64, 100, seed=630)
+    K1, _ = s1.read_corr()
+    K2, _ = s2.read_corr()
+    np.testing.assert_array_equal(K1, K2)
+    s1.set_profile(True)
+    a, b = torch.from_numpy(v[:100]).cuda(), torch.from_numpy(W[:100]).cuda()
+    s1.push(a, b)
+    s1.push(a, b)
+    ms, n = s1.kernel_time()
+    assert n == 2 and ms > 0
+    s1.close()
+    s2.close()
 
 
 def test_shc_lag_zero_is_total_current_and_host_equals_device():

@@ -23,7 +23,7 @@ def need_gpu():
         pytest.skip("no CUDA device")
 
 
-def setup(name, n_blocks):
+def setup(name, n_blocks, direction=False):
     from paper_2102_03691_gb300.mhc import ModalHeatCurrent
     w = synth.WORKLOADS[name]
     N, M, K, L, B = w["N"], w["M"], w["K"], w["L"], w["B"]
@@ -35,7 +35,7 @@ def setup(name, n_blocks):
         if w.get("kappa_drive") else 0.0
     tr = synth.Trajectory(mass, drive_g=drive, seed=w["seed"])
     h = ModalHeatCurrent(precision="fp16x3", k_max=K, n_lags=L, dt_ps=w["dt_ps"], T_K=w["T_K"],
-                         V_A3=V, F_e=w["Fe"])
+                         V_A3=V, F_e=w["Fe"], direction=direction)
     h.set_modes(Ed, mass, f)
     h.set_bins_uniform(w["f"][0], w["f"][1], B)
     blocks, Jb, J = [], [], []
@@ -85,6 +85,36 @@ def test_gkma_si_n8000_full_size():
     assert s["h"].info()["graph_replays"] == 1
     check_sampled_steps(s, [0, 255, 256, 511])
     hcacf_sum_rule(s)
+    s["h"].close()
+
+
+def test_gkma_si_n8000_direction_split_full_size():
+    # the direction-resolved split at the Si-8000 sizes (24000 modes, 64 bins, 500 lags):
+    # sampled steps against the oracle's J_n^{ab}; per-direction completeness over the bins
+    need_gpu()
+    s = setup("gkma_si_n8000", n_blocks=2, direction=True)
+    K, B = s["w"]["K"], s["w"]["B"]
+    assert s["Jb"].shape == (2 * K, 3, B, 3)
+    scale = np.abs(s["Jb"]).max(axis=0)
+    for t in [0, 255, 256, 511]:
+        v, W = s["blocks"][t // K]
+        o = oracle.modal_current_dir(s["E"], s["mass"], v[t % K:t % K + 1], W[t % K:t % K + 1],
+                                     s["bins"], B)
+        np.testing.assert_allclose(s["J"][t], o["Jd"][0].sum(axis=0), rtol=1e-12, atol=1e-9)
+        err = np.abs(s["Jb"][t] - o["Jbd"][0]) / np.where(scale > 0, scale, 1.0)
+        assert np.all(err <= REL_TOL), (t, float(err.max()))
+        # all 3N modes kept: the bins of direction b add up to J^{ab}, within the bins' bounds
+        tot = s["Jb"][t].sum(axis=1)
+        assert np.all(np.abs(tot - o["Jd"][0]) <= REL_TOL * scale.sum(axis=1))
+    C, cnt = s["h"].read_corr()
+    assert C.shape == (3, B, 3, 3, s["w"]["L"])
+    # Eq. 18 over bins and directions
+    J = s["J"]
+    T, L = J.shape[0], C.shape[-1]
+    ref = np.stack([[[(J[l:, m] * J[:T - l, n]).sum() for l in range(L)] for n in range(3)]
+                    for m in range(3)])
+    tot = C.sum(axis=(0, 1))
+    assert np.all(np.abs(tot - ref) / np.abs(ref).max(axis=-1, keepdims=True) <= REL_TOL)
     s["h"].close()
 
 
