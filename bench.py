@@ -468,14 +468,14 @@ def run_shc(args):
                 "achieved": flops_step / k_launch_s / 1e12, "unit": "TFLOP/s", "peak": fp32_peak,
                 "peak_source": "derived: SMs x 128 FP32 FMA/clk x 2 flop x max SM clock"}
     else:
-        # 128 x 128 tiles touching the band 0 <= t - tau < nc of a block at t0 = multiple of K
-        t0s, Tt = 4 * K, 128
+        # 128 (tau) x 256 (t) tiles touching the band 0 <= t - tau < nc of a block at t0 = 4K
+        t0s, Tt, Ts = 4 * K, 128, 256
         pairs = 0
-        for q in range((K + Tt - 1) // Tt):
-            tmin, tmax = t0s + q * Tt, t0s + min((q + 1) * Tt, K) - 1
+        for q in range((K + Ts - 1) // Ts):
+            tmin, tmax = t0s + q * Ts, t0s + min((q + 1) * Ts, K) - 1
             pairs += tmax // Tt - max(0, (tmin - nc + 1) // Tt) + 1
         n_pad = (N + 127) // 128 * 128
-        executed = 3 * 2.0 * Tt * Tt * n_pad * 9 * pairs
+        executed = 3 * 2.0 * Tt * Ts * n_pad * 9 * pairs
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         roof = {"bound": "tensor", "kernel": "shc_tc_kernel (banded contraction, split 16-bit)",
                 "achieved": flops_step / k_launch_s / 1e12, "unit": "TFLOP/s", "peak": peak,
@@ -483,7 +483,7 @@ def run_shc(args):
                 "executed_tflops": executed / k_launch_s / 1e12,
                 "executed_frac": executed / k_launch_s / 1e12 / peak,
                 "note": "achieved counts the 2*9*N*nc*K flops of the definition; the tensor cores "
-                        f"execute {executed / flops_step:.2f}x that (3 split products, 128 x 128 tiles "
+                        f"execute {executed / flops_step:.2f}x that (3 split products, 128 x 256 tiles "
                         "over the band)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel_ms_per_launch"] = 1e3 * k_launch_s

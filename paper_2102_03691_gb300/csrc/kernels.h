@@ -128,15 +128,17 @@ __host__ __device__ inline uint32_t tc_tile_id(int prob, int mt, int ct) {
 }
 
 // ---------------------------------------------------------------- SHC on the tensor cores
-// Tile pairs (tau tile p, step tile q) of one block, 128 x 128 each; see k_shc_tc.cu.
+// Tile pairs (tau tile p, step tile q) of one block, 128 x 256 each; see k_shc_tc.cu.
 constexpr int SHC_TC_MAX_PAIRS = 288;
-constexpr int SHC_TC_TILE = 128;
+constexpr int SHC_TC_TILE = 128;        // times tau per tile (ring rows)
+constexpr int SHC_TC_STEP_TILE = 256;   // steps t per tile
+constexpr int SHC_TC_PART = 384;        // floats per unit: the 383 diagonals of a tile
 struct ShcTcParams {
     CUtensorMap tmA_hi, tmA_lo;   // virial ring [9 R][N_pad]: row (3a+b) R + slot, 16-bit hi/lo
     CUtensorMap tmB_hi, tmB_lo;   // velocities [3 Kpad][N_pad]: row b Kpad + k
     const float *scaleA;          // [9 R] 2^-s of each virial row
     const float *scaleB;          // [3 Kpad] 2^-s of each velocity row
-    float *partials;              // [units][256] diagonal sums of each unit's tile
+    float *partials;              // [units][SHC_TC_PART] diagonal sums of each unit's tile
     long long t0;                 // first sample of the block
     int R, nR, Kpad, K, nc;
     int n_pairs, splits, kb_per_split, n_kb;
@@ -144,15 +146,18 @@ struct ShcTcParams {
     int *status;
     uint32_t idesc;
     int p_tile[SHC_TC_MAX_PAIRS]; // tau tile index (tau0 = 128 p, p >= 0)
-    int q_tile[SHC_TC_MAX_PAIRS]; // step tile index in the block (k0 = 128 q)
+    int q_tile[SHC_TC_MAX_PAIRS]; // step tile index in the block (k0 = 256 q)
 };
 // Split/scale one block into the operands: velocities of step k to rows b Kpad + k and the
 // virials to ring rows (3a+b) R + (t0+k) mod R, with one power-of-two scale per row.
-void launch_shc_tc_pack(const float *v, const float *W, int N, int N_pad, int K, int Kpad, int R,
+cudaError_t launch_shc_tc_pack(const float *v, const float *W, int N, int N_pad, int K, int Kpad, int R,
                         long long t0, int split, void *A_hi, void *A_lo, void *B_hi, void *B_lo,
                         float *scaleA, float *scaleB, cudaStream_t s);
-// One CTA per unit (pair c = 3a+b, tile pair, atom split): 9 n_pairs splits CTAs.
+// One CTA per unit (pair c = 3a+b, tile pair, atom split): 9 n_pairs splits CTAs in clusters
+// of two (tile pairs 2j, 2j+1 share their step tile; n_pairs must be even).
 cudaError_t launch_shc_tc(const ShcTcParams &p, cudaStream_t s);
+// Clusters of two that can be resident at once (0 on error).
+int shc_tc_max_clusters();
 size_t shc_tc_smem_bytes();
 // Ksum[c][l] += sum over the units of pair c, in order, of their diagonal sums at lag l (FP64).
 void launch_shc_tc_reduce(const ShcTcParams &p, double *Ksum, cudaStream_t s);

@@ -126,38 +126,53 @@ __global__ void __launch_bounds__(RED_WARPS * 32) shc_reduce_kernel(const float 
     }
 }
 
-// kappa[c][k] = 2 Ktilde_c(2 pi f_k) / (V T |F_e|), Ktilde = 2 dt sum_l trap_l w_l K_l cos(omega l dt).
-// One CTA per tensor pair c: the per-lag coefficients trap_l w_l K_l go to shared memory once;
-// each thread takes frequencies and runs the Chebyshev recurrence
-//   cos((l+1) x) = 2 cos(x) cos(l x) - cos((l-1) x),  x = omega dt,
-// so the lag sum costs FP64 FMAs only (one cos per frequency).
+// kappa[c][k] = 2 Ktilde_c(2 pi f_k) / (V T |F_e|), Ktilde = 2 dt sum_l trap_l w_l K_l cos(omega_k l dt),
+// as a small FP64 product: the per-lag coefficients cl = trap_l w_l K_l (K_l = Ksum / count) of
+// pair c times a table C[l][k] = cos(2 pi f_k l dt) that is rebuilt only when the frequencies
+// change.  CTA = (16 frequencies, pair c); thread (g, kk) sums lags g, g + 8, ... of frequency kk,
+// the eight lag groups are added in order (deterministic).
 constexpr int KAPPA_MAX_LAGS = 4096;
-__global__ void __launch_bounds__(256) shc_kappa_kernel(const double *Ksum, int nc, long long T_s,
-                                                        double dt, double coef, int window,
-                                                        const double *f, int n_freq, double *kappa) {
-    __shared__ double cl[KAPPA_MAX_LAGS];
-    const int c = blockIdx.x;
+constexpr int KAPPA_FREQ = 16, KAPPA_GROUPS = 8;
+__global__ void shc_cos_table_kernel(const double *f, int n_freq, int nc, double dt, double *C) {
     const double PI = 3.14159265358979323846;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)nc * n_freq) return;
+    const int l = (int)(q / n_freq), k = (int)(q % n_freq);
+    C[q] = cos(2.0 * PI * f[k] * dt * (double)l);
+}
+
+// tw[w][l] = trap_l w_l for window w = 0 (none) and 1 (Hann), once per handle
+__global__ void shc_weight_table_kernel(int nc, double *tw) {
+    const double PI = 3.14159265358979323846;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nc) return;
+    const double trap = (l == 0 || l == nc - 1) ? 0.5 : 1.0;
+    tw[l] = trap;
+    tw[nc + l] = trap * (nc > 1 ? 0.5 * (1.0 + cos(PI * l / (double)(nc - 1))) : 1.0);
+}
+
+__global__ void __launch_bounds__(KAPPA_FREQ * KAPPA_GROUPS) shc_kappa_kernel(
+    const double *Ksum, int nc, long long T_s, double dt, double coef, const double *tw,
+    const double *C, int n_freq, double *kappa) {
+    __shared__ double cl[KAPPA_MAX_LAGS];
+    __shared__ double part[KAPPA_GROUPS][KAPPA_FREQ];
+    const int c = blockIdx.y;
     for (int l = threadIdx.x; l < nc; l += blockDim.x) {
         const long long cnt = T_s - l;
-        const double Kl = cnt > 0 ? Ksum[(size_t)c * nc + l] / (double)cnt : 0.0;
-        const double w = (window == 1 && nc > 1) ? 0.5 * (1.0 + cos(PI * l / (double)(nc - 1))) : 1.0;
-        const double trap = (l == 0 || l == nc - 1) ? 0.5 : 1.0;
-        cl[l] = trap * w * Kl;
+        cl[l] = cnt > 0 ? tw[l] * (Ksum[(size_t)c * nc + l] / (double)cnt) : 0.0;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < n_freq; k += blockDim.x) {
-        const double x = 2.0 * PI * f[k] * dt;
-        const double c1 = cos(x);
-        double cprev = c1, ccur = 1.0;   // cos(-x), cos(0)
-        double s = 0.0;
-        for (int l = 0; l < nc; ++l) {
-            s = fma(cl[l], ccur, s);
-            const double cnext = 2.0 * c1 * ccur - cprev;
-            cprev = ccur;
-            ccur = cnext;
-        }
-        kappa[(size_t)c * n_freq + k] = coef * 2.0 * (2.0 * s * dt);
+    const int kk = threadIdx.x % KAPPA_FREQ, g = threadIdx.x / KAPPA_FREQ;
+    const int k = blockIdx.x * KAPPA_FREQ + kk;
+    double s = 0.0;
+    if (k < n_freq)
+        for (int l = g; l < nc; l += KAPPA_GROUPS) s = fma(cl[l], C[(size_t)l * n_freq + k], s);
+    part[g][kk] = s;
+    __syncthreads();
+    if (g == 0 && k < n_freq) {
+        double t = 0.0;
+        for (int q = 0; q < KAPPA_GROUPS; ++q) t += part[q][kk];
+        kappa[(size_t)c * n_freq + k] = coef * 2.0 * (2.0 * t * dt);
     }
 }
 
@@ -179,10 +194,14 @@ struct mhc_shc {
     // tensor-core path: 16-bit virial ring [9 R_tc][N_pad], velocities [3 Kpad][N_pad]
     int64_t N_pad = 0;
     int R_tc = 0, Kpad = 0;
+    int cta_slots = 0;   // CTAs of the tensor-core kernel resident at once (clusters of two)
     void *A_hi = nullptr, *A_lo = nullptr, *B_hi = nullptr, *B_lo = nullptr;
     float *scaleA = nullptr, *scaleB = nullptr, *tc_partials = nullptr;
     mhc::ShcTcParams tcp{};
     int *status = nullptr;   // sticky device status (a bounded wait that gave up)
+    // frequencies of the last spectrum read, as uploaded (a pageable upload per read would
+    // make the host wait for the stream)
+    std::vector<double> freq_dev_copy;
     // optional CUDA-event timing of the correlation kernel
     bool profile = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
@@ -244,14 +263,16 @@ cudaError_t alloc_path(mhc_shc *s) {
     if (!get(&s->A_hi, a) || !get(&s->A_lo, a) || !get(&s->B_hi, b) || !get(&s->B_lo, b) ||
         !get((void **)&s->scaleA, sizeof(float) * 9 * s->R_tc) ||
         !get((void **)&s->scaleB, sizeof(float) * 3 * s->Kpad) ||
-        !get((void **)&s->tc_partials, sizeof(float) * units * 256))
+        !get((void **)&s->tc_partials, sizeof(float) * units * mhc::SHC_TC_PART))
         return e;
     mhc::ShcTcParams &P = s->tcp;
-    const uint32_t T = mhc::SHC_TC_TILE;
-    if (mhc::tc_make_tmap(&P.tmA_hi, s->A_hi, (uint64_t)9 * s->R_tc, s->N_pad, s->N_pad, T, 64) ||
-        mhc::tc_make_tmap(&P.tmA_lo, s->A_lo, (uint64_t)9 * s->R_tc, s->N_pad, s->N_pad, T, 64) ||
-        mhc::tc_make_tmap(&P.tmB_hi, s->B_hi, (uint64_t)3 * s->Kpad, s->N_pad, s->N_pad, T, 64) ||
-        mhc::tc_make_tmap(&P.tmB_lo, s->B_lo, (uint64_t)3 * s->Kpad, s->N_pad, s->N_pad, T, 64))
+    const uint32_t T = mhc::SHC_TC_TILE, TS = mhc::SHC_TC_STEP_TILE;
+    // boxes of 32 atoms (64-byte rows, 64-byte swizzle) x 128 ring rows / 128 velocity rows
+    // (each CTA of a cluster loads one half of the 256 velocity rows of a tile)
+    if (mhc::tc_make_tmap(&P.tmA_hi, s->A_hi, (uint64_t)9 * s->R_tc, s->N_pad, s->N_pad, T, 32) ||
+        mhc::tc_make_tmap(&P.tmA_lo, s->A_lo, (uint64_t)9 * s->R_tc, s->N_pad, s->N_pad, T, 32) ||
+        mhc::tc_make_tmap(&P.tmB_hi, s->B_hi, (uint64_t)3 * s->Kpad, s->N_pad, s->N_pad, TS / 2, 32) ||
+        mhc::tc_make_tmap(&P.tmB_lo, s->B_lo, (uint64_t)3 * s->Kpad, s->N_pad, s->N_pad, TS / 2, 32))
         return cudaErrorInvalidValue;
     P.scaleA = s->scaleA;
     P.scaleB = s->scaleB;
@@ -260,10 +281,12 @@ cudaError_t alloc_path(mhc_shc *s) {
     P.nR = s->R_tc / (int)T;
     P.Kpad = s->Kpad;
     P.nc = s->nc;
-    P.n_kb = (int)(s->N_pad / 64);
+    P.n_kb = (int)(s->N_pad / 32);
     P.wait_limit = 2000000000ll;
     P.status = s->status;
-    P.idesc = mhc::idesc_f16(s->precision == MHC_PREC_BF16X3 ? 1u : 0u, T, T);
+    const int clusters = mhc::shc_tc_max_clusters();
+    s->cta_slots = clusters > 0 ? 2 * clusters : s->sm_count;
+    P.idesc = mhc::idesc_f16(s->precision == MHC_PREC_BF16X3 ? 1u : 0u, T, TS);
     return cudaSuccess;
 }
 
@@ -283,12 +306,15 @@ long long floor_div(long long a, long long b) { return a >= 0 ? a / b : -((-a + 
 // and the split of the atom axis that fills the SMs.
 bool plan_tiles(mhc_shc *s, int K) {
     mhc::ShcTcParams &P = s->tcp;
-    const long long T = mhc::SHC_TC_TILE, t0 = s->steps;
+    const long long T = mhc::SHC_TC_TILE, TS = mhc::SHC_TC_STEP_TILE, t0 = s->steps;
     int n = 0;
-    for (int q = 0; q * T < K; ++q) {
-        const long long tmin = t0 + q * T, tmax = t0 + std::min<long long>((q + 1) * T, K) - 1;
+    for (int q = 0; q * TS < K; ++q) {
+        const long long tmin = t0 + q * TS, tmax = t0 + std::min<long long>((q + 1) * TS, K) - 1;
         const long long p0 = std::max<long long>(0, floor_div(tmin - s->nc + 1, T));
-        for (long long pp = p0; pp <= tmax / T; ++pp) {
+        long long p1 = tmax / T;
+        // tiles go to clusters in pairs (p, p+1); an extra tile past tmax only holds lags < 0
+        if ((p1 - p0 + 1) % 2) ++p1;
+        for (long long pp = p0; pp <= p1; ++pp) {
             if (n == mhc::SHC_TC_MAX_PAIRS) return false;
             P.p_tile[n] = (int)pp;
             P.q_tile[n] = q;
@@ -299,10 +325,10 @@ bool plan_tiles(mhc_shc *s, int K) {
     P.t0 = t0;
     P.K = K;
     const int chunks = (int)(s->N_pad / 128);
-    int splits = std::max(1, s->sm_count / (9 * n));
+    int splits = std::max(1, s->cta_slots / (9 * n));
     splits = std::min(splits, chunks);
     const int per = (chunks + splits - 1) / splits;   // chunks per split
-    P.kb_per_split = 2 * per;
+    P.kb_per_split = per * (128 / 32);
     P.splits = (chunks + per - 1) / per;
     return true;
 }
@@ -336,7 +362,7 @@ mhc_status mhc_shc_create(mhc_shc **out, int32_t device, void *stream, int64_t n
     s->n_tiles = (int)((n_atoms + SHC_ATILE - 1) / SHC_ATILE);
     s->sm_count = prop.multiProcessorCount;
     s->N_pad = (n_atoms + 127) / 128 * 128;
-    s->Kpad = (k_max + 127) / 128 * 128;
+    s->Kpad = (k_max + mhc::SHC_TC_STEP_TILE - 1) / mhc::SHC_TC_STEP_TILE * mhc::SHC_TC_STEP_TILE;
     s->R_tc = (k_max + n_lags + 127) / 128 * 128;   // >= K + nc - 1 live samples, whole tiles
     s->dt = dt_ps;
     s->T = T_K;
@@ -410,9 +436,10 @@ mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, i
             W = s->W_stage;
         }
         if (!plan_tiles(s, K)) return sfail(s, MHC_ERR_UNSUPPORTED, "too many tile pairs for K=%d", K);
-        mhc::launch_shc_tc_pack(v, W, (int)s->N, (int)s->N_pad, K, s->Kpad, s->R_tc, s->steps,
-                                s->precision == MHC_PREC_BF16X3 ? mhc::SPLIT_BF16 : mhc::SPLIT_FP16,
-                                s->A_hi, s->A_lo, s->B_hi, s->B_lo, s->scaleA, s->scaleB, s->stream);
+        SHC_CUDA(s, mhc::launch_shc_tc_pack(v, W, (int)s->N, (int)s->N_pad, K, s->Kpad, s->R_tc, s->steps,
+                                            s->precision == MHC_PREC_BF16X3 ? mhc::SPLIT_BF16 : mhc::SPLIT_FP16,
+                                            s->A_hi, s->A_lo, s->B_hi, s->B_lo, s->scaleA, s->scaleB,
+                                            s->stream));
         cudaEvent_t ev1 = nullptr;
         if (s->profile) {
             if (s->prof_used == s->prof_events.size()) {
@@ -506,19 +533,33 @@ mhc_status mhc_shc_read_kappa(mhc_shc *s, const double *f_THz, int32_t n_freq, i
     if (!f_THz || !kappa || n_freq < 1 || (window != 0 && window != 1))
         return sfail(s, MHC_ERR_INVALID_ARG, "need frequencies, an output, window 0 or 1");
     SHC_CUDA(s, cudaSetDevice(s->device));
-    const size_t need = sizeof(double) * (size_t)n_freq * 10;
+    const size_t need = sizeof(double) * ((size_t)n_freq * 10 + (size_t)n_freq * s->nc + 2 * (size_t)s->nc);
     if (s->out_cap < need) {
         cudaStreamSynchronize(s->stream);
         cudaFree(s->out);
         s->out = nullptr;
+        s->freq_dev_copy.clear();
         SHC_CUDA(s, cudaMalloc(&s->out, need));
         s->out_cap = need;
     }
     double *df = s->out + (size_t)n_freq * 9;
-    SHC_CUDA(s, cudaMemcpyAsync(df, f_THz, sizeof(double) * n_freq, cudaMemcpyHostToDevice, s->stream));
+    double *ctab = df + n_freq;   // [nc][n_freq] cos(2 pi f_k l dt)
+    double *tw = ctab + (size_t)n_freq * s->nc;   // [2][nc] trapezoid x window weights
+    if (s->freq_dev_copy.size() != (size_t)n_freq ||
+        std::memcmp(s->freq_dev_copy.data(), f_THz, sizeof(double) * n_freq) != 0) {
+        s->freq_dev_copy.assign(f_THz, f_THz + n_freq);
+        SHC_CUDA(s, cudaMemcpyAsync(df, s->freq_dev_copy.data(), sizeof(double) * n_freq,
+                                    cudaMemcpyHostToDevice, s->stream));
+        const long long n = (long long)s->nc * n_freq;
+        shc_cos_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(df, n_freq, s->nc, s->dt, ctab);
+        shc_weight_table_kernel<<<(s->nc + 255) / 256, 256, 0, s->stream>>>(s->nc, tw);
+        SHC_CUDA(s, cudaGetLastError());
+        SHC_CUDA(s, cudaStreamSynchronize(s->stream));   // the host copy may change before the copy runs
+    }
     const double coef = s->Fe > 0 ? WMK / (s->V * s->T * s->Fe) : 0.0;
-    shc_kappa_kernel<<<9, 256, 0, s->stream>>>(s->Ksum, s->nc, s->steps, s->dt, coef, window, df,
-                                                n_freq, s->out);
+    shc_kappa_kernel<<<dim3((n_freq + KAPPA_FREQ - 1) / KAPPA_FREQ, 9), KAPPA_FREQ * KAPPA_GROUPS, 0,
+                       s->stream>>>(s->Ksum, s->nc, s->steps, s->dt, coef, tw + (size_t)window * s->nc,
+                                    ctab, n_freq, s->out);
     SHC_CUDA(s, cudaGetLastError());
     const cudaMemcpyKind kind = where == MHC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     SHC_CUDA(s, cudaMemcpyAsync(kappa, s->out, sizeof(double) * 9 * n_freq, kind, s->stream));

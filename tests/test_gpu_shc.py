@@ -68,6 +68,20 @@ def test_shc_precisions_ragged_blocks(precision):
     s.close()
 
 
+@pytest.mark.parametrize("N", [17000, 33000])
+def test_shc_large_systems_pack_paths(N):
+    # N = 17000 packs with 8 atoms per thread in a cluster of 5 CTAs per step; N = 33000 is past
+    # what a cluster of 8 holds and takes the two-pass one-CTA-per-step kernel
+    need_gpu()
+    s, v, W = run(N, 24, 8, 12, seed=640 + N % 7)
+    Kg, cnt = s.read_corr()
+    Ko, _ = oracle.shc_corr(v, W, 8)
+    err = series_rel_err(Kg.T, Ko.T)
+    print(f"shc N={N}: max {err.max():.3e}")
+    assert np.all(err <= REL_TOL)
+    s.close()
+
+
 def test_shc_tensor_path_is_deterministic_and_profiled():
     need_gpu()
     s1, v, W = run(300, 200, 64, 100, seed=630)
