@@ -117,6 +117,14 @@ struct mhc_handle {
     int64_t graph_replays = 0;
     cudaStream_t cap_stream = nullptr;
 
+    // host-input staging: two buffer pairs filled on a copy stream, so that the upload of one
+    // push overlaps the kernels of the previous one (each buffer is reused only after the
+    // push that read it has finished)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_done[2] = {nullptr, nullptr}, use_done[2] = {nullptr, nullptr};
+    bool use_pending[2] = {false, false};
+    int stage_next = 0, stage_used = -1;
+
     // optional CUDA-event timing of the projection kernel (MHC_FLAG_PROFILE)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
     size_t prof_used = 0;
@@ -502,13 +510,39 @@ mhc_status autotune(mhc_handle *h, int K) {
     return set_tc_config(h, best_c);
 }
 
+// Host inputs: copy into the next staging pair on the copy stream once the push that last
+// read that pair is done, and wait for the copy (host inputs are read before the call
+// returns); the previous push's kernels keep running meanwhile.
 mhc_status stage_inputs(mhc_handle *h, const float *&v, const float *&W, int K, int where) {
     if (where == MHC_MEM_DEVICE) return MHC_OK;
+    if (!h->copy_stream) {
+        MHC_CUDA(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        for (int q = 0; q < 2; ++q) {
+            MHC_CUDA(h, cudaEventCreateWithFlags(&h->copy_done[q], cudaEventDisableTiming));
+            MHC_CUDA(h, cudaEventCreateWithFlags(&h->use_done[q], cudaEventDisableTiming));
+        }
+    }
+    const int b = h->stage_next;
     const size_t nv = (size_t)K * h->N * 3, nw = (size_t)K * h->N * 9;
-    MHC_CUDA(h, cudaMemcpyAsync(dptr<float>(h, "v_stage"), v, nv * 4, cudaMemcpyHostToDevice, h->stream));
-    MHC_CUDA(h, cudaMemcpyAsync(dptr<float>(h, "W_stage"), W, nw * 4, cudaMemcpyHostToDevice, h->stream));
-    v = dptr<float>(h, "v_stage");
-    W = dptr<float>(h, "W_stage");
+    float *dv = dptr<float>(h, b ? "v_stage1" : "v_stage"), *dw = dptr<float>(h, b ? "W_stage1" : "W_stage");
+    if (h->use_pending[b]) MHC_CUDA(h, cudaStreamWaitEvent(h->copy_stream, h->use_done[b], 0));
+    MHC_CUDA(h, cudaMemcpyAsync(dv, v, nv * 4, cudaMemcpyHostToDevice, h->copy_stream));
+    MHC_CUDA(h, cudaMemcpyAsync(dw, W, nw * 4, cudaMemcpyHostToDevice, h->copy_stream));
+    MHC_CUDA(h, cudaEventRecord(h->copy_done[b], h->copy_stream));
+    MHC_CUDA(h, cudaEventSynchronize(h->copy_done[b]));
+    h->stage_used = b;
+    h->stage_next ^= 1;
+    v = dv;
+    W = dw;
+    return MHC_OK;
+}
+
+// After the kernels of a push that read a staging pair: mark when the pair is free again.
+mhc_status release_stage(mhc_handle *h) {
+    if (h->stage_used < 0) return MHC_OK;
+    MHC_CUDA(h, cudaEventRecord(h->use_done[h->stage_used], h->stream));
+    h->use_pending[h->stage_used] = true;
+    h->stage_used = -1;
     return MHC_OK;
 }
 
@@ -738,6 +772,14 @@ void mhc_destroy(mhc_handle *h) {
     }
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+        for (int q = 0; q < 2; ++q) {
+            cudaEventDestroy(h->copy_done[q]);
+            cudaEventDestroy(h->use_done[q]);
+        }
+    }
     for (auto &kv : h->buf)
         if (kv.second.p) cudaFree(kv.second.p);
     if (h->status) cudaFree(h->status);
@@ -864,8 +906,10 @@ mhc_status mhc_set_modes(mhc_handle *h, int64_t n_atoms, int64_t n_modes, const 
     }
     if ((s = dev_alloc(h, "col_scale", sizeof(float) * 4 * K)) != MHC_OK) return s;
     if ((s = dev_alloc(h, "Jtot", sizeof(double) * 3 * K)) != MHC_OK) return s;
-    if ((s = dev_alloc(h, "v_stage", sizeof(float) * K * n_atoms * 3, false)) != MHC_OK) return s;
-    if ((s = dev_alloc(h, "W_stage", sizeof(float) * K * n_atoms * 9, false)) != MHC_OK) return s;
+    for (const char *nm : {"v_stage", "v_stage1"})
+        if ((s = dev_alloc(h, nm, sizeof(float) * K * n_atoms * 3, false)) != MHC_OK) return s;
+    for (const char *nm : {"W_stage", "W_stage1"})
+        if ((s = dev_alloc(h, nm, sizeof(float) * K * n_atoms * 9, false)) != MHC_OK) return s;
     MHC_CUDA(h, cudaStreamSynchronize(h->stream));
     h->modes_ready = true;
     h->tuned.clear();
@@ -909,7 +953,8 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     const bool tuned = !is_tc(h) || h->prm.tile_config != 0 || h->tuned.count(K);
     if (tuned && !(h->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL))) {
         if (is_tc(h) && h->prm.tile_config == 0 && (s = set_tc_config(h, h->tuned[K])) != MHC_OK) return s;
-        return push_graph(h, v, W, K);
+        if ((s = push_graph(h, v, W, K)) != MHC_OK) return s;
+        return release_stage(h);
     }
     if ((s = pack_block(h, v, W, K)) != MHC_OK) return s;
     if (is_tc(h) && h->prm.tile_config == 0) {
@@ -935,7 +980,8 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     }
     if ((s = run_projection(h, K)) != MHC_OK) return s;
     if (ev1) MHC_CUDA(h, cudaEventRecord(ev1, h->stream));
-    return finish_block(h, K);
+    if ((s = finish_block(h, K)) != MHC_OK) return s;
+    return release_stage(h);
 }
 
 mhc_status mhc_sync(mhc_handle *h) {
@@ -1487,7 +1533,10 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
         MHC_CUDA(h0, cudaGraphLaunch(it->second.exec, h0->stream));
         h0->launches += it->second.nodes;
         h0->graph_replays++;
-        for (size_t j = 0; j < n; ++j) count_push(g->hs[j], Ks[j]);
+        for (size_t j = 0; j < n; ++j) {
+            count_push(g->hs[j], Ks[j]);
+            if ((s = release_stage(g->hs[j])) != MHC_OK) return s;
+        }
         return MHC_OK;
     }
     for (size_t j = 0; j < n; ++j)
@@ -1509,8 +1558,10 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
     }
     if ((s = group_launch(g, Ks)) != MHC_OK) return s;
     if (ev1) MHC_CUDA(h0, cudaEventRecord(ev1, h0->stream));
-    for (size_t j = 0; j < n; ++j)
+    for (size_t j = 0; j < n; ++j) {
         if ((s = finish_block(g->hs[j], Ks[j])) != MHC_OK) return s;
+        if ((s = release_stage(g->hs[j])) != MHC_OK) return s;
+    }
     return MHC_OK;
 }
 

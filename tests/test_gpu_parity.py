@@ -216,6 +216,42 @@ def test_gkma_and_hnema_small(precision):
     assert np.all(errH <= TOL[precision])
 
 
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_inputs_back_to_back_reuse_one_buffer(pinned):
+    # Host inputs go through two staging buffers on a copy stream; the call returns only once
+    # it has read the caller's memory, so one host buffer can be refilled right after each push
+    # while earlier pushes are still running.  Bitwise equal to device inputs.
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import ModalHeatCurrent
+    K, T = 8, 64
+    c = make_case(N=64, M=192, T=T, B=4, seed=108)
+
+    def run(host):
+        h = ModalHeatCurrent(precision="fp16x3", k_max=K, n_lags=6)
+        h.set_modes(c["E"], c["mass"], c["f"])
+        h.set_bins_uniform(0.0, c["f_hi"], 4)
+        if pinned:
+            bv = torch.empty((K, 64, 3), dtype=torch.float32).pin_memory()
+            bw = torch.empty((K, 64, 9), dtype=torch.float32).pin_memory()
+        else:
+            bv, bw = np.empty((K, 64, 3), np.float32), np.empty((K, 64, 9), np.float32)
+        for t0 in range(0, T, K):
+            if host:
+                bv[:] = torch.from_numpy(c["v"][t0:t0 + K]) if pinned else c["v"][t0:t0 + K]
+                bw[:] = torch.from_numpy(c["W"][t0:t0 + K]) if pinned else c["W"][t0:t0 + K]
+                h.push(bv, bw)
+            else:
+                h.push(torch.from_numpy(c["v"][t0:t0 + K]).cuda(), torch.from_numpy(c["W"][t0:t0 + K]).cuda())
+        C, _ = h.read_corr()
+        m, _ = h.read_hnema()
+        h.close()
+        return C, m
+    Ca, ma = run(True)
+    Cb, mb = run(False)
+    np.testing.assert_array_equal(Ca, Cb)
+    np.testing.assert_array_equal(ma, mb)
+
+
 def test_state_roundtrip_is_bitwise():
     need_gpu()
     L, K = 10, 8
