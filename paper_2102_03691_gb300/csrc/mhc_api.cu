@@ -511,9 +511,9 @@ mhc_status autotune(mhc_handle *h, int K) {
 }
 
 // Host inputs: copy into the next staging pair on the copy stream once the push that last
-// read that pair is done, and wait for the copy (host inputs are read before the call
-// returns); the previous push's kernels keep running meanwhile.
-mhc_status stage_inputs(mhc_handle *h, const float *&v, const float *&W, int K, int where) {
+// read that pair is done (stage_issue), then wait for the copy (stage_wait: host inputs are
+// read before the call returns); the previous push's kernels keep running meanwhile.
+mhc_status stage_issue(mhc_handle *h, const float *&v, const float *&W, int K, int where) {
     if (where == MHC_MEM_DEVICE) return MHC_OK;
     if (!h->copy_stream) {
         MHC_CUDA(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
@@ -529,12 +529,21 @@ mhc_status stage_inputs(mhc_handle *h, const float *&v, const float *&W, int K, 
     MHC_CUDA(h, cudaMemcpyAsync(dv, v, nv * 4, cudaMemcpyHostToDevice, h->copy_stream));
     MHC_CUDA(h, cudaMemcpyAsync(dw, W, nw * 4, cudaMemcpyHostToDevice, h->copy_stream));
     MHC_CUDA(h, cudaEventRecord(h->copy_done[b], h->copy_stream));
-    MHC_CUDA(h, cudaEventSynchronize(h->copy_done[b]));
     h->stage_used = b;
     h->stage_next ^= 1;
     v = dv;
     W = dw;
     return MHC_OK;
+}
+
+mhc_status stage_wait(mhc_handle *h) {
+    if (h->stage_used >= 0) MHC_CUDA(h, cudaEventSynchronize(h->copy_done[h->stage_used]));
+    return MHC_OK;
+}
+
+mhc_status stage_inputs(mhc_handle *h, const float *&v, const float *&W, int K, int where) {
+    mhc_status s = stage_issue(h, v, W, K, where);
+    return s == MHC_OK ? stage_wait(h) : s;
 }
 
 // After the kernels of a push that read a staging pair: mark when the pair is free again.
@@ -1450,8 +1459,11 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
     MHC_CUDA(h0, cudaSetDevice(h0->prm.device));
     mhc_status s;
     std::vector<const float *> vs(v, v + n), ws(W, W + n);
+    // all systems' uploads first, one wait after them
     for (size_t j = 0; j < n; ++j)
-        if ((s = stage_inputs(g->hs[j], vs[j], ws[j], Ks[j], where)) != MHC_OK) return s;
+        if ((s = stage_issue(g->hs[j], vs[j], ws[j], Ks[j], where)) != MHC_OK) return s;
+    for (size_t j = 0; j < n; ++j)
+        if ((s = stage_wait(g->hs[j])) != MHC_OK) return s;
     const bool tuned = g->tuned || h0->prm.tile_config != 0;
     const bool profile = (h0->prm.flags & MHC_FLAG_PROFILE) != 0;
     if (tuned && !(h0->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL))) {

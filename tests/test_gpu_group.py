@@ -133,3 +133,32 @@ def test_group_graph_replay_matches_direct():
     for x, y in zip(results[0][1], results[1][1]):
         np.testing.assert_array_equal(x, y)
     assert results[0][2] == 0 and results[1][2] == 3
+
+
+def test_group_host_inputs_back_to_back():
+    # host inputs of every system are uploaded before the group push returns (staging
+    # overlaps the previous push); the caller's buffers are refilled right after each push
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import ModalHeatCurrentGroup
+    sizes = [120, 80, 200]
+    K, L, T = 16, 6, 5
+    systems = [system(N, 700 + j) for j, N in enumerate(sizes)]
+    blocks = [[s["tr"].next_block(K) for _ in range(T)] for s in systems]
+    res = []
+    for host in (True, False):
+        hs = [handle(s, K, L) for s in systems]
+        grp = ModalHeatCurrentGroup(hs)
+        bufs = [(np.empty_like(bl[0][0]), np.empty_like(bl[0][1])) for bl in blocks]
+        for step in range(T):
+            if host:
+                for (bv, bw), bl in zip(bufs, blocks):
+                    bv[:], bw[:] = bl[step]
+                grp.push([b[0] for b in bufs], [b[1] for b in bufs])
+            else:
+                grp.push([torch.from_numpy(bl[step][0]).cuda() for bl in blocks],
+                         [torch.from_numpy(bl[step][1]).cuda() for bl in blocks])
+        res.append(([h.read_corr()[0] for h in hs], grp.read_hnema()))
+        grp.close()
+    for x, y in zip(res[0][0], res[1][0]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(res[0][1], res[1][1])
