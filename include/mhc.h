@@ -188,7 +188,9 @@ mhc_status mhc_set_bin_ids(mhc_handle *h, const int32_t *bin_of_mode, int32_t n_
  * Computes J(t) (Eq. 10), the binned modal currents J_b(t) (Eq. 13, 16), adds
  * them to the HNEMA sums (Eq. 19) and, with MHC_FLAG_GKMA, to the lag
  * correlation sums (Eq. 17).  Asynchronous: device inputs must stay valid until
- * the stream reaches the push; host inputs are copied before the call returns.
+ * the stream reaches the push; host inputs are copied before the call returns (into one of
+ * two device staging buffers, on an internal copy stream, so that the upload overlaps the
+ * kernels of the previous push; page-locked host memory uploads fastest).
  * Errors: INVALID_ARG (no modes/bins yet, K out of range, null), CUDA.
  */
 mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, int32_t where);

@@ -265,6 +265,127 @@ __global__ void __launch_bounds__(PACK_THREADS, 1) shc_tc_pack_cluster_vec_kerne
     }
 }
 
+// Cluster of ceil(N / APC) CTAs per step k; CTA r bulk-copies the contiguous velocities and
+// virials of its atoms r*APC .. into shared memory (one TMA bulk copy per 16 KB), so every
+// load is asynchronous and registers stay few (four 256-thread CTAs per SM for APC = 1024).
+// Thread t then takes the four consecutive atoms 4t .. 4t+3 (16-byte shared-memory reads,
+// conflict-free), the 12 row maxima are combined across the cluster in distributed shared
+// memory, and each operand row gets one 8-byte store per thread.  Needs N % 4 == 0 and
+// 16-byte aligned inputs.  A copy that does not land within the wait limit sets the status
+// word; the CTA then writes nothing.
+template <int SPLIT, int THREADS>
+__global__ void __launch_bounds__(THREADS) shc_tc_pack_bulk_kernel(
+    const float *__restrict__ v, const float *__restrict__ W, int N, int N_pad, int Kpad, int R,
+    long long t0, void *A_hi, void *A_lo, void *B_hi, void *B_lo, float *scaleA, float *scaleB,
+    int *status, long long wait_limit) {
+    constexpr int APC = 4 * THREADS;
+    extern __shared__ float4 pk_smem4[];
+    float *sv = reinterpret_cast<float *>(pk_smem4);   // [APC][3]
+    float *sw = sv + APC * 3;                          // [APC][9]
+    __shared__ float s_mx[THREADS / 32][12];
+    __shared__ float s_loc[12], s_mul[12];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    const uint32_t rank = cluster_ctarank(), nrank = cluster_nctarank();
+    const int k = (int)(blockIdx.x / nrank);
+    const int a0 = (int)rank * APC;
+    const int na = max(0, min(APC, N - a0));   // atoms of this CTA (a multiple of 4)
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && na > 0) {
+        const uint32_t vb = (uint32_t)na * 12, wb = (uint32_t)na * 36;
+        mbar_arrive_expect_tx(&bar, vb + wb);
+        const char *gv = reinterpret_cast<const char *>(v + ((size_t)k * N + a0) * 3);
+        const char *gw = reinterpret_cast<const char *>(W + ((size_t)k * N + a0) * 9);
+        for (uint32_t o = 0; o < vb; o += 16384)
+            bulk_load(reinterpret_cast<char *>(sv) + o, gv + o, min(16384u, vb - o), &bar);
+        for (uint32_t o = 0; o < wb; o += 16384)
+            bulk_load(reinterpret_cast<char *>(sw) + o, gw + o, min(16384u, wb - o), &bar);
+    }
+    bool ok = true;
+    if (na > 0) ok = mbar_wait(&bar, 0, &abort_flag, wait_limit);
+    const int i = 4 * (int)threadIdx.x;   // first of this thread's atoms within the CTA
+    const bool in = ok && i < na;
+    float mx[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) mx[c] = 0.f;
+    if (in) {
+        const float4 *pv = reinterpret_cast<const float4 *>(sv + i * 3);
+        const float4 *pw = reinterpret_cast<const float4 *>(sw + i * 9);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float4 t = pv[q];
+            const float e[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) mx[(4 * q + u) % 3] = fmaxf(mx[(4 * q + u) % 3], fabsf(e[u]));
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float4 t = pw[q];
+            const float e[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) mx[3 + (4 * q + u) % 9] = fmaxf(mx[3 + (4 * q + u) % 9], fabsf(e[u]));
+        }
+    }
+    // block maximum (THREADS-wide version of block_max12)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 12; ++c) mx[c] = fmaxf(mx[c], __shfl_down_sync(FULL_MASK, mx[c], o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 12; ++c) s_mx[warp][c] = mx[c];
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        float m = 0.f;
+        for (int w = 0; w < THREADS / 32; ++w) m = fmaxf(m, s_mx[w][threadIdx.x]);
+        s_loc[threadIdx.x] = m;
+    }
+    cluster_sync_all();
+    const int slot = (int)((t0 + k) % R);
+    if (threadIdx.x < 12) {
+        const int c = threadIdx.x;
+        float m = 0.f;
+        for (uint32_t q = 0; q < nrank; ++q) m = fmaxf(m, ld_shared_cluster_f32(mapa_shared(smem_u32(&s_loc[c]), q)));
+        const int sc = row_shift<SPLIT>(m);
+        s_mul[c] = ldexpf(1.f, sc);
+        if (rank == 0) {
+            if (c < 3) scaleB[(size_t)c * Kpad + k] = ldexpf(1.f, -sc);
+            else scaleA[(size_t)(c - 3) * R + slot] = ldexpf(1.f, -sc);
+        }
+    }
+    cluster_sync_all();
+    if (!ok) {   // the CTA stays alive until its copy has landed (bounded) or given up on
+        if (threadIdx.x == 0) {
+            set_status(status, DEV_TIMEOUT);
+            const long long c0 = clock64();
+            while (!mbar_try_wait(&bar, 0) && clock64() - c0 < wait_limit) {
+            }
+        }
+        return;
+    }
+    if (!in) return;
+    const float *xv = sv + i * 3, *xw = sw + i * 9;
+    const int g = a0 + i;   // global atom index
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const float m = s_mul[b];
+        put_split4<SPLIT>(B_hi, B_lo, ((size_t)b * Kpad + k) * N_pad + g, xv[b] * m, xv[3 + b] * m,
+                          xv[6 + b] * m, xv[9 + b] * m);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const float m = s_mul[3 + c];
+        put_split4<SPLIT>(A_hi, A_lo, ((size_t)c * R + slot) * N_pad + g, xw[c] * m, xw[9 + c] * m,
+                          xw[18 + c] * m, xw[27 + c] * m);
+    }
+}
+
 // Fallback for systems larger than a cluster of 8 CTAs holds: one CTA per step, phase 1 the
 // row maxima, phase 2 the operands (the step's inputs are read twice).
 template <int SPLIT>
@@ -575,13 +696,49 @@ cudaError_t launch_pack_cluster_vec(int csize, const float *v, const float *W, i
                               A_hi, A_lo, B_hi, B_lo, scaleA, scaleB);
 }
 
+template <int SPLIT, int THREADS>
+cudaError_t launch_pack_bulk(const float *v, const float *W, int N, int N_pad, int K, int Kpad, int R,
+                             long long t0, void *A_hi, void *A_lo, void *B_hi, void *B_lo,
+                             float *scaleA, float *scaleB, int *status, long long wait_limit,
+                             cudaStream_t s) {
+    constexpr int APC = 4 * THREADS;
+    const int smem = APC * 48;
+    auto kern = shc_tc_pack_bulk_kernel<SPLIT, THREADS>;
+    static cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    const int csize = (N + APC - 1) / APC;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(K * csize), 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeClusterDimension;
+    la[0].val.clusterDim.x = (unsigned)csize;
+    la[0].val.clusterDim.y = 1;
+    la[0].val.clusterDim.z = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, v, W, N, N_pad, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA,
+                              scaleB, status, wait_limit);
+}
+
 cudaError_t launch_shc_tc_pack(const float *v, const float *W, int N, int N_pad, int K, int Kpad, int R,
                                long long t0, int split, void *A_hi, void *A_lo, void *B_hi, void *B_lo,
-                               float *scaleA, float *scaleB, cudaStream_t s) {
+                               float *scaleA, float *scaleB, int *status, long long wait_limit,
+                               cudaStream_t s) {
     if (K <= 0) return cudaSuccess;
     const int per4 = PACK_THREADS * 4, per8 = PACK_THREADS * 8;
     const bool bf = split == SPLIT_BF16;
     const bool vec = N % 4 == 0 && ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(W)) & 15) == 0;
+    if (vec && N <= 8 * 1024) {   // bulk copies into shared memory, 1024 atoms per CTA
+        return bf ? launch_pack_bulk<SPLIT_BF16, 256>(v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, status, wait_limit, s)
+                  : launch_pack_bulk<SPLIT_FP16, 256>(v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, status, wait_limit, s);
+    }
+    if (vec && N <= 8 * 2048) {   // 2048 atoms per CTA
+        return bf ? launch_pack_bulk<SPLIT_BF16, 512>(v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, status, wait_limit, s)
+                  : launch_pack_bulk<SPLIT_FP16, 512>(v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, status, wait_limit, s);
+    }
     if (vec && N <= 8 * per4) {   // 4 consecutive atoms per thread, 16-byte loads, 8-byte stores
         const int cs = (N + per4 - 1) / per4;
         return bf ? launch_pack_cluster_vec<SPLIT_BF16>(cs, v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, s)

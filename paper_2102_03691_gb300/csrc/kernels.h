@@ -150,9 +150,11 @@ struct ShcTcParams {
 };
 // Split/scale one block into the operands: velocities of step k to rows b Kpad + k and the
 // virials to ring rows (3a+b) R + (t0+k) mod R, with one power-of-two scale per row.
+// A bounded wait that runs out sets DEV_TIMEOUT in *status.
 cudaError_t launch_shc_tc_pack(const float *v, const float *W, int N, int N_pad, int K, int Kpad, int R,
-                        long long t0, int split, void *A_hi, void *A_lo, void *B_hi, void *B_lo,
-                        float *scaleA, float *scaleB, cudaStream_t s);
+                               long long t0, int split, void *A_hi, void *A_lo, void *B_hi, void *B_lo,
+                               float *scaleA, float *scaleB, int *status, long long wait_limit,
+                               cudaStream_t s);
 // One CTA per unit (pair c = 3a+b, tile pair, atom split): 9 n_pairs splits CTAs in clusters
 // of two (tile pairs 2j, 2j+1 share their step tile; n_pairs must be even).
 cudaError_t launch_shc_tc(const ShcTcParams &p, cudaStream_t s);

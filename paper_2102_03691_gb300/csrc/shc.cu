@@ -439,7 +439,7 @@ mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, i
         SHC_CUDA(s, mhc::launch_shc_tc_pack(v, W, (int)s->N, (int)s->N_pad, K, s->Kpad, s->R_tc, s->steps,
                                             s->precision == MHC_PREC_BF16X3 ? mhc::SPLIT_BF16 : mhc::SPLIT_FP16,
                                             s->A_hi, s->A_lo, s->B_hi, s->B_lo, s->scaleA, s->scaleB,
-                                            s->stream));
+                                            s->status, s->tcp.wait_limit, s->stream));
         cudaEvent_t ev1 = nullptr;
         if (s->profile) {
             if (s->prof_used == s->prof_events.size()) {

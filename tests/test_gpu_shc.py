@@ -68,10 +68,11 @@ def test_shc_precisions_ragged_blocks(precision):
     s.close()
 
 
-@pytest.mark.parametrize("N", [17000, 33000])
+@pytest.mark.parametrize("N", [12000, 17000, 33000])
 def test_shc_large_systems_pack_paths(N):
-    # N = 17000 packs with 8 atoms per thread in a cluster of 5 CTAs per step; N = 33000 is past
-    # what a cluster of 8 holds and takes the two-pass one-CTA-per-step kernel
+    # N = 12000 packs by bulk copies with 2048 atoms per CTA (clusters of 6); N = 17000 with 8
+    # atoms per thread in registers (clusters of 5); N = 33000 is past what a cluster of 8
+    # holds and takes the two-pass one-CTA-per-step kernel
     need_gpu()
     s, v, W = run(N, 24, 8, 12, seed=640 + N % 7)
     Kg, cnt = s.read_corr()
