@@ -195,76 +195,6 @@ __device__ __forceinline__ void put_split4(void *hi, void *lo, size_t idx, float
     *reinterpret_cast<uint2 *>(static_cast<uint16_t *>(lo) + idx) = make_uint2(l0 | (l1 << 16), l2 | (l3 << 16));
 }
 
-// As shc_tc_pack_cluster_kernel with thread t of CTA r holding the four consecutive atoms
-// r*2048 + 4t .. +3: their 12 velocity and 36 virial floats are 3 + 9 aligned 16-byte loads
-// (N % 4 == 0, 16-byte aligned inputs), and each operand row takes one 8-byte store.
-template <int SPLIT>
-__global__ void __launch_bounds__(PACK_THREADS, 1) shc_tc_pack_cluster_vec_kernel(
-    const float *__restrict__ v, const float *__restrict__ W, int N, int N_pad, int Kpad, int R,
-    long long t0, void *A_hi, void *A_lo, void *B_hi, void *B_lo, float *scaleA, float *scaleB) {
-    __shared__ float s_mx[PACK_THREADS / 32][12];
-    __shared__ float s_loc[12], s_mul[12];
-    const uint32_t rank = cluster_ctarank(), nrank = cluster_nctarank();
-    const int k = (int)(blockIdx.x / nrank);
-    const int i0 = (int)rank * PACK_THREADS * 4 + 4 * (int)threadIdx.x;
-    const bool in = i0 < N;   // N % 4 == 0: the four atoms are all in or all out
-    float xv[12], xw[36];
-    if (in) {
-        const float4 *pv = reinterpret_cast<const float4 *>(v + ((size_t)k * N + i0) * 3);
-        const float4 *pw = reinterpret_cast<const float4 *>(W + ((size_t)k * N + i0) * 9);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const float4 t = __ldg(pv + q);
-            xv[4 * q] = t.x; xv[4 * q + 1] = t.y; xv[4 * q + 2] = t.z; xv[4 * q + 3] = t.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float4 t = __ldg(pw + q);
-            xw[4 * q] = t.x; xw[4 * q + 1] = t.y; xw[4 * q + 2] = t.z; xw[4 * q + 3] = t.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 12; ++q) xv[q] = 0.f;
-#pragma unroll
-        for (int q = 0; q < 36; ++q) xw[q] = 0.f;
-    }
-    float mx[12];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-        mx[b] = fmaxf(fmaxf(fabsf(xv[b]), fabsf(xv[3 + b])), fmaxf(fabsf(xv[6 + b]), fabsf(xv[9 + b])));
-#pragma unroll
-    for (int c = 0; c < 9; ++c)
-        mx[3 + c] = fmaxf(fmaxf(fabsf(xw[c]), fabsf(xw[9 + c])), fmaxf(fabsf(xw[18 + c]), fabsf(xw[27 + c])));
-    block_max12(mx, s_mx, s_loc);
-    cluster_sync_all();
-    const int slot = (int)((t0 + k) % R);
-    if (threadIdx.x < 12) {
-        const int c = threadIdx.x;
-        float m = 0.f;
-        for (uint32_t q = 0; q < nrank; ++q) m = fmaxf(m, ld_shared_cluster_f32(mapa_shared(smem_u32(&s_loc[c]), q)));
-        const int sc = row_shift<SPLIT>(m);
-        s_mul[c] = ldexpf(1.f, sc);
-        if (rank == 0) {
-            if (c < 3) scaleB[(size_t)c * Kpad + k] = ldexpf(1.f, -sc);
-            else scaleA[(size_t)(c - 3) * R + slot] = ldexpf(1.f, -sc);
-        }
-    }
-    cluster_sync_all();
-    if (!in) return;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        const float m = s_mul[b];
-        put_split4<SPLIT>(B_hi, B_lo, ((size_t)b * Kpad + k) * N_pad + i0, xv[b] * m, xv[3 + b] * m,
-                          xv[6 + b] * m, xv[9 + b] * m);
-    }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-        const float m = s_mul[3 + c];
-        put_split4<SPLIT>(A_hi, A_lo, ((size_t)c * R + slot) * N_pad + i0, xw[c] * m, xw[9 + c] * m,
-                          xw[18 + c] * m, xw[27 + c] * m);
-    }
-}
-
 // Cluster of ceil(N / APC) CTAs per step k; CTA r bulk-copies the contiguous velocities and
 // virials of its atoms r*APC .. into shared memory (one TMA bulk copy per 16 KB), so every
 // load is asynchronous and registers stay few (four 256-thread CTAs per SM for APC = 1024).
@@ -677,25 +607,6 @@ cudaError_t launch_pack_cluster(int csize, const float *v, const float *W, int N
                               A_hi, A_lo, B_hi, B_lo, scaleA, scaleB);
 }
 
-template <int SPLIT>
-cudaError_t launch_pack_cluster_vec(int csize, const float *v, const float *W, int N, int N_pad, int K,
-                                    int Kpad, int R, long long t0, void *A_hi, void *A_lo, void *B_hi,
-                                    void *B_lo, float *scaleA, float *scaleB, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(K * csize), 1, 1);
-    cfg.blockDim = dim3(PACK_THREADS, 1, 1);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)csize;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, shc_tc_pack_cluster_vec_kernel<SPLIT>, v, W, N, N_pad, Kpad, R, t0,
-                              A_hi, A_lo, B_hi, B_lo, scaleA, scaleB);
-}
-
 template <int SPLIT, int THREADS>
 cudaError_t launch_pack_bulk(const float *v, const float *W, int N, int N_pad, int K, int Kpad, int R,
                              long long t0, void *A_hi, void *A_lo, void *B_hi, void *B_lo,
@@ -738,11 +649,6 @@ cudaError_t launch_shc_tc_pack(const float *v, const float *W, int N, int N_pad,
     if (vec && N <= 8 * 2048) {   // 2048 atoms per CTA
         return bf ? launch_pack_bulk<SPLIT_BF16, 512>(v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, status, wait_limit, s)
                   : launch_pack_bulk<SPLIT_FP16, 512>(v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, status, wait_limit, s);
-    }
-    if (vec && N <= 8 * per4) {   // 4 consecutive atoms per thread, 16-byte loads, 8-byte stores
-        const int cs = (N + per4 - 1) / per4;
-        return bf ? launch_pack_cluster_vec<SPLIT_BF16>(cs, v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, s)
-                  : launch_pack_cluster_vec<SPLIT_FP16>(cs, v, W, N, N_pad, K, Kpad, R, t0, A_hi, A_lo, B_hi, B_lo, scaleA, scaleB, s);
     }
     if (N <= 8 * per4) {   // clusters of up to 8 CTAs, 4 atoms per thread
         const int cs = (N + per4 - 1) / per4;
