@@ -315,7 +315,9 @@ mhc_status mhc_shc_set_precision(mhc_shc *s, int32_t precision);
  * resets them.  INVALID_ARG when profiling is off. */
 mhc_status mhc_shc_set_profile(mhc_shc *s, int32_t on);
 mhc_status mhc_shc_kernel_time(mhc_shc *s, double *ms, int64_t *launches);
-/* One block of K samples (host or device memory). */
+/* One block of K samples (host or device memory).  Device inputs must stay valid until the
+ * stream reaches the push; host inputs are copied before the call returns (two staging
+ * buffers on an internal copy stream: the upload overlaps the previous push's kernels). */
 mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, int32_t where);
 /* Raw sums Ksum [9][L] (float64) and origin counts [L] (int64); either may be NULL. */
 mhc_status mhc_shc_read_corr(mhc_shc *s, double *Ksum, int64_t *count, int32_t where);

@@ -186,7 +186,14 @@ struct mhc_shc {
     int precision = MHC_PREC_FP16X3;
     double dt = 0, T = 0, V = 0, Fe = 0;
     long long steps = 0;
-    float *Wring = nullptr, *partials = nullptr, *v_stage = nullptr, *W_stage = nullptr;
+    float *Wring = nullptr, *partials = nullptr;
+    // host inputs: two staging pairs filled on a copy stream (the upload of one push overlaps
+    // the kernels of the previous one; a pair is reused only after the push that read it)
+    float *v_stage[2] = {nullptr, nullptr}, *W_stage[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_done[2] = {nullptr, nullptr}, use_done[2] = {nullptr, nullptr};
+    bool use_pending[2] = {false, false};
+    int stage_next = 0;
     double *Ksum = nullptr, *out = nullptr;
     long long *counts = nullptr;
     size_t out_cap = 0;
@@ -379,8 +386,13 @@ mhc_status mhc_shc_create(mhc_shc **out, int32_t device, void *stream, int64_t n
     if ((e = alloc_path(s)) != cudaSuccess) return fail_free(e);
     if ((e = cudaMalloc(&s->Ksum, sizeof(double) * 9 * n_lags)) != cudaSuccess) return fail_free(e);
     if ((e = cudaMalloc(&s->counts, sizeof(long long) * n_lags)) != cudaSuccess) return fail_free(e);
-    if ((e = cudaMalloc(&s->v_stage, sizeof(float) * (size_t)k_max * n_atoms * 3)) != cudaSuccess) return fail_free(e);
-    if ((e = cudaMalloc(&s->W_stage, sizeof(float) * (size_t)k_max * n_atoms * 9)) != cudaSuccess) return fail_free(e);
+    for (int q = 0; q < 2; ++q) {
+        if ((e = cudaMalloc(&s->v_stage[q], sizeof(float) * (size_t)k_max * n_atoms * 3)) != cudaSuccess) return fail_free(e);
+        if ((e = cudaMalloc(&s->W_stage[q], sizeof(float) * (size_t)k_max * n_atoms * 9)) != cudaSuccess) return fail_free(e);
+        if ((e = cudaEventCreateWithFlags(&s->copy_done[q], cudaEventDisableTiming)) != cudaSuccess) return fail_free(e);
+        if ((e = cudaEventCreateWithFlags(&s->use_done[q], cudaEventDisableTiming)) != cudaSuccess) return fail_free(e);
+    }
+    if ((e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail_free(e);
     if ((e = cudaMemsetAsync(s->Ksum, 0, sizeof(double) * 9 * n_lags, s->stream)) != cudaSuccess) return fail_free(e);
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return fail_free(e);
     *out = s;
@@ -398,8 +410,16 @@ void mhc_shc_destroy(mhc_shc *s) {
     cudaFree(s->status);
     cudaFree(s->Ksum);
     cudaFree(s->counts);
-    cudaFree(s->v_stage);
-    cudaFree(s->W_stage);
+    if (s->copy_stream) {
+        cudaStreamSynchronize(s->copy_stream);
+        cudaStreamDestroy(s->copy_stream);
+    }
+    for (int q = 0; q < 2; ++q) {
+        cudaFree(s->v_stage[q]);
+        cudaFree(s->W_stage[q]);
+        if (s->copy_done[q]) cudaEventDestroy(s->copy_done[q]);
+        if (s->use_done[q]) cudaEventDestroy(s->use_done[q]);
+    }
     cudaFree(s->out);
     delete s;
 }
@@ -426,15 +446,26 @@ mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, i
         return sfail(s, MHC_ERR_INVALID_ARG, "bad inputs or K=%d outside [1, %d]", K, s->k_max);
     SHC_CUDA(s, cudaSetDevice(s->device));
     const size_t nv = (size_t)K * s->N * 3, nwf = (size_t)K * s->N * 9;
-    if (where == MHC_MEM_HOST) {
-        SHC_CUDA(s, cudaMemcpyAsync(s->v_stage, v, nv * 4, cudaMemcpyHostToDevice, s->stream));
-        v = s->v_stage;
+    int stage = -1;
+    if (where == MHC_MEM_HOST) {   // upload, and return only once the caller's memory is read
+        stage = s->stage_next;
+        s->stage_next ^= 1;
+        if (s->use_pending[stage]) SHC_CUDA(s, cudaStreamWaitEvent(s->copy_stream, s->use_done[stage], 0));
+        SHC_CUDA(s, cudaMemcpyAsync(s->v_stage[stage], v, nv * 4, cudaMemcpyHostToDevice, s->copy_stream));
+        SHC_CUDA(s, cudaMemcpyAsync(s->W_stage[stage], W, nwf * 4, cudaMemcpyHostToDevice, s->copy_stream));
+        SHC_CUDA(s, cudaEventRecord(s->copy_done[stage], s->copy_stream));
+        SHC_CUDA(s, cudaEventSynchronize(s->copy_done[stage]));
+        v = s->v_stage[stage];
+        W = s->W_stage[stage];
     }
-    if (shc_is_tc(s)) {
-        if (where == MHC_MEM_HOST) {
-            SHC_CUDA(s, cudaMemcpyAsync(s->W_stage, W, nwf * 4, cudaMemcpyHostToDevice, s->stream));
-            W = s->W_stage;
+    auto release = [&]() -> mhc_status {
+        if (stage >= 0) {
+            SHC_CUDA(s, cudaEventRecord(s->use_done[stage], s->stream));
+            s->use_pending[stage] = true;
         }
+        return MHC_OK;
+    };
+    if (shc_is_tc(s)) {
         if (!plan_tiles(s, K)) return sfail(s, MHC_ERR_UNSUPPORTED, "too many tile pairs for K=%d", K);
         SHC_CUDA(s, mhc::launch_shc_tc_pack(v, W, (int)s->N, (int)s->N_pad, K, s->Kpad, s->R_tc, s->steps,
                                             s->precision == MHC_PREC_BF16X3 ? mhc::SPLIT_BF16 : mhc::SPLIT_FP16,
@@ -456,11 +487,11 @@ mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, i
         mhc::launch_shc_tc_reduce(s->tcp, s->Ksum, s->stream);
         SHC_CUDA(s, cudaGetLastError());
         s->steps += K;
-        return MHC_OK;
+        return release();
     }
     // this block's virials into the ring at rows (t0 + k) mod R (at most two segments)
     const size_t row = (size_t)s->N * 9 * sizeof(float);
-    const cudaMemcpyKind kind = where == MHC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kind = cudaMemcpyDeviceToDevice;
     const int r0 = (int)(s->steps % s->R);
     const int first = std::min(K, s->R - r0);
     SHC_CUDA(s, cudaMemcpyAsync((char *)s->Wring + r0 * row, W, first * row, kind, s->stream));
@@ -487,7 +518,7 @@ mhc_status mhc_shc_push(mhc_shc *s, const float *v, const float *W, int32_t K, i
         s->partials, s->n_tiles, s->nc, s->nc_pad, s->Ksum);
     SHC_CUDA(s, cudaGetLastError());
     s->steps += K;
-    return MHC_OK;
+    return release();
 }
 
 mhc_status mhc_shc_set_profile(mhc_shc *s, int32_t on) {

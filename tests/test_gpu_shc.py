@@ -125,3 +125,30 @@ def test_shc_si_n8000_full_size():
     Ko, cnto = oracle.shc_corr(v, W, nc)
     assert np.all(series_rel_err(Kg.T, Ko.T) <= REL_TOL)
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3"])
+def test_shc_host_inputs_back_to_back_reuse_one_buffer(precision):
+    # host blocks are read before each push returns; one pinned buffer refilled after every
+    # push (no sync in between) gives bitwise the device-input result
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import SpectralHeatCurrent
+    N, T, nc, K = 96, 160, 24, 32
+    mass = synth.masses(N, isotopes=synth.SI_ISOTOPES, seed=650)
+    v, W = synth.Trajectory(mass, seed=650).next_block(T)
+    out = []
+    for host in (True, False):
+        s = SpectralHeatCurrent(N, nc, k_max=K, dt_ps=0.002, T_K=300.0, V_A3=N * 20.02,
+                                F_e=(1e-4, 0.0, 0.0), precision=precision)
+        bv = torch.empty((K, N, 3), dtype=torch.float32).pin_memory()
+        bw = torch.empty((K, N, 9), dtype=torch.float32).pin_memory()
+        for t0 in range(0, T, K):
+            if host:
+                bv.copy_(torch.from_numpy(v[t0:t0 + K]))
+                bw.copy_(torch.from_numpy(W[t0:t0 + K]))
+                s.push(bv, bw)
+            else:
+                s.push(torch.from_numpy(v[t0:t0 + K]).cuda(), torch.from_numpy(W[t0:t0 + K]).cuda())
+        out.append(s.read_corr()[0])
+        s.close()
+    np.testing.assert_array_equal(out[0], out[1])
