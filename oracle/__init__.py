@@ -3,7 +3,7 @@
 Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of bench.py
 may import this package.  The CUDA library never calls it and shares no code
 with it.  ``mhc_oracle.c`` holds the plain FP64 loops (Eqs. 10, 13, 16, 17,
-19 and frequency binning; the direction split of Sec. II.A; the SHC correlation and spectrum of Eqs. 20-23);
+19 and frequency binning; the direction split of Sec. II.A; bin-bin cross-correlations; the SHC correlation and spectrum of Eqs. 20-23);
 ``brute.py`` restates the same definitions with per-atom 3-vectors in scalar
 Python for tiny systems.
 
@@ -58,6 +58,7 @@ def lib():
             L.orc_modal_current_dir.argtypes = [_i64, _i64, _p, _p, _i64, _p, _p, _p, _i32,
                                                 _p, _p, _p]
             L.orc_gkma_corr.argtypes = [_i64, _i32, _p, _p, _i32, _p, _p]
+            L.orc_gkma_xcorr.argtypes = [_i64, _i32, _p, _i32, _p]
             L.orc_gk_kappa.argtypes = [_i32, _i32, _p, _p, _dbl, _dbl, _dbl, _p]
             L.orc_kappa_window.argtypes = [_i32, _i32, _p, _dbl, _dbl, _dbl, _p]
             L.orc_kappa_window.restype = _i32
@@ -154,6 +155,15 @@ def gkma_corr(Jb: np.ndarray, J: np.ndarray, L: int):
     cnt = np.empty(L, dtype=np.int64)
     lib().orc_gkma_corr(T, B, _ptr(Jb), _ptr(J), L, _ptr(C), _ptr(cnt))
     return C, cnt
+
+
+def gkma_xcorr(Jb: np.ndarray, L: int):
+    """Bin-bin cross-correlation sums Xsum [B][B][3][3][L] (first bin lagged, as in Eq. 17)."""
+    Jb = np.ascontiguousarray(Jb, dtype=np.float64)
+    T, B, _ = Jb.shape
+    X = np.empty((B, B, 3, 3, L))
+    lib().orc_gkma_xcorr(T, B, _ptr(Jb), L, _ptr(X))
+    return X
 
 
 def gk_kappa(Csum: np.ndarray, count: np.ndarray, dt_ps: float, T_K: float, V_A3: float):

@@ -243,6 +243,29 @@ void orc_gkma_corr(int64_t T, int32_t B, const double *Jb, const double *J, int3
 }
 
 /*
+ * Cross-correlations of binned modal heat currents (the mode-mode correlations the paper
+ * notes GKMA allows, Sec. II.B after Eq. 17 and Sec. III.C.i; with one bin per mode they are
+ * the mode-mode correlations themselves).  Same lag convention as Eq. 17: the first current
+ * is lagged, the second sits at the time origin; all origins with t - l >= 0:
+ *   Xsum[b][b2][mu][nu][l] = sum_{t=l}^{T-1} Jb[t][b][mu] * Jb[t-l][b2][nu]
+ * With every mode binned, sum_b2 Jb[t][b2] = J[t] (Eq. 15), so sum_b2 Xsum = Csum of Eq. 17.
+ */
+void orc_gkma_xcorr(int64_t T, int32_t B, const double *Jb, int32_t L, double *Xsum)
+{
+#pragma omp parallel for schedule(static)
+    for (int32_t b = 0; b < B; ++b)
+        for (int32_t b2 = 0; b2 < B; ++b2)
+            for (int mu = 0; mu < 3; ++mu)
+                for (int nu = 0; nu < 3; ++nu)
+                    for (int32_t l = 0; l < L; ++l) {
+                        double s = 0.0;
+                        for (int64_t t = l; t < T; ++t)
+                            s += Jb[(t * B + b) * 3 + mu] * Jb[((t - l) * B + b2) * 3 + nu];
+                        Xsum[((((int64_t)b * B + b2) * 3 + mu) * 3 + nu) * L + l] = s;
+                    }
+}
+
+/*
  * Eq. 17 running integral by the trapezoid rule, kappa(0) = 0:
  *   C(l)      = Csum(l) / count(l)          (0 where count is 0)
  *   kappa(l)  = c * dt * sum_{j=1}^{l} (C(j-1) + C(j)) / 2

@@ -324,6 +324,46 @@ def test_correlation_matches_fft_and_hcacf():
     np.testing.assert_allclose(C.sum(axis=0), hcacf, rtol=1e-9, atol=1e-8)
 
 
+# ---------------------------------------------------------------- bin-bin cross-correlation
+def test_xcorr_golden_two_atoms():
+    # hand example: bins 0, 1 of the two-atom case, lag 0 and 1 (values from the golden Jb;
+    # step 1 is twice step 0 here, so the lag direction is pinned by the FFT test below)
+    ex = golden("two_atoms_mixed_basis_two_steps")
+    Jb = np.array(ex["Jb"], float)          # [2][2][3]
+    X = oracle.gkma_xcorr(Jb, 2)
+    # bin0 x with bin1 z: lag 0 = 10*4.5 + 20*9, lag 1 = Jb[1][0][x] * Jb[0][1][z] = 20 * 4.5
+    np.testing.assert_allclose(X[0, 1, 0, 2], [10 * 4.5 + 20 * 9, 20 * 4.5], rtol=0, atol=1e-12)
+    # bin1 y with bin0 y: lag 0 = 0.5*2.5 + 1*5, lag 1 = 1 * 2.5
+    np.testing.assert_allclose(X[1, 0, 1, 1], [0.5 * 2.5 + 1 * 5, 1 * 2.5], rtol=0, atol=1e-12)
+
+
+def test_xcorr_sums_to_eq17_with_every_mode_binned():
+    # all 3N modes binned: sum over the second bin is the total current (Eq. 15), so the
+    # cross-correlations add up to the Eq. 17 sums
+    N, T, L, B = 6, 40, 7, 4
+    E, mass, v, W = tiny_system(N, T=T, seed=52)
+    bins = np.arange(3 * N) % B
+    r = oracle.modal_current(E, mass, v, W, bins, B)
+    X = oracle.gkma_xcorr(r["Jb"], L)
+    C, _ = oracle.gkma_corr(r["Jb"], r["J"], L)
+    np.testing.assert_allclose(X.sum(axis=1), C, rtol=1e-10, atol=1e-10 * np.abs(C).max())
+
+
+def test_xcorr_matches_fft_and_lag0_symmetry():
+    rng = np.random.default_rng(53)
+    T, B, L = 64, 3, 9
+    Jb = rng.standard_normal((T, B, 3))
+    X = oracle.gkma_xcorr(Jb, L)
+    n = 2 * T
+    F = np.fft.rfft(Jb, n=n, axis=0)                                  # [f][B][3]
+    # sum_t x(t) y(t - l) = irfft(X(f) conj(Y(f)))[l]
+    full = np.fft.irfft(F[:, :, None, :, None] * np.conj(F[:, None, :, None, :]), n=n, axis=0)
+    ref = np.moveaxis(full[:L], 0, -1)                                 # [B][B][3][3][L]
+    np.testing.assert_allclose(X, ref, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(X[:, :, :, :, 0], np.transpose(X[:, :, :, :, 0], (1, 0, 3, 2)),
+                               rtol=1e-13, atol=1e-13)
+
+
 def test_impulse_correlation():
     # A single nonzero modal-current sample at t0 gives one term per lag.
     T, B, L, t0 = 10, 2, 4, 6
@@ -389,6 +429,8 @@ MUTATIONS = {
                                    "y += (double)Wt[i * 9 + 3 * a + b] * e[3 * i + a] / sqrt(mass[i]);"),
     "dir_bin_layout_swapped": ("jb[((int64_t)b * B + bn) * 3 + a] += jn[n * 9 + 3 * b + a];",
                                "jb[((int64_t)b * B + bn) * 3 + a] += jn[n * 9 + 3 * a + b];"),
+    "xcorr_lag_on_second_bin": ("s += Jb[(t * B + b) * 3 + mu] * Jb[((t - l) * B + b2) * 3 + nu];",
+                                "s += Jb[((t - l) * B + b) * 3 + mu] * Jb[(t * B + b2) * 3 + nu];"),
     "shc_trapezoid_dropped": ("const double trap = (l == 0 || l == nc - 1) ? 0.5 : 1.0;",
                               "const double trap = 1.0;"),
 }
@@ -411,7 +453,7 @@ def _pins_pass(L):
     real = oracle.lib()
     for fn in ("orc_bins_uniform", "orc_modal_current", "orc_gkma_corr", "orc_gk_kappa",
                "orc_hnema", "orc_kappa_window", "orc_orthonormality", "orc_shc_corr",
-               "orc_shc_kappa", "orc_modal_current_dir"):
+               "orc_shc_kappa", "orc_modal_current_dir", "orc_gkma_xcorr"):
         getattr(L, fn).argtypes = getattr(real, fn).argtypes
         getattr(L, fn).restype = getattr(real, fn).restype
     checks = [test_golden_one_atom_identity_basis, test_golden_two_atoms_mixed_basis,
@@ -421,7 +463,8 @@ def _pins_pass(L):
               lambda: test_oracle_matches_scalar_brute_force(3, 7, 6, 4),
               lambda: test_shc_matches_scalar_brute_force(3, 7, 4),
               test_shc_spectrum_constant_input_closed_form,
-              test_golden_direction_split_rotated_basis, test_golden_direction_split_two_atoms]
+              test_golden_direction_split_rotated_basis, test_golden_direction_split_two_atoms,
+              test_xcorr_golden_two_atoms, test_xcorr_matches_fft_and_lag0_symmetry]
     oracle._lib = L
     try:
         for c in checks:
