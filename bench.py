@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--basis", default="qr", choices=["qr", "gaussian"],
                     help="qr: orthonormal E from a seeded QR; gaussian: seeded N(0, 1/3N) "
                          "entries (same sizes and work, for tools that cannot load torch.linalg)")
+    ap.add_argument("--xcorr", action="store_true",
+                    help="also accumulate the bin-bin cross-correlations (GKMA workloads)")
     ap.add_argument("--direction", action="store_true",
                     help="direction-resolved split J_n^{ab} (every per-bin output x 3, same "
                          "tensor work; one-SM 128-column tiles)")
@@ -267,7 +269,8 @@ def config_dict(w, args, precision):
             "bins": w["B"], "lags": w["L"], "gkma": bool(w["gkma"]), "precision": precision,
             "l2": "inputs larger than L2 (eigenvectors streamed every step; 8-block input pool)",
             "basis": getattr(args, "basis", "qr"),
-            "direction_split": bool(getattr(args, "direction", False))}
+            "direction_split": bool(getattr(args, "direction", False)),
+            "bin_xcorr": bool(getattr(args, "xcorr", False))}
 
 
 
@@ -571,7 +574,8 @@ def main():
     def make(precision):
         h = ModalHeatCurrent(precision=precision, k_max=K, n_lags=L, dt_ps=w["dt_ps"],
                              T_K=w["T_K"], V_A3=V, F_e=w["Fe"], device=local,
-                             tile_config=args.tile_config, direction=args.direction)
+                             tile_config=args.tile_config, direction=args.direction,
+                             xcorr=args.xcorr and L > 0)
         h.set_modes(E, mass, f)
         h.set_bins_uniform(w["f"][0], w["f"][1], B)
         return h

@@ -93,6 +93,14 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
                                       Same tensor work as without the split.  Tensor-core
                                       precisions take tile_config 0 (autotuned among 3, 4), 3 or 4;
                                       set at mhc_create, not with mhc_set_flags; not for groups. */
+#define MHC_FLAG_XCORR 0x20        /* with MHC_FLAG_GKMA: also accumulate the cross-correlations of
+                                      the binned currents, X_{b b'}^{mu nu}(l) = sum over origins of
+                                      J_b^mu(t) J_{b'}^nu(t - l) (the mode-mode correlations that the
+                                      modal currents of GKMA allow, at bin resolution; one bin per
+                                      mode gives them per mode).  Summed over b' they equal the
+                                      Eq. 17 sums when every mode is binned.  State: R^2 * 9 * L FP64
+                                      values (R = output rows, B or 3B); read with mhc_read_xcorr /
+                                      mhc_read_kappa_xcorr.  Set at mhc_create. */
 
 typedef struct {
     int32_t device;      /* CUDA device ordinal */
@@ -229,6 +237,18 @@ mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, do
 
 /* Last basis check of mhc_set_modes (FP64 on the GPU): max |E^T E - I|.
  * Returns WARN_NOT_ORTHONORMAL above tol, INVALID_ARG if no check was run. */
+/*
+ * Bin-bin cross-correlation sums (MHC_FLAG_XCORR): xsum [R][R][3][3][L] float64 with
+ * xsum[b][b'][mu][nu][l] = sum_{t=l}^{T_s-1} J_b^mu(t) J_{b'}^nu(t-l), R = B (3B with the
+ * direction split, rows b*B + bin), and the origin counts [L] as for mhc_read_corr.
+ * mhc_read_kappa_xcorr applies the Eq. 17 running integral of mhc_read_kappa_gk to every
+ * pair: kappa_tau [R][R][3][3][L], kappa_w [R][R][3][3], W/(m K).  Either pointer may be NULL.
+ * Errors: INVALID_ARG without MHC_FLAG_XCORR.
+ */
+mhc_status mhc_read_xcorr(mhc_handle *h, double *xsum, int64_t *count, int32_t where);
+mhc_status mhc_read_kappa_xcorr(mhc_handle *h, double *kappa_tau, double tau_lo, double tau_hi,
+                                double *kappa_w, int32_t where);
+
 mhc_status mhc_check_orthonormality(mhc_handle *h, double tol, double *max_abs_err);
 
 /* Counters and sizes. */

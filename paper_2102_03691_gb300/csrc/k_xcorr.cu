@@ -1,0 +1,125 @@
+// Bin-bin cross-correlations of the binned modal heat currents (the mode-mode correlations
+// the paper notes GKMA allows; at one bin per mode they are exactly those).  Same lag
+// convention as Eq. 17: the first current is lagged, the second sits at the time origin.
+//   X[l][i][j] += sum_{k: t0+k-l >= 0} Jb[k][i] * Jb(t0+k-l)[j],   i = 3b+mu, j = 3b'+nu
+// The state is lag-major so that one CTA (one lag, a 64 x 64 block of (i, j)) writes its
+// FP64 sums coalesced; the read-out transposes to [b][b'][mu][nu][l].
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mhc {
+
+namespace {
+
+constexpr int XC_TILE = 64;      // rows / columns of a CTA's block
+constexpr int XC_KC = 32;        // steps per FP32 partial (folded into FP64 after each)
+constexpr int XC_THREADS = 256;  // 16 x 16 threads, 4 x 4 outputs each
+
+// ring[(t0 + k) mod R][j] = Jb[k][j]: the block's binned currents join the history ring
+__global__ void jb_ring_store_kernel(const float *__restrict__ Jb, int K, int n, float *ring,
+                                     int R, long long t0_host, const long long *t0_dev) {
+    const long long t0 = t0_dev ? *t0_dev : t0_host;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)K * n) return;
+    const long long k = q / n, j = q - k * n;
+    ring[((t0 + k) % R) * n + j] = Jb[q];
+}
+
+__global__ void __launch_bounds__(XC_THREADS) bin_xcorr_kernel(
+    const float *__restrict__ Jb, const float *__restrict__ ring, int R, double *X, int K, int n,
+    long long t0_host, const long long *t0_dev) {
+    __shared__ __align__(16) float sA[XC_KC][XC_TILE];
+    __shared__ __align__(16) float sS[XC_KC][XC_TILE];
+    const long long t0 = t0_dev ? *t0_dev : t0_host;
+    const int l = blockIdx.z;
+    const int i0 = blockIdx.y * XC_TILE, j0 = blockIdx.x * XC_TILE;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+    float part[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += XC_KC) {
+        for (int q = threadIdx.x; q < XC_KC * XC_TILE; q += XC_THREADS) {
+            const int kk = q / XC_TILE, c = q - kk * XC_TILE;
+            const int k = k0 + kk;
+            float a = 0.f, s = 0.f;
+            if (k < K) {
+                if (i0 + c < n) a = Jb[(size_t)k * n + i0 + c];
+                const long long t = t0 + k - l;   // the origin of this step at lag l
+                if (t >= 0 && j0 + c < n) s = ring[(size_t)(t % R) * n + j0 + c];
+            }
+            sA[kk][c] = a;
+            sS[kk][c] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) part[a][b] = 0.f;
+#pragma unroll 8
+        for (int kk = 0; kk < XC_KC; ++kk) {
+            const float4 av = *reinterpret_cast<const float4 *>(&sA[kk][ty * 4]);
+            const float4 sv = *reinterpret_cast<const float4 *>(&sS[kk][tx * 4]);
+            const float ar[4] = {av.x, av.y, av.z, av.w}, sr[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) part[a][b] = fmaf(ar[a], sr[b], part[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += (double)part[a][b];
+        __syncthreads();
+    }
+    double *Xl = X + (size_t)l * n * n;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = i0 + ty * 4 + a;
+        if (i >= n) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int j = j0 + tx * 4 + b;
+            if (j < n) Xl[(size_t)i * n + j] += acc[a][b];
+        }
+    }
+}
+
+// out[((b B + b2) 3 + mu) 3 + nu][l] = X[l][3b+mu][3b2+nu]
+__global__ void xcorr_transpose_kernel(const double *__restrict__ X, int nb, int L, double *out) {
+    const int n = 3 * nb;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)n * n * L) return;
+    const long long l = q % L, r = q / L;   // r = ((b nb + b2) 3 + mu) 3 + nu
+    const int nu = (int)(r % 3), mu = (int)((r / 3) % 3);
+    const long long bb = r / 9;
+    const int b2 = (int)(bb % nb), b = (int)(bb / nb);
+    out[q] = X[(size_t)l * n * n + (size_t)(3 * b + mu) * n + 3 * b2 + nu];
+}
+
+}  // namespace
+
+void launch_jb_ring_store(const float *Jb, int K, int nb, float *ring, int R, long long t0,
+                          const long long *t0_dev, cudaStream_t s) {
+    const long long total = (long long)K * nb * 3;
+    if (total <= 0) return;
+    jb_ring_store_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Jb, K, 3 * nb, ring, R, t0, t0_dev);
+}
+
+void launch_bin_xcorr(const float *Jb, const float *ring, int R, double *X, int K, int nb, int L,
+                      long long t0, const long long *t0_dev, cudaStream_t s) {
+    const int n = 3 * nb;
+    if (L <= 0 || K <= 0 || n <= 0) return;
+    dim3 grid((n + XC_TILE - 1) / XC_TILE, (n + XC_TILE - 1) / XC_TILE, L);
+    bin_xcorr_kernel<<<grid, XC_THREADS, 0, s>>>(Jb, ring, R, X, K, n, t0, t0_dev);
+}
+
+void launch_xcorr_transpose(const double *X, int nb, int L, double *out, cudaStream_t s) {
+    const long long total = 9ll * nb * nb * L;
+    if (total <= 0) return;
+    xcorr_transpose_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, nb, L, out);
+}
+
+}  // namespace mhc

@@ -226,6 +226,8 @@ int64_t n_out_bins(const mhc_handle *h) { return (int64_t)h->B * (h->dir ? 3 : 1
 // Partial-sum slots per step component (one set per direction with the split).
 int64_t slot_stride(const mhc_handle *h) { return h->n_slots * (h->dir ? 3 : 1); }
 
+bool has_xcorr(const mhc_handle *h) { return (h->prm.flags & MHC_FLAG_XCORR) != 0; }
+
 // The direction split parks its bracket sums in TMEM beside one-SM 128-column tiles.
 bool dir_config_ok(const TcConfig &c) { return c.bn == 128 && !c.pair; }
 
@@ -256,6 +258,10 @@ mhc_status reset_accumulators(mhc_handle *h) {
     if (h->prm.flags & MHC_FLAG_GKMA) {
         if ((s = dev_alloc(h, "Csum", sizeof(double) * B * 9 * L)) != MHC_OK) return s;
         if ((s = dev_alloc(h, "Jring", sizeof(double) * h->R_ring * 3)) != MHC_OK) return s;
+    }
+    if (has_xcorr(h)) {   // lag-major [L][3R][3R] sums and the ring of past binned currents
+        if ((s = dev_alloc(h, "Xsum", sizeof(double) * L * 9 * B * B)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "Jbring", sizeof(float) * h->R_ring * 3 * B)) != MHC_OK) return s;
     }
     return MHC_OK;
 }
@@ -594,6 +600,14 @@ mhc_status finish_kernels(mhc_handle *h, int K) {
                         dptr<long long>(h, "steps_dev"), h->stream);
         h->launches++;
     }
+    if (has_xcorr(h)) {
+        launch_jb_ring_store(dptr<float>(h, "Jb"), K, (int)n_out_bins(h), dptr<float>(h, "Jbring"),
+                             h->R_ring, h->steps, dptr<long long>(h, "steps_dev"), h->stream);
+        launch_bin_xcorr(dptr<float>(h, "Jb"), dptr<float>(h, "Jbring"), h->R_ring,
+                         dptr<double>(h, "Xsum"), K, (int)n_out_bins(h), h->prm.n_lags, h->steps,
+                         dptr<long long>(h, "steps_dev"), h->stream);
+        h->launches += 2;
+    }
     launch_advance_steps(dptr<long long>(h, "steps_dev"), K, h->stream);
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
@@ -724,6 +738,8 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
     if (p->n_lags < 0) return fail(nullptr, MHC_ERR_INVALID_ARG, "n_lags must be >= 0");
     if ((p->flags & MHC_FLAG_GKMA) && p->n_lags < 1)
         return fail(nullptr, MHC_ERR_INVALID_ARG, "GKMA needs n_lags >= 1");
+    if ((p->flags & MHC_FLAG_XCORR) && !(p->flags & MHC_FLAG_GKMA))
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "MHC_FLAG_XCORR needs MHC_FLAG_GKMA");
     if (p->precision < MHC_PREC_FP32 || p->precision > MHC_PREC_FP16X3)
         return fail(nullptr, MHC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
     if (p->tile_config < 0 || p->tile_config > TC_NUM_CONFIGS)
@@ -1068,6 +1084,54 @@ mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, do
     return MHC_OK;
 }
 
+mhc_status mhc_read_xcorr(mhc_handle *h, double *xsum, int64_t *count, int32_t where) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!has_xcorr(h) || !h->bins_ready)
+        return fail(h, MHC_ERR_INVALID_ARG, "MHC_FLAG_XCORR is not set or no bins");
+    const int L = h->prm.n_lags;
+    const int nb = (int)n_out_bins(h);
+    const size_t n = (size_t)9 * nb * nb * L;
+    mhc_status s;
+    if (xsum) {
+        if ((s = dev_alloc(h, "xc_out", sizeof(double) * n, false)) != MHC_OK) return s;
+        launch_xcorr_transpose(dptr<double>(h, "Xsum"), nb, L, dptr<double>(h, "xc_out"), h->stream);
+        h->launches++;
+        MHC_CUDA(h, cudaGetLastError());
+        if ((s = copy_out(h, xsum, dptr<double>(h, "xc_out"), sizeof(double) * n, where)) != MHC_OK) return s;
+    }
+    if (count) {
+        if ((s = dev_alloc(h, "counts", sizeof(long long) * L, false)) != MHC_OK) return s;
+        launch_lag_counts(h->steps, L, dptr<long long>(h, "counts"), h->stream);
+        h->launches++;
+        if ((s = copy_out(h, count, dptr<long long>(h, "counts"), sizeof(long long) * L, where)) != MHC_OK)
+            return s;
+    }
+    return MHC_OK;
+}
+
+mhc_status mhc_read_kappa_xcorr(mhc_handle *h, double *kappa_tau, double tau_lo, double tau_hi,
+                                double *kappa_w, int32_t where) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!has_xcorr(h) || !h->bins_ready)
+        return fail(h, MHC_ERR_INVALID_ARG, "MHC_FLAG_XCORR is not set or no bins");
+    const int L = h->prm.n_lags;
+    const int nb = (int)n_out_bins(h);
+    const size_t rows = (size_t)9 * nb * nb;
+    mhc_status s;
+    if ((s = dev_alloc(h, "xc_out", sizeof(double) * rows * L, false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "xk_out", sizeof(double) * rows * (L + 1), false)) != MHC_OK) return s;
+    launch_xcorr_transpose(dptr<double>(h, "Xsum"), nb, L, dptr<double>(h, "xc_out"), h->stream);
+    double *dk = dptr<double>(h, "xk_out"), *dw = dk + rows * L;
+    const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
+    launch_gk_kappa(dptr<double>(h, "xc_out"), nb * nb, L, h->steps, coef * h->prm.dt_ps, tau_lo,
+                    tau_hi, h->prm.dt_ps, dk, dw, h->stream);
+    h->launches += 2;
+    MHC_CUDA(h, cudaGetLastError());
+    if (kappa_tau && (s = copy_out(h, kappa_tau, dk, sizeof(double) * rows * L, where)) != MHC_OK) return s;
+    if (kappa_w && (s = copy_out(h, kappa_w, dw, sizeof(double) * rows, where)) != MHC_OK) return s;
+    return MHC_OK;
+}
+
 mhc_status mhc_check_orthonormality(mhc_handle *h, double tol, double *max_abs_err) {
     if (!h) return MHC_ERR_INVALID_ARG;
     if (h->ortho_err < 0) return fail(h, MHC_ERR_INVALID_ARG, "no basis check was run (ortho_probe < 0)");
@@ -1154,7 +1218,10 @@ mhc_status mhc_state_size(mhc_handle *h, size_t *bytes) {
     const bool g = h->prm.flags & MHC_FLAG_GKMA;
     const size_t nb = (size_t)n_out_bins(h);
     *bytes = sizeof(StateHeader) + sizeof(double) * (nb * 3 + 3) +
-             (g ? sizeof(double) * (nb * 9 * h->prm.n_lags + (size_t)h->R_ring * 3) : 0);
+             (g ? sizeof(double) * (nb * 9 * h->prm.n_lags + (size_t)h->R_ring * 3) : 0) +
+             (has_xcorr(h) ? sizeof(double) * 9 * nb * nb * h->prm.n_lags +
+                                 sizeof(float) * (size_t)h->R_ring * 3 * nb
+                           : 0);
     return MHC_OK;
 }
 
@@ -1168,7 +1235,7 @@ mhc_status mhc_get_state(mhc_handle *h, void *blob, size_t bytes) {
     const bool g = h->prm.flags & MHC_FLAG_GKMA;
     const size_t nb = (size_t)n_out_bins(h);
     *hd = StateHeader{STATE_MAGIC, (int32_t)nb, h->prm.n_lags, h->prm.k_max, h->R_ring,
-                      (g ? 1 : 0) | (h->dir ? 2 : 0), h->steps, h->M_eff};
+                      (g ? 1 : 0) | (h->dir ? 2 : 0) | (has_xcorr(h) ? 4 : 0), h->steps, h->M_eff};
     char *p = static_cast<char *>(blob) + sizeof(StateHeader);
     MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "hsum"), sizeof(double) * nb * 3, cudaMemcpyDeviceToHost));
     p += sizeof(double) * nb * 3;
@@ -1179,6 +1246,13 @@ mhc_status mhc_get_state(mhc_handle *h, void *blob, size_t bytes) {
         MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Csum"), sizeof(double) * nc, cudaMemcpyDeviceToHost));
         p += sizeof(double) * nc;
         MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Jring"), sizeof(double) * h->R_ring * 3, cudaMemcpyDeviceToHost));
+        p += sizeof(double) * h->R_ring * 3;
+    }
+    if (has_xcorr(h)) {
+        const size_t nx = 9 * nb * nb * h->prm.n_lags, nr = (size_t)h->R_ring * 3 * nb;
+        MHC_CUDA(h, cudaMemcpy(p, dptr<double>(h, "Xsum"), sizeof(double) * nx, cudaMemcpyDeviceToHost));
+        p += sizeof(double) * nx;
+        MHC_CUDA(h, cudaMemcpy(p, dptr<float>(h, "Jbring"), sizeof(float) * nr, cudaMemcpyDeviceToHost));
     }
     return MHC_OK;
 }
@@ -1193,7 +1267,8 @@ mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes) {
     const size_t nb = (size_t)n_out_bins(h);
     if (hd->magic != STATE_MAGIC || hd->B != (int32_t)nb || hd->L != h->prm.n_lags ||
         hd->k_max != h->prm.k_max || hd->R_ring != h->R_ring ||
-        hd->kind != ((g ? 1 : 0) | (h->dir ? 2 : 0)) || hd->M_eff != h->M_eff || hd->steps < 0)
+        hd->kind != ((g ? 1 : 0) | (h->dir ? 2 : 0) | (has_xcorr(h) ? 4 : 0)) || hd->M_eff != h->M_eff ||
+        hd->steps < 0)
         return fail(h, MHC_ERR_STATE, "state blob does not match this handle's modes/bins/lags/k_max");
     MHC_CUDA(h, cudaStreamSynchronize(h->stream));
     const char *p = static_cast<const char *>(blob) + sizeof(StateHeader);
@@ -1206,6 +1281,13 @@ mhc_status mhc_set_state(mhc_handle *h, const void *blob, size_t bytes) {
         MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Csum"), p, sizeof(double) * nc, cudaMemcpyHostToDevice));
         p += sizeof(double) * nc;
         MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Jring"), p, sizeof(double) * h->R_ring * 3, cudaMemcpyHostToDevice));
+        p += sizeof(double) * h->R_ring * 3;
+    }
+    if (has_xcorr(h)) {
+        const size_t nx = 9 * nb * nb * h->prm.n_lags, nr = (size_t)h->R_ring * 3 * nb;
+        MHC_CUDA(h, cudaMemcpy(dptr<double>(h, "Xsum"), p, sizeof(double) * nx, cudaMemcpyHostToDevice));
+        p += sizeof(double) * nx;
+        MHC_CUDA(h, cudaMemcpy(dptr<float>(h, "Jbring"), p, sizeof(float) * nr, cudaMemcpyHostToDevice));
     }
     h->steps = hd->steps;
     h->K_last = 0;

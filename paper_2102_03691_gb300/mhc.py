@@ -25,6 +25,7 @@ F32, F64 = 0, 1
 DOF_MAJOR, MODE_MAJOR = 0, 1
 FLAG_GKMA, FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_TEST_STALL = 0x1, 0x2, 0x4, 0x8
 FLAG_DIRECTION = 0x10
+FLAG_XCORR = 0x20
 
 # Every entry point declared in include/mhc.h.
 EXPORTS = (
@@ -32,7 +33,7 @@ EXPORTS = (
     "mhc_set_modes", "mhc_set_bins_uniform", "mhc_set_bin_ids", "mhc_push", "mhc_sync",
     "mhc_read_binned_current", "mhc_read_total_current", "mhc_read_hnema", "mhc_read_corr",
     "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_set_flags",
-    "mhc_kernel_time",
+    "mhc_kernel_time", "mhc_read_xcorr", "mhc_read_kappa_xcorr",
     "mhc_reset",
     "mhc_state_size", "mhc_get_state", "mhc_set_state", "mhc_group_create",
     "mhc_group_destroy", "mhc_group_push", "mhc_group_read_hnema", "mhc_binned_current_noalloc",
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_read_hnema.argtypes = [vp, vp, vp, i32]
     L.mhc_read_corr.argtypes = [vp, vp, vp, i32]
     L.mhc_read_kappa_gk.argtypes = [vp, vp, dbl, dbl, vp, i32]
+    L.mhc_read_xcorr.argtypes = [vp, vp, vp, i32]
+    L.mhc_read_kappa_xcorr.argtypes = [vp, vp, dbl, dbl, vp, i32]
     L.mhc_check_orthonormality.argtypes = [vp, dbl, ctypes.POINTER(dbl)]
     L.mhc_get_info.argtypes = [vp, ctypes.POINTER(MhcInfo)]
     L.mhc_kernel_time.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
@@ -325,7 +328,7 @@ class ModalHeatCurrent:
                  gkma: bool | None = None, dt_ps: float = 0.01, T_K: float = 300.0,
                  V_A3: float = 1.0, F_e=(1e-5, 0.0, 0.0), device: int = 0, stream=None,
                  tile_config: int = 0, ortho_probe: int = -1, flags: int = 0,
-                 direction: bool = False):
+                 direction: bool = False, xcorr: bool = False):
         self._L = load()
         p = MhcParams()
         self._L.mhc_default_params(ctypes.byref(p))
@@ -336,7 +339,8 @@ class ModalHeatCurrent:
         p.n_lags = n_lags
         p.precision = PRECISIONS[precision]
         gk = (n_lags > 0) if gkma is None else gkma
-        p.flags = flags | (FLAG_GKMA if gk else 0) | (FLAG_DIRECTION if direction else 0)
+        p.flags = (flags | (FLAG_GKMA if gk else 0) | (FLAG_DIRECTION if direction else 0)
+                   | (FLAG_XCORR if xcorr else 0))
         p.tile_config = tile_config
         p.ortho_probe = ortho_probe
         p.dt_ps, p.T_K, p.V_A3 = dt_ps, T_K, V_A3
@@ -473,6 +477,26 @@ class ModalHeatCurrent:
         self._check(self._L.mhc_read_kappa_gk(self._h, kt.ctypes.data_as(ctypes.c_void_p), tau_lo,
                                               tau_hi, kw.ctypes.data_as(ctypes.c_void_p),
                                               MEM_HOST))
+        return kt, kw
+
+    def read_xcorr(self):
+        """Bin-bin cross-correlation sums [rows][rows][3][3][L] and origin counts [L]
+        (rows = B, or (3, B) with the direction split)."""
+        L_ = self.params.n_lags
+        X = np.empty((*self._rows(), *self._rows(), 3, 3, L_))
+        cnt = np.empty(L_, np.int64)
+        self._check(self._L.mhc_read_xcorr(self._h, X.ctypes.data_as(ctypes.c_void_p),
+                                           cnt.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
+        return X, cnt
+
+    def read_kappa_xcorr(self, tau_lo: float, tau_hi: float):
+        """Eq. 17 running integral of every bin pair: kappa_tau [rows][rows][3][3][L] and its
+        tau-window average [rows][rows][3][3], W/(m K)."""
+        L_ = self.params.n_lags
+        kt = np.empty((*self._rows(), *self._rows(), 3, 3, L_))
+        kw = np.empty((*self._rows(), *self._rows(), 3, 3))
+        self._check(self._L.mhc_read_kappa_xcorr(self._h, kt.ctypes.data_as(ctypes.c_void_p), tau_lo,
+                                                 tau_hi, kw.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
         return kt, kw
 
     def check_orthonormality(self, tol: float = 1e-6) -> float:
