@@ -2,8 +2,10 @@
 // the paper notes GKMA allows; at one bin per mode they are exactly those).  Same lag
 // convention as Eq. 17: the first current is lagged, the second sits at the time origin.
 //   X[l][i][j] += sum_{k: t0+k-l >= 0} Jb[k][i] * Jb(t0+k-l)[j],   i = 3b+mu, j = 3b'+nu
-// The state is lag-major so that one CTA (one lag, a 64 x 64 block of (i, j)) writes its
-// FP64 sums coalesced; the read-out transposes to [b][b'][mu][nu][l].
+// FP32 products and 32-step FP32 partials are summed over the block in a float pair and added
+// to the FP64 state once per launch.  The state is lag-major so that one CTA (one lag, a
+// 64 x 64 block of (i, j)) writes its sums coalesced; the read-out transposes to
+// [b][b'][mu][nu][l].
 #include "common.cuh"
 #include "kernels.h"
 
@@ -12,8 +14,19 @@ namespace mhc {
 namespace {
 
 constexpr int XC_TILE = 64;      // rows / columns of a CTA's block
-constexpr int XC_KC = 32;        // steps per FP32 partial (folded into FP64 after each)
+constexpr int XC_KC = 32;        // steps per FP32 partial (folded into a float pair after each)
 constexpr int XC_THREADS = 256;  // 16 x 16 threads, 4 x 4 outputs each
+
+// (s, c) += x exactly as an unevaluated float pair (TwoSum; _rn keeps it from being contracted).
+// GB300's FP64 pipe is narrow: folding each 32-step partial into FP64 registers cost more issue
+// time than the 512 FMAs of the chunk; the pair carries ~48 bits with FP32 instructions only.
+__device__ __forceinline__ void pair_add(float &s, float &c, float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+}
 
 // ring[(t0 + k) mod R][j] = Jb[k][j]: the block's binned currents join the history ring
 __global__ void jb_ring_store_kernel(const float *__restrict__ Jb, int K, int n, float *ring,
@@ -34,21 +47,24 @@ __global__ void __launch_bounds__(XC_THREADS) bin_xcorr_kernel(
     const int l = blockIdx.z;
     const int i0 = blockIdx.y * XC_TILE, j0 = blockIdx.x * XC_TILE;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4];
-    float part[4][4];
+    float acc[4][4], cmp[4][4], part[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < 4; ++b) acc[a][b] = cmp[a][b] = 0.f;
     for (int k0 = 0; k0 < K; k0 += XC_KC) {
+        // origin of step k0 + kk at lag l: time tb + kk, ring row (rb + kk) mod R
+        const long long tb = t0 + k0 - l;
+        const int rb = tb >= 0 ? (int)(tb % R) : (int)(((tb % R) + R) % R);
         for (int q = threadIdx.x; q < XC_KC * XC_TILE; q += XC_THREADS) {
             const int kk = q / XC_TILE, c = q - kk * XC_TILE;
             const int k = k0 + kk;
             float a = 0.f, s = 0.f;
             if (k < K) {
                 if (i0 + c < n) a = Jb[(size_t)k * n + i0 + c];
-                const long long t = t0 + k - l;   // the origin of this step at lag l
-                if (t >= 0 && j0 + c < n) s = ring[(size_t)(t % R) * n + j0 + c];
+                int row = rb + kk;
+                if (row >= R) row -= R;
+                if (tb + kk >= 0 && j0 + c < n) s = ring[(size_t)row * n + j0 + c];
             }
             sA[kk][c] = a;
             sS[kk][c] = s;
@@ -71,7 +87,7 @@ __global__ void __launch_bounds__(XC_THREADS) bin_xcorr_kernel(
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += (double)part[a][b];
+            for (int b = 0; b < 4; ++b) pair_add(acc[a][b], cmp[a][b], part[a][b]);
         __syncthreads();
     }
     double *Xl = X + (size_t)l * n * n;
@@ -82,7 +98,7 @@ __global__ void __launch_bounds__(XC_THREADS) bin_xcorr_kernel(
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int j = j0 + tx * 4 + b;
-            if (j < n) Xl[(size_t)i * n + j] += acc[a][b];
+            if (j < n) Xl[(size_t)i * n + j] += (double)acc[a][b] + (double)cmp[a][b];
         }
     }
 }

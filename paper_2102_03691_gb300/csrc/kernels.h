@@ -196,7 +196,7 @@ void launch_hnema_finalize_group(const HnemaGroupArgs &a, double *mean, double *
 void launch_jb_ring_store(const float *Jb, int K, int nb, float *ring, int R, long long t0,
                           const long long *t0_dev, cudaStream_t s);
 // X[l][3b+mu][3b'+nu] += sum_k Jb[k][b][mu] Jb(t0+k-l)[b'][nu] over t0+k-l >= 0 (FP32 products,
-// 32-step FP32 partials, FP64 sums); the ring must already hold the block.
+// 32-step FP32 partials in a float pair, FP64 state); the ring must already hold the block.
 void launch_bin_xcorr(const float *Jb, const float *ring, int R, double *X, int K, int nb, int L,
                       long long t0, const long long *t0_dev, cudaStream_t s);
 // out[b][b'][mu][nu][l] = X[l][3b+mu][3b'+nu]

@@ -1,0 +1,102 @@
+"""Degenerate and extreme cases through the C ABI against the FP64 oracle: one atom, one-step
+pushes, every mode excluded, a single bin, one lag, more lags than steps, and the same for the
+direction split and the spectral heat current."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_03691_gb300 import synth
+from tests.parity import REL_TOL, series_rel_err
+from tests.test_gpu_parity import TOL, make_case, need_gpu, run_gpu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3"])
+def test_one_atom_one_step_pushes(precision):
+    # N = 1 (three modes), K = 1 per push, 2 bins, 3 lags over 5 steps.  (BF16x3 is left out:
+    # its ~16-bit operand pairs give errors that only average down over many atoms.)
+    need_gpu()
+    c = make_case(N=1, M=3, T=5, B=2, seed=901)
+    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], 2)
+    C0, _ = oracle.gkma_corr(o["Jb"], o["J"], 3)
+    h, Jb, J = run_gpu(c, precision, K=1, L=3)
+    np.testing.assert_allclose(J, o["J"], rtol=1e-12, atol=1e-12)
+    assert np.all(series_rel_err(Jb, o["Jb"]) <= TOL[precision])
+    C, cnt = h.read_corr()
+    np.testing.assert_array_equal(cnt, [5, 4, 3])
+    assert np.all(series_rel_err(C.reshape(-1, 3).T, C0.reshape(-1, 3).T) <= TOL[precision])
+    h.close()
+
+
+def test_every_mode_excluded_gives_zeros():
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import ModalHeatCurrent
+    c = make_case(N=20, M=60, T=8, B=3, seed=902)
+    h = ModalHeatCurrent(precision="fp16x3", k_max=8, n_lags=4)
+    h.set_modes(c["E"], c["mass"], c["f"])
+    h.set_bin_ids(np.full(60, -1, np.int32), 3)
+    assert h.info()["n_modes_kept"] == 0
+    h.push(c["v"], c["W"])
+    assert np.all(h.read_binned_current() == 0)
+    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], np.full(60, -1, np.int32), 3)
+    np.testing.assert_allclose(h.read_total_current(), o["J"], rtol=1e-12, atol=1e-12)
+    C, _ = h.read_corr()
+    assert np.all(C == 0)
+    mean, kap = h.read_hnema()
+    assert np.all(mean == 0) and np.all(kap == 0)
+    h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3"])
+def test_single_bin_single_lag_and_lags_beyond_the_run(precision):
+    need_gpu()
+    c = make_case(N=30, M=90, T=12, B=1, seed=903)
+    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], 1)
+    # one lag
+    h, Jb, _ = run_gpu(c, precision, K=5, L=1)
+    C, cnt = h.read_corr()
+    C0, cnt0 = oracle.gkma_corr(o["Jb"], o["J"], 1)
+    np.testing.assert_array_equal(cnt, cnt0)
+    assert np.all(np.abs(C - C0) <= TOL[precision] * np.abs(C0).max())
+    h.close()
+    # 20 lags over 12 steps: lags 12..19 have no origins and stay zero
+    h, Jb, _ = run_gpu(c, precision, K=5, L=20)
+    C, cnt = h.read_corr()
+    C0, cnt0 = oracle.gkma_corr(o["Jb"], o["J"], 20)
+    np.testing.assert_array_equal(cnt, cnt0)
+    assert np.all(C[..., 12:] == 0) and np.all(cnt[12:] == 0)
+    assert np.all(series_rel_err(C[..., :12].reshape(-1, 12).T, C0[..., :12].reshape(-1, 12).T)
+                  <= TOL[precision])
+    kt, kw = h.read_kappa_gk(0.0, 0.19)
+    assert np.all(np.isfinite(kt)) and np.all(np.isfinite(kw))
+    h.close()
+
+
+def test_direction_split_one_atom():
+    need_gpu()
+    c = make_case(N=1, M=3, T=4, B=1, seed=904)
+    od = oracle.modal_current_dir(c["E"], c["mass"], c["v"], c["W"], c["bins"], 1)
+    h, Jb, _ = run_gpu(c, "fp16x3", K=2, direction=True)
+    assert np.all(series_rel_err(Jb, od["Jbd"]) <= REL_TOL)
+    h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3"])
+def test_shc_one_atom_and_lags_beyond_the_run(precision):
+    # one atom, 10 lags over 6 samples pushed one at a time
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import SpectralHeatCurrent
+    mass = synth.masses(1, 28.085)
+    v, W = synth.Trajectory(mass, seed=905).next_block(6)
+    s = SpectralHeatCurrent(1, 10, k_max=1, dt_ps=0.002, T_K=300.0, V_A3=20.02,
+                            F_e=(1e-4, 0.0, 0.0), precision=precision)
+    for t in range(6):
+        s.push(torch.from_numpy(v[t:t + 1]).cuda(), torch.from_numpy(W[t:t + 1]).cuda())
+    K, cnt = s.read_corr()
+    Ko, cnto = oracle.shc_corr(v, W, 10)
+    np.testing.assert_array_equal(cnt, cnto)
+    assert np.all(K[:, 6:] == 0)
+    assert np.all(series_rel_err(K[:, :6].T, Ko[:, :6].T) <= REL_TOL)
+    s.close()
