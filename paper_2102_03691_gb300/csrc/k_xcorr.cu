@@ -52,24 +52,40 @@ __global__ void __launch_bounds__(XC_THREADS) bin_xcorr_kernel(
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = cmp[a][b] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += XC_KC) {
+    // Each thread stages the same 8 (kk, c) slots of both tiles for every chunk; the next
+    // chunk's values are loaded into registers while the current one is multiplied.
+    constexpr int PER = XC_KC * XC_TILE / XC_THREADS;   // 8
+    float ra[PER], rs[PER];
+    auto fetch = [&](int k0) {
         // origin of step k0 + kk at lag l: time tb + kk, ring row (rb + kk) mod R
         const long long tb = t0 + k0 - l;
         const int rb = tb >= 0 ? (int)(tb % R) : (int)(((tb % R) + R) % R);
-        for (int q = threadIdx.x; q < XC_KC * XC_TILE; q += XC_THREADS) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int q = threadIdx.x + u * XC_THREADS;
             const int kk = q / XC_TILE, c = q - kk * XC_TILE;
             const int k = k0 + kk;
-            float a = 0.f, s = 0.f;
+            float a = 0.f, sv = 0.f;
             if (k < K) {
                 if (i0 + c < n) a = Jb[(size_t)k * n + i0 + c];
                 int row = rb + kk;
                 if (row >= R) row -= R;
-                if (tb + kk >= 0 && j0 + c < n) s = ring[(size_t)row * n + j0 + c];
+                if (tb + kk >= 0 && j0 + c < n) sv = ring[(size_t)row * n + j0 + c];
             }
-            sA[kk][c] = a;
-            sS[kk][c] = s;
+            ra[u] = a;
+            rs[u] = sv;
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < K; k0 += XC_KC) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int q = threadIdx.x + u * XC_THREADS;
+            sA[q / XC_TILE][q % XC_TILE] = ra[u];
+            sS[q / XC_TILE][q % XC_TILE] = rs[u];
         }
         __syncthreads();
+        if (k0 + XC_KC < K) fetch(k0 + XC_KC);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
