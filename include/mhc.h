@@ -91,8 +91,9 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
                                       binned current [K][3][B][3], HNEMA [3][B][3], GKMA sums
                                       [3][B][3][3][L], each correlated with the total J (Eq. 17).
                                       Same tensor work as without the split.  Tensor-core
-                                      precisions take tile_config 0 (autotuned among 3, 4), 3 or 4;
-                                      set at mhc_create, not with mhc_set_flags; not for groups. */
+                                      precisions take tile_config 0 (autotuned among the
+                                      128-column tiles 3, 4, 7, 8) or one of those; set at
+                                      mhc_create, not with mhc_set_flags; not for groups. */
 #define MHC_FLAG_XCORR 0x20        /* with MHC_FLAG_GKMA: also accumulate the cross-correlations of
                                       the binned currents, X_{b b'}^{mu nu}(l) = sum over origins of
                                       J_b^mu(t) J_{b'}^nu(t - l) (the mode-mode correlations that the
@@ -111,8 +112,9 @@ typedef struct {
     int32_t flags;       /* MHC_FLAG_* */
     int32_t tile_config; /* tensor-core tile: 0 = autotune on the first push of each K;
                             1..4 = one-SM tiles of 128 modes x (columns, k per stage, stages)
-                            (256,64,2), (256,32,4), (128,64,3), (128,32,6); 5..6 = two-SM tiles
-                            (CTA pair, 256 modes x 256 columns) with (64,3), (32,6). */
+                            (256,64,2), (256,32,4), (128,64,3), (128,32,6); 5..8 = two-SM tiles
+                            (CTA pair, 256 modes x columns) with (256,64,3), (256,32,6),
+                            (128,64,4), (128,32,8). */
     int32_t ortho_probe; /* -1: no basis check in set_modes; 0: full E^T E; P>0: P probe modes */
     double dt_ps;        /* sampling interval between pushed steps (Eq. 17 dt') */
     double T_K;          /* temperature T (Eq. 17, 19) */

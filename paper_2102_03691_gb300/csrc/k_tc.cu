@@ -127,6 +127,42 @@ __device__ __forceinline__ void unpark_y(float (&acc)[128], uint32_t taddr) {
     }
 }
 
+// After promoting the chunk that ends at k-block kn: park the finished direction segment.
+// `lanes` is the TMEM address of this warp's lane quarter (column 0).
+__device__ __forceinline__ void dir_maybe_park(float (&acc)[128], const TcProblem &P, int kn,
+                                               uint32_t lanes) {
+    if (P.dir_seg_kb && kn % P.dir_seg_kb == 0 && kn < P.n_kb)
+        park_y(acc, lanes + PARK_COL + (uint32_t)(96 * (kn / P.dir_seg_kb - 1)));
+}
+
+// Direction-resolved epilogue of one warp's 32 steps starting at kbase:
+// J_n^{ab}(k) = Xdot_n(k) Y_n^{ab}(k), direction 2 from the registers, directions 1 and 0
+// from their parked columns; bin-run sums into partials[k][a][b n_slots + slot].
+__device__ __forceinline__ void dir_epilogue(float (&acc)[128], const TcProblem &P, int kbase,
+                                             uint32_t take, int slot, uint32_t lanes) {
+    const size_t row = 3 * (size_t)P.n_slots;
+    for (int b = 2; b >= 0; --b) {
+        if (b < 2) unpark_y(acc, lanes + PARK_COL + (uint32_t)(96 * b));
+        // opaque per pass: keeps the 128 scale loads from being hoisted out of the direction
+        // loop (they would not fit in registers beside acc)
+        const float *csb = P.col_scale;
+        asm volatile("" : "+l"(csb));
+#pragma unroll
+        for (int s4 = 0; s4 < 32; ++s4) {
+            const int k = kbase + s4;
+            if (k >= P.K) break;   // warp-uniform
+            const float *cs = csb + 4 * k;
+            const float x = acc[4 * s4] * __ldg(cs);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float y = acc[4 * s4 + 1 + a] * __ldg(cs + 1 + a);
+                const float v = seg_scan(x * y, take);
+                if (slot >= 0) P.partials[((size_t)k * 3 + a) * row + (size_t)b * P.n_slots + slot] = v;
+            }
+        }
+    }
+}
+
 template <int BN, int BK, int STAGES, int NPROB>
 __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_constant__ TcParams<NPROB> p) {
     using L = TcLayout<BN, BK, STAGES>;
@@ -301,44 +337,15 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
                 tc_fence_before();
                 mbar_arrive(&acc_empty[abuf]);
                 if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
-                if constexpr (BN == 128) {
-                    const int kn = kb0 + CHUNK_KB;
-                    if (P.dir_seg_kb && kn % P.dir_seg_kb == 0 && kn < P.n_kb)
-                        park_y(acc, tmem_base + ((uint32_t)(qw * 32) << 16) + PARK_COL +
-                                        (uint32_t)(96 * (kn / P.dir_seg_kb - 1)));
-                }
+                if constexpr (BN == 128)
+                    dir_maybe_park(acc, P, kb0 + CHUNK_KB, tmem_base + ((uint32_t)(qw * 32) << 16));
             }
             if (!ok) break;
             // Eq. 16 product and the bin-run sums of this warp's 32 steps
             const int kbase = ct * (BN / 4) + ch * 32;
             if constexpr (BN == 128) {
                 if (P.dir_seg_kb) {
-                    // direction-resolved: J_n^{ab}(k) = Xdot_n(k) Y_n^{ab}(k), direction 2 from
-                    // the registers, directions 1 and 0 from their parked columns
-                    const size_t row = 3 * (size_t)P.n_slots;
-                    for (int b = 2; b >= 0; --b) {
-                        if (b < 2)
-                            unpark_y(acc, tmem_base + ((uint32_t)(qw * 32) << 16) + PARK_COL +
-                                              (uint32_t)(96 * b));
-                        // opaque per pass: keeps the 128 scale loads from being hoisted out of
-                        // the direction loop (they would not fit in registers beside acc)
-                        const float *csb = P.col_scale;
-                        asm volatile("" : "+l"(csb));
-#pragma unroll
-                        for (int s4 = 0; s4 < 32; ++s4) {
-                            const int k = kbase + s4;
-                            if (k >= P.K) break;   // warp-uniform
-                            const float *cs = csb + 4 * k;
-                            const float x = acc[4 * s4] * __ldg(cs);
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                const float y = acc[4 * s4 + 1 + a] * __ldg(cs + 1 + a);
-                                const float v = seg_scan(x * y, take);
-                                if (slot >= 0)
-                                    P.partials[((size_t)k * 3 + a) * row + (size_t)b * P.n_slots + slot] = v;
-                            }
-                        }
-                    }
+                    dir_epilogue(acc, P, kbase, take, slot, tmem_base + ((uint32_t)(qw * 32) << 16));
                     continue;
                 }
             }
@@ -370,28 +377,31 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
 
 // =====================================================================================
 // CTA-pair variant (tcgen05 cta_group::2).  A cluster of two CTAs on two SMs computes a
-// 256-mode x 256-column tile: each CTA stages its own 128 modes of E and its own half
-// (128 columns) of B, the leader CTA (rank 0) issues M=256 MMAs that read both CTAs'
-// shared memory, and each CTA's TMEM receives the accumulator of its own 128 modes
-// (all 256 columns).  Per SM this halves the B bytes per flop against the one-SM tile
-// (64 KB instead of 96 KB per 64-wide k-block at the same tensor work).
+// 256-mode x BN-column tile (BN = 256 or 128): each CTA stages its own 128 modes of E and
+// its own half (BN/2 columns) of B, the leader CTA (rank 0) issues M=256 MMAs that read both
+// CTAs' shared memory, and each CTA's TMEM receives the accumulator of its own 128 modes
+// (all BN columns).  Per SM this halves the B bytes per flop against the one-SM tile of the
+// same width (BN = 256: 64 KB instead of 96 KB per 64-wide k-block at the same tensor work).
+// With BN = 128 the TMEM keeps 256 free columns, where the direction split parks its sums.
 //   - TMA loads of both CTAs complete on the leader's `full` barrier (armed by the
 //     leader with both CTAs' bytes);
 //   - the leader's commits arrive on `empty`/`acc_full` of both CTAs (multicast);
 //   - each epilogue warp of both CTAs arrives on the leader's `acc_empty` after
 //     promoting a chunk.
-template <int BK, int STAGES>
+template <int BN_, int BK, int STAGES>
 struct TcPairLayout {
-    static constexpr int BN = 256;
+    static constexpr int BN = BN_;
     static constexpr int A_BYTES = TC_BM * BK * 2;
     static constexpr int B_BYTES = (BN / 2) * BK * 2;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int TILE_BYTES = STAGES * STAGE_BYTES;
     static constexpr int SMEM_BYTES = TILE_BYTES + 256 + 1024;
+    // 128-column pair tiles keep 2 x 96 columns of it for the direction split's parked sums
     static constexpr uint32_t TMEM_COLS = 512;
     static constexpr uint32_t SWIZZLE_CODE = BK == 64 ? 2u : 4u;
     static constexpr uint32_t SBO = 8 * BK * 2;
-    static constexpr int EPI_WARPS = 8;
+    static constexpr int EPI_WARPS = BN / 32;
+    static_assert(BN == 128 || BN == 256, "BN");
     static constexpr int THREADS = 128 + 32 * EPI_WARPS;
     static_assert(STAGES * 2 + 5 <= 28, "barrier area");
 };
@@ -428,10 +438,9 @@ struct PairTileIter {
     }
 };
 
-template <int BK, int STAGES, int NPROB>
-__global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_constant__ TcParams<NPROB> p) {
-    using L = TcPairLayout<BK, STAGES>;
-    constexpr int BN = L::BN;
+template <int BN, int BK, int STAGES, int NPROB>
+__global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid_constant__ TcParams<NPROB> p) {
+    using L = TcPairLayout<BN, BK, STAGES>;
     constexpr int CHUNK_KB = PROMOTE_D / BK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -614,9 +623,17 @@ __global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_cons
                     else mbar_arrive_cluster_relaxed(empty_leader[abuf]);
                 }
                 if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+                if constexpr (BN == 128)   // parked in this CTA's own TMEM (its 128 modes)
+                    dir_maybe_park(acc, P, kb0 + CHUNK_KB, tmem_base + ((uint32_t)(qw * 32) << 16));
             }
             if (!ok) break;
             const int kbase = ct * (BN / 4) + ch * 32;
+            if constexpr (BN == 128) {
+                if (P.dir_seg_kb) {
+                    dir_epilogue(acc, P, kbase, take, slot, tmem_base + ((uint32_t)(qw * 32) << 16));
+                    continue;
+                }
+            }
 #pragma unroll
             for (int s4 = 0; s4 < 32; ++s4) {
                 const int k = kbase + s4;
@@ -644,10 +661,10 @@ __global__ void __launch_bounds__(384, 1) tc_modal_pair_kernel(const __grid_cons
     if (warp == 2) tmem_dealloc_pair(tmem_base, L::TMEM_COLS);
 }
 
-template <int BK, int STAGES, int NPROB>
+template <int BN, int BK, int STAGES, int NPROB>
 cudaError_t launch_pair_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
-    using L = TcPairLayout<BK, STAGES>;
-    auto kern = tc_modal_pair_kernel<BK, STAGES, NPROB>;
+    using L = TcPairLayout<BN, BK, STAGES>;
+    auto kern = tc_modal_pair_kernel<BN, BK, STAGES, NPROB>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -670,10 +687,10 @@ cudaError_t launch_pair_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s)
     return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-template <int BK, int STAGES, int NPROB>
+template <int BN, int BK, int STAGES, int NPROB>
 int max_pairs_impl() {
-    using L = TcPairLayout<BK, STAGES>;
-    auto kern = tc_modal_pair_kernel<BK, STAGES, NPROB>;
+    using L = TcPairLayout<BN, BK, STAGES>;
+    auto kern = tc_modal_pair_kernel<BN, BK, STAGES, NPROB>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES) !=
         cudaSuccess)
         return 0;
@@ -714,8 +731,10 @@ cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
 template <int NPROB>
 cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s) {
     if (c.pair) {
-        if (c.bn == 256 && c.bk == 64 && c.stages == 3) return launch_pair_impl<64, 3, NPROB>(p, c.grid, s);
-        if (c.bn == 256 && c.bk == 32 && c.stages == 6) return launch_pair_impl<32, 6, NPROB>(p, c.grid, s);
+        if (c.bn == 256 && c.bk == 64 && c.stages == 3) return launch_pair_impl<256, 64, 3, NPROB>(p, c.grid, s);
+        if (c.bn == 256 && c.bk == 32 && c.stages == 6) return launch_pair_impl<256, 32, 6, NPROB>(p, c.grid, s);
+        if (c.bn == 128 && c.bk == 64 && c.stages == 4) return launch_pair_impl<128, 64, 4, NPROB>(p, c.grid, s);
+        if (c.bn == 128 && c.bk == 32 && c.stages == 8) return launch_pair_impl<128, 32, 8, NPROB>(p, c.grid, s);
         return cudaErrorInvalidValue;
     }
     if (c.bn == 256 && c.bk == 64 && c.stages == 2) return launch_impl<256, 64, 2, NPROB>(p, c.grid, s);
@@ -729,7 +748,7 @@ cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s
 
 const TcConfig TC_CONFIGS[TC_NUM_CONFIGS] = {
     {256, 64, 2, 0, 0}, {256, 32, 4, 0, 0}, {128, 64, 3, 0, 0}, {128, 32, 6, 0, 0},
-    {256, 64, 3, 1, 0}, {256, 32, 6, 1, 0}};
+    {256, 64, 3, 1, 0}, {256, 32, 6, 1, 0}, {128, 64, 4, 1, 0}, {128, 32, 8, 1, 0}};
 
 bool tc_config_supported(const TcConfig &c) {
     for (const TcConfig &k : TC_CONFIGS)
@@ -739,8 +758,8 @@ bool tc_config_supported(const TcConfig &c) {
 
 int tc_max_pairs(const TcConfig &c) {
     if (!c.pair) return 0;
-    if (c.bk == 64) return max_pairs_impl<64, 3, 1>();
-    return max_pairs_impl<32, 6, 1>();
+    if (c.bn == 256) return c.bk == 64 ? max_pairs_impl<256, 64, 3, 1>() : max_pairs_impl<256, 32, 6, 1>();
+    return c.bk == 64 ? max_pairs_impl<128, 64, 4, 1>() : max_pairs_impl<128, 32, 8, 1>();
 }
 
 size_t tc_smem_bytes(const TcConfig &c) {   // must match TcLayout / TcPairLayout::SMEM_BYTES

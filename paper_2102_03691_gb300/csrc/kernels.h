@@ -107,11 +107,11 @@ struct TcConfig {
     int bn;       // columns per tile (MMA N): 128 or 256
     int bk;       // K elements per stage: 64 (128-byte swizzle) or 32 (64-byte swizzle)
     int stages;   // shared-memory pipeline depth
-    int pair;     // 1: two-SM tile (cta_group::2, 256 modes per CTA pair)
+    int pair;     // 1: two-SM tile (cta_group::2, 256 modes per CTA pair, bn columns shared)
     int grid;
 };
 // Pipeline shapes the autotuner chooses from (index + 1 = mhc_params.tile_config).
-constexpr int TC_NUM_CONFIGS = 6;
+constexpr int TC_NUM_CONFIGS = 8;
 extern const TcConfig TC_CONFIGS[TC_NUM_CONFIGS];
 // Clusters of two CTAs of a two-SM configuration that can be resident at once (0 on error).
 int tc_max_pairs(const TcConfig &c);

@@ -228,8 +228,8 @@ int64_t slot_stride(const mhc_handle *h) { return h->n_slots * (h->dir ? 3 : 1);
 
 bool has_xcorr(const mhc_handle *h) { return (h->prm.flags & MHC_FLAG_XCORR) != 0; }
 
-// The direction split parks its bracket sums in TMEM beside one-SM 128-column tiles.
-bool dir_config_ok(const TcConfig &c) { return c.bn == 128 && !c.pair; }
+// The direction split parks its bracket sums in TMEM beside 128-column tiles (one SM or a pair).
+bool dir_config_ok(const TcConfig &c) { return c.bn == 128; }
 
 void drop_graphs(mhc_handle *h) {
     for (auto &kv : h->graphs)
@@ -426,7 +426,7 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
 mhc_status set_tc_config(mhc_handle *h, const TcConfig &c) {
     if (!tc_config_supported(c)) return fail(h, MHC_ERR_INVALID_ARG, "unsupported tile configuration");
     if (h->dir && !dir_config_ok(c))
-        return fail(h, MHC_ERR_INVALID_ARG, "the direction split needs a one-SM 128-column tile (tile_config 3 or 4)");
+        return fail(h, MHC_ERR_INVALID_ARG, "the direction split needs a 128-column tile (tile_config 3, 4, 7 or 8)");
     const bool remap = h->bins_ready && (c.bn != h->tc.bn || c.bk != h->tc.bk || c.pair != h->tc.pair);
     h->tc = c;
     if (remap) {
@@ -747,7 +747,7 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
     if ((p->flags & MHC_FLAG_DIRECTION) && p->tile_config > 0 &&
         !dir_config_ok(TC_CONFIGS[p->tile_config - 1]))
         return fail(nullptr, MHC_ERR_INVALID_ARG,
-                    "MHC_FLAG_DIRECTION needs tile_config 0, 3 or 4 (one-SM 128-column tiles)");
+                    "MHC_FLAG_DIRECTION needs tile_config 0, 3, 4, 7 or 8 (128-column tiles)");
     if (!(p->dt_ps > 0) || !(p->T_K > 0) || !(p->V_A3 > 0))
         return fail(nullptr, MHC_ERR_INVALID_ARG, "dt_ps, T_K and V_A3 must be positive");
     int ndev = 0;

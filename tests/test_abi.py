@@ -38,7 +38,7 @@ def test_default_params_and_status_strings():
 
 
 @pytest.mark.parametrize("field,value", [("k_max", 0), ("k_max", 5000), ("n_lags", -1),
-                                         ("precision", 7), ("tile_config", 7), ("dt_ps", 0.0)])
+                                         ("precision", 7), ("tile_config", 9), ("dt_ps", 0.0)])
 def test_create_rejects_bad_params(field, value):
     L = mhc.load()
     p = mhc.MhcParams()
