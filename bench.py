@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -187,6 +188,20 @@ def profiled_traffic(workload: str, precision: str, tile: dict):
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
+def host_cpu() -> str:
+    """CPU model of the host, from /proc/cpuinfo (Arm reports no model name: take the part)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "CPU part"):
+            for line in txt.splitlines():
+                if line.startswith(key):
+                    return f"{key}: {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def oracle_sample(w: dict, budget_s: float, seed: int):
     """Time the FP64 oracle on a bounded sample of the workload: S MD steps of the
     full atom count N, restricted to the first Ms modes, plus the GKMA correlation
@@ -215,7 +230,8 @@ def oracle_sample(w: dict, budget_s: float, seed: int):
     el = time.perf_counter() - t
     return {"value": Ms * N * S / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{S} MD steps x {Ms} of {M} modes x {N} atoms (FP64 oracle: Eq. 10/13/16, "
-                      f"binning, GKMA correlation), {el:.1f} s"}
+                      f"binning, GKMA correlation), {el:.1f} s",
+            "cpu": host_cpu(), "nproc": os.cpu_count()}
 
 
 def run_reference(args, w):
@@ -685,6 +701,25 @@ def main():
                 "ms_per_step": 1e3 * el32 / args.fp32_steps, "steps": args.fp32_steps,
                 "projection_tflops": 2.0 * M * D * 4 * K * n32 / (ms32 / 1e3) / 1e12 if ms32 else None}
         h32.close()
+        # sanity point for the FP32 CUDA-core GEMM: cuBLAS SGEMM (TF32 off) of the same shape
+        tf32 = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        a = torch.randn(M, D, device=dev)
+        b = torch.randn(D, 4 * K, device=dev)
+        torch.mm(a, b)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(5):
+            torch.mm(a, b)
+        g1.record()
+        torch.cuda.synchronize()
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        fp32["cublas_sgemm_tflops"] = 2.0 * M * D * 4 * K * 5 / (g0.elapsed_time(g1) / 1e3) / 1e12
+        props = torch.cuda.get_device_properties(dev)
+        fp32["fp32_peak_derived_tflops"] = (props.multi_processor_count * 128 * 2 *
+                                            float(measured_peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6 / 1e12)
+        del a, b
 
     if rank != 0:
         return
