@@ -317,9 +317,10 @@ mhc_status mhc_group_read_hnema(mhc_group *g, double *kappa, double *mean_J, int
  *   n_lags  L correlation lags, L <= 4096 (the paper uses 250 lags of 2 fs); k_max <= 1024.
  * Arithmetic (mhc_shc_set_precision, default MHC_PREC_FP16X3): the tensor-core precisions
  * compute each block as a banded contraction over the atoms, G_b[(a,tau)][t] =
- * sum_i W_i^{ab}(tau) v_i^b(t), in 128 x 128 tiles with split 16-bit operands (one
- * power-of-two scale per row) and FP32 accumulation, whose diagonals t - tau = l are the
- * lag sums; MHC_PREC_FP32 runs FP32 FMAs on the CUDA cores.  Lag sums are FP64 in both.
+ * sum_i W_i^{ab}(tau) v_i^b(t), in 128 x 256 tiles (two per CTA pair) with split 16-bit
+ * operands (one power-of-two scale per row) and FP32 accumulation, whose diagonals
+ * t - tau = l are the lag sums; MHC_PREC_FP32 runs FP32 FMAs on the CUDA cores.  Lag sums
+ * are FP64 in both.
  * Errors as for the modal handle; messages through mhc_shc_last_error.  A kernel that waited
  * too long on a barrier is reported as MHC_ERR_TIMEOUT by the next host read.
  */

@@ -8,15 +8,17 @@
 // so that each is a contiguous run of rows of the virial ring); only the tiles that touch
 // the band 0 <= t - tau < nc are computed, and the atom axis is split into ranges so that
 // the units (pair 3a+b, tile, atom range) fill the SMs.  Two units that differ only in
-// their tau tile (p, p+1) form a cluster of two CTAs and share the velocity tile: each
-// loads one half of it and multicasts it to both (the kernel is bound by L2-to-SM traffic;
-// this cuts it from 48 to 32 KB per CTA and stage).
+// their tau tile (p, p+1) form a CTA pair (tcgen05 cta_group::2): the leader issues M = 256
+// MMAs over both tau tiles, each CTA stages its own 128 ring rows and one half (128 rows) of
+// the shared velocity tile, and each CTA's TMEM receives its own 128 x 256 accumulator.  The
+// kernel is bound by the bytes that reach each SM: 32 KB per CTA and stage, against 48 KB when
+// every CTA held the whole velocity tile.
 //
 // Operands are 16-bit hi/lo pairs with one power-of-two scale per row (FP16: the row maximum
 // is scaled below 2^14); three tcgen05.mma per 16-atom slice (hi*lo, lo*hi, hi*hi) into an
 // FP32 TMEM accumulator that is promoted into FP32 registers every 128 atoms (the tensor
-// core truncates when it accumulates; see k_tc.cu).  Warp roles as in k_tc.cu: warp 0 TMA,
-// warp 1 MMA, warp 2 TMEM, warps 4..11 promotion + epilogue.
+// core truncates when it accumulates; see k_tc.cu).  Warp roles as in k_tc.cu's pair kernel:
+// warp 0 TMA (both CTAs), warp 1 MMA (leader), warp 2 TMEM, warps 4..11 promotion + epilogue.
 //
 // Epilogue: thread (warp q + 4h, lane r) holds row 32q + r, columns 128h .. 128h+127 of the
 // tile in registers.  The sums along the diagonals c - r = j of the warp's 32 x 128 block use
@@ -40,10 +42,9 @@ namespace {
 constexpr int ST_BM = SHC_TC_TILE;       // rows: times tau
 constexpr int ST_BN = SHC_TC_STEP_TILE;  // columns: steps t of the block
 constexpr int ST_BK = 32;                // atoms per pipeline stage (64-byte rows)
-constexpr int ST_STAGES = 4;
+constexpr int ST_STAGES = 6;
 constexpr int ST_A_BYTES = ST_BM * ST_BK * 2;
-constexpr int ST_B_BYTES = ST_BN * ST_BK * 2;
-constexpr int ST_B_HALF = ST_B_BYTES / 2;          // the rows each CTA of a cluster loads
+constexpr int ST_B_BYTES = (ST_BN / 2) * ST_BK * 2;   // this CTA's half of the velocity rows
 constexpr int ST_STAGE_BYTES = 2 * ST_A_BYTES + 2 * ST_B_BYTES;
 constexpr int ST_TILE_BYTES = ST_STAGES * ST_STAGE_BYTES;
 constexpr int ST_EPI_WARPS = ST_BN / 32;          // 4 lane quarters x column halves
@@ -389,26 +390,27 @@ __global__ void __launch_bounds__(ST_THREADS, 1) shc_tc_kernel(const __grid_cons
     const int kb0 = split * p.kb_per_split;
     const int kb1 = min(kb0 + p.kb_per_split, p.n_kb);
 
+    const bool leader = rank == 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST_STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 2);   // both CTAs' MMAs have read the stage
+            mbar_init(&full[s], 1);    // leader: both CTAs' bytes landed
+            mbar_init(&empty[s], 1);   // the leader's MMAs have read the stage (both CTAs)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 32 * ST_EPI_WARPS);
+            mbar_init(&acc_empty[b], 2 * ST_EPI_WARPS);   // leader: one arrival per epilogue warp
         }
         mbar_init(done_bar, 1);
         *abort = 0;
         fence_mbar_init();
     }
     if (warp == 2) {
-        tmem_alloc(tmem_slot, ST_TMEM_COLS);
-        tmem_relinquish();
+        tmem_alloc_pair(tmem_slot, ST_TMEM_COLS);
+        tmem_relinquish_pair();
     }
     tc_fence_before();
     __syncwarp();
-    cluster_sync_all();   // both CTAs' barriers initialised before any multicast lands
+    cluster_sync_all();   // both CTAs' barriers initialised, TMEM allocated in both
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -425,19 +427,17 @@ __global__ void __launch_bounds__(ST_THREADS, 1) shc_tc_kernel(const __grid_cons
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
+        const int bhalf = brow + (int)rank * (ST_BN / 2);   // this CTA's velocity rows
         for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&empty[stage], phase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
             uint8_t *sa = smem + stage * ST_STAGE_BYTES;
-            mbar_arrive_expect_tx(&full[stage], ST_STAGE_BYTES);
+            if (leader) mbar_arrive_expect_tx(&full[stage], 2 * ST_STAGE_BYTES);
+            const uint32_t fb = mapa_shared(smem_u32(&full[stage]), 0);
             const int x = kb * ST_BK;
-            tma_load_2d(sa, &p.tmA_hi, &full[stage], x, arow, pol);
-            tma_load_2d(sa + ST_A_BYTES, &p.tmA_lo, &full[stage], x, arow, pol);
-            // this CTA's half of the velocity rows, into both CTAs
-            const int half = (int)rank * ST_B_HALF;
-            tma_load_2d_mc(sa + 2 * ST_A_BYTES + half, &p.tmB_hi, &full[stage], x,
-                           brow + (int)rank * (ST_BN / 2), 0x3, pol);
-            tma_load_2d_mc(sa + 2 * ST_A_BYTES + ST_B_BYTES + half, &p.tmB_lo, &full[stage], x,
-                           brow + (int)rank * (ST_BN / 2), 0x3, pol);
+            tma_load_2d_pair(sa, &p.tmA_hi, fb, x, arow, pol);
+            tma_load_2d_pair(sa + ST_A_BYTES, &p.tmA_lo, fb, x, arow, pol);
+            tma_load_2d_pair(sa + 2 * ST_A_BYTES, &p.tmB_hi, fb, x, bhalf, pol);
+            tma_load_2d_pair(sa + 2 * ST_A_BYTES + ST_B_BYTES, &p.tmB_lo, fb, x, bhalf, pol);
             issued[stage] = true;
             issued_phase[stage] = phase;
             if (++stage == ST_STAGES) { stage = 0; phase ^= 1u; }
@@ -446,13 +446,14 @@ __global__ void __launch_bounds__(ST_THREADS, 1) shc_tc_kernel(const __grid_cons
             *abort = 1;
             set_status(p.status, DEV_TIMEOUT);
         }
-        for (int s = 0; s < ST_STAGES; ++s)
-            if (issued[s]) {
-                const long long c0 = clock64();
-                while (!mbar_try_wait(&full[s], issued_phase[s]) && clock64() - c0 < p.wait_limit) {
+        if (leader)   // the leader's barriers count both CTAs' copies
+            for (int s = 0; s < ST_STAGES; ++s)
+                if (issued[s]) {
+                    const long long c0 = clock64();
+                    while (!mbar_try_wait(&full[s], issued_phase[s]) && clock64() - c0 < p.wait_limit) {
+                    }
                 }
-            }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0 && leader) {
         // ------------------------------------------------------------ MMA issuer
         int stage = 0, abuf = 0;
         uint32_t phase = 0, aphase = 0;
@@ -477,22 +478,22 @@ __global__ void __launch_bounds__(ST_THREADS, 1) shc_tc_kernel(const __grid_cons
                     const uint64_t dal = smem_desc_kmajor(a_lo + off, ST_SBO, ST_SWIZZLE);
                     const uint64_t dbh = smem_desc_kmajor(b_hi + off, ST_SBO, ST_SWIZZLE);
                     const uint64_t dbl = smem_desc_kmajor(b_lo + off, ST_SBO, ST_SWIZZLE);
-                    umma_f16(d_tmem, dah, dbl, p.idesc, (kb != c0 || kk != 0) ? 1u : 0u);
-                    umma_f16(d_tmem, dal, dbh, p.idesc, 1u);
-                    umma_f16(d_tmem, dah, dbh, p.idesc, 1u);
+                    umma_f16_pair(d_tmem, dah, dbl, p.idesc, (kb != c0 || kk != 0) ? 1u : 0u);
+                    umma_f16_pair(d_tmem, dal, dbh, p.idesc, 1u);
+                    umma_f16_pair(d_tmem, dah, dbh, p.idesc, 1u);
                 }
-                umma_commit_mc(&empty[stage], 0x3);   // the stage is free in both CTAs' eyes
+                umma_commit_pair(&empty[stage], (uint16_t)0x3);   // the stage is free in both CTAs
                 if (++stage == ST_STAGES) { stage = 0; phase ^= 1u; }
             }
             if (!ok) break;
-            umma_commit(&acc_full[abuf]);
+            umma_commit_pair(&acc_full[abuf], (uint16_t)0x3);
             if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
         }
         if (!ok) {
             *abort = 1;
             set_status(p.status, DEV_TIMEOUT);
         }
-        umma_commit(done_bar);
+        umma_commit_pair(done_bar, (uint16_t)0x1);
         const long long c0 = clock64();
         while (!mbar_try_wait(done_bar, 0) && clock64() - c0 < p.wait_limit) {
         }
@@ -506,6 +507,8 @@ __global__ void __launch_bounds__(ST_THREADS, 1) shc_tc_kernel(const __grid_cons
         int abuf = 0;
         uint32_t aphase = 0;
         bool ok = true;
+        const uint32_t empty_leader[2] = {mapa_shared(smem_u32(&acc_empty[0]), 0),
+                                          mapa_shared(smem_u32(&acc_empty[1]), 0)};
         for (int c0 = kb0; c0 < kb1; c0 += ST_CHUNK_KB) {
             if (!mbar_wait(&acc_full[abuf], aphase, abort, p.wait_limit)) { ok = false; break; }
             tc_fence_after();
@@ -520,7 +523,12 @@ __global__ void __launch_bounds__(ST_THREADS, 1) shc_tc_kernel(const __grid_cons
                 for (int j = 0; j < 16; ++j) acc[c * 16 + j] += __uint_as_float(r[j]);
             }
             tc_fence_before();
-            mbar_arrive(&acc_empty[abuf]);
+            __syncwarp();
+            // the chunk's TMEM reads have completed (wait::ld): the leader may reuse it
+            if (lane == 0) {
+                if (leader) mbar_arrive(&acc_empty[abuf]);
+                else mbar_arrive_cluster_relaxed(empty_leader[abuf]);
+            }
             if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
         }
         if (!ok) {
@@ -559,9 +567,9 @@ __global__ void __launch_bounds__(ST_THREADS, 1) shc_tc_kernel(const __grid_cons
 
     tc_fence_before();
     __syncwarp();
-    cluster_sync_all();   // neither CTA leaves while the other may still write into it
+    cluster_sync_all();   // neither CTA leaves while the pair still shares barriers or TMEM
     tc_fence_after();
-    if (warp == 2) tmem_dealloc(tmem_base, ST_TMEM_COLS);
+    if (warp == 2) tmem_dealloc_pair(tmem_base, ST_TMEM_COLS);
 }
 
 // Ksum[c][l] += sum over tile pairs (in order) and atom ranges (in order) of the unit diagonal

@@ -293,7 +293,7 @@ cudaError_t alloc_path(mhc_shc *s) {
     P.status = s->status;
     const int clusters = mhc::shc_tc_max_clusters();
     s->cta_slots = clusters > 0 ? 2 * clusters : s->sm_count;
-    P.idesc = mhc::idesc_f16(s->precision == MHC_PREC_BF16X3 ? 1u : 0u, T, TS);
+    P.idesc = mhc::idesc_f16(s->precision == MHC_PREC_BF16X3 ? 1u : 0u, 2 * T, TS);   // M = 256 (CTA pair)
     return cudaSuccess;
 }
 
