@@ -134,11 +134,233 @@ __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ cluster / bulk-copy pack
+__device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ float ld_cluster_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Four consecutive values of one row: one 8-byte store each for hi and lo (16-byte for FP32).
+__device__ __forceinline__ void store_split4(const PackArgs &a, size_t idx, float x0, float x1,
+                                             float x2, float x3) {
+    if (a.split == SPLIT_FP32) {
+        *reinterpret_cast<float4 *>(a.Bt32 + idx) = make_float4(x0, x1, x2, x3);
+        return;
+    }
+    const float x[4] = {x0, x1, x2, x3};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (a.split == SPLIT_BF16) {
+            const __nv_bfloat16 hv = __float2bfloat16_rn(x[q]);
+            h[q] = __bfloat16_as_ushort(hv);
+            l[q] = __bfloat16_as_ushort(__float2bfloat16_rn(x[q] - __bfloat162float(hv)));
+        } else {
+            const __half hv = __float2half_rn(x[q]);
+            h[q] = __half_as_ushort(hv);
+            l[q] = __half_as_ushort(__float2half_rn(x[q] - __half2float(hv)));
+        }
+    }
+    *reinterpret_cast<uint2 *>(static_cast<uint16_t *>(a.Bt_hi) + idx) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+    *reinterpret_cast<uint2 *>(static_cast<uint16_t *>(a.Bt_lo) + idx) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+}
+
+// A cluster of ceil(N / (4 THREADS)) CTAs per step k.  CTA r bulk-copies the contiguous
+// velocities and virials of its atoms r*4*THREADS .. into shared memory (TMA, so the loads are
+// asynchronous and the inputs are read once); thread t takes the four consecutive atoms 4t ..
+// 4t+3: row maxima and the exact total-current pairs (acc_exact), combined per CTA (FP64, fixed
+// order) and across the cluster in rank order through distributed shared memory (the result is
+// deterministic); then the four B rows of step k from shared memory with 8-byte stores.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) pack_bulk_kernel(const PackArgs a) {
+    constexpr int APC = 4 * THREADS;
+    extern __shared__ float4 pk_smem4[];
+    float *sv = reinterpret_cast<float *>(pk_smem4);   // [APC][3]
+    float *sw = sv + APC * 3;                          // [APC][9]
+    __shared__ float s_mx[THREADS / 32][4];
+    __shared__ double s_j[THREADS / 32][3];
+    __shared__ float s_loc[4], s_mul[4];
+    __shared__ double s_jc[3];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    const uint32_t rank = cluster_ctarank(), nrank = cluster_nctarank();
+    const int k = (int)(blockIdx.x / nrank);
+    const int a0 = (int)rank * APC;
+    const int na = max(0, min(APC, a.N - a0));
+    const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT_CYCLES;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && na > 0) {
+        const uint32_t vb = (uint32_t)na * 12, wb = (uint32_t)na * 36;
+        mbar_arrive_expect_tx(&bar, vb + wb);
+        const char *gv = reinterpret_cast<const char *>(a.v + ((size_t)k * a.N + a0) * 3);
+        const char *gw = reinterpret_cast<const char *>(a.W + ((size_t)k * a.N + a0) * 9);
+        for (uint32_t o = 0; o < vb; o += 16384)
+            bulk_load(reinterpret_cast<char *>(sv) + o, gv + o, min(16384u, vb - o), &bar);
+        for (uint32_t o = 0; o < wb; o += 16384)
+            bulk_load(reinterpret_cast<char *>(sw) + o, gw + o, min(16384u, wb - o), &bar);
+    }
+    bool ok = true;
+    if (na > 0) ok = mbar_wait(&bar, 0, &abort_flag, limit);
+    const int i = 4 * (int)threadIdx.x;   // this thread's first atom within the CTA
+    const bool in = ok && i < na;         // N % 4 == 0: all four atoms or none
+    float mx[4] = {0.f, 0.f, 0.f, 0.f};
+    float js[3] = {0.f, 0.f, 0.f}, jc[3] = {0.f, 0.f, 0.f};
+    float sm[4] = {0.f, 0.f, 0.f, 0.f}, ism[4] = {0.f, 0.f, 0.f, 0.f};
+    if (in) {
+        const float4 s4 = *reinterpret_cast<const float4 *>(a.sqm + a0 + i);
+        const float4 is4 = *reinterpret_cast<const float4 *>(a.isqm + a0 + i);
+        sm[0] = s4.x; sm[1] = s4.y; sm[2] = s4.z; sm[3] = s4.w;
+        ism[0] = is4.x; ism[1] = is4.y; ism[2] = is4.z; ism[3] = is4.w;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float *vu = sv + (i + u) * 3, *wu = sw + (i + u) * 9;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) mx[0] = fmaxf(mx[0], fabsf(sm[u] * vu[b]));
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    mx[1 + al] = fmaxf(mx[1 + al], fabsf(wu[3 * al + b] * ism[u]));
+                    acc_exact(js[al], jc[al], wu[3 * al + b], vu[b]);
+                }
+        }
+    }
+    double j[3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al) j[al] = (double)js[al] + (double)jc[al];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) mx[c] = fmaxf(mx[c], __shfl_down_sync(FULL_MASK, mx[c], o));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) j[c] += __shfl_down_sync(FULL_MASK, j[c], o);
+    }
+    if (lane == 0) {
+        for (int c = 0; c < 4; ++c) s_mx[warp][c] = mx[c];
+        for (int c = 0; c < 3; ++c) s_j[warp][c] = j[c];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float m = 0.f;
+        for (int w = 0; w < THREADS / 32; ++w) m = fmaxf(m, s_mx[w][threadIdx.x]);
+        s_loc[threadIdx.x] = m;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 35) {
+        double t = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) t += s_j[w][threadIdx.x - 32];
+        s_jc[threadIdx.x - 32] = t;
+    }
+    cluster_sync_all();   // every CTA's maxima and current partials are complete
+    if (threadIdx.x < 4) {
+        const int c = threadIdx.x;
+        float m = 0.f;
+        for (uint32_t q = 0; q < nrank; ++q) m = fmaxf(m, ld_cluster_f32(mapa_shared(smem_u32(&s_loc[c]), q)));
+        int sc = 0;
+        if (a.split == SPLIT_FP16 && m > 0.f && isfinite(m)) {
+            int e;
+            frexpf(m, &e);   // m < 2^e
+            sc = 14 - e;     // scaled row maximum < 2^14 keeps the lo parts normal
+        }
+        s_mul[c] = ldexpf(1.f, sc);
+        if (rank == 0) a.col_scale[4 * k + c] = ldexpf(1.f, -(sc + a.e_exp));
+    } else if (rank == 0 && threadIdx.x >= 32 && threadIdx.x < 35) {
+        const int c = threadIdx.x - 32;
+        double t = 0.0;
+        for (uint32_t q = 0; q < nrank; ++q) t += ld_cluster_f64(mapa_shared(smem_u32(&s_jc[c]), q));
+        a.Jtot[3 * k + c] = t;
+        if (a.Jring) {
+            const long long t0 = a.t0_dev ? *a.t0_dev : a.t0;
+            a.Jring[((t0 + k) % a.R) * 3 + c] = t;
+        }
+    }
+    cluster_sync_all();   // peers are done reading this CTA's partials; s_mul is visible
+    if (!ok) {   // the CTA stays alive until its copy has landed (bounded) or given up on
+        if (threadIdx.x == 0) {
+            if (a.status) set_status(a.status, DEV_TIMEOUT);
+            const long long c0 = clock64();
+            while (!mbar_try_wait(&bar, 0) && clock64() - c0 < limit) {
+            }
+        }
+        return;
+    }
+    if (!in) return;
+    const float m0 = s_mul[0], m1 = s_mul[1], m2 = s_mul[2], m3 = s_mul[3];
+    const float mul[4] = {m0, m1, m2, m3};
+    const size_t ld = (size_t)a.D_ld;
+    const size_t r0 = (size_t)(4 * k) * ld;
+    const int g = a0 + i;   // global index of the first atom
+    float x[4][12];         // per row c: the 12 values of the four atoms (3 per atom, b fastest)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float *vu = sv + (i + u) * 3, *wu = sw + (i + u) * 9;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            x[0][3 * u + b] = (sm[u] * vu[b]) * mul[0];
+#pragma unroll
+            for (int al = 0; al < 3; ++al) x[1 + al][3 * u + b] = (wu[3 * al + b] * ism[u]) * mul[1 + al];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const size_t row = r0 + (size_t)c * ld;
+        if (a.npad) {   // direction-major: column b*npad + i, four consecutive atoms per b
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                store_split4(a, row + (size_t)b * a.npad + g, x[c][b], x[c][3 + b], x[c][6 + b], x[c][9 + b]);
+        } else {        // column 3i+b: twelve consecutive values
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                store_split4(a, row + 3 * (size_t)g + 4 * q, x[c][4 * q], x[c][4 * q + 1], x[c][4 * q + 2],
+                             x[c][4 * q + 3]);
+        }
+    }
+}
+
+template <int THREADS>
+cudaError_t launch_pack_bulk(const PackArgs &a, cudaStream_t s) {
+    constexpr int APC = 4 * THREADS;
+    const int smem = APC * 48;
+    static cudaError_t attr = cudaFuncSetAttribute(pack_bulk_kernel<THREADS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    const int csize = (a.N + APC - 1) / APC;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(a.K * csize), 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeClusterDimension;
+    la[0].val.clusterDim.x = (unsigned)csize;
+    la[0].val.clusterDim.y = 1;
+    la[0].val.clusterDim.z = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pack_bulk_kernel<THREADS>, a);
+}
+
 }  // namespace
 
-void launch_pack(const PackArgs &a, cudaStream_t s) {
-    if (a.K <= 0) return;
+cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
+    if (a.K <= 0) return cudaSuccess;
+    const auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    const bool bulk = a.N % 4 == 0 && al16(a.v) && al16(a.W) && al16(a.sqm) && al16(a.isqm) &&
+                      (a.split == SPLIT_FP32 ? al16(a.Bt32) : true);
+    if (bulk && a.N <= 8 * 1024) return launch_pack_bulk<256>(a, s);
+    if (bulk && a.N <= 8 * 2048) return launch_pack_bulk<512>(a, s);
     pack_kernel<<<a.K, PACK_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace mhc

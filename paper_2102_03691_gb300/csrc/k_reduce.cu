@@ -49,9 +49,20 @@ __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__r
 // current step t in registers.  Moving to step t+1 shifts that window by one lag with a
 // warp shuffle (lane l takes lane l-1's value) and lane 0 takes the one new sample from
 // the CTA's copy of the J samples it needs, staged in shared memory from the ring once
-// per launch.  Products and 32-step partial sums are FP32, the lag sums are FP64.
+// per launch.  Products and 32-step partial sums are FP32; the partials are summed over the
+// block in an unevaluated float pair (TwoSum, ~48 bits; GB300's narrow FP64 pipe made per-chunk
+// FP64 folds the kernel's largest cost) and added to the FP64 lag sums once per launch.
 constexpr int LC_THREADS = 128;
 constexpr int LC_BINS = 2;
+
+// (s, c) += x exactly as an unevaluated float pair (_rn keeps it from being contracted)
+__device__ __forceinline__ void lc_pair_add(float &s, float &c, float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+}
 __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__restrict__ Jb,
                                                               const double *__restrict__ Jring,
                                                               int R, double *Csum, int K, int B,
@@ -86,15 +97,11 @@ __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__res
     };
     float j[3];
     load_j(t0 - l, j);
-    float acc[LC_BINS][9];
-    double dacc[LC_BINS][9];
+    float acc[LC_BINS][9], hs[LC_BINS][9], hc[LC_BINS][9];
 #pragma unroll
     for (int bb = 0; bb < LC_BINS; ++bb)
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-            acc[bb][c] = 0.f;
-            dacc[bb][c] = 0.0;
-        }
+        for (int c = 0; c < 9; ++c) acc[bb][c] = hs[bb][c] = hc[bb][c] = 0.f;
     for (int k = 0; k < K; ++k) {
         if (k > 0) {
             float nj[3];
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__res
             for (int bb = 0; bb < LC_BINS; ++bb)
 #pragma unroll
                 for (int c = 0; c < 9; ++c) {
-                    dacc[bb][c] += (double)acc[bb][c];
+                    lc_pair_add(hs[bb][c], hc[bb][c], acc[bb][c]);
                     acc[bb][c] = 0.f;
                 }
         }
@@ -126,7 +133,8 @@ __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__res
     if (l < L) {
         for (int bb = 0; bb < nb; ++bb)
 #pragma unroll
-            for (int c = 0; c < 9; ++c) Csum[((size_t)(b0 + bb) * 9 + c) * L + l] += dacc[bb][c];
+            for (int c = 0; c < 9; ++c)
+                Csum[((size_t)(b0 + bb) * 9 + c) * L + l] += (double)hs[bb][c] + (double)hc[bb][c];
     }
 }
 

@@ -41,8 +41,13 @@ struct PackArgs {
     double *Jring;         // [R][3] ring of past J (GKMA) or null
     int R;
     int npad;              // 0: column 3i+b; > 0: column b*npad + i
+    int *status;           // sticky status for a bounded wait that runs out (may be null)
+    long long wait_limit;  // SM cycles (0: a default of about a second)
 };
-void launch_pack(const PackArgs &a, cudaStream_t s);
+// Systems with N % 4 == 0 (up to 16384 atoms) and 16-byte aligned inputs are packed by a
+// cluster of CTAs per step that bulk-copies its atoms into shared memory (the inputs are read
+// once); other shapes by one CTA per step that reads them twice.
+cudaError_t launch_pack(const PackArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------- E preparation
 // max |E| over the valid D x M region (bit pattern of a non-negative float)

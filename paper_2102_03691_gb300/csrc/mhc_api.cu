@@ -582,7 +582,9 @@ mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
     a.Jring = (h->prm.flags & MHC_FLAG_GKMA) ? dptr<double>(h, "Jring") : nullptr;
     a.R = h->R_ring;
     a.npad = h->dir ? (int)h->N_pad : 0;
-    launch_pack(a, h->stream);
+    a.status = h->status;
+    a.wait_limit = 0;
+    MHC_CUDA(h, launch_pack(a, h->stream));
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
     return MHC_OK;

@@ -100,3 +100,17 @@ def test_shc_one_atom_and_lags_beyond_the_run(precision):
     assert np.all(K[:, 6:] == 0)
     assert np.all(series_rel_err(K[:, :6].T, Ko[:, :6].T) <= REL_TOL)
     s.close()
+
+
+@pytest.mark.parametrize("N", [9000, 9001])
+def test_pack_paths_large_system(N):
+    # N = 9000 is packed by clusters of 5 CTAs of 2048 atoms (bulk copies), N = 9001 (not a
+    # multiple of 4) by the one-CTA-per-step kernel; 300 kept modes, 8 steps, 4 bins
+    need_gpu()
+    from tests.test_gpu_parity import make_case
+    c = make_case(N=N, M=300, T=8, B=4, seed=906)
+    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], 4)
+    h, Jb, J = run_gpu(c, "fp16x3", K=8, L=3)
+    np.testing.assert_allclose(J, o["J"], rtol=1e-12, atol=1e-9 * np.abs(o["J"]).max())
+    assert np.all(series_rel_err(Jb, o["Jb"]) <= REL_TOL)
+    h.close()
