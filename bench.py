@@ -62,7 +62,7 @@ def parse():
                     help="also accumulate the bin-bin cross-correlations (GKMA workloads)")
     ap.add_argument("--direction", action="store_true",
                     help="direction-resolved split J_n^{ab} (every per-bin output x 3, same "
-                         "tensor work; one-SM 128-column tiles)")
+                         "tensor work)")
     return ap.parse_args()
 
 

@@ -90,9 +90,10 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
                                       has 3 B rows, row b * B + bin (b = direction of the motion):
                                       binned current [K][3][B][3], HNEMA [3][B][3], GKMA sums
                                       [3][B][3][3][L], each correlated with the total J (Eq. 17).
-                                      Same tensor work as without the split.  Tensor-core
-                                      precisions take tile_config 0 (autotuned among the
-                                      128-column tiles 3, 4, 7, 8) or one of those; set at
+                                      Same tensor work as without the split, on every tile
+                                      configuration; each running CTA keeps the finished bracket
+                                      sums of two directions in a device scratch of 192 KB (about
+                                      30 MB on a 152-SM GPU, allocated with the bins).  Set at
                                       mhc_create, not with mhc_set_flags; not for groups. */
 #define MHC_FLAG_XCORR 0x20        /* with MHC_FLAG_GKMA: also accumulate the cross-correlations of
                                       the binned currents, X_{b b'}^{mu nu}(l) = sum over origins of

@@ -42,9 +42,7 @@ struct TcLayout {
     static constexpr int TILE_BYTES = STAGES * STAGE_BYTES;
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM_BYTES = TILE_BYTES + BAR_BYTES + 1024;   // + alignment slack
-    // two chunk accumulators; 128-column tiles also keep 2 x 96 columns for the parked
-    // bracket sums of the direction-resolved split (the allocation is a power of two)
-    static constexpr uint32_t TMEM_COLS = BN == 128 ? 512 : 2 * BN;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;   // two chunk accumulators
     static constexpr uint32_t SWIZZLE_CODE = BK == 64 ? 2u : 4u;        // 128 B or 64 B rows
     static constexpr uint32_t SBO = 8 * BK * 2;                         // 8-row core group
     static_assert(BK == 64 || BK == 32, "BK");
@@ -88,82 +86,105 @@ struct TileIter {
 
 constexpr int PROMOTE_D = 128;   // d elements per TMEM chunk accumulator
 
-// Direction-resolved split (one-SM 128-column tiles).  The d axis is stored direction-major
-// (segment b holds the dofs 3i+b), so every chunk lies inside one segment.  The epilogue keeps
-// Xdot (columns 4s) accumulating over all segments; at the end of segment b < 2 it parks the
-// finished bracket sums Y^{a b} (columns 4s+1+a of 32 steps: 96 values a lane) in TMEM
-// columns PARK_COL + 96 b and restarts them from zero.
-constexpr uint32_t PARK_COL = 256;
+// Direction-resolved split.  The d axis is stored direction-major (segment b holds the dofs
+// 3i+b), so every chunk lies inside one segment.  The epilogue keeps Xdot (columns 4s)
+// accumulating over all segments; at the end of segment b < 2 it parks the finished bracket
+// sums Y^{a b} (columns 4s+1+a of its 32 steps: 96 values a thread) in a per-CTA scratch in
+// global memory and restarts them from zero.  Scratch layout [CTA][segment][j][epilogue
+// thread] (DIR_PARK_CTA_FLOATS a CTA): each warp stores and reloads 128 contiguous bytes per
+// value, and each thread reads back only what it wrote itself (program order), so the
+// ~200 KB a CTA holds stays in L2 and no barrier is needed.
+__device__ __forceinline__ float *dir_park_base(const TcProblem &P) {
+    return P.dir_park + (size_t)blockIdx.x * DIR_PARK_CTA_FLOATS + (threadIdx.x - 128);
+}
 
-__device__ __forceinline__ void park_y(float (&acc)[128], uint32_t taddr) {
+__device__ __forceinline__ void park_y(float (&acc)[128], float *dst) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        uint32_t r[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int j = 16 * c + q;   // j = 3 s + a
-            r[q] = __float_as_uint(acc[4 * (j / 3) + 1 + j % 3]);
-        }
-        tmem_st_32x32b_x16(taddr + (uint32_t)(16 * c), r);
-    }
-    tmem_st_wait();
+    for (int j = 0; j < 96; ++j)   // j = 3 s + a
+        __stcg(dst + j * DIR_PARK_THREADS, acc[4 * (j / 3) + 1 + j % 3]);
 #pragma unroll
     for (int s = 0; s < 32; ++s)
 #pragma unroll
         for (int a = 0; a < 3; ++a) acc[4 * s + 1 + a] = 0.f;
 }
 
-__device__ __forceinline__ void unpark_y(float (&acc)[128], uint32_t taddr) {
+__device__ __forceinline__ void unpark_y(float (&acc)[128], const float *src) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        uint32_t r[16];
-        tmem_ld_32x32b_x16(taddr + (uint32_t)(16 * c), r);
-        tmem_ld_wait();
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int j = 16 * c + q;
-            acc[4 * (j / 3) + 1 + j % 3] = __uint_as_float(r[q]);
-        }
-    }
+    for (int j = 0; j < 96; ++j) acc[4 * (j / 3) + 1 + j % 3] = __ldcg(src + j * DIR_PARK_THREADS);
 }
 
 // After promoting the chunk that ends at k-block kn: park the finished direction segment.
-// `lanes` is the TMEM address of this warp's lane quarter (column 0).
-__device__ __forceinline__ void dir_maybe_park(float (&acc)[128], const TcProblem &P, int kn,
-                                               uint32_t lanes) {
+__device__ __forceinline__ void dir_maybe_park(float (&acc)[128], const TcProblem &P, int kn) {
     if (P.dir_seg_kb && kn % P.dir_seg_kb == 0 && kn < P.n_kb)
-        park_y(acc, lanes + PARK_COL + (uint32_t)(96 * (kn / P.dir_seg_kb - 1)));
+        park_y(acc, dir_park_base(P) + (size_t)(kn / P.dir_seg_kb - 1) * DIR_PARK_SEG_FLOATS);
 }
 
-// Direction-resolved epilogue of one warp's 32 steps starting at kbase:
-// J_n^{ab}(k) = Xdot_n(k) Y_n^{ab}(k), direction 2 from the registers, directions 1 and 0
-// from their parked columns; bin-run sums into partials[k][a][b n_slots + slot].
-__device__ __forceinline__ void dir_epilogue(float (&acc)[128], const TcProblem &P, int kbase,
-                                             uint32_t take, int slot, uint32_t lanes) {
-    const size_t row = 3 * (size_t)P.n_slots;
-    for (int b = 2; b >= 0; --b) {
-        if (b < 2) unpark_y(acc, lanes + PARK_COL + (uint32_t)(96 * b));
-        // opaque per pass: keeps the 128 scale loads from being hoisted out of the direction
-        // loop (they would not fit in registers beside acc)
-        const float *csb = P.col_scale;
-        asm volatile("" : "+l"(csb));
+// Eq. 16 product and bin-run sums of one warp's 32 steps kbase .. kbase+31 (those < K), from
+// the promoted sums in acc (columns 4s: Xdot, 4s+1+a: the bracket sums): the products
+// overwrite the bracket columns, and each run tail stores its sums to
+// partials[(k*3 + a) * row + col0 + slot].  `sc` holds lane l's four row scales of step
+// kbase + l.  Written to be throughput-bound: the scales come by broadcast shuffles, and the
+// 96 segmented scans advance level by level so that their shuffles overlap (each value still
+// takes the same additions in the same order as a scan on its own).
+__device__ __forceinline__ void epilogue_steps(float (&acc)[128], const float4 sc, const TcProblem &P,
+                                               int kbase, uint32_t take, int slot, size_t row,
+                                               size_t col0) {
 #pragma unroll
-        for (int s4 = 0; s4 < 32; ++s4) {
-            const int k = kbase + s4;
-            if (k >= P.K) break;   // warp-uniform
-            const float *cs = csb + 4 * k;
-            const float x = acc[4 * s4] * __ldg(cs);
+    for (int s4 = 0; s4 < 32; ++s4) {
+        const float x = acc[4 * s4] * __shfl_sync(FULL_MASK, sc.x, s4);
+        acc[4 * s4 + 1] = x * (acc[4 * s4 + 1] * __shfl_sync(FULL_MASK, sc.y, s4));
+        acc[4 * s4 + 2] = x * (acc[4 * s4 + 2] * __shfl_sync(FULL_MASK, sc.z, s4));
+        acc[4 * s4 + 3] = x * (acc[4 * s4 + 3] * __shfl_sync(FULL_MASK, sc.w, s4));
+    }
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float y = acc[4 * s4 + 1 + a] * __ldg(cs + 1 + a);
-                const float v = seg_scan(x * y, take);
-                if (slot >= 0) P.partials[((size_t)k * 3 + a) * row + (size_t)b * P.n_slots + slot] = v;
-            }
+    for (int r = 0; r < 5; ++r) {
+        const bool add = (take >> r) & 1u;
+#pragma unroll
+        for (int j = 0; j < 96; ++j) {
+            const int c = 4 * (j / 3) + 1 + j % 3;
+            const float o = __shfl_up_sync(FULL_MASK, acc[c], 1u << r);
+            if (add) acc[c] += o;
+        }
+    }
+    if (slot < 0) return;
+    const int nk = P.K - kbase;   // steps of this warp inside the block
+#pragma unroll
+    for (int s4 = 0; s4 < 32; ++s4) {
+        if (s4 >= nk) break;
+        float *dst = P.partials + ((size_t)(kbase + s4) * 3) * row + col0 + (size_t)slot;
+        dst[0] = acc[4 * s4 + 1];
+        dst[row] = acc[4 * s4 + 2];
+        dst[2 * row] = acc[4 * s4 + 3];
+    }
+}
+
+// Lane l's four row scales of step kbase + l (zero past the block).
+__device__ __forceinline__ float4 step_scales(const TcProblem &P, int kbase, int lane) {
+    if (kbase + lane >= P.K) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return __ldg(reinterpret_cast<const float4 *>(P.col_scale) + (kbase + lane));
+}
+
+// The epilogue of one warp's 32 steps: plain, or the direction-resolved split
+// J_n^{ab}(k) = Xdot_n(k) Y_n^{ab}(k) (direction 2 from the registers, directions 1 and 0
+// from their parked sums) into the slot columns b n_slots + slot of rows of 3 n_slots.
+template <bool DIR>
+__device__ __forceinline__ void tile_epilogue(float (&acc)[128], const TcProblem &P, int kbase,
+                                              uint32_t take, int slot, int lane) {
+    const float4 sc = step_scales(P, kbase, lane);
+    if constexpr (!DIR) {
+        epilogue_steps(acc, sc, P, kbase, take, slot, (size_t)P.n_slots, 0);
+    } else {
+        const size_t row = 3 * (size_t)P.n_slots;
+        for (int b = 2; b >= 0; --b) {
+            if (b < 2) unpark_y(acc, dir_park_base(P) + (size_t)b * DIR_PARK_SEG_FLOATS);
+            epilogue_steps(acc, sc, P, kbase, take, slot, row, (size_t)b * P.n_slots);
         }
     }
 }
 
-template <int BN, int BK, int STAGES, int NPROB>
+// DIR: the direction-resolved epilogue (single problems only); the plain kernels keep their own
+// register allocation.
+template <int BN, int BK, int STAGES, int NPROB, bool DIR>
 __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_constant__ TcParams<NPROB> p) {
     using L = TcLayout<BN, BK, STAGES>;
     constexpr int CHUNK_KB = PROMOTE_D / BK;
@@ -337,31 +358,12 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
                 tc_fence_before();
                 mbar_arrive(&acc_empty[abuf]);
                 if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
-                if constexpr (BN == 128)
-                    dir_maybe_park(acc, P, kb0 + CHUNK_KB, tmem_base + ((uint32_t)(qw * 32) << 16));
+                if constexpr (DIR) dir_maybe_park(acc, P, kb0 + CHUNK_KB);
             }
             if (!ok) break;
             // Eq. 16 product and the bin-run sums of this warp's 32 steps
             const int kbase = ct * (BN / 4) + ch * 32;
-            if constexpr (BN == 128) {
-                if (P.dir_seg_kb) {
-                    dir_epilogue(acc, P, kbase, take, slot, tmem_base + ((uint32_t)(qw * 32) << 16));
-                    continue;
-                }
-            }
-#pragma unroll
-            for (int s4 = 0; s4 < 32; ++s4) {
-                const int k = kbase + s4;
-                if (k >= P.K) break;   // warp-uniform
-                const float *cs = P.col_scale + 4 * k;
-                const float x = acc[4 * s4] * __ldg(cs);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float y = acc[4 * s4 + 1 + a] * __ldg(cs + 1 + a);
-                    const float v = seg_scan(x * y, take);
-                    if (slot >= 0) P.partials[((size_t)k * 3 + a) * P.n_slots + slot] = v;
-                }
-            }
+            tile_epilogue<DIR>(acc, P, kbase, take, slot, lane);
         }
         if (!ok) {
             *abort = 1;
@@ -382,7 +384,6 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
 // CTAs' shared memory, and each CTA's TMEM receives the accumulator of its own 128 modes
 // (all BN columns).  Per SM this halves the B bytes per flop against the one-SM tile of the
 // same width (BN = 256: 64 KB instead of 96 KB per 64-wide k-block at the same tensor work).
-// With BN = 128 the TMEM keeps 256 free columns, where the direction split parks its sums.
 //   - TMA loads of both CTAs complete on the leader's `full` barrier (armed by the
 //     leader with both CTAs' bytes);
 //   - the leader's commits arrive on `empty`/`acc_full` of both CTAs (multicast);
@@ -396,8 +397,7 @@ struct TcPairLayout {
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int TILE_BYTES = STAGES * STAGE_BYTES;
     static constexpr int SMEM_BYTES = TILE_BYTES + 256 + 1024;
-    // 128-column pair tiles keep 2 x 96 columns of it for the direction split's parked sums
-    static constexpr uint32_t TMEM_COLS = 512;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;   // two chunk accumulators of this CTA's modes
     static constexpr uint32_t SWIZZLE_CODE = BK == 64 ? 2u : 4u;
     static constexpr uint32_t SBO = 8 * BK * 2;
     static constexpr int EPI_WARPS = BN / 32;
@@ -438,7 +438,7 @@ struct PairTileIter {
     }
 };
 
-template <int BN, int BK, int STAGES, int NPROB>
+template <int BN, int BK, int STAGES, int NPROB, bool DIR>
 __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid_constant__ TcParams<NPROB> p) {
     using L = TcPairLayout<BN, BK, STAGES>;
     constexpr int CHUNK_KB = PROMOTE_D / BK;
@@ -623,30 +623,11 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
                     else mbar_arrive_cluster_relaxed(empty_leader[abuf]);
                 }
                 if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
-                if constexpr (BN == 128)   // parked in this CTA's own TMEM (its 128 modes)
-                    dir_maybe_park(acc, P, kb0 + CHUNK_KB, tmem_base + ((uint32_t)(qw * 32) << 16));
+                if constexpr (DIR) dir_maybe_park(acc, P, kb0 + CHUNK_KB);
             }
             if (!ok) break;
             const int kbase = ct * (BN / 4) + ch * 32;
-            if constexpr (BN == 128) {
-                if (P.dir_seg_kb) {
-                    dir_epilogue(acc, P, kbase, take, slot, tmem_base + ((uint32_t)(qw * 32) << 16));
-                    continue;
-                }
-            }
-#pragma unroll
-            for (int s4 = 0; s4 < 32; ++s4) {
-                const int k = kbase + s4;
-                if (k >= P.K) break;   // warp-uniform
-                const float *cs = P.col_scale + 4 * k;
-                const float x = acc[4 * s4] * __ldg(cs);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float y = acc[4 * s4 + 1 + a] * __ldg(cs + 1 + a);
-                    const float v = seg_scan(x * y, take);
-                    if (slot >= 0) P.partials[((size_t)k * 3 + a) * P.n_slots + slot] = v;
-                }
-            }
+            tile_epilogue<DIR>(acc, P, kbase, take, slot, lane);
         }
         if (!ok) {
             *abort = 1;
@@ -661,10 +642,10 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
     if (warp == 2) tmem_dealloc_pair(tmem_base, L::TMEM_COLS);
 }
 
-template <int BN, int BK, int STAGES, int NPROB>
+template <int BN, int BK, int STAGES, int NPROB, bool DIR>
 cudaError_t launch_pair_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
     using L = TcPairLayout<BN, BK, STAGES>;
-    auto kern = tc_modal_pair_kernel<BN, BK, STAGES, NPROB>;
+    auto kern = tc_modal_pair_kernel<BN, BK, STAGES, NPROB, DIR>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -690,7 +671,7 @@ cudaError_t launch_pair_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s)
 template <int BN, int BK, int STAGES, int NPROB>
 int max_pairs_impl() {
     using L = TcPairLayout<BN, BK, STAGES>;
-    auto kern = tc_modal_pair_kernel<BN, BK, STAGES, NPROB>;
+    auto kern = tc_modal_pair_kernel<BN, BK, STAGES, NPROB, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES) !=
         cudaSuccess)
         return 0;
@@ -713,10 +694,10 @@ int max_pairs_impl() {
     return n;
 }
 
-template <int BN, int BK, int STAGES, int NPROB>
+template <int BN, int BK, int STAGES, int NPROB, bool DIR>
 cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
     using L = TcLayout<BN, BK, STAGES>;
-    auto kern = tc_modal_kernel<BN, BK, STAGES, NPROB>;
+    auto kern = tc_modal_kernel<BN, BK, STAGES, NPROB, DIR>;
     static bool attr_set = false;   // per process; the attribute is per function
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -728,19 +709,19 @@ cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int NPROB>
+template <int NPROB, bool DIR>
 cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s) {
     if (c.pair) {
-        if (c.bn == 256 && c.bk == 64 && c.stages == 3) return launch_pair_impl<256, 64, 3, NPROB>(p, c.grid, s);
-        if (c.bn == 256 && c.bk == 32 && c.stages == 6) return launch_pair_impl<256, 32, 6, NPROB>(p, c.grid, s);
-        if (c.bn == 128 && c.bk == 64 && c.stages == 4) return launch_pair_impl<128, 64, 4, NPROB>(p, c.grid, s);
-        if (c.bn == 128 && c.bk == 32 && c.stages == 8) return launch_pair_impl<128, 32, 8, NPROB>(p, c.grid, s);
+        if (c.bn == 256 && c.bk == 64 && c.stages == 3) return launch_pair_impl<256, 64, 3, NPROB, DIR>(p, c.grid, s);
+        if (c.bn == 256 && c.bk == 32 && c.stages == 6) return launch_pair_impl<256, 32, 6, NPROB, DIR>(p, c.grid, s);
+        if (c.bn == 128 && c.bk == 64 && c.stages == 4) return launch_pair_impl<128, 64, 4, NPROB, DIR>(p, c.grid, s);
+        if (c.bn == 128 && c.bk == 32 && c.stages == 8) return launch_pair_impl<128, 32, 8, NPROB, DIR>(p, c.grid, s);
         return cudaErrorInvalidValue;
     }
-    if (c.bn == 256 && c.bk == 64 && c.stages == 2) return launch_impl<256, 64, 2, NPROB>(p, c.grid, s);
-    if (c.bn == 256 && c.bk == 32 && c.stages == 4) return launch_impl<256, 32, 4, NPROB>(p, c.grid, s);
-    if (c.bn == 128 && c.bk == 64 && c.stages == 3) return launch_impl<128, 64, 3, NPROB>(p, c.grid, s);
-    if (c.bn == 128 && c.bk == 32 && c.stages == 6) return launch_impl<128, 32, 6, NPROB>(p, c.grid, s);
+    if (c.bn == 256 && c.bk == 64 && c.stages == 2) return launch_impl<256, 64, 2, NPROB, DIR>(p, c.grid, s);
+    if (c.bn == 256 && c.bk == 32 && c.stages == 4) return launch_impl<256, 32, 4, NPROB, DIR>(p, c.grid, s);
+    if (c.bn == 128 && c.bk == 64 && c.stages == 3) return launch_impl<128, 64, 3, NPROB, DIR>(p, c.grid, s);
+    if (c.bn == 128 && c.bk == 32 && c.stages == 6) return launch_impl<128, 32, 6, NPROB, DIR>(p, c.grid, s);
     return cudaErrorInvalidValue;
 }
 
@@ -768,10 +749,16 @@ size_t tc_smem_bytes(const TcConfig &c) {   // must match TcLayout / TcPairLayou
 }
 
 cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream_t s) {
-    return dispatch<1>(p, c, s);
+    if (p.prob[0].dir_seg_kb) {
+        if (!p.prob[0].dir_park || c.grid > p.dir_park_ctas) return cudaErrorInvalidValue;
+        return dispatch<1, true>(p, c, s);
+    }
+    return dispatch<1, false>(p, c, s);
 }
 cudaError_t launch_tc_group(const TcParams<TC_MAX_GROUP> &p, const TcConfig &c, cudaStream_t s) {
-    return dispatch<TC_MAX_GROUP>(p, c, s);
+    for (int q = 0; q < p.n_prob; ++q)   // the direction split runs on single problems only
+        if (p.prob[q].dir_seg_kb) return cudaErrorInvalidValue;
+    return dispatch<TC_MAX_GROUP, false>(p, c, s);
 }
 
 }  // namespace mhc

@@ -91,10 +91,15 @@ struct TcProblem {   // 128-byte aligned through CUtensorMap
     const float *col_scale;       // [4K]
     float *partials;              // [K][3][n_slots] ([K][3][3 n_slots] with the direction split)
     int n_slots, n_kb, K, n_col_tiles, n_tiles;
-    // Direction-resolved split (one-SM tiles of 128 columns only): k-blocks per direction
-    // segment of the direction-major d axis, 0 when off.
+    // Direction-resolved split: k-blocks per direction segment of the direction-major d axis
+    // (0 when off), and the scratch where each CTA parks the bracket sums of the finished
+    // segments ([grid][2][96][DIR_PARK_THREADS] floats, grid <= the SM count).
     int dir_seg_kb;
+    float *dir_park;
 };
+constexpr int DIR_PARK_THREADS = 256;                        // epilogue threads of the widest tile
+constexpr int DIR_PARK_SEG_FLOATS = 96 * DIR_PARK_THREADS;   // one parked segment of a CTA
+constexpr int DIR_PARK_CTA_FLOATS = 2 * DIR_PARK_SEG_FLOATS;
 
 template <int NPROB>
 struct TcParams {
@@ -106,6 +111,7 @@ struct TcParams {
     int stall_inject;        // test hook: arm the first stage barrier 16 bytes short of done
     int *status;
     uint32_t idesc;
+    int dir_park_ctas;       // CTAs the direction-split scratch has room for
 };
 
 struct TcConfig {

@@ -228,9 +228,6 @@ int64_t slot_stride(const mhc_handle *h) { return h->n_slots * (h->dir ? 3 : 1);
 
 bool has_xcorr(const mhc_handle *h) { return (h->prm.flags & MHC_FLAG_XCORR) != 0; }
 
-// The direction split parks its bracket sums in TMEM beside 128-column tiles (one SM or a pair).
-bool dir_config_ok(const TcConfig &c) { return c.bn == 128; }
-
 void drop_graphs(mhc_handle *h) {
     for (auto &kv : h->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -388,6 +385,9 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         dev_free(h, "Et32");
         if ((s = dev_alloc(h, "Et_hi", ecount * 2, false)) != MHC_OK) return s;
         if ((s = dev_alloc(h, "Et_lo", ecount * 2, false)) != MHC_OK) return s;
+        if (h->dir && (s = dev_alloc(h, "dir_park", sizeof(float) * DIR_PARK_CTA_FLOATS * h->sm_count,
+                                     false)) != MHC_OK)
+            return s;
     } else {
         if ((s = dev_alloc(h, "Et32", ecount * 4, false)) != MHC_OK) return s;
         if ((s = dev_alloc(h, "R", sizeof(float) * h->B_rows * h->M_pad * (h->dir ? 3 : 1), false)) != MHC_OK)
@@ -412,6 +412,8 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
         P.n_slots = (int)h->n_slots;
         P.n_kb = (int)(h->D_ld / c.bk);
         P.dir_seg_kb = h->dir ? (int)(h->N_pad / c.bk) : 0;
+        P.dir_park = h->dir ? dptr<float>(h, "dir_park") : nullptr;
+        h->tcp.dir_park_ctas = h->dir ? h->sm_count : 0;
         h->tcp.sched = nullptr;
         h->tcp.cta_begin = nullptr;
         h->tcp.n_prob = 1;
@@ -425,8 +427,6 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
 
 mhc_status set_tc_config(mhc_handle *h, const TcConfig &c) {
     if (!tc_config_supported(c)) return fail(h, MHC_ERR_INVALID_ARG, "unsupported tile configuration");
-    if (h->dir && !dir_config_ok(c))
-        return fail(h, MHC_ERR_INVALID_ARG, "the direction split needs a 128-column tile (tile_config 3, 4, 7 or 8)");
     const bool remap = h->bins_ready && (c.bn != h->tc.bn || c.bk != h->tc.bk || c.pair != h->tc.pair);
     h->tc = c;
     if (remap) {
@@ -494,7 +494,6 @@ mhc_status autotune(mhc_handle *h, int K) {
     float best = 1e30f;
     TcConfig best_c = h->tc;
     for (const TcConfig &c : TC_CONFIGS) {
-        if (h->dir && !dir_config_ok(c)) continue;
         mhc_status s = set_tc_config(h, c);
         if (s != MHC_OK) return s;
         if ((s = run_projection(h, K)) != MHC_OK) return s;   // warm-up
@@ -746,10 +745,6 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
         return fail(nullptr, MHC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
     if (p->tile_config < 0 || p->tile_config > TC_NUM_CONFIGS)
         return fail(nullptr, MHC_ERR_INVALID_ARG, "tile_config must be in [0, %d]", TC_NUM_CONFIGS);
-    if ((p->flags & MHC_FLAG_DIRECTION) && p->tile_config > 0 &&
-        !dir_config_ok(TC_CONFIGS[p->tile_config - 1]))
-        return fail(nullptr, MHC_ERR_INVALID_ARG,
-                    "MHC_FLAG_DIRECTION needs tile_config 0, 3, 4, 7 or 8 (128-column tiles)");
     if (!(p->dt_ps > 0) || !(p->T_K > 0) || !(p->V_A3 > 0))
         return fail(nullptr, MHC_ERR_INVALID_ARG, "dt_ps, T_K and V_A3 must be positive");
     int ndev = 0;

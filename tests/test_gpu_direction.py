@@ -2,9 +2,9 @@
 
 J_n^{ab} = Xdot_n sum_i m_i^{-1/2} W_i^{ab} e^b_{i,n}: the current along a carried by the
 atoms' motion along b (Sec. II.A), per mode and binned.  The library stores the d axis
-direction-major and parks the finished bracket sums of the first two directions in TMEM,
-so these cases span several direction segments, promotion chunks, mode tiles and ragged
-column tiles.
+direction-major and parks the finished bracket sums of the first two directions in a
+per-CTA device scratch, so these cases span several direction segments, promotion chunks,
+mode tiles and ragged column tiles, on every tile configuration.
 """
 import numpy as np
 import pytest
@@ -42,7 +42,11 @@ def test_direction_split_ragged(precision):
     h.close()
 
 
-@pytest.mark.parametrize("tile_config", [3, 4, 7, 8, 0])
+TILES = {1: (256, False), 2: (256, False), 3: (128, False), 4: (128, False),
+         5: (256, True), 6: (256, True), 7: (128, True), 8: (128, True)}
+
+
+@pytest.mark.parametrize("tile_config", [1, 2, 3, 4, 5, 6, 7, 8, 0])
 def test_direction_split_multi_segment(tile_config):
     # N = 300: three segments of 384 columns (three promotion chunks each); all 900 modes
     # (eight mode tiles); K = 150 steps = 600 columns (five column tiles, the last ragged)
@@ -58,9 +62,8 @@ def test_direction_split_multi_segment(tile_config):
     errc = series_rel_err(Jb.sum(axis=2), o["Jd"])
     assert np.all(errc <= REL_TOL)
     info = h.info()
-    assert info["tile_n"] == 128
     if tile_config:
-        assert info["tile_pair"] == (tile_config >= 7)
+        assert (info["tile_n"], info["tile_pair"]) == TILES[tile_config]
     h.close()
 
 
@@ -68,7 +71,7 @@ def test_direction_split_is_bitwise_across_its_tiles():
     need_gpu()
     c = make_case(N=120, M=360, T=64, B=6, seed=203)
     _, a, _ = run_gpu(c, "fp16x3", K=64, tile_config=3, direction=True)
-    for cfg in (4, 7, 8):
+    for cfg in (1, 2, 4, 5, 6, 7, 8):
         _, b, _ = run_gpu(c, "fp16x3", K=64, tile_config=cfg, direction=True)
         np.testing.assert_array_equal(a, b)
 
@@ -136,12 +139,9 @@ def test_direction_split_gkma_hnema_and_state():
         p.set_state(blob)
 
 
-def test_direction_split_rejects_two_sm_and_256_column_tiles():
+def test_direction_split_not_in_groups():
     need_gpu()
     from paper_2102_03691_gb300.mhc import MhcError, ModalHeatCurrent, ModalHeatCurrentGroup
-    for cfg in (1, 2, 5, 6):   # 256-column tiles have no TMEM left to park in
-        with pytest.raises(MhcError):
-            ModalHeatCurrent(precision="fp16x3", tile_config=cfg, direction=True)
     c = make_case(N=16, M=48, T=4, B=2, seed=206)
     h = ModalHeatCurrent(precision="fp16x3", k_max=4, direction=True)
     h.set_modes(c["E"], c["mass"], c["f"])
@@ -149,3 +149,25 @@ def test_direction_split_rejects_two_sm_and_256_column_tiles():
     with pytest.raises(MhcError):
         ModalHeatCurrentGroup([h])
     h.close()
+
+
+@pytest.fixture(scope="module")
+def case_n2000():
+    return make_case(N=2000, M=6000, T=256, B=16, seed=207)
+
+
+@pytest.mark.parametrize("tile_config", [1, 5])
+def test_direction_split_several_tiles_per_cta(case_n2000, tile_config):
+    # N = 2000, all 6000 modes, K = 256: 188 one-SM or 96 CTA-pair tiles of 256 columns, more
+    # than the CTAs (pairs) resident at once, so CTAs reuse their parking scratch across tiles
+    need_gpu()
+    c = case_n2000
+    h, Jb, J = run_gpu(c, "fp16x3", K=256, tile_config=tile_config, direction=True)
+    steps = [0, 101, 255]
+    o = oracle.modal_current_dir(c["E"], c["mass"], c["v"][steps], c["W"][steps], c["bins"], c["B"])
+    err = series_rel_err(Jb[steps], o["Jbd"])
+    report(f"direction N=2000 cfg{tile_config}", err)
+    assert np.all(err <= REL_TOL)
+    h.close()
+    _, Jb3, _ = run_gpu(c, "fp16x3", K=256, tile_config=3, direction=True)
+    np.testing.assert_array_equal(Jb, Jb3)
