@@ -155,6 +155,29 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def h2d_bandwidth(block, dev, reps: int = 5):
+    """GB/s of one step's upload (the pinned v and W of `block`) copied alone on a side stream,
+    with no kernels running: the floor under the end-to-end step time when inputs live on
+    the host."""
+    import torch
+    v, W = block
+    dv = torch.empty_like(v, device=dev)
+    dw = torch.empty_like(W, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        dv.copy_(v, non_blocking=True)
+        dw.copy_(W, non_blocking=True)
+        a.record(st)
+        for _ in range(reps):
+            dv.copy_(v, non_blocking=True)
+            dw.copy_(W, non_blocking=True)
+        b.record(st)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return (v.numel() + W.numel()) * v.element_size() / (ms * 1e6) if ms > 0 else None
+
+
 # ----------------------------------------------------------------------------- roofline inputs
 def measured_peaks():
     try:
@@ -671,15 +694,19 @@ def main():
         e2e_step(i)
     torch.cuda.synchronize()
     barrier(world)
+    clocks_e2e = ClockSampler(gpu_uuid)
+    clocks_e2e.start()
     t0 = time.perf_counter()
     for i in range(n_e2e):
         e2e_step(i)
     torch.cuda.synchronize()
     e2e_el = time.perf_counter() - t0
+    clk_e2e = clocks_e2e.stop()
     assert torch.isfinite(res_host).all()
     e2e_max, e2e_units = aggregate(e2e_el, float(M) * N * K * n_e2e, world)
     h2d = 4 * K * N * 12
     d2h = 8 * (rows * 9 if L else rows * 3)
+    h2d_gbs = h2d_bandwidth(host_pool[0], dev)
 
     # ---- FP32 CUDA-core path on the same workload (comparison)
     fp32 = None
@@ -749,7 +776,11 @@ def main():
         "config": config_dict(w, args, args.precision),
         "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": e2e_units / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": n_e2e},
+                "d2h_bytes_per_step": d2h, "steps": n_e2e,
+                "ms_per_step": 1e3 * e2e_max / n_e2e,
+                "h2d_gbs_alone": h2d_gbs,
+                "h2d_ms_per_step_alone": h2d / h2d_gbs / 1e6 if h2d_gbs else None,
+                "clocks": clk_e2e},
         "clocks": clk, "gpu_launches": int(launches) * world,
         "fp32_path": fp32,
         "mixed_vs_fp32": (value / world) / fp32["value"] if fp32 else None,
