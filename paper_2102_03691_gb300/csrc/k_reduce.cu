@@ -8,10 +8,12 @@ namespace mhc {
 namespace {
 
 // ------------------------------------------------------------------ K3
-// One CTA per bin.  Thread t handles component a = t % 3 and steps k = t/3 + 64 j.
-// J_b^a(k) = sum of the bin's partial slots in slot order; HNEMA sum in FP64 with a
-// fixed reduction tree (deterministic).  CTA 0 also sums the total current.
-constexpr int BF_THREADS = 192;
+// One CTA per bin, one thread per (step, component) of a 256-step pass: thread t handles
+// component a = t % 3 and steps k = t/3 + 256 j.  J_b^a(k) = sum of the bin's partial slots in
+// slot order; the HNEMA sums over the block's steps in FP64 with a fixed reduction tree
+// (deterministic).  CTA 0 also sums the total current.
+constexpr int BF_STEPS = 256;
+constexpr int BF_THREADS = 3 * BF_STEPS;
 __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__restrict__ partials,
                                                                 int n_slots, const int *slot_begin,
                                                                 int B, int K, float *Jb,
@@ -21,7 +23,7 @@ __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__r
     const int a = threadIdx.x % 3, k0 = threadIdx.x / 3;
     const int s0 = slot_begin[b], s1 = slot_begin[b + 1];
     double acc = 0.0, acc_tot = 0.0;
-    for (int k = k0; k < K; k += BF_THREADS / 3) {
+    for (int k = k0; k < K; k += BF_STEPS) {
         const float *row = partials + ((size_t)k * 3 + a) * n_slots;
         float s = 0.f;
         for (int q = s0; q < s1; ++q) s += row[q];
@@ -33,26 +35,33 @@ __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__r
     red[0][threadIdx.x] = acc;
     red[1][threadIdx.x] = acc_tot;
     __syncthreads();
-    if (threadIdx.x < 3) {
-        double t = 0.0, u = 0.0;
-        for (int q = threadIdx.x; q < BF_THREADS; q += 3) {
-            t += red[0][q];
-            u += red[1][q];
+    for (int off = BF_STEPS / 2; off > 0; off >>= 1) {   // over k0, per component
+        if (k0 < off) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + 3 * off];
+            if (b == 0) red[1][threadIdx.x] += red[1][threadIdx.x + 3 * off];
         }
-        hsum[b * 3 + threadIdx.x] += t;
-        if (b == 0) Jsum[threadIdx.x] += u;
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) {
+        hsum[b * 3 + threadIdx.x] += red[0][threadIdx.x];
+        if (b == 0) Jsum[threadIdx.x] += red[1][threadIdx.x];
     }
 }
 
 // ------------------------------------------------------------------ K4
-// Each warp owns 32 consecutive lags; lane l holds the total current J(t - l) of the
-// current step t in registers.  Moving to step t+1 shifts that window by one lag with a
-// warp shuffle (lane l takes lane l-1's value) and lane 0 takes the one new sample from
-// the CTA's copy of the J samples it needs, staged in shared memory from the ring once
-// per launch.  Products and 32-step partial sums are FP32; the partials are summed over the
-// block in an unevaluated float pair (TwoSum, ~48 bits; GB300's narrow FP64 pipe made per-chunk
-// FP64 folds the kernel's largest cost) and added to the FP64 lag sums once per launch.
-constexpr int LC_THREADS = 128;
+// A CTA covers 128 consecutive lags (four lag warps) of LC_BINS bins, and each lag warp runs
+// in LC_SPLIT copies over consecutive quarters of the block's steps, so that 16 warps hide the
+// latency of the per-step window shift.  Lane l of a warp holds the total current J(t - l) of
+// its current step t in registers; moving to step t+1 shifts that window by one lag with a
+// warp shuffle (lane l takes lane l-1's value) and lane 0 takes the one new sample from the
+// CTA's copy of the J samples it needs, staged in shared memory from the ring once per launch.
+// Products and 32-step partial sums are FP32; the partials are summed over the quarter in an
+// unevaluated float pair (TwoSum, ~48 bits; GB300's FP64 pipe is narrow), the quarters' pairs
+// are added in quarter order (deterministic), and one FP64 value per lag sum is added to the
+// FP64 lag sums.
+constexpr int LC_LAGS = 128;   // lags per CTA: four lag warps
+constexpr int LC_SPLIT = 4;    // step quarters
+constexpr int LC_THREADS = LC_LAGS * LC_SPLIT;
 constexpr int LC_BINS = 2;
 
 // (s, c) += x exactly as an unevaluated float pair (_rn keeps it from being contracted)
@@ -69,26 +78,33 @@ __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__res
                                                               int L, long long t0_host,
                                                               const long long *t0_dev) {
     const long long t0 = t0_dev ? *t0_dev : t0_host;
-    extern __shared__ float sJ[];   // [K][LC_BINS][3] then the J window [K + LC_THREADS - 1][3]
+    // [K][LC_BINS][3] binned currents, the J window [K + LC_LAGS - 1][3], then the quarters'
+    // float pairs [LC_SPLIT - 1][2][LC_BINS * 9][LC_LAGS]
+    extern __shared__ float sJ[];
     float *sW = sJ + K * LC_BINS * 3;
+    const int nw = K + LC_LAGS - 1;
+    float *sQ = sW + nw * 3;
     const int b0 = blockIdx.y * LC_BINS;
     const int nb = min(LC_BINS, B - b0);
     for (int q = threadIdx.x; q < K * LC_BINS * 3; q += LC_THREADS) {
         const int k = q / (LC_BINS * 3), r = q % (LC_BINS * 3), bb = r / 3, mu = r % 3;
         sJ[q] = bb < nb ? Jb[((size_t)k * B + b0 + bb) * 3 + mu] : 0.f;
     }
-    // window entry j holds J(tw0 + j), tw0 = t0 - (first lag of the CTA) - (LC_THREADS - 1)
-    const int lc0 = blockIdx.x * LC_THREADS;
-    const long long tw0 = t0 - lc0 - (LC_THREADS - 1);
-    const int nw = K + LC_THREADS - 1;
+    // window entry j holds J(tw0 + j), tw0 = t0 - (first lag of the CTA) - (LC_LAGS - 1)
+    const int lc0 = blockIdx.x * LC_LAGS;
+    const long long tw0 = t0 - lc0 - (LC_LAGS - 1);
     for (int q = threadIdx.x; q < nw * 3; q += LC_THREADS) {
         const long long tt = tw0 + q / 3;
         sW[q] = tt >= 0 ? (float)Jring[(tt % R) * 3 + q % 3] : 0.f;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int l0 = lc0 + (threadIdx.x & ~31);   // first lag of this warp
+    const int lw = (threadIdx.x >> 5) % (LC_LAGS / 32);   // lag warp
+    const int quarter = (threadIdx.x >> 5) / (LC_LAGS / 32);
+    const int l0 = lc0 + 32 * lw;                          // first lag of this warp
     const int l = l0 + lane;
+    const int kq = (K + LC_SPLIT - 1) / LC_SPLIT;
+    const int k_begin = min(K, quarter * kq), k_end = min(K, k_begin + kq);
     auto load_j = [&](long long tt, float (&j)[3]) {   // J(tt) from the staged window
         const float *src = sW + (tt - tw0) * 3;
         j[0] = src[0];
@@ -96,14 +112,14 @@ __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__res
         j[2] = src[2];
     };
     float j[3];
-    load_j(t0 - l, j);
+    load_j(t0 + k_begin - l, j);
     float acc[LC_BINS][9], hs[LC_BINS][9], hc[LC_BINS][9];
 #pragma unroll
     for (int bb = 0; bb < LC_BINS; ++bb)
 #pragma unroll
         for (int c = 0; c < 9; ++c) acc[bb][c] = hs[bb][c] = hc[bb][c] = 0.f;
-    for (int k = 0; k < K; ++k) {
-        if (k > 0) {
+    for (int k = k_begin; k < k_end; ++k) {
+        if (k > k_begin) {
             float nj[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) nj[c] = __shfl_up_sync(FULL_MASK, j[c], 1);
@@ -120,7 +136,7 @@ __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__res
 #pragma unroll
                 for (int nu = 0; nu < 3; ++nu) acc[bb][mu * 3 + nu] = fmaf(x, j[nu], acc[bb][mu * 3 + nu]);
             }
-        if ((k & 31) == 31 || k == K - 1) {
+        if (((k - k_begin) & 31) == 31 || k == k_end - 1) {
 #pragma unroll
             for (int bb = 0; bb < LC_BINS; ++bb)
 #pragma unroll
@@ -130,22 +146,57 @@ __global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__res
                 }
         }
     }
-    if (l < L) {
+    const int li = 32 * lw + lane;   // lag index within the CTA
+    constexpr int QSTRIDE = 2 * LC_BINS * 9 * LC_LAGS;   // floats of one quarter's pairs
+    if (quarter > 0) {
+#pragma unroll
+        for (int bb = 0; bb < LC_BINS; ++bb)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                float *q = sQ + (size_t)(quarter - 1) * QSTRIDE + (bb * 9 + c) * LC_LAGS + li;
+                q[0] = hs[bb][c];
+                q[LC_BINS * 9 * LC_LAGS] = hc[bb][c];
+            }
+    }
+    __syncthreads();
+    if (quarter == 0 && l < L) {
         for (int bb = 0; bb < nb; ++bb)
 #pragma unroll
-            for (int c = 0; c < 9; ++c)
-                Csum[((size_t)(b0 + bb) * 9 + c) * L + l] += (double)hs[bb][c] + (double)hc[bb][c];
+            for (int c = 0; c < 9; ++c) {
+                float s = hs[bb][c], cc = hc[bb][c];
+#pragma unroll
+                for (int qq = 0; qq < LC_SPLIT - 1; ++qq) {
+                    const float *q = sQ + (size_t)qq * QSTRIDE + (bb * 9 + c) * LC_LAGS + li;
+                    lc_pair_add(s, cc, q[0]);
+                    cc = __fadd_rn(cc, q[LC_BINS * 9 * LC_LAGS]);
+                }
+                Csum[((size_t)(b0 + bb) * 9 + c) * L + l] += (double)s + (double)cc;
+            }
     }
 }
 
+size_t lag_corr_smem(int K) {
+    return ((size_t)K * LC_BINS * 3 + (size_t)(K + LC_LAGS - 1) * 3 +
+            (size_t)(LC_SPLIT - 1) * 2 * LC_BINS * 9 * LC_LAGS) * sizeof(float);
+}
+
 // ------------------------------------------------------------------ K5
+// inv_count(l) = 1 / (T_s - l) (0 when no origin has lag l), computed once per read so that
+// the rows below multiply instead of dividing (an FP64 division is ~8 instructions on a pipe
+// GB300 keeps narrow).
+__global__ void inv_counts_kernel(long long T_s, int L, double *inv) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < L) inv[l] = T_s > l ? 1.0 / (double)(T_s - l) : 0.0;
+}
+
 // One CTA per (b, mu, nu) row, GK_THREADS threads, each owning GK_PER consecutive lags.
 // C(l) = Csum(l) * inv_count(l); trapezoid increments (C(l-1)+C(l))/2 for l >= 1;
 // block-wide exclusive scan of the per-thread totals (fixed tree: deterministic);
 // kappa(l) = c dt * prefix(l).  The tau-window average is a block reduction.
 constexpr int GK_THREADS = 128;
 __global__ void __launch_bounds__(GK_THREADS) gk_kappa_kernel(const double *Csum, int L,
-                                                              long long T_s, double coef_dt,
+                                                              const double *__restrict__ inv,
+                                                              double coef_dt,
                                                               double tau_lo, double tau_hi,
                                                               double dt, double *kappa_tau,
                                                               double *kappa_w) {
@@ -153,10 +204,7 @@ __global__ void __launch_bounds__(GK_THREADS) gk_kappa_kernel(const double *Csum
     const double *cs = Csum + (size_t)r * L;
     const int per = (L + GK_THREADS - 1) / GK_THREADS;
     const int l0 = threadIdx.x * per;
-    auto C = [&](int l) -> double {
-        const long long cnt = T_s - l;
-        return cnt > 0 ? cs[l] / (double)cnt : 0.0;
-    };
+    auto C = [&](int l) -> double { return cs[l] * inv[l]; };
     double prev = (l0 > 0 && l0 <= L) ? C(l0 - 1) : 0.0;
     double tot = 0.0;
     for (int l = l0; l < min(L, l0 + per); ++l) {
@@ -241,15 +289,24 @@ void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
                      int L, long long t0, const long long *t0_dev, cudaStream_t s) {
     if (L <= 0 || K <= 0 || B <= 0) return;
-    dim3 grid((L + LC_THREADS - 1) / LC_THREADS, (B + LC_BINS - 1) / LC_BINS);
-    const size_t sm = ((size_t)K * LC_BINS * 3 + (size_t)(K + LC_THREADS - 1) * 3) * sizeof(float);
+    dim3 grid((L + LC_LAGS - 1) / LC_LAGS, (B + LC_BINS - 1) / LC_BINS);
+    const size_t sm = lag_corr_smem(K);
+    static size_t sm_set = 48 * 1024;   // the largest dynamic size opted into so far
+    if (sm > sm_set) {
+        if (cudaFuncSetAttribute(lag_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm) != cudaSuccess)
+            return;   // the launch below is skipped; the caller's cudaGetLastError reports it
+        sm_set = sm;
+    }
     lag_corr_kernel<<<grid, LC_THREADS, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0, t0_dev);
 }
 
 void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
                      double tau_lo, double tau_hi, double dt, double *kappa_tau, double *kappa_w,
-                     cudaStream_t s) {
-    gk_kappa_kernel<<<B * 9, GK_THREADS, 0, s>>>(Csum, L, T_s, coef_dt, tau_lo, tau_hi, dt,
+                     double *inv_scratch, cudaStream_t s) {
+    if (L <= 0 || B <= 0) return;
+    inv_counts_kernel<<<(L + 255) / 256, 256, 0, s>>>(T_s, L, inv_scratch);
+    gk_kappa_kernel<<<B * 9, GK_THREADS, 0, s>>>(Csum, L, inv_scratch, coef_dt, tau_lo, tau_hi, dt,
                                                  kappa_tau, kappa_w);
 }
 

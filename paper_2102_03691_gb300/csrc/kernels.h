@@ -186,9 +186,10 @@ void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, 
 // *steps += K (one thread; last kernel of a push)
 void launch_advance_steps(long long *steps, int K, cudaStream_t s);
 // kappa_tau[r][l] (r = b*9+mu*3+nu) and window averages kappa_w[r], FP64.
+// inv_scratch: [L] doubles of device scratch (the reciprocal lag counts of this read).
 void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
                      double tau_lo, double tau_hi, double dt, double *kappa_tau,
-                     double *kappa_w, cudaStream_t s);
+                     double *kappa_w, double *inv_scratch, cudaStream_t s);
 // mean[b][a] = hsum/T_s; kappa[b][a] = mean * coef
 void launch_hnema_finalize(const double *hsum, int B, long long T_s, double coef, double *mean,
                            double *kappa, cudaStream_t s);

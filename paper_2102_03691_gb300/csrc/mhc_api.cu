@@ -1069,12 +1069,12 @@ mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, do
     const int L = h->prm.n_lags;
     const size_t rows = (size_t)n_out_bins(h) * 9;
     mhc_status s;
-    if ((s = dev_alloc(h, "gk_out", sizeof(double) * rows * (L + 1), false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "gk_out", sizeof(double) * (rows * (L + 1) + L), false)) != MHC_OK) return s;
     double *dk = dptr<double>(h, "gk_out"), *dw = dk + rows * L;
     const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
     launch_gk_kappa(dptr<double>(h, "Csum"), (int)n_out_bins(h), L, h->steps, coef * h->prm.dt_ps, tau_lo, tau_hi,
-                    h->prm.dt_ps, dk, dw, h->stream);
-    h->launches++;
+                    h->prm.dt_ps, dk, dw, dw + rows, h->stream);
+    h->launches += 2;
     MHC_CUDA(h, cudaGetLastError());
     if (kappa_tau && (s = copy_out(h, kappa_tau, dk, sizeof(double) * rows * L, where)) != MHC_OK) return s;
     if (kappa_w && (s = copy_out(h, kappa_w, dw, sizeof(double) * rows, where)) != MHC_OK) return s;
@@ -1116,13 +1116,13 @@ mhc_status mhc_read_kappa_xcorr(mhc_handle *h, double *kappa_tau, double tau_lo,
     const size_t rows = (size_t)9 * nb * nb;
     mhc_status s;
     if ((s = dev_alloc(h, "xc_out", sizeof(double) * rows * L, false)) != MHC_OK) return s;
-    if ((s = dev_alloc(h, "xk_out", sizeof(double) * rows * (L + 1), false)) != MHC_OK) return s;
+    if ((s = dev_alloc(h, "xk_out", sizeof(double) * (rows * (L + 1) + L), false)) != MHC_OK) return s;
     launch_xcorr_transpose(dptr<double>(h, "Xsum"), nb, L, dptr<double>(h, "xc_out"), h->stream);
     double *dk = dptr<double>(h, "xk_out"), *dw = dk + rows * L;
     const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
     launch_gk_kappa(dptr<double>(h, "xc_out"), nb * nb, L, h->steps, coef * h->prm.dt_ps, tau_lo,
-                    tau_hi, h->prm.dt_ps, dk, dw, h->stream);
-    h->launches += 2;
+                    tau_hi, h->prm.dt_ps, dk, dw, dw + rows, h->stream);
+    h->launches += 3;
     MHC_CUDA(h, cudaGetLastError());
     if (kappa_tau && (s = copy_out(h, kappa_tau, dk, sizeof(double) * rows * L, where)) != MHC_OK) return s;
     if (kappa_w && (s = copy_out(h, kappa_w, dw, sizeof(double) * rows, where)) != MHC_OK) return s;
