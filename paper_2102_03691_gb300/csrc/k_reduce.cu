@@ -49,20 +49,15 @@ __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__r
 }
 
 // ------------------------------------------------------------------ K4
-// A CTA covers 128 consecutive lags (four lag warps) of LC_BINS bins, and each lag warp runs
-// in LC_SPLIT copies over consecutive quarters of the block's steps, so that 16 warps hide the
-// latency of the per-step window shift.  Lane l of a warp holds the total current J(t - l) of
-// its current step t in registers; moving to step t+1 shifts that window by one lag with a
-// warp shuffle (lane l takes lane l-1's value) and lane 0 takes the one new sample from the
-// CTA's copy of the J samples it needs, staged in shared memory from the ring once per launch.
-// Products and 32-step partial sums are FP32; the partials are summed over the quarter in an
-// unevaluated float pair (TwoSum, ~48 bits; GB300's FP64 pipe is narrow), the quarters' pairs
-// are added in quarter order (deterministic), and one FP64 value per lag sum is added to the
-// FP64 lag sums.
-constexpr int LC_LAGS = 128;   // lags per CTA: four lag warps
-constexpr int LC_SPLIT = 4;    // step quarters
-constexpr int LC_THREADS = LC_LAGS * LC_SPLIT;
-constexpr int LC_BINS = 2;
+// Register-tiled like a GEMM micro-kernel.  A CTA owns 32 consecutive lags (one per lane) and
+// LC_ROWS rows (b, mu) of LC_ROWS / 3 bins; warp s of the CTA takes the block's steps
+// 32 s .. 32 s + 31.  Per step a thread loads its lag's total current J(t - l) (one 16-byte
+// shared-memory load from the CTA's window of J samples) and the step's LC_ROWS binned currents
+// (broadcast 16-byte loads) and does 3 LC_ROWS FMAs into FP32 partial sums over the warp's
+// 32 steps.  The warps' partials are then added in step order in an unevaluated float pair
+// (TwoSum, ~48 bits; GB300's FP64 pipe is narrow) and each lag sum gets one FP64 add.
+constexpr int LC_ROWS = 12;   // 4 bins x 3 components a thread
+constexpr int LC_OUT = 3 * LC_ROWS;
 
 // (s, c) += x exactly as an unevaluated float pair (_rn keeps it from being contracted)
 __device__ __forceinline__ void lc_pair_add(float &s, float &c, float x) {
@@ -72,112 +67,82 @@ __device__ __forceinline__ void lc_pair_add(float &s, float &c, float x) {
     s = t;
     c = __fadd_rn(c, e);
 }
-__global__ void __launch_bounds__(LC_THREADS) lag_corr_kernel(const float *__restrict__ Jb,
-                                                              const double *__restrict__ Jring,
-                                                              int R, double *Csum, int K, int B,
-                                                              int L, long long t0_host,
-                                                              const long long *t0_dev) {
+__global__ void __launch_bounds__(1024) lag_corr_kernel(const float *__restrict__ Jb,
+                                                        const double *__restrict__ Jring, int R,
+                                                        double *Csum, int K, int B, int L,
+                                                        long long t0_host, const long long *t0_dev) {
     const long long t0 = t0_dev ? *t0_dev : t0_host;
-    // [K][LC_BINS][3] binned currents, the J window [K + LC_LAGS - 1][3], then the quarters'
-    // float pairs [LC_SPLIT - 1][2][LC_BINS * 9][LC_LAGS]
-    extern __shared__ float sJ[];
-    float *sW = sJ + K * LC_BINS * 3;
-    const int nw = K + LC_LAGS - 1;
-    float *sQ = sW + nw * 3;
-    const int b0 = blockIdx.y * LC_BINS;
-    const int nb = min(LC_BINS, B - b0);
-    for (int q = threadIdx.x; q < K * LC_BINS * 3; q += LC_THREADS) {
-        const int k = q / (LC_BINS * 3), r = q % (LC_BINS * 3), bb = r / 3, mu = r % 3;
-        sJ[q] = bb < nb ? Jb[((size_t)k * B + b0 + bb) * 3 + mu] : 0.f;
+    // staging: rows [K][LC_ROWS], then the J window [K + 31] as float4 (x, y, z, 0); after the
+    // step loop the same space holds the warps' partials [warp][LC_OUT][32]
+    extern __shared__ float4 lc_smem4[];
+    float *sA = reinterpret_cast<float *>(lc_smem4);
+    float4 *sW = lc_smem4 + (K * LC_ROWS) / 4;
+    float *sP = reinterpret_cast<float *>(lc_smem4);
+    const int l0 = blockIdx.x * 32;
+    const int b0 = blockIdx.y * (LC_ROWS / 3);
+    const int nthreads = blockDim.x;
+    for (int q = threadIdx.x; q < K * LC_ROWS; q += nthreads) {
+        const int k = q / LC_ROWS, r = q % LC_ROWS, b = b0 + r / 3;
+        sA[q] = b < B ? Jb[((size_t)k * B + b) * 3 + r % 3] : 0.f;
     }
-    // window entry j holds J(tw0 + j), tw0 = t0 - (first lag of the CTA) - (LC_LAGS - 1)
-    const int lc0 = blockIdx.x * LC_LAGS;
-    const long long tw0 = t0 - lc0 - (LC_LAGS - 1);
-    for (int q = threadIdx.x; q < nw * 3; q += LC_THREADS) {
-        const long long tt = tw0 + q / 3;
-        sW[q] = tt >= 0 ? (float)Jring[(tt % R) * 3 + q % 3] : 0.f;
+    // window entry w holds J(tw0 + w), tw0 = t0 - l0 - 31: lane l at step k reads w = k - l + 31
+    const long long tw0 = t0 - l0 - 31;
+    for (int w = threadIdx.x; w < K + 31; w += nthreads) {
+        const long long tt = tw0 + w;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tt >= 0) {
+            const double *src = Jring + (tt % R) * 3;
+            v = make_float4((float)src[0], (float)src[1], (float)src[2], 0.f);
+        }
+        sW[w] = v;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int lw = (threadIdx.x >> 5) % (LC_LAGS / 32);   // lag warp
-    const int quarter = (threadIdx.x >> 5) / (LC_LAGS / 32);
-    const int l0 = lc0 + 32 * lw;                          // first lag of this warp
-    const int l = l0 + lane;
-    const int kq = (K + LC_SPLIT - 1) / LC_SPLIT;
-    const int k_begin = min(K, quarter * kq), k_end = min(K, k_begin + kq);
-    auto load_j = [&](long long tt, float (&j)[3]) {   // J(tt) from the staged window
-        const float *src = sW + (tt - tw0) * 3;
-        j[0] = src[0];
-        j[1] = src[1];
-        j[2] = src[2];
-    };
-    float j[3];
-    load_j(t0 + k_begin - l, j);
-    float acc[LC_BINS][9], hs[LC_BINS][9], hc[LC_BINS][9];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k_begin = 32 * warp, k_end = min(K, k_begin + 32);
+    float acc[LC_OUT];
 #pragma unroll
-    for (int bb = 0; bb < LC_BINS; ++bb)
-#pragma unroll
-        for (int c = 0; c < 9; ++c) acc[bb][c] = hs[bb][c] = hc[bb][c] = 0.f;
+    for (int o = 0; o < LC_OUT; ++o) acc[o] = 0.f;
+    const float4 *wp = sW + (k_begin - lane + 31);
+    const float4 *ap = reinterpret_cast<const float4 *>(sA) + k_begin * (LC_ROWS / 4);
+#pragma unroll 4
     for (int k = k_begin; k < k_end; ++k) {
-        if (k > k_begin) {
-            float nj[3];
+        const float4 j = *wp++;
+        float x[LC_ROWS];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) nj[c] = __shfl_up_sync(FULL_MASK, j[c], 1);
-            if (lane == 0) load_j(t0 + k - l0, nj);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) j[c] = nj[c];
+        for (int q = 0; q < LC_ROWS / 4; ++q) {
+            const float4 a4 = ap[q];
+            x[4 * q] = a4.x;
+            x[4 * q + 1] = a4.y;
+            x[4 * q + 2] = a4.z;
+            x[4 * q + 3] = a4.w;
         }
-        const float *jb = sJ + k * LC_BINS * 3;
+        ap += LC_ROWS / 4;
 #pragma unroll
-        for (int bb = 0; bb < LC_BINS; ++bb)
-#pragma unroll
-            for (int mu = 0; mu < 3; ++mu) {
-                const float x = jb[bb * 3 + mu];
-#pragma unroll
-                for (int nu = 0; nu < 3; ++nu) acc[bb][mu * 3 + nu] = fmaf(x, j[nu], acc[bb][mu * 3 + nu]);
-            }
-        if (((k - k_begin) & 31) == 31 || k == k_end - 1) {
-#pragma unroll
-            for (int bb = 0; bb < LC_BINS; ++bb)
-#pragma unroll
-                for (int c = 0; c < 9; ++c) {
-                    lc_pair_add(hs[bb][c], hc[bb][c], acc[bb][c]);
-                    acc[bb][c] = 0.f;
-                }
+        for (int r = 0; r < LC_ROWS; ++r) {
+            acc[3 * r] = fmaf(x[r], j.x, acc[3 * r]);
+            acc[3 * r + 1] = fmaf(x[r], j.y, acc[3 * r + 1]);
+            acc[3 * r + 2] = fmaf(x[r], j.z, acc[3 * r + 2]);
         }
     }
-    const int li = 32 * lw + lane;   // lag index within the CTA
-    constexpr int QSTRIDE = 2 * LC_BINS * 9 * LC_LAGS;   // floats of one quarter's pairs
-    if (quarter > 0) {
+    __syncthreads();   // staging no longer read: its space takes the partials
 #pragma unroll
-        for (int bb = 0; bb < LC_BINS; ++bb)
-#pragma unroll
-            for (int c = 0; c < 9; ++c) {
-                float *q = sQ + (size_t)(quarter - 1) * QSTRIDE + (bb * 9 + c) * LC_LAGS + li;
-                q[0] = hs[bb][c];
-                q[LC_BINS * 9 * LC_LAGS] = hc[bb][c];
-            }
-    }
+    for (int o = 0; o < LC_OUT; ++o) sP[(warp * LC_OUT + o) * 32 + lane] = acc[o];
     __syncthreads();
-    if (quarter == 0 && l < L) {
-        for (int bb = 0; bb < nb; ++bb)
-#pragma unroll
-            for (int c = 0; c < 9; ++c) {
-                float s = hs[bb][c], cc = hc[bb][c];
-#pragma unroll
-                for (int qq = 0; qq < LC_SPLIT - 1; ++qq) {
-                    const float *q = sQ + (size_t)qq * QSTRIDE + (bb * 9 + c) * LC_LAGS + li;
-                    lc_pair_add(s, cc, q[0]);
-                    cc = __fadd_rn(cc, q[LC_BINS * 9 * LC_LAGS]);
-                }
-                Csum[((size_t)(b0 + bb) * 9 + c) * L + l] += (double)s + (double)cc;
-            }
+    const int nwarps = nthreads >> 5;
+    for (int q = threadIdx.x; q < LC_OUT * 32; q += nthreads) {
+        const int o = q >> 5, ln = q & 31;
+        const int l = l0 + ln, r = o / 3, b = b0 + r / 3;
+        if (l >= L || b >= B) continue;
+        float s = 0.f, c = 0.f;
+        for (int w = 0; w < nwarps; ++w) lc_pair_add(s, c, sP[(w * LC_OUT + o) * 32 + ln]);
+        Csum[((size_t)b * 9 + (r % 3) * 3 + o % 3) * L + l] += (double)s + (double)c;
     }
 }
 
 size_t lag_corr_smem(int K) {
-    return ((size_t)K * LC_BINS * 3 + (size_t)(K + LC_LAGS - 1) * 3 +
-            (size_t)(LC_SPLIT - 1) * 2 * LC_BINS * 9 * LC_LAGS) * sizeof(float);
+    const size_t staging = (size_t)K * LC_ROWS * sizeof(float) + (size_t)(K + 31) * sizeof(float4);
+    const size_t partials = (size_t)((K + 31) / 32) * LC_OUT * 32 * sizeof(float);
+    return staging > partials ? staging : partials;
 }
 
 // ------------------------------------------------------------------ K5
@@ -289,7 +254,8 @@ void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
                      int L, long long t0, const long long *t0_dev, cudaStream_t s) {
     if (L <= 0 || K <= 0 || B <= 0) return;
-    dim3 grid((L + LC_LAGS - 1) / LC_LAGS, (B + LC_BINS - 1) / LC_BINS);
+    dim3 grid((L + 31) / 32, (B + LC_ROWS / 3 - 1) / (LC_ROWS / 3));
+    const int threads = 32 * ((K + 31) / 32);   // one warp per 32 steps (K <= 1024)
     const size_t sm = lag_corr_smem(K);
     static size_t sm_set = 48 * 1024;   // the largest dynamic size opted into so far
     if (sm > sm_set) {
@@ -298,7 +264,7 @@ void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, 
             return;   // the launch below is skipped; the caller's cudaGetLastError reports it
         sm_set = sm;
     }
-    lag_corr_kernel<<<grid, LC_THREADS, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0, t0_dev);
+    lag_corr_kernel<<<grid, threads, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0, t0_dev);
 }
 
 void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
