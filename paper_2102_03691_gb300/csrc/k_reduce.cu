@@ -251,19 +251,27 @@ void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin
     bin_finish_kernel<<<B, BF_THREADS, 0, s>>>(partials, n_slots, slot_begin, B, K, Jb, hsum, Jtot, Jsum);
 }
 
+namespace {
+size_t lc_sm_set = 48 * 1024;   // the largest dynamic shared memory opted into so far
+}
+
+cudaError_t lag_corr_prepare(int k_max) {
+    const size_t sm = lag_corr_smem(k_max);
+    if (sm <= lc_sm_set) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(lag_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sm);
+    if (e == cudaSuccess) lc_sm_set = sm;
+    return e;
+}
+
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
                      int L, long long t0, const long long *t0_dev, cudaStream_t s) {
     if (L <= 0 || K <= 0 || B <= 0) return;
     dim3 grid((L + 31) / 32, (B + LC_ROWS / 3 - 1) / (LC_ROWS / 3));
     const int threads = 32 * ((K + 31) / 32);   // one warp per 32 steps (K <= 1024)
     const size_t sm = lag_corr_smem(K);
-    static size_t sm_set = 48 * 1024;   // the largest dynamic size opted into so far
-    if (sm > sm_set) {
-        if (cudaFuncSetAttribute(lag_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm) != cudaSuccess)
-            return;   // the launch below is skipped; the caller's cudaGetLastError reports it
-        sm_set = sm;
-    }
+    if (sm > lc_sm_set && lag_corr_prepare(K) != cudaSuccess)
+        return;   // the launch is skipped; the caller's cudaGetLastError reports the failure
     lag_corr_kernel<<<grid, threads, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0, t0_dev);
 }
 

@@ -181,6 +181,9 @@ void launch_shc_tc_reduce(const ShcTcParams &p, double *Ksum, cudaStream_t s);
 void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin, int B, int K,
                        float *Jb, double *hsum, const double *Jtot, double *Jsum, cudaStream_t s);
 // Csum[b][mu][nu][l] += sum_k Jb[k][b][mu] J(t0+k-l)^nu over t0+k-l >= 0.
+// lag_corr_prepare(k_max): opt into the shared memory of blocks up to k_max steps (call outside
+// any stream capture).
+cudaError_t lag_corr_prepare(int k_max);
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
                      int L, long long t0, const long long *t0_dev, cudaStream_t s);
 // *steps += K (one thread; last kernel of a push)
@@ -207,12 +210,35 @@ void launch_hnema_finalize_group(const HnemaGroupArgs &a, double *mean, double *
 // ring[(t0 + k) mod R][3b+mu] = Jb[k][b][mu] (nb output rows of 3 components)
 void launch_jb_ring_store(const float *Jb, int K, int nb, float *ring, int R, long long t0,
                           const long long *t0_dev, cudaStream_t s);
-// X[l][3b+mu][3b'+nu] += sum_k Jb[k][b][mu] Jb(t0+k-l)[b'][nu] over t0+k-l >= 0 (FP32 products,
-// 32-step FP32 partials in a float pair, FP64 state); the ring must already hold the block.
-void launch_bin_xcorr(const float *Jb, const float *ring, int R, double *X, int K, int nb, int L,
-                      long long t0, const long long *t0_dev, cudaStream_t s);
-// out[b][b'][mu][nu][l] = X[l][3b+mu][3b'+nu]
-void launch_xcorr_transpose(const double *X, int nb, int L, double *out, cudaStream_t s);
+// Tensor-core cross-correlation (k_xcorr.cu): n = 3 nb rows; column tiles of nj <= XC_NJ_MAX
+// rows j; row tiles of 128 rows i; the window copies hold 8 x rows_pad rows of U_pad steps.
+constexpr int XC_NJ_MAX = 192;
+struct XcPlan {
+    int n, nj, n_jt, n_it, rows_pad, U_pad, cpt, grid;
+};
+struct XcTcParams {
+    CUtensorMap tmA_hi, tmA_lo;   // window copies [8 rows_pad][U_pad] FP16 hi/lo, 128-row boxes
+    CUtensorMap tmB_hi, tmB_lo;   // the same arrays, nj-row boxes
+    const float *inv_scale;       // [rows_pad] 2^-s of each window row (written per block)
+    float2 *X;                    // [L][n][n] float-pair sums, X[l][j][i]
+    int n, L, n_kb, nj, n_jt, rows_pad, cpt;
+    long long wait_limit;
+    int *status;
+    uint32_t idesc;
+};
+void xcorr_plan(int nb, int L, int k_max, int nsm, XcPlan &pl);
+// Opt the tensor-core kernel into its shared memory (once; outside any stream capture).
+cudaError_t xcorr_prepare();
+// Encode the four tensor maps over the window copies and fill the plan's fields of p.
+int xcorr_make_maps(const XcPlan &pl, const void *Whi, const void *Wlo, XcTcParams &p);
+// X[l][3b'+nu][3b+mu] += sum_k Jb[k][b][mu] Jb(t0+k-l)[b'][nu] over t0+k-l >= 0, the block
+// already in the ring: the window kernel (scales + eight shifted FP16 hi/lo copies of
+// [t0 - L + 1, t0 + K)) then the tensor-core kernel.  Needs K + L - 1 <= min(R, U_pad).
+cudaError_t launch_bin_xcorr(const XcPlan &pl, XcTcParams p, const float *ring, int R, int K,
+                             long long t0, const long long *t0_dev, void *Whi, void *Wlo,
+                             cudaStream_t s);
+// out[b][b'][mu][nu][l] = X[l][3b'+nu][3b+mu] (float pair -> FP64)
+void launch_xcorr_transpose(const float2 *X, int nb, int L, double *out, cudaStream_t s);
 // count[l] = max(T_s - l, 0)
 void launch_lag_counts(long long T_s, int L, long long *count, cudaStream_t s);
 

@@ -133,6 +133,8 @@ struct mhc_handle {
     TcConfig tc{256, 64, 2, 0, 0};
     std::map<int, TcConfig> tuned;  // K -> config
     TcParams<1> tcp{};
+    XcPlan xc_plan{};     // cross-correlations (MHC_FLAG_XCORR): tensor-core plan and parameters
+    XcTcParams xcp{};
 };
 
 struct GroupSchedule {
@@ -255,10 +257,27 @@ mhc_status reset_accumulators(mhc_handle *h) {
     if (h->prm.flags & MHC_FLAG_GKMA) {
         if ((s = dev_alloc(h, "Csum", sizeof(double) * B * 9 * L)) != MHC_OK) return s;
         if ((s = dev_alloc(h, "Jring", sizeof(double) * h->R_ring * 3)) != MHC_OK) return s;
+        MHC_CUDA(h, lag_corr_prepare(h->prm.k_max));
     }
-    if (has_xcorr(h)) {   // lag-major [L][3R][3R] sums and the ring of past binned currents
-        if ((s = dev_alloc(h, "Xsum", sizeof(double) * L * 9 * B * B)) != MHC_OK) return s;
+    if (has_xcorr(h)) {   // lag-major [L][3R][3R] float-pair sums, the ring of past binned
+                          // currents, and the tensor-core kernel's window copies
+        if ((s = dev_alloc(h, "Xsum", sizeof(float2) * L * 9 * B * B)) != MHC_OK) return s;
         if ((s = dev_alloc(h, "Jbring", sizeof(float) * h->R_ring * 3 * B)) != MHC_OK) return s;
+        XcPlan &pl = h->xc_plan;
+        xcorr_plan((int)B, (int)L, h->prm.k_max, h->sm_count, pl);
+        const size_t wbytes = sizeof(uint16_t) * 8 * (size_t)pl.rows_pad * pl.U_pad;
+        if ((s = dev_alloc(h, "Xwin_hi", wbytes)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "Xwin_lo", wbytes)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "Xinv", sizeof(float) * pl.rows_pad)) != MHC_OK) return s;
+        XcTcParams &xp = h->xcp;
+        if (xcorr_make_maps(pl, dptr<void>(h, "Xwin_hi"), dptr<void>(h, "Xwin_lo"), xp))
+            return fail(h, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed (cross-correlation windows)");
+        xp.inv_scale = dptr<float>(h, "Xinv");
+        xp.X = dptr<float2>(h, "Xsum");
+        xp.L = (int)L;
+        xp.status = h->status;
+        xp.wait_limit = 2000000000ll;
+        MHC_CUDA(h, xcorr_prepare());
     }
     return MHC_OK;
 }
@@ -604,10 +623,10 @@ mhc_status finish_kernels(mhc_handle *h, int K) {
     if (has_xcorr(h)) {
         launch_jb_ring_store(dptr<float>(h, "Jb"), K, (int)n_out_bins(h), dptr<float>(h, "Jbring"),
                              h->R_ring, h->steps, dptr<long long>(h, "steps_dev"), h->stream);
-        launch_bin_xcorr(dptr<float>(h, "Jb"), dptr<float>(h, "Jbring"), h->R_ring,
-                         dptr<double>(h, "Xsum"), K, (int)n_out_bins(h), h->prm.n_lags, h->steps,
-                         dptr<long long>(h, "steps_dev"), h->stream);
-        h->launches += 2;
+        MHC_CUDA(h, launch_bin_xcorr(h->xc_plan, h->xcp, dptr<float>(h, "Jbring"), h->R_ring, K,
+                                     h->steps, dptr<long long>(h, "steps_dev"),
+                                     dptr<void>(h, "Xwin_hi"), dptr<void>(h, "Xwin_lo"), h->stream));
+        h->launches += 3;
     }
     launch_advance_steps(dptr<long long>(h, "steps_dev"), K, h->stream);
     h->launches++;
@@ -1091,7 +1110,7 @@ mhc_status mhc_read_xcorr(mhc_handle *h, double *xsum, int64_t *count, int32_t w
     mhc_status s;
     if (xsum) {
         if ((s = dev_alloc(h, "xc_out", sizeof(double) * n, false)) != MHC_OK) return s;
-        launch_xcorr_transpose(dptr<double>(h, "Xsum"), nb, L, dptr<double>(h, "xc_out"), h->stream);
+        launch_xcorr_transpose(dptr<float2>(h, "Xsum"), nb, L, dptr<double>(h, "xc_out"), h->stream);
         h->launches++;
         MHC_CUDA(h, cudaGetLastError());
         if ((s = copy_out(h, xsum, dptr<double>(h, "xc_out"), sizeof(double) * n, where)) != MHC_OK) return s;
@@ -1117,7 +1136,7 @@ mhc_status mhc_read_kappa_xcorr(mhc_handle *h, double *kappa_tau, double tau_lo,
     mhc_status s;
     if ((s = dev_alloc(h, "xc_out", sizeof(double) * rows * L, false)) != MHC_OK) return s;
     if ((s = dev_alloc(h, "xk_out", sizeof(double) * (rows * (L + 1) + L), false)) != MHC_OK) return s;
-    launch_xcorr_transpose(dptr<double>(h, "Xsum"), nb, L, dptr<double>(h, "xc_out"), h->stream);
+    launch_xcorr_transpose(dptr<float2>(h, "Xsum"), nb, L, dptr<double>(h, "xc_out"), h->stream);
     double *dk = dptr<double>(h, "xk_out"), *dw = dk + rows * L;
     const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
     launch_gk_kappa(dptr<double>(h, "xc_out"), nb * nb, L, h->steps, coef * h->prm.dt_ps, tau_lo,

@@ -114,3 +114,26 @@ def test_pack_paths_large_system(N):
     np.testing.assert_allclose(J, o["J"], rtol=1e-12, atol=1e-9 * np.abs(o["J"]).max())
     assert np.all(series_rel_err(Jb, o["Jb"]) <= REL_TOL)
     h.close()
+
+
+@pytest.mark.parametrize("direction", [False, True])
+def test_largest_block_with_lag_correlation(direction):
+    # K = 1024 (the largest block): the lag correlation runs 32 step warps a CTA and needs more
+    # than 48 KB of shared memory; 2200 steps end in a ragged block of 152; 7 bins (row groups
+    # of 4 bins end ragged), 70 lags (the last lag CTA half full)
+    need_gpu()
+    L, K, T, B = 70, 1024, 2200, 7
+    c = make_case(N=40, M=120, T=T, B=B, seed=905, drive=2e-3)
+    h, Jb, J = run_gpu(c, "fp16x3", K=K, L=L, direction=direction)
+    if direction:
+        od = oracle.modal_current_dir(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
+        rows, Jt = od["Jbd"].reshape(T, 3 * B, 3), od["Jd"].sum(axis=1)
+    else:
+        o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
+        rows, Jt = o["Jb"], o["J"]
+    C0, cnt0 = oracle.gkma_corr(rows, Jt, L)
+    C, cnt = h.read_corr()
+    np.testing.assert_array_equal(cnt, cnt0)
+    err = series_rel_err(C.reshape(-1, L).T, C0.reshape(-1, L).T)
+    assert np.all(err <= REL_TOL)
+    h.close()
