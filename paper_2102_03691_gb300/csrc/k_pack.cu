@@ -3,6 +3,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -177,8 +179,9 @@ __device__ __forceinline__ void store_split4(const PackArgs &a, size_t idx, floa
 // 4t+3: row maxima and the exact total-current pairs (acc_exact), combined per CTA (FP64, fixed
 // order) and across the cluster in rank order through distributed shared memory (the result is
 // deterministic); then the four B rows of step k from shared memory with 8-byte stores.
+// The body of one CTA: step k of the system `a`, rank `rank` of its cluster of `nrank` CTAs.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) pack_bulk_kernel(const PackArgs a) {
+__device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_t rank, uint32_t nrank) {
     constexpr int APC = 4 * THREADS;
     extern __shared__ float4 pk_smem4[];
     float *sv = reinterpret_cast<float *>(pk_smem4);   // [APC][3]
@@ -189,8 +192,6 @@ __global__ void __launch_bounds__(THREADS) pack_bulk_kernel(const PackArgs a) {
     __shared__ double s_jc[3];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int abort_flag;
-    const uint32_t rank = cluster_ctarank(), nrank = cluster_nctarank();
-    const int k = (int)(blockIdx.x / nrank);
     const int a0 = (int)rank * APC;
     const int na = max(0, min(APC, a.N - a0));
     const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT_CYCLES;
@@ -328,6 +329,24 @@ __global__ void __launch_bounds__(THREADS) pack_bulk_kernel(const PackArgs a) {
 }
 
 template <int THREADS>
+__global__ void __launch_bounds__(THREADS) pack_bulk_kernel(const PackArgs a) {
+    const uint32_t nrank = cluster_nctarank();
+    pack_bulk_body<THREADS>(a, (int)(blockIdx.x / nrank), cluster_ctarank(), nrank);
+}
+
+// Several systems in one launch: system j owns the CTAs cta_begin[j] .. cta_begin[j+1) (K_j
+// clusters of the common cluster size; ranks beyond a system's atoms hold no atoms and only
+// take part in the cluster's combination).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) pack_bulk_group_kernel(const __grid_constant__ PackGroupArgs g) {
+    int j = 0;
+    while (j + 1 < g.n && (int)blockIdx.x >= g.cta_begin[j + 1]) ++j;
+    const uint32_t nrank = cluster_nctarank();
+    pack_bulk_body<THREADS>(g.a[j], (int)((blockIdx.x - (uint32_t)g.cta_begin[j]) / nrank),
+                            cluster_ctarank(), nrank);
+}
+
+template <int THREADS>
 cudaError_t launch_pack_bulk(const PackArgs &a, cudaStream_t s) {
     constexpr int APC = 4 * THREADS;
     const int smem = APC * 48;
@@ -352,11 +371,54 @@ cudaError_t launch_pack_bulk(const PackArgs &a, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+bool bulk_ok(const PackArgs &a) {
+    const auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    return a.N % 4 == 0 && al16(a.v) && al16(a.W) && al16(a.sqm) && al16(a.isqm) &&
+           (a.split == SPLIT_FP32 ? al16(a.Bt32) : true);
+}
+
+template <int THREADS>
+cudaError_t launch_pack_bulk_group(PackGroupArgs g, int csize, cudaStream_t s) {
+    constexpr int APC = 4 * THREADS;
+    const int smem = APC * 48;
+    static cudaError_t attr = cudaFuncSetAttribute(pack_bulk_group_kernel<THREADS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
+    g.cta_begin[0] = 0;
+    for (int j = 0; j < g.n; ++j) g.cta_begin[j + 1] = g.cta_begin[j] + g.a[j].K * csize;
+    if (g.cta_begin[g.n] == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g.cta_begin[g.n], 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeClusterDimension;
+    la[0].val.clusterDim.x = (unsigned)csize;
+    la[0].val.clusterDim.y = 1;
+    la[0].val.clusterDim.z = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pack_bulk_group_kernel<THREADS>, g);
+}
+}  // namespace
+
+cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s) {
+    if (g.n < 1 || g.n > TC_MAX_GROUP) return cudaErrorInvalidValue;
+    int nmax = 0;
+    for (int j = 0; j < g.n; ++j) {
+        if (!bulk_ok(g.a[j])) return cudaErrorNotSupported;
+        nmax = std::max(nmax, g.a[j].N);
+    }
+    if (nmax <= 8 * 1024) return launch_pack_bulk_group<256>(g, (nmax + 1023) / 1024, s);
+    if (nmax <= 8 * 2048) return launch_pack_bulk_group<512>(g, (nmax + 2047) / 2048, s);
+    return cudaErrorNotSupported;
+}
+
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
-    const auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    const bool bulk = a.N % 4 == 0 && al16(a.v) && al16(a.W) && al16(a.sqm) && al16(a.isqm) &&
-                      (a.split == SPLIT_FP32 ? al16(a.Bt32) : true);
+    const bool bulk = bulk_ok(a);
     if (bulk && a.N <= 8 * 1024) return launch_pack_bulk<256>(a, s);
     if (bulk && a.N <= 8 * 2048) return launch_pack_bulk<512>(a, s);
     pack_kernel<<<a.K, PACK_THREADS, 0, s>>>(a);

@@ -14,12 +14,10 @@ namespace {
 // (deterministic).  CTA 0 also sums the total current.
 constexpr int BF_STEPS = 256;
 constexpr int BF_THREADS = 3 * BF_STEPS;
-__global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__restrict__ partials,
-                                                                int n_slots, const int *slot_begin,
-                                                                int B, int K, float *Jb,
-                                                                double *hsum, const double *Jtot,
-                                                                double *Jsum) {
-    const int b = blockIdx.x;
+__device__ __forceinline__ void bin_finish_body(const float *__restrict__ partials, int n_slots,
+                                                const int *slot_begin, int B, int K, float *Jb,
+                                                double *hsum, const double *Jtot, double *Jsum,
+                                                int b) {
     const int a = threadIdx.x % 3, k0 = threadIdx.x / 3;
     const int s0 = slot_begin[b], s1 = slot_begin[b + 1];
     double acc = 0.0, acc_tot = 0.0;
@@ -46,6 +44,27 @@ __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__r
         hsum[b * 3 + threadIdx.x] += red[0][threadIdx.x];
         if (b == 0) Jsum[threadIdx.x] += red[1][threadIdx.x];
     }
+}
+
+__global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__restrict__ partials,
+                                                                int n_slots, const int *slot_begin,
+                                                                int B, int K, float *Jb,
+                                                                double *hsum, const double *Jtot,
+                                                                double *Jsum) {
+    bin_finish_body(partials, n_slots, slot_begin, B, K, Jb, hsum, Jtot, Jsum, blockIdx.x);
+}
+
+// All systems of a group in one launch: CTAs cta_begin[j] .. cta_begin[j+1) are system j's bins.
+__global__ void __launch_bounds__(BF_THREADS) bin_finish_group_kernel(const __grid_constant__ FinishGroupArgs g) {
+    int j = 0;
+    while (j + 1 < g.n && (int)blockIdx.x >= g.cta_begin[j + 1]) ++j;
+    bin_finish_body(g.partials[j], g.n_slots[j], g.slot_begin[j], g.B[j], g.K[j], g.Jb[j],
+                    g.hsum[j], g.Jtot[j], g.Jsum[j], (int)blockIdx.x - g.cta_begin[j]);
+}
+
+__global__ void advance_steps_group_kernel(const __grid_constant__ FinishGroupArgs g) {
+    const int j = threadIdx.x;
+    if (j < g.n) *g.steps[j] += g.K[j];
 }
 
 // ------------------------------------------------------------------ K4
@@ -262,6 +281,17 @@ cudaError_t lag_corr_prepare(int k_max) {
                                                (int)sm);
     if (e == cudaSuccess) lc_sm_set = sm;
     return e;
+}
+
+void launch_bin_finish_group(FinishGroupArgs g, cudaStream_t s) {
+    if (g.n < 1) return;
+    g.cta_begin[0] = 0;
+    for (int j = 0; j < g.n; ++j) g.cta_begin[j + 1] = g.cta_begin[j] + (g.K[j] > 0 ? g.B[j] : 0);
+    if (g.cta_begin[g.n] > 0) bin_finish_group_kernel<<<g.cta_begin[g.n], BF_THREADS, 0, s>>>(g);
+}
+
+void launch_advance_steps_group(const FinishGroupArgs &g, cudaStream_t s) {
+    if (g.n >= 1) advance_steps_group_kernel<<<1, 32, 0, s>>>(g);
 }
 
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,

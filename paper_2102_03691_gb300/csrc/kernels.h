@@ -9,6 +9,8 @@ namespace mhc {
 
 enum Split { SPLIT_FP32 = 0, SPLIT_BF16 = 1, SPLIT_FP16 = 2 };
 
+constexpr int TC_MAX_GROUP = 16;  // systems per grouped launch
+
 // Sticky device status codes (same values as mhc_status).
 constexpr int DEV_OK = 0, DEV_TIMEOUT = 4, DEV_STATE = 5;
 
@@ -48,6 +50,15 @@ struct PackArgs {
 // cluster of CTAs per step that bulk-copies its atoms into shared memory (the inputs are read
 // once); other shapes by one CTA per step that reads them twice.
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s);
+// The packs of up to TC_MAX_GROUP systems in one launch of clusters of a common size (each
+// system's K steps; cta_begin is filled by the launcher).  cudaErrorNotSupported when a system
+// does not qualify for the bulk-copy pack (the caller then packs the systems one by one).
+struct PackGroupArgs {
+    PackArgs a[TC_MAX_GROUP];
+    int cta_begin[TC_MAX_GROUP + 1];
+    int n;
+};
+cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s);
 
 // ---------------------------------------------------------------- E preparation
 // max |E| over the valid D x M region (bit pattern of a non-negative float)
@@ -81,7 +92,6 @@ void launch_fp32_dir_epilogue(const float *R, size_t rstride, int Mp, int K, con
 
 // ---------------------------------------------------------------- tensor-core path
 constexpr int TC_BM = 128;        // modes per tile = TMEM lanes
-constexpr int TC_MAX_GROUP = 16;  // systems per grouped launch
 
 struct TcProblem {   // 128-byte aligned through CUtensorMap
     CUtensorMap tmA_hi, tmA_lo;   // Et hi/lo [M_pad][D_ld]
@@ -180,6 +190,23 @@ void launch_shc_tc_reduce(const ShcTcParams &p, double *Ksum, cudaStream_t s);
 // Jsum[a] += sum_k Jtot[k][a].
 void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin, int B, int K,
                        float *Jb, double *hsum, const double *Jtot, double *Jsum, cudaStream_t s);
+// The bin finish (as launch_bin_finish) and the step counters (*steps += K) of up to
+// TC_MAX_GROUP systems, one launch each; cta_begin is filled by the launcher.
+struct FinishGroupArgs {
+    const float *partials[TC_MAX_GROUP];
+    int n_slots[TC_MAX_GROUP];
+    const int *slot_begin[TC_MAX_GROUP];
+    int B[TC_MAX_GROUP], K[TC_MAX_GROUP];
+    float *Jb[TC_MAX_GROUP];
+    double *hsum[TC_MAX_GROUP];
+    const double *Jtot[TC_MAX_GROUP];
+    double *Jsum[TC_MAX_GROUP];
+    long long *steps[TC_MAX_GROUP];
+    int cta_begin[TC_MAX_GROUP + 1];
+    int n;
+};
+void launch_bin_finish_group(FinishGroupArgs g, cudaStream_t s);
+void launch_advance_steps_group(const FinishGroupArgs &g, cudaStream_t s);
 // Csum[b][mu][nu][l] += sum_k Jb[k][b][mu] J(t0+k-l)^nu over t0+k-l >= 0.
 // lag_corr_prepare(k_max): opt into the shared memory of blocks up to k_max steps (call outside
 // any stream capture).

@@ -157,8 +157,6 @@ struct mhc_group {
     std::map<std::tuple<std::vector<int>, std::vector<const void *>, int>, GraphEntry> graphs;
     uint64_t graph_clock = 0;
     cudaStream_t cap_stream = nullptr;
-    std::vector<cudaStream_t> branch;      // side streams: per-system kernels as parallel graph branches
-    std::vector<cudaEvent_t> branch_ev;    // fork/join events used during capture
 };
 
 namespace {
@@ -579,7 +577,7 @@ mhc_status release_stage(mhc_handle *h) {
     return MHC_OK;
 }
 
-mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
+PackArgs pack_args(mhc_handle *h, const float *v, const float *W, int K) {
     PackArgs a{};
     a.v = v;
     a.W = W;
@@ -602,18 +600,19 @@ mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
     a.npad = h->dir ? (int)h->N_pad : 0;
     a.status = h->status;
     a.wait_limit = 0;
-    MHC_CUDA(h, launch_pack(a, h->stream));
+    return a;
+}
+
+mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
+    MHC_CUDA(h, launch_pack(pack_args(h, v, W, K), h->stream));
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
     return MHC_OK;
 }
 
-// Kernels that close a push: bin finish + HNEMA sums, GKMA lag correlation, step counter.
-mhc_status finish_kernels(mhc_handle *h, int K) {
-    launch_bin_finish(dptr<float>(h, "partials"), (int)slot_stride(h), dptr<int>(h, "slot_begin"),
-                      (int)n_out_bins(h), K, dptr<float>(h, "Jb"), dptr<double>(h, "hsum"),
-                      dptr<double>(h, "Jtot"), dptr<double>(h, "Jsum"), h->stream);
-    h->launches++;
+// The correlation kernels of a push (after its bin finish): GKMA lag correlation and the
+// cross-correlations.
+mhc_status correlate_block(mhc_handle *h, int K) {
     if (h->prm.flags & MHC_FLAG_GKMA) {
         launch_lag_corr(dptr<float>(h, "Jb"), dptr<double>(h, "Jring"), h->R_ring,
                         dptr<double>(h, "Csum"), K, (int)n_out_bins(h), h->prm.n_lags, h->steps,
@@ -628,6 +627,18 @@ mhc_status finish_kernels(mhc_handle *h, int K) {
                                      dptr<void>(h, "Xwin_hi"), dptr<void>(h, "Xwin_lo"), h->stream));
         h->launches += 3;
     }
+    MHC_CUDA(h, cudaGetLastError());
+    return MHC_OK;
+}
+
+// Kernels that close a push: bin finish + HNEMA sums, correlations, step counter.
+mhc_status finish_kernels(mhc_handle *h, int K) {
+    launch_bin_finish(dptr<float>(h, "partials"), (int)slot_stride(h), dptr<int>(h, "slot_begin"),
+                      (int)n_out_bins(h), K, dptr<float>(h, "Jb"), dptr<double>(h, "hsum"),
+                      dptr<double>(h, "Jtot"), dptr<double>(h, "Jsum"), h->stream);
+    h->launches++;
+    mhc_status s = correlate_block(h, K);
+    if (s != MHC_OK) return s;
     launch_advance_steps(dptr<long long>(h, "steps_dev"), K, h->stream);
     h->launches++;
     MHC_CUDA(h, cudaGetLastError());
@@ -1401,6 +1412,59 @@ mhc_status group_schedule(mhc_group *g, const std::vector<int> &Ks, GroupSchedul
     return MHC_OK;
 }
 
+// The packs of all systems in one launch (clusters of a common size), or one by one when a
+// system does not qualify for the bulk-copy pack.  All handles of a group share one stream.
+mhc_status group_pack(mhc_group *g, const std::vector<const float *> &vs,
+                      const std::vector<const float *> &ws, const std::vector<int> &Ks) {
+    mhc_handle *h0 = g->hs[0];
+    PackGroupArgs pg{};
+    pg.n = (int)g->hs.size();
+    for (int j = 0; j < pg.n; ++j) pg.a[j] = pack_args(g->hs[j], vs[j], ws[j], Ks[j]);
+    const cudaError_t e = launch_pack_group(pg, h0->stream);
+    if (e == cudaErrorNotSupported) {
+        for (int j = 0; j < pg.n; ++j) {
+            const mhc_status s = pack_block(g->hs[j], vs[j], ws[j], Ks[j]);
+            if (s != MHC_OK) return s;
+        }
+        return MHC_OK;
+    }
+    MHC_CUDA(h0, e);
+    h0->launches++;
+    return MHC_OK;
+}
+
+// The kernels that close a group push: one bin-finish launch for all systems, each system's
+// correlation kernels, one launch for all step counters.
+mhc_status group_finish(mhc_group *g, const std::vector<int> &Ks) {
+    mhc_handle *h0 = g->hs[0];
+    FinishGroupArgs fg{};
+    fg.n = (int)g->hs.size();
+    for (int j = 0; j < fg.n; ++j) {
+        mhc_handle *h = g->hs[j];
+        fg.partials[j] = dptr<float>(h, "partials");
+        fg.n_slots[j] = (int)slot_stride(h);
+        fg.slot_begin[j] = dptr<int>(h, "slot_begin");
+        fg.B[j] = (int)n_out_bins(h);
+        fg.K[j] = Ks[j];
+        fg.Jb[j] = dptr<float>(h, "Jb");
+        fg.hsum[j] = dptr<double>(h, "hsum");
+        fg.Jtot[j] = dptr<double>(h, "Jtot");
+        fg.Jsum[j] = dptr<double>(h, "Jsum");
+        fg.steps[j] = dptr<long long>(h, "steps_dev");
+    }
+    launch_bin_finish_group(fg, h0->stream);
+    h0->launches++;
+    MHC_CUDA(h0, cudaGetLastError());
+    for (int j = 0; j < fg.n; ++j) {
+        const mhc_status s = correlate_block(g->hs[j], Ks[j]);
+        if (s != MHC_OK) return s;
+    }
+    launch_advance_steps_group(fg, h0->stream);
+    h0->launches++;
+    MHC_CUDA(h0, cudaGetLastError());
+    return MHC_OK;
+}
+
 mhc_status group_launch(mhc_group *g, const std::vector<int> &Ks) {
     mhc_handle *h0 = g->hs[0];
     GroupSchedule *gs = nullptr;
@@ -1493,8 +1557,6 @@ void mhc_group_destroy(mhc_group *g) {
     for (auto &kv : g->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
-    for (cudaStream_t b : g->branch) cudaStreamDestroy(b);
-    for (cudaEvent_t e : g->branch_ev) cudaEventDestroy(e);
     for (auto &kv : g->sched_cache) {
         if (kv.second.sched.p) cudaFree(kv.second.sched.p);
         if (kv.second.cta_begin.p) cudaFree(kv.second.cta_begin.p);
@@ -1591,36 +1653,14 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
             if (!g->cap_stream) MHC_CUDA(h0, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
             std::vector<int64_t> l0(n);
             for (size_t j = 0; j < n; ++j) l0[j] = g->hs[j]->launches;
-            if (g->branch.empty()) {
-                g->branch.resize(n);
-                g->branch_ev.resize(2 * n + 2);
-                for (size_t j = 0; j < n; ++j)
-                    MHC_CUDA(h0, cudaStreamCreateWithFlags(&g->branch[j], cudaStreamNonBlocking));
-                for (auto &e : g->branch_ev)
-                    MHC_CUDA(h0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            }
             cudaStream_t user = h0->stream;
-            // graph: fork -> per-system packs on parallel branches -> join -> grouped launch
-            //        -> fork -> per-system finish kernels on parallel branches -> join
-            auto fork_join = [&](int ev_base, auto &&body) -> mhc_status {
-                MHC_CUDA(h0, cudaEventRecord(g->branch_ev[ev_base], g->cap_stream));
-                mhc_status r = MHC_OK;
-                for (size_t j = 0; j < n && r == MHC_OK; ++j) {
-                    MHC_CUDA(h0, cudaStreamWaitEvent(g->branch[j], g->branch_ev[ev_base], 0));
-                    g->hs[j]->stream = g->branch[j];
-                    r = body(j);
-                    g->hs[j]->stream = g->cap_stream;
-                    MHC_CUDA(h0, cudaEventRecord(g->branch_ev[ev_base + 1 + j], g->branch[j]));
-                    MHC_CUDA(h0, cudaStreamWaitEvent(g->cap_stream, g->branch_ev[ev_base + 1 + j], 0));
-                }
-                return r;
-            };
+            // graph: grouped pack -> grouped projection -> grouped bin finish -> correlations
+            //        -> step counters
             MHC_CUDA(h0, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
             for (size_t j = 0; j < n; ++j) g->hs[j]->stream = g->cap_stream;
-            s = fork_join(0, [&](size_t j) { return pack_block(g->hs[j], vs[j], ws[j], Ks[j]); });
+            s = group_pack(g, vs, ws, Ks);
             if (s == MHC_OK) s = group_launch(g, Ks);
-            if (s == MHC_OK)
-                s = fork_join(0, [&](size_t j) { return finish_kernels(g->hs[j], Ks[j]); });
+            if (s == MHC_OK) s = group_finish(g, Ks);
             for (size_t j = 0; j < n; ++j) g->hs[j]->stream = user;
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
@@ -1649,8 +1689,7 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
         }
         return MHC_OK;
     }
-    for (size_t j = 0; j < n; ++j)
-        if ((s = pack_block(g->hs[j], vs[j], ws[j], Ks[j])) != MHC_OK) return s;
+    if ((s = group_pack(g, vs, ws, Ks)) != MHC_OK) return s;
     if (!g->tuned && h0->prm.tile_config == 0) {
         if ((s = group_autotune(g, Ks)) != MHC_OK) return s;
     }
@@ -1668,8 +1707,9 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
     }
     if ((s = group_launch(g, Ks)) != MHC_OK) return s;
     if (ev1) MHC_CUDA(h0, cudaEventRecord(ev1, h0->stream));
+    if ((s = group_finish(g, Ks)) != MHC_OK) return s;
     for (size_t j = 0; j < n; ++j) {
-        if ((s = finish_block(g->hs[j], Ks[j])) != MHC_OK) return s;
+        count_push(g->hs[j], Ks[j]);
         if ((s = release_stage(g->hs[j])) != MHC_OK) return s;
     }
     return MHC_OK;

@@ -162,3 +162,29 @@ def test_group_host_inputs_back_to_back():
     for x, y in zip(res[0][0], res[1][0]):
         np.testing.assert_array_equal(x, y)
     np.testing.assert_array_equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("sizes", [[1100, 40, 200], [81, 120, 50]])
+def test_group_pack_clusters_and_fallback(sizes):
+    # [1100, 40, 200]: one pack launch for all systems in clusters of two CTAs (the 40- and
+    # 200-atom systems leave their second rank without atoms); [81, 120, 50]: a system with
+    # N % 4 != 0 sends the group back to one pack per system.  Both bitwise the solo pushes.
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import ModalHeatCurrentGroup
+    K, L = 24, 6
+    systems = [system(N, 900 + j) for j, N in enumerate(sizes)]
+    blocks = [[s["tr"].next_block(K) for _ in range(2)] for s in systems]
+    solo = [handle(s, K, L) for s in systems]
+    grouped = [handle(s, K, L) for s in systems]
+    grp = ModalHeatCurrentGroup(grouped)
+    for step in range(2):
+        for h, bl in zip(solo, blocks):
+            h.push(*bl[step])
+        grp.push([bl[step][0] for bl in blocks], [bl[step][1] for bl in blocks])
+        for hs, hg in zip(solo, grouped):
+            np.testing.assert_array_equal(hs.read_binned_current(), hg.read_binned_current())
+            np.testing.assert_array_equal(hs.read_total_current(), hg.read_total_current())
+    for hs, hg in zip(solo, grouped):
+        np.testing.assert_array_equal(hs.read_corr()[0], hg.read_corr()[0])
+        np.testing.assert_array_equal(hs.read_hnema()[0], hg.read_hnema()[0])
+    grp.close()
