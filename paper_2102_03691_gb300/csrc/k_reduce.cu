@@ -1,5 +1,7 @@
 // K3 bin finish + HNEMA sums (Eq. 19), K4 GKMA lag correlation (Eq. 17 integrand),
 // K5 running Green-Kubo integral (Eq. 17) and the HNEMA normalisation (Eq. 19).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -173,67 +175,91 @@ __global__ void inv_counts_kernel(long long T_s, int L, double *inv) {
     if (l < L) inv[l] = T_s > l ? 1.0 / (double)(T_s - l) : 0.0;
 }
 
-// One CTA per (b, mu, nu) row, GK_THREADS threads, each owning GK_PER consecutive lags.
-// C(l) = Csum(l) * inv_count(l); trapezoid increments (C(l-1)+C(l))/2 for l >= 1;
-// block-wide exclusive scan of the per-thread totals (fixed tree: deterministic);
-// kappa(l) = c dt * prefix(l).  The tau-window average is a block reduction.
+// One CTA per (b, mu, nu) row, GK_THREADS threads, each owning per = ceil(L / GK_THREADS)
+// consecutive lags.  C(l) = Csum(l) inv_count(l); the running trapezoid sum
+// S(l) = sum_{1 <= l' <= l} (C(l'-1) + C(l')) comes from per-thread totals and a block-wide
+// exclusive scan (warp shuffles, then the four warp totals: a fixed tree, deterministic);
+// kappa(l) = (c dt / 2) S(l).  The window average runs over the lags l_lo .. l_hi (the host
+// picks them with the same FP64 test on l dt as the oracle).  The pipe GB300 keeps narrow
+// bounds the kernel, so each lag costs a few FP64 operations: C(l) is computed once and kept
+// in registers when a thread owns at most GK_CACHE lags.
 constexpr int GK_THREADS = 128;
+constexpr int GK_CACHE = 8;
+__device__ __forceinline__ double gk_block_exclusive_scan(double x, double *s_w) {   // all threads
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(FULL_MASK, v, o);
+        if (lane >= o) v += y;
+    }
+    double ex = __shfl_up_sync(FULL_MASK, v, 1);   // exclusive within the warp
+    if (lane == 0) ex = 0.0;
+    if (lane == 31) s_w[w] = v;
+    __syncthreads();
+    double base = 0.0;
+    for (int q = 0; q < w; ++q) base += s_w[q];
+    __syncthreads();
+    return base + ex;
+}
+
 __global__ void __launch_bounds__(GK_THREADS) gk_kappa_kernel(const double *Csum, int L,
                                                               const double *__restrict__ inv,
-                                                              double coef_dt,
-                                                              double tau_lo, double tau_hi,
-                                                              double dt, double *kappa_tau,
-                                                              double *kappa_w) {
+                                                              double coef_half, int l_lo, int l_hi,
+                                                              double *kappa_tau, double *kappa_w) {
+    __shared__ double s_w[GK_THREADS / 32];
     const int r = blockIdx.x;
     const double *cs = Csum + (size_t)r * L;
     const int per = (L + GK_THREADS - 1) / GK_THREADS;
-    const int l0 = threadIdx.x * per;
-    auto C = [&](int l) -> double { return cs[l] * inv[l]; };
-    double prev = (l0 > 0 && l0 <= L) ? C(l0 - 1) : 0.0;
-    double tot = 0.0;
-    for (int l = l0; l < min(L, l0 + per); ++l) {
-        const double c = C(l);
-        if (l > 0) tot += 0.5 * (prev + c);
-        prev = c;
+    const int l0 = min(L, threadIdx.x * per), l1 = min(L, l0 + per);
+    const double c_before = (l0 > 0 && l0 < l1) ? cs[l0 - 1] * inv[l0 - 1] : 0.0;
+    double cc[GK_CACHE];
+    double tot = 0.0, prev = c_before;
+    if (per <= GK_CACHE) {
+#pragma unroll
+        for (int u = 0; u < GK_CACHE; ++u) {
+            const int l = l0 + u;
+            cc[u] = l < l1 ? cs[l] * inv[l] : 0.0;
+            if (l < l1) {
+                if (l > 0) tot += prev + cc[u];
+                prev = cc[u];
+            }
+        }
+    } else {
+        for (int l = l0; l < l1; ++l) {
+            const double c = cs[l] * inv[l];
+            if (l > 0) tot += prev + c;
+            prev = c;
+        }
     }
-    __shared__ double sc[GK_THREADS];
-    sc[threadIdx.x] = tot;
-    __syncthreads();
-    for (int off = 1; off < GK_THREADS; off <<= 1) {   // Hillis-Steele inclusive scan
-        const double add = threadIdx.x >= off ? sc[threadIdx.x - off] : 0.0;
-        __syncthreads();
-        sc[threadIdx.x] += add;
-        __syncthreads();
-    }
-    double acc = threadIdx.x > 0 ? sc[threadIdx.x - 1] : 0.0;   // exclusive prefix
+    double acc = gk_block_exclusive_scan(tot, s_w);
     double wsum = 0.0;
-    int wn = 0;
-    prev = (l0 > 0 && l0 <= L) ? C(l0 - 1) : 0.0;
-    for (int l = l0; l < min(L, l0 + per); ++l) {
-        const double c = C(l);
-        if (l > 0) acc += 0.5 * (prev + c);
+    prev = c_before;
+    auto emit = [&](int l, double c) {
+        if (l > 0) acc += prev + c;
         prev = c;
-        const double kap = coef_dt * acc;
+        const double kap = coef_half * acc;
         if (kappa_tau) kappa_tau[(size_t)r * L + l] = kap;
-        const double tau = l * dt;
-        if (tau >= tau_lo && tau <= tau_hi) {
-            wsum += kap;
-            ++wn;
-        }
+        if (l >= l_lo && l <= l_hi) wsum += kap;
+    };
+    if (per <= GK_CACHE) {
+#pragma unroll
+        for (int u = 0; u < GK_CACHE; ++u)
+            if (l0 + u < l1) emit(l0 + u, cc[u]);
+    } else {
+        for (int l = l0; l < l1; ++l) emit(l, cs[l] * inv[l]);
     }
+    // window average: block sum of wsum (fixed tree)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_down_sync(FULL_MASK, wsum, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = wsum;
     __syncthreads();
-    __shared__ int sn[GK_THREADS];
-    sc[threadIdx.x] = wsum;
-    sn[threadIdx.x] = wn;
-    __syncthreads();
-    for (int off = GK_THREADS / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) {
-            sc[threadIdx.x] += sc[threadIdx.x + off];
-            sn[threadIdx.x] += sn[threadIdx.x + off];
-        }
-        __syncthreads();
+    if (threadIdx.x == 0 && kappa_w) {
+        double t = 0.0;
+        for (int q = 0; q < GK_THREADS / 32; ++q) t += s_w[q];
+        const int n = l_hi >= l_lo ? l_hi - l_lo + 1 : 0;
+        kappa_w[r] = n > 0 ? t / n : 0.0;
     }
-    if (threadIdx.x == 0 && kappa_w) kappa_w[r] = sn[0] > 0 ? sc[0] / sn[0] : 0.0;
 }
 
 __global__ void hnema_finalize_kernel(const double *hsum, int n, long long T_s, double coef,
@@ -309,8 +335,17 @@ void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coe
                      double tau_lo, double tau_hi, double dt, double *kappa_tau, double *kappa_w,
                      double *inv_scratch, cudaStream_t s) {
     if (L <= 0 || B <= 0) return;
+    // the window's lags: l dt in [tau_lo, tau_hi], tested in FP64 as the oracle tests it
+    int l_lo = L, l_hi = -1;
+    for (int l = 0; l < L; ++l) {
+        const double tau = l * dt;
+        if (tau >= tau_lo && tau <= tau_hi) {
+            l_lo = std::min(l_lo, l);
+            l_hi = l;
+        }
+    }
     inv_counts_kernel<<<(L + 255) / 256, 256, 0, s>>>(T_s, L, inv_scratch);
-    gk_kappa_kernel<<<B * 9, GK_THREADS, 0, s>>>(Csum, L, inv_scratch, coef_dt, tau_lo, tau_hi, dt,
+    gk_kappa_kernel<<<B * 9, GK_THREADS, 0, s>>>(Csum, L, inv_scratch, 0.5 * coef_dt, l_lo, l_hi,
                                                  kappa_tau, kappa_w);
 }
 
