@@ -100,9 +100,12 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
                                       J_b^mu(t) J_{b'}^nu(t - l) (the mode-mode correlations that the
                                       modal currents of GKMA allow, at bin resolution; one bin per
                                       mode gives them per mode).  Summed over b' they equal the
-                                      Eq. 17 sums when every mode is binned.  State: R^2 * 9 * L FP64
-                                      values (R = output rows, B or 3B); read with mhc_read_xcorr /
-                                      mhc_read_kappa_xcorr.  Set at mhc_create. */
+                                      Eq. 17 sums when every mode is binned.  Computed on the tensor
+                                      cores (FP16x3 operands, per-lag contractions over each block);
+                                      state: R^2 * 9 * L sums kept as float pairs (~48 bits, 8 bytes
+                                      each; R = output rows, B or 3B) plus ~7 MB of window copies;
+                                      read as FP64 with mhc_read_xcorr / mhc_read_kappa_xcorr.  Set
+                                      at mhc_create. */
 
 typedef struct {
     int32_t device;      /* CUDA device ordinal */
