@@ -404,16 +404,28 @@ cudaError_t launch_pack_bulk_group(PackGroupArgs g, int csize, cudaStream_t s) {
 }
 }  // namespace
 
-cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s) {
+cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s, int *n_launches) {
+    *n_launches = 0;
     if (g.n < 1 || g.n > TC_MAX_GROUP) return cudaErrorInvalidValue;
     int nmax = 0;
     for (int j = 0; j < g.n; ++j) {
         if (!bulk_ok(g.a[j])) return cudaErrorNotSupported;
         nmax = std::max(nmax, g.a[j].N);
     }
-    if (nmax <= 8 * 1024) return launch_pack_bulk_group<256>(g, (nmax + 1023) / 1024, s);
-    if (nmax <= 8 * 2048) return launch_pack_bulk_group<512>(g, (nmax + 2047) / 2048, s);
-    return cudaErrorNotSupported;
+    if (nmax > 8 * 2048) return cudaErrorNotSupported;
+    // one launch per cluster size (systems of similar size together), so no rank is idle
+    const int threads = nmax <= 8 * 1024 ? 256 : 512, apc = 4 * threads;
+    for (int cs = 1; cs <= 8; ++cs) {
+        PackGroupArgs sub{};
+        for (int j = 0; j < g.n; ++j)
+            if ((g.a[j].N + apc - 1) / apc == cs || (g.a[j].N == 0 && cs == 1)) sub.a[sub.n++] = g.a[j];
+        if (sub.n == 0) continue;
+        const cudaError_t e = threads == 256 ? launch_pack_bulk_group<256>(sub, cs, s)
+                                             : launch_pack_bulk_group<512>(sub, cs, s);
+        if (e != cudaSuccess) return e;
+        ++*n_launches;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {

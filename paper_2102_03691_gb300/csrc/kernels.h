@@ -50,15 +50,16 @@ struct PackArgs {
 // cluster of CTAs per step that bulk-copies its atoms into shared memory (the inputs are read
 // once); other shapes by one CTA per step that reads them twice.
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s);
-// The packs of up to TC_MAX_GROUP systems in one launch of clusters of a common size (each
-// system's K steps; cta_begin is filled by the launcher).  cudaErrorNotSupported when a system
-// does not qualify for the bulk-copy pack (the caller then packs the systems one by one).
+// The packs of up to TC_MAX_GROUP systems in one launch per cluster size (systems needing the
+// same number of CTAs a step go together; cta_begin is filled by the launcher).
+// cudaErrorNotSupported when a system does not qualify for the bulk-copy pack (the caller then
+// packs the systems one by one).
 struct PackGroupArgs {
     PackArgs a[TC_MAX_GROUP];
     int cta_begin[TC_MAX_GROUP + 1];
     int n;
 };
-cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s);
+cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s, int *n_launches);
 
 // ---------------------------------------------------------------- E preparation
 // max |E| over the valid D x M region (bit pattern of a non-negative float)

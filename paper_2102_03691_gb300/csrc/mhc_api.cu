@@ -1420,7 +1420,8 @@ mhc_status group_pack(mhc_group *g, const std::vector<const float *> &vs,
     PackGroupArgs pg{};
     pg.n = (int)g->hs.size();
     for (int j = 0; j < pg.n; ++j) pg.a[j] = pack_args(g->hs[j], vs[j], ws[j], Ks[j]);
-    const cudaError_t e = launch_pack_group(pg, h0->stream);
+    int nl = 0;
+    const cudaError_t e = launch_pack_group(pg, h0->stream, &nl);
     if (e == cudaErrorNotSupported) {
         for (int j = 0; j < pg.n; ++j) {
             const mhc_status s = pack_block(g->hs[j], vs[j], ws[j], Ks[j]);
@@ -1429,7 +1430,7 @@ mhc_status group_pack(mhc_group *g, const std::vector<const float *> &vs,
         return MHC_OK;
     }
     MHC_CUDA(h0, e);
-    h0->launches++;
+    h0->launches += nl;
     return MHC_OK;
 }
 
