@@ -121,3 +121,26 @@ def test_xcorr_in_grouped_pushes_equals_single_handles():
     for hs, hg in zip(solo, grouped):
         np.testing.assert_array_equal(hs.read_xcorr()[0], hg.read_xcorr()[0])
     grp.close()
+
+
+@pytest.mark.parametrize("B,direction", [(70, False), (40, True)])
+def test_xcorr_several_row_and_column_tiles(B, direction):
+    # 3B = 210 rows (two column tiles of 192 and a ragged one of 18; two row tiles of 128) and,
+    # with the direction split, 9B = 360 rows (two column tiles, three row tiles); ragged blocks
+    need_gpu()
+    L, K, T = 20, 64, 150
+    c = make_case(N=100, M=300, T=T, B=B, seed=804, drive=2e-3)
+    if direction:
+        od = oracle.modal_current_dir(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
+        rows = od["Jbd"].reshape(T, 3 * B, 3)
+    else:
+        rows = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)["Jb"]
+    Xo = oracle.gkma_xcorr(rows, L)
+    h, Jb, J = run_gpu(c, "fp16x3", K=K, L=L, xcorr=True, direction=direction)
+    X, cnt = h.read_xcorr()
+    np.testing.assert_array_equal(cnt, np.maximum(T - np.arange(L), 0))
+    n = 3 * rows.shape[1]   # rows (bin row, component) of the contraction
+    err = series_rel_err(X.reshape(-1, L).T, Xo.reshape(-1, L).T)
+    report(f"xcorr {n} rows", err)
+    assert np.all(err <= REL_TOL)
+    h.close()
