@@ -137,3 +137,25 @@ def test_largest_block_with_lag_correlation(direction):
     err = series_rel_err(C.reshape(-1, L).T, C0.reshape(-1, L).T)
     assert np.all(err <= REL_TOL)
     h.close()
+
+
+def test_green_kubo_read_out_beyond_1024_lags():
+    # L = 1100 lags: more than 8 lags a thread of the read-out (the path that recomputes C(l)
+    # instead of keeping it in registers); 1300 steps in ragged blocks of 256; kappa(tau) at
+    # every lag and the window average against the oracle
+    need_gpu()
+    from tests.parity import spectrum_rel_err
+    L, K, T, B = 1100, 256, 1300, 3
+    dt, TK, V = 0.01, 300.0, 16 * 20.02
+    c = make_case(N=16, M=48, T=T, B=B, seed=906, drive=2e-3)
+    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
+    C0, cnt0 = oracle.gkma_corr(o["Jb"], o["J"], L)
+    h, Jb, J = run_gpu(c, "fp16x3", K=K, L=L, dt_ps=dt, T_K=TK, V_A3=V)
+    kt, kw = h.read_kappa_gk(8.0, 10.5)
+    okt = oracle.gk_kappa(C0, cnt0, dt, TK, V)
+    okw, n = oracle.kappa_window(okt, dt, 8.0, 10.5)
+    assert n == 251
+    errT = series_rel_err(kt.reshape(-1, L).T, okt.reshape(-1, L).T)
+    assert np.all(errT <= REL_TOL)
+    assert np.all(spectrum_rel_err(kw.reshape(B, 9), okw.reshape(B, 9)) <= REL_TOL)
+    h.close()
