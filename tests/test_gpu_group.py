@@ -188,3 +188,26 @@ def test_group_pack_clusters_and_fallback(sizes):
         np.testing.assert_array_equal(hs.read_corr()[0], hg.read_corr()[0])
         np.testing.assert_array_equal(hs.read_hnema()[0], hg.read_hnema()[0])
     grp.close()
+
+
+def test_group_pack_large_system_uses_wide_ctas():
+    # a 9000-atom system (120 modes of a thin basis) sends the whole group to 512-thread pack
+    # CTAs (clusters of 5 for it, of 1 for the 200-atom system): bitwise the solo pushes
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import ModalHeatCurrentGroup
+    K, L = 16, 4
+    big = system(9000, 950, E=synth.eigvecs(27000, 120, 950))
+    big["f"] = synth.frequencies(120, 0.0, 52.0, 950)
+    systems = [big, system(200, 951)]
+    blocks = [[s["tr"].next_block(K) for _ in range(2)] for s in systems]
+    solo = [handle(s, K, L) for s in systems]
+    grouped = [handle(s, K, L) for s in systems]
+    grp = ModalHeatCurrentGroup(grouped)
+    for step in range(2):
+        for h, bl in zip(solo, blocks):
+            h.push(*bl[step])
+        grp.push([bl[step][0] for bl in blocks], [bl[step][1] for bl in blocks])
+        for hs, hg in zip(solo, grouped):
+            np.testing.assert_array_equal(hs.read_binned_current(), hg.read_binned_current())
+            np.testing.assert_array_equal(hs.read_total_current(), hg.read_total_current())
+    grp.close()
