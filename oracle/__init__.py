@@ -5,7 +5,8 @@ may import this package.  The CUDA library never calls it and shares no code
 with it.  ``mhc_oracle.c`` holds the plain FP64 loops (Eqs. 10, 13, 16, 17,
 19 and frequency binning; the direction split of Sec. II.A; bin-bin cross-correlations; the SHC correlation and spectrum of Eqs. 20-23);
 ``brute.py`` restates the same definitions with per-atom 3-vectors in scalar
-Python for tiny systems.
+Python for tiny systems.  ``modal_current_mm`` below writes the projections of Eqs. 13
+and 16 as FP64 matrix products for full-size systems.
 
 This module compiles ``mhc_oracle.c`` with gcc on first use (or through
 ``build()``) and wraps it with ctypes and numpy.
@@ -116,6 +117,75 @@ def modal_current(E: np.ndarray, mass, v, W, bin_of_mode, B: int,
     if want_modes:
         out["xdot"] = xd
         out["Jn"] = Jn
+    return out
+
+
+def modal_current_mm(E: np.ndarray, mass, v, W, bin_of_mode, B: int, parts: bool = False,
+                     direction: bool = False, steps_per_product: int = 256):
+    """The outputs of modal_current (Eqs. 10, 13, 16 and the frequency binning) for systems
+    too large for the loops of mhc_oracle.c, with each group of steps' projections written as
+    FP64 matrix products (numpy's matmul serves as the projection step; nothing is blocked,
+    fused or reordered beyond the definitions):
+
+      Eq. 13       X[t][n]    = sum_d (sqrt(m_i) v_i^b(t))[d] E[d, n]          (d = 3i + b)
+      Eq. 16       Y^a[t][n]  = sum_d (W_i^{ab}(t) / sqrt(m_i))[d] E[d, n]
+                   J_n^a(t)   = X[t][n] Y^a[t][n]
+      binning      J_b^a(t)   = sum_{n: bin(n) = b} J_n^a(t)   (product with a 0/1 indicator)
+      Eq. 10       J^a(t)     = sum_i sum_b W_i^{ab}(t) v_i^b(t)
+
+    With direction=True the bracket keeps the direction b of the motion (Sec. II.A split):
+    Y^{ab}[t][n] = sum_i W_i^{ab}(t) e^b_{i,n} / sqrt(m_i) and J_n^{ab} = X Y^{ab}; the binned
+    output is then [T][3 (b)][B][3 (a)] as for modal_current_dir.
+
+    E is dof-major [3N][M] (float64); v [T][N][3], W [T][N][9] float32.  Returns dict with Jb,
+    J and, with parts=True, the factors of Eq. 16: xdot [T][M] and y [T][M][3] (direction:
+    [T][M][3 (b)][3 (a)]).  Called on the absolute values of E, v and W it gives the sums of
+    the absolute values of the terms of Eq. 13 and of the Eq. 16 bracket."""
+    E = np.asarray(E, dtype=np.float64)
+    D, M = E.shape
+    mass = np.asarray(mass, dtype=np.float64)
+    N = mass.shape[0]
+    if D != 3 * N:
+        raise ValueError("E must have 3N rows")
+    v = np.asarray(v, dtype=np.float32).reshape(-1, N, 3)
+    W = np.asarray(W, dtype=np.float32).reshape(-1, N, 3, 3)
+    T = v.shape[0]
+    bins = np.asarray(bin_of_mode, dtype=np.int64)
+    ind = np.zeros((M, B))
+    kept = (bins >= 0) & (bins < B)
+    ind[np.nonzero(kept)[0], bins[kept]] = 1.0
+    sqm = np.sqrt(mass)
+    J = np.empty((T, 3))
+    Jb = np.empty((T, 3, B, 3)) if direction else np.empty((T, B, 3))
+    xs = np.empty((T, M)) if parts else None
+    ys = (np.empty((T, M, 3, 3)) if direction else np.empty((T, M, 3))) if parts else None
+    for t0 in range(0, T, steps_per_product):
+        t1 = min(T, t0 + steps_per_product)
+        vt = v[t0:t1].astype(np.float64)                       # [S][N][3]
+        Wt = W[t0:t1].astype(np.float64)                       # [S][N][3 (a)][3 (b)]
+        S = t1 - t0
+        X = (vt * sqm[None, :, None]).reshape(S, D) @ E          # Eq. 13
+        U = Wt / sqm[None, :, None, None]                       # W_i^{ab} / sqrt(m_i)
+        J[t0:t1] = np.einsum("siab,sib->sa", Wt, vt)            # Eq. 10
+        if direction:
+            Y = np.empty((S, M, 3, 3))
+            for b in range(3):
+                Eb = E[b::3]                                    # rows d = 3i + b
+                for a in range(3):
+                    Y[:, :, b, a] = U[:, :, a, b] @ Eb
+            Jn = X[:, :, None, None] * Y                        # [S][M][b][a]
+            Jb[t0:t1] = (Jn.transpose(0, 2, 3, 1) @ ind).transpose(0, 1, 3, 2)
+        else:
+            Y = np.stack([U[:, :, a, :].reshape(S, D) @ E for a in range(3)], axis=-1)
+            Jn = X[:, :, None] * Y                              # Eq. 16, [S][M][3]
+            Jb[t0:t1] = (Jn.transpose(0, 2, 1) @ ind).transpose(0, 2, 1)
+        if parts:
+            xs[t0:t1] = X
+            ys[t0:t1] = Y
+    out = {"Jb": Jb, "J": J}
+    if parts:
+        out["xdot"] = xs
+        out["y"] = ys
     return out
 
 
