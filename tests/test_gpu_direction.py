@@ -10,8 +10,8 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.parity import REL_TOL, series_rel_err, spectrum_rel_err
-from tests.test_gpu_parity import TOL, make_case, need_gpu, report, run_gpu
+from tests.parity import REL_TOL, ModalRef, check
+from tests.test_gpu_parity import TOL, make_case, need_gpu, oracle_ref, run_gpu
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -20,7 +20,7 @@ PRECISIONS = ["fp32", "bf16x3", "fp16x3"]
 
 
 def oracle_dir(c):
-    return oracle.modal_current_dir(c["E"], c["mass"], c["v"], c["W"], c["bins"], c["B"])
+    return oracle_ref(c, direction=True)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
@@ -35,10 +35,8 @@ def test_direction_split_ragged(precision):
     o = oracle_dir(c)
     h, Jb, J = run_gpu(c, precision, K=23, direction=True)
     assert Jb.shape == (46, 3, 5, 3)
-    np.testing.assert_allclose(J, o["Jd"].sum(axis=1), rtol=1e-12, atol=1e-12)
-    err = series_rel_err(Jb, o["Jbd"])
-    report(f"direction ragged {precision}", err)
-    assert np.all(err <= TOL[precision])
+    np.testing.assert_allclose(J, o.J, rtol=1e-12, atol=1e-12)
+    o.check_current(Jb, TOL[precision], f"direction ragged {precision}")
     h.close()
 
 
@@ -54,13 +52,10 @@ def test_direction_split_multi_segment(tile_config):
     c = make_case(N=300, M=900, T=300, B=8, seed=202)
     o = oracle_dir(c)
     h, Jb, J = run_gpu(c, "fp16x3", K=150, tile_config=tile_config, direction=True)
-    err = series_rel_err(Jb, o["Jbd"])
-    report(f"direction multi-segment cfg{tile_config}", err)
-    assert np.all(err <= REL_TOL)
+    o.check_current(Jb, REL_TOL, f"direction multi-segment cfg{tile_config}")
     # completeness per direction (all 3N modes): the bins of direction b add up to
-    # J^{ab} = sum_i W_i^{ab} v_i^b
-    errc = series_rel_err(Jb.sum(axis=2), o["Jd"])
-    assert np.all(errc <= REL_TOL)
+    # J^{ab} = sum_i W_i^{ab} v_i^b, within the sum of the bins' bounds
+    check(Jb.sum(axis=2), o.Jd, o.S.sum(axis=2), True, REL_TOL, "completeness per direction")
     info = h.info()
     if tile_config:
         assert (info["tile_n"], info["tile_pair"]) == TILES[tile_config]
@@ -82,9 +77,11 @@ def test_direction_split_adds_up_to_the_plain_path(precision):
     c = make_case(N=96, M=288, T=48, B=6, seed=204)
     _, Jd, _ = run_gpu(c, precision, K=48, direction=True)
     _, Jp, _ = run_gpu(c, precision, K=48)
-    err = series_rel_err(Jd.sum(axis=1), Jp)
-    report(f"direction sum vs plain {precision}", err)
-    assert np.all(err <= 2 * TOL[precision])
+    o = oracle_dir(c)
+    o.check_current(Jd, TOL[precision], f"direction split {precision}")
+    # the split summed over b against the plain path: each within its bound of the oracle
+    check(Jd.sum(axis=1), Jp, 2 * o.S.sum(axis=1), True, TOL[precision],
+          f"direction sum vs plain {precision}")
 
 
 def test_direction_split_gkma_hnema_and_state():
@@ -95,21 +92,15 @@ def test_direction_split_gkma_hnema_and_state():
     dt, TK, V = 0.01, 300.0, 64 * 20.02
     kw_ = dict(dt_ps=dt, T_K=TK, V_A3=V, direction=True)
     h, Jb, J = run_gpu(c, "fp16x3", K=K, L=L, **kw_)
-    Jrows = o["Jbd"].reshape(T, 3 * B, 3)          # row b * B + bin
-    C0, cnt0 = oracle.gkma_corr(Jrows, o["Jd"].sum(axis=1), L)
     C, cnt = h.read_corr()
     assert C.shape == (3, B, 3, 3, L)
+    _, cnt0 = o.check_corr(C, L, REL_TOL, "direction corr")
     np.testing.assert_array_equal(cnt, cnt0)
-    errC = series_rel_err(C.reshape(-1, L).T, C0.reshape(-1, L).T)
-    report("direction corr", errC)
-    assert np.all(errC <= REL_TOL)
     kt, kw = h.read_kappa_gk(0.05, 0.11)
-    okw, _ = oracle.kappa_window(oracle.gk_kappa(C0, cnt0, dt, TK, V), dt, 0.05, 0.11)
-    assert np.all(spectrum_rel_err(kw.reshape(3 * B, 9), okw.reshape(3 * B, 9)) <= REL_TOL)
+    o.check_kappa(kt, kw, L, dt, TK, V, 0.05, 0.11, REL_TOL, "direction kappa")
     mean, kap = h.read_hnema()
-    omean, okap = oracle.hnema(Jrows, TK, V, [1e-5, 0, 0])
     assert mean.shape == (3, B, 3)
-    assert np.all(spectrum_rel_err(kap.reshape(3 * B, 3), okap) <= REL_TOL)
+    o.check_hnema(mean, kap, TK, V, [1e-5, 0, 0], REL_TOL, "direction HNEMA")
 
     # resume from a state blob: bitwise the uninterrupted run
     from paper_2102_03691_gb300.mhc import ModalHeatCurrent
@@ -164,10 +155,9 @@ def test_direction_split_several_tiles_per_cta(case_n2000, tile_config):
     c = case_n2000
     h, Jb, J = run_gpu(c, "fp16x3", K=256, tile_config=tile_config, direction=True)
     steps = [0, 101, 255]
-    o = oracle.modal_current_dir(c["E"], c["mass"], c["v"][steps], c["W"][steps], c["bins"], c["B"])
-    err = series_rel_err(Jb[steps], o["Jbd"])
-    report(f"direction N=2000 cfg{tile_config}", err)
-    assert np.all(err <= REL_TOL)
+    o = ModalRef(c["E"], c["mass"], c["v"][steps], c["W"][steps], c["bins"], c["B"],
+                 direction=True)
+    o.check_current(Jb[steps], REL_TOL, f"direction N=2000 cfg{tile_config}")
     h.close()
     _, Jb3, _ = run_gpu(c, "fp16x3", K=256, tile_config=3, direction=True)
     np.testing.assert_array_equal(Jb, Jb3)

@@ -6,8 +6,8 @@ import pytest
 
 import oracle
 from paper_2102_03691_gb300 import synth
-from tests.parity import REL_TOL, series_rel_err
-from tests.test_gpu_parity import TOL, make_case, need_gpu, run_gpu
+from tests.parity import REL_TOL, ModalRef, check, stage_corr_check
+from tests.test_gpu_parity import TOL, make_case, need_gpu, oracle_ref, run_gpu
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -19,14 +19,13 @@ def test_one_atom_one_step_pushes(precision):
     # its ~16-bit operand pairs give errors that only average down over many atoms.)
     need_gpu()
     c = make_case(N=1, M=3, T=5, B=2, seed=901)
-    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], 2)
-    C0, _ = oracle.gkma_corr(o["Jb"], o["J"], 3)
+    o = oracle_ref(c)
     h, Jb, J = run_gpu(c, precision, K=1, L=3)
-    np.testing.assert_allclose(J, o["J"], rtol=1e-12, atol=1e-12)
-    assert np.all(series_rel_err(Jb, o["Jb"]) <= TOL[precision])
+    np.testing.assert_allclose(J, o.J, rtol=1e-12, atol=1e-12)
+    o.check_current(Jb, TOL[precision], f"one atom {precision}")
     C, cnt = h.read_corr()
     np.testing.assert_array_equal(cnt, [5, 4, 3])
-    assert np.all(series_rel_err(C.reshape(-1, 3).T, C0.reshape(-1, 3).T) <= TOL[precision])
+    o.check_corr(C, 3, TOL[precision], f"one atom corr {precision}")
     h.close()
 
 
@@ -53,33 +52,33 @@ def test_every_mode_excluded_gives_zeros():
 def test_single_bin_single_lag_and_lags_beyond_the_run(precision):
     need_gpu()
     c = make_case(N=30, M=90, T=12, B=1, seed=903)
-    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], 1)
+    o = oracle_ref(c)
     # one lag
     h, Jb, _ = run_gpu(c, precision, K=5, L=1)
+    o.check_current(Jb, TOL[precision], f"single bin {precision}")
     C, cnt = h.read_corr()
-    C0, cnt0 = oracle.gkma_corr(o["Jb"], o["J"], 1)
+    _, cnt0 = o.check_corr(C, 1, TOL[precision], f"one lag {precision}")
     np.testing.assert_array_equal(cnt, cnt0)
-    assert np.all(np.abs(C - C0) <= TOL[precision] * np.abs(C0).max())
     h.close()
     # 20 lags over 12 steps: lags 12..19 have no origins and stay zero
     h, Jb, _ = run_gpu(c, precision, K=5, L=20)
     C, cnt = h.read_corr()
-    C0, cnt0 = oracle.gkma_corr(o["Jb"], o["J"], 20)
+    _, cnt0 = o.check_corr(C, 20, TOL[precision], f"lags beyond the run {precision}")
     np.testing.assert_array_equal(cnt, cnt0)
     assert np.all(C[..., 12:] == 0) and np.all(cnt[12:] == 0)
-    assert np.all(series_rel_err(C[..., :12].reshape(-1, 12).T, C0[..., :12].reshape(-1, 12).T)
-                  <= TOL[precision])
     kt, kw = h.read_kappa_gk(0.0, 0.19)
     assert np.all(np.isfinite(kt)) and np.all(np.isfinite(kw))
+    o.check_kappa(kt, None, 20, 0.01, 300.0, 1.0, 0.0, 0.19, TOL[precision],
+                  f"kappa beyond the run {precision}")
     h.close()
 
 
 def test_direction_split_one_atom():
     need_gpu()
     c = make_case(N=1, M=3, T=4, B=1, seed=904)
-    od = oracle.modal_current_dir(c["E"], c["mass"], c["v"], c["W"], c["bins"], 1)
+    od = oracle_ref(c, direction=True)
     h, Jb, _ = run_gpu(c, "fp16x3", K=2, direction=True)
-    assert np.all(series_rel_err(Jb, od["Jbd"]) <= REL_TOL)
+    od.check_current(Jb, REL_TOL, "direction split, one atom")
     h.close()
 
 
@@ -98,7 +97,8 @@ def test_shc_one_atom_and_lags_beyond_the_run(precision):
     Ko, cnto = oracle.shc_corr(v, W, 10)
     np.testing.assert_array_equal(cnt, cnto)
     assert np.all(K[:, 6:] == 0)
-    assert np.all(series_rel_err(K[:, :6].T, Ko[:, :6].T) <= REL_TOL)
+    check(K, Ko, oracle.shc_corr(np.abs(v), np.abs(W), 10)[0], True, REL_TOL,
+          f"SHC one atom {precision}")
     s.close()
 
 
@@ -109,10 +109,10 @@ def test_pack_paths_large_system(N):
     need_gpu()
     from tests.test_gpu_parity import make_case
     c = make_case(N=N, M=300, T=8, B=4, seed=906)
-    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], 4)
+    o = oracle_ref(c)
     h, Jb, J = run_gpu(c, "fp16x3", K=8, L=3)
-    np.testing.assert_allclose(J, o["J"], rtol=1e-12, atol=1e-9 * np.abs(o["J"]).max())
-    assert np.all(series_rel_err(Jb, o["Jb"]) <= REL_TOL)
+    np.testing.assert_allclose(J, o.J, rtol=1e-12, atol=1e-9 * np.abs(o.J).max())
+    o.check_current(Jb, REL_TOL, f"pack path N={N}")
     h.close()
 
 
@@ -125,17 +125,13 @@ def test_largest_block_with_lag_correlation(direction):
     L, K, T, B = 70, 1024, 2200, 7
     c = make_case(N=40, M=120, T=T, B=B, seed=905, drive=2e-3)
     h, Jb, J = run_gpu(c, "fp16x3", K=K, L=L, direction=direction)
-    if direction:
-        od = oracle.modal_current_dir(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
-        rows, Jt = od["Jbd"].reshape(T, 3 * B, 3), od["Jd"].sum(axis=1)
-    else:
-        o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
-        rows, Jt = o["Jb"], o["J"]
-    C0, cnt0 = oracle.gkma_corr(rows, Jt, L)
+    o = oracle_ref(c, direction=direction)
+    o.check_current(Jb, REL_TOL, f"K=1024 currents direction={direction}")
     C, cnt = h.read_corr()
+    _, cnt0 = o.check_corr(C, L, REL_TOL, f"K=1024 Eq. 17 sums direction={direction}")
     np.testing.assert_array_equal(cnt, cnt0)
-    err = series_rel_err(C.reshape(-1, L).T, C0.reshape(-1, L).T)
-    assert np.all(err <= REL_TOL)
+    # the lag stage alone, fed with the library's own binned currents
+    stage_corr_check(C, o.rows(Jb), J, L, REL_TOL, "K=1024 lag stage")
     h.close()
 
 
@@ -144,18 +140,17 @@ def test_green_kubo_read_out_beyond_1024_lags():
     # instead of keeping it in registers); 1300 steps in ragged blocks of 256; kappa(tau) at
     # every lag and the window average against the oracle
     need_gpu()
-    from tests.parity import spectrum_rel_err
     L, K, T, B = 1100, 256, 1300, 3
     dt, TK, V = 0.01, 300.0, 16 * 20.02
     c = make_case(N=16, M=48, T=T, B=B, seed=906, drive=2e-3)
-    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
-    C0, cnt0 = oracle.gkma_corr(o["Jb"], o["J"], L)
+    o = oracle_ref(c)
     h, Jb, J = run_gpu(c, "fp16x3", K=K, L=L, dt_ps=dt, T_K=TK, V_A3=V)
     kt, kw = h.read_kappa_gk(8.0, 10.5)
-    okt = oracle.gk_kappa(C0, cnt0, dt, TK, V)
-    okw, n = oracle.kappa_window(okt, dt, 8.0, 10.5)
+    _, n = o.check_kappa(kt, kw, L, dt, TK, V, 8.0, 10.5, REL_TOL, "1100 lags kappa")
     assert n == 251
-    errT = series_rel_err(kt.reshape(-1, L).T, okt.reshape(-1, L).T)
-    assert np.all(errT <= REL_TOL)
-    assert np.all(spectrum_rel_err(kw.reshape(B, 9), okw.reshape(B, 9)) <= REL_TOL)
+    # the Green-Kubo stage alone: the oracle's integral of the library's own Eq. 17 sums
+    C, cnt = h.read_corr()
+    okt = oracle.gk_kappa(C, cnt, dt, TK, V)
+    skt = oracle.gk_kappa(np.abs(C), cnt, dt, TK, V)
+    check(kt, okt, skt, True, 1e-12, "1100 lags Green-Kubo stage")
     h.close()

@@ -1,6 +1,6 @@
 """Failure detection on the GPU without a fault: every barrier wait of the tensor-core
-kernels is bounded.  MHC_FLAG_TEST_STALL arms the first stage barrier 16 bytes short of
-what its copies deliver, so the wait runs out (0.1 s), the kernel writes the sticky
+kernels is bounded.  MHC_FLAG_TEST_STALL arms the first stage barrier to expect 16 bytes
+more than its copies deliver, so the wait runs out (0.1 s), the kernel writes the sticky
 status word and returns; the host reports MHC_ERR_TIMEOUT, and after mhc_reset the same
 handle computes correct results again (the context stays usable)."""
 import numpy as np
@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2102_03691_gb300 import synth
-from tests.parity import REL_TOL, series_rel_err
+from tests.parity import REL_TOL, ModalRef
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -36,6 +36,6 @@ def test_bounded_wait_times_out_and_context_survives(tile_config):
     h.reset()                              # clears the sticky status
     h.push(torch.from_numpy(v).cuda(), torch.from_numpy(W).cuda())
     Jb = h.read_binned_current()
-    o = oracle.modal_current(E, mass, v, W, oracle.bins_uniform(f, 0.0, 16.0, B), B)
-    assert np.all(series_rel_err(Jb, o["Jb"]) <= REL_TOL)
+    o = ModalRef(E, mass, v, W, oracle.bins_uniform(f, 0.0, 16.0, B), B)
+    o.check_current(Jb, REL_TOL, f"after the timeout, tile {tile_config}")
     h.close()

@@ -6,7 +6,8 @@ import pytest
 
 import oracle
 from paper_2102_03691_gb300 import synth
-from tests.parity import REL_TOL, series_rel_err
+from tests.parity import ModalRef
+from tests.test_gpu_parity import TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -54,25 +55,22 @@ def test_group_equals_individual_pushes_and_oracle(precision):
             np.testing.assert_array_equal(hs.read_binned_current(), hg.read_binned_current())
             np.testing.assert_array_equal(hs.read_total_current(), hg.read_total_current())
     grp.close()
-    if precision != "fp16x3":
-        return   # BF16x3 is not held to the 1e-5 bar; bins of ~5 modes make it ill-conditioned
-    tol = REL_TOL
+    tol = TOL[precision]
     for s, bl, hg in zip(systems, blocks, grouped):
         Cg, _ = hg.read_corr()
         v = np.concatenate([b[0] for b in bl])
         W = np.concatenate([b[1] for b in bl])
         bins = oracle.bins_uniform(s["f"], 0.0, 52.0, B)
-        o = oracle.modal_current(s["E"], s["mass"], v, W, bins, B)
-        Co, _ = oracle.gkma_corr(o["Jb"], o["J"], L)
-        hg_last = hg.read_binned_current()
-        assert np.all(series_rel_err(hg_last, o["Jb"][K:]) <= tol)
-        assert np.all(series_rel_err(Cg.reshape(-1, L).T, Co.reshape(-1, L).T) <= tol)
+        o = ModalRef(s["E"], s["mass"], v, W, bins, B)
+        o.check_current(hg.read_binned_current(), tol, f"group N={s['N']} {precision}",
+                        steps=slice(K, 2 * K))
+        o.check_corr(Cg, L, tol, f"group N={s['N']} corr {precision}")
 
 
-def test_cnt_batch_16_systems_full_size_sampled():
+def test_cnt_batch_16_systems_full_size():
     # The uneven CNT (10,10) batch: 16 systems, N = 40 u with u in [12, 100], all 3N modes,
-    # 52 bins of 1 THz.  One grouped block of K = 64 steps; the oracle recomputes two
-    # sampled steps of every system (all modes) from the same inputs.
+    # 52 bins of 1 THz.  One grouped block of K = 64 steps; the oracle recomputes every step
+    # of every system (all modes) from the same inputs.
     need_gpu()
     from paper_2102_03691_gb300.mhc import ModalHeatCurrentGroup
     sizes = synth.cnt_group_sizes()
@@ -90,18 +88,12 @@ def test_cnt_batch_16_systems_full_size_sampled():
         blocks.append(s["tr"].next_block(K))
     grp = ModalHeatCurrentGroup(handles)
     grp.push([b[0] for b in blocks], [b[1] for b in blocks])
-    samples = [0, K - 1]
     for s, h, (v, W) in zip(systems, handles, blocks):
         Jb = h.read_binned_current()
         bins = oracle.bins_uniform(s["f"], 0.0, 52.0, B)
-        o = oracle.modal_current(s["E"], s["mass"], v[samples], W[samples], bins, B)
-        # every step of the block in one relative series per bin: the sampled steps'
-        # errors are measured against the bin's scale over the whole block
-        scale = np.abs(Jb).max(axis=0)
-        err = np.abs(Jb[samples] - o["Jb"]).max(axis=0) / np.where(scale > 0, scale, 1.0)
-        assert np.all(err <= REL_TOL), (s["N"], float(err.max()))
-        empty = np.abs(o["Jb"]).max(axis=0) == 0
-        assert np.all(Jb[:, empty] == 0)
+        # the whole block of every system: the projections as FP64 matrix products
+        o = ModalRef(s["E"], s["mass"], v, W, bins, B, mm=True)
+        o.check_current(Jb, TOL["fp16x3"], f"CNT batch N={s['N']}")
     grp.close()
 
 

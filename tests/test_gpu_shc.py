@@ -4,7 +4,8 @@ import pytest
 
 import oracle
 from paper_2102_03691_gb300 import synth
-from tests.parity import REL_TOL, series_rel_err, spectrum_rel_err
+from tests.parity import REL_TOL, check_shc_corr, spectrum_rel_err
+from tests.test_gpu_parity import TOL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -13,10 +14,6 @@ pytestmark = pytest.mark.gpu
 def need_gpu():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-
-
-# BF16x3 keeps ~16 significand bits per operand pair (see test_gpu_parity.py)
-TOL = {"fp32": REL_TOL, "fp16x3": REL_TOL, "bf16x3": 6e-5}
 
 
 def run(N, T, nc, K, seed, device_inputs=True, drive=0.0, precision="fp16x3", blocks=None):
@@ -40,9 +37,8 @@ def test_shc_corr_and_kappa_match_oracle(N, T, nc, K):
     need_gpu()
     s, v, W = run(N, T, nc, K, seed=600 + N, drive=1e-3)
     Kg, cnt = s.read_corr()
-    Ko, cnto = oracle.shc_corr(v, W, nc)
+    _, Ko, cnto = check_shc_corr(Kg, v, W, nc, REL_TOL, f"SHC N={N}")
     np.testing.assert_array_equal(cnt, cnto)
-    assert np.all(series_rel_err(Kg.T, Ko.T) <= REL_TOL)
     f = np.linspace(0.0, 60.0, 97)
     for window in (0, 1):
         kg = s.read_kappa(f, window)
@@ -60,11 +56,8 @@ def test_shc_precisions_ragged_blocks(precision):
     starts = [0, 37, 137, 142, 270]
     s, v, W = run(150, 300, 140, 128, seed=620, drive=1e-3, precision=precision, blocks=starts)
     Kg, cnt = s.read_corr()
-    Ko, cnto = oracle.shc_corr(v, W, 140)
+    _, Ko, cnto = check_shc_corr(Kg, v, W, 140, TOL[precision], f"SHC ragged {precision}")
     np.testing.assert_array_equal(cnt, cnto)
-    err = series_rel_err(Kg.T, Ko.T)
-    print(f"shc {precision}: max {err.max():.3e}")
-    assert np.all(err <= TOL[precision])
     s.close()
 
 
@@ -76,10 +69,7 @@ def test_shc_large_systems_pack_paths(N):
     need_gpu()
     s, v, W = run(N, 24, 8, 12, seed=640 + N % 7)
     Kg, cnt = s.read_corr()
-    Ko, _ = oracle.shc_corr(v, W, 8)
-    err = series_rel_err(Kg.T, Ko.T)
-    print(f"shc N={N}: max {err.max():.3e}")
-    assert np.all(err <= REL_TOL)
+    check_shc_corr(Kg, v, W, 8, REL_TOL, f"SHC N={N}")
     s.close()
 
 
@@ -122,8 +112,7 @@ def test_shc_si_n8000_full_size():
     N, nc, K, T = 8000, 250, 256, 512
     s, v, W = run(N, T, nc, K, seed=20210211)
     Kg, cnt = s.read_corr()
-    Ko, cnto = oracle.shc_corr(v, W, nc)
-    assert np.all(series_rel_err(Kg.T, Ko.T) <= REL_TOL)
+    check_shc_corr(Kg, v, W, nc, REL_TOL, "SHC Si-8000")
     s.close()
 
 

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_2102_03691_gb300 import synth
-from tests.parity import series_rel_err
+from tests.parity import ModalRef
 from tests.test_gpu_parity import TOL, need_gpu
 
 torch = pytest.importorskip("torch")
@@ -56,29 +56,16 @@ def test_random_shapes_and_options(i):
         J.append(h.read_total_current().copy())
     Jb, J = np.concatenate(Jb), np.concatenate(J)
     tol = TOL[d["precision"]]
-    o = oracle.modal_current(E, mass, v, W, bins, B)
-    np.testing.assert_allclose(J, o["J"], rtol=1e-12, atol=1e-9 * max(1.0, np.abs(o["J"]).max()))
-    if d["direction"]:
-        rows = oracle.modal_current_dir(E, mass, v, W, bins, B)["Jbd"]
-        assert np.all(series_rel_err(Jb, rows) <= tol), d
-        rows = rows.reshape(T, 3 * B, 3)
-        Jb = Jb.reshape(T, 3 * B, 3)
-    else:
-        rows = o["Jb"]
-        assert np.all(series_rel_err(Jb, rows) <= tol), d
+    print(d)
+    o = ModalRef(E, mass, v, W, bins, B, direction=d["direction"])
+    np.testing.assert_allclose(J, o.J, rtol=1e-12, atol=1e-9 * max(1.0, np.abs(o.J).max()))
+    o.check_current(Jb, tol, f"sweep {i} currents")
     C, cnt = h.read_corr()
-    C0, cnt0 = oracle.gkma_corr(rows, o["J"], L)
+    _, cnt0 = o.check_corr(C, L, tol, f"sweep {i} Eq. 17 sums")
     np.testing.assert_array_equal(cnt, cnt0)
-    nrow = rows.shape[1]
-    assert np.all(series_rel_err(C.reshape(-1, L).T, C0.reshape(-1, L).T) <= tol), d
     mean, _ = h.read_hnema()
-    m0 = rows.mean(axis=0)
-    # a time average inherits each step's error bound: scale by the bin's largest |J_b(t)|
-    scale = np.abs(rows).max(axis=0)
-    err = np.abs(mean.reshape(nrow, 3) - m0)
-    assert np.all(np.where(scale > 0, err <= tol * scale, err == 0)), d
+    o.check_hnema(mean, None, 300.0, 1.0, [1e-5, 0.0, 0.0], tol, f"sweep {i} HNEMA")
     if d["xcorr"]:
         X, _ = h.read_xcorr()
-        X0 = oracle.gkma_xcorr(rows, L)
-        assert np.all(series_rel_err(X.reshape(-1, L).T, X0.reshape(-1, L).T) <= tol), d
+        o.check_xcorr(X, L, tol, f"sweep {i} bin-bin sums")
     h.close()

@@ -5,8 +5,8 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.parity import REL_TOL, series_rel_err, spectrum_rel_err
-from tests.test_gpu_parity import TOL, make_case, need_gpu, report, run_gpu
+from tests.parity import REL_TOL, check
+from tests.test_gpu_parity import TOL, make_case, need_gpu, oracle_ref, run_gpu
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -18,19 +18,18 @@ def test_xcorr_small_ragged_blocks(precision):
     need_gpu()
     L, K, T, B = 12, 16, 70, 6
     c = make_case(N=48, M=144, T=T, B=B, seed=801, drive=2e-3)
-    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
-    Xo = oracle.gkma_xcorr(o["Jb"], L)
+    o = oracle_ref(c)
     h, Jb, J = run_gpu(c, precision, K=K, L=L, xcorr=True)
     X, cnt = h.read_xcorr()
     assert X.shape == (B, B, 3, 3, L)
     np.testing.assert_array_equal(cnt, np.maximum(T - np.arange(L), 0))
-    err = series_rel_err(X.reshape(-1, L).T, Xo.reshape(-1, L).T)
-    report(f"xcorr {precision}", err)
-    assert np.all(err <= TOL[precision])
+    o.check_xcorr(X, L, TOL[precision], f"xcorr {precision}")
     # every mode binned: the second bin summed out gives the Eq. 17 sums of the same run
+    # (each side within its bound of the oracle)
     C, _ = h.read_corr()
-    errs = series_rel_err(X.sum(axis=1).reshape(-1, L).T, C.reshape(-1, L).T)
-    assert np.all(errs <= TOL[precision])
+    _, _, SC = o.corr(L)
+    _, SX = o.xcorr(L)
+    check(X.sum(axis=1), C, SX.sum(axis=1) + SC, True, TOL[precision], "xcorr sum rule")
     h.close()
 
 
@@ -40,8 +39,8 @@ def test_xcorr_kappa_and_state_roundtrip():
     L, K, T, B = 10, 8, 48, 4
     dt, TK, V = 0.01, 300.0, 32 * 20.02
     c = make_case(N=32, M=96, T=T, B=B, seed=802, drive=2e-3)
-    o = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
-    Xo = oracle.gkma_xcorr(o["Jb"], L)
+    o = oracle_ref(c)
+    Xo, SX = o.xcorr(L)
     cnt = np.maximum(T - np.arange(L), 0).astype(np.int64)
 
     def fresh():
@@ -54,12 +53,13 @@ def test_xcorr_kappa_and_state_roundtrip():
     for t0 in range(0, T, K):
         a.push(c["v"][t0:t0 + K], c["W"][t0:t0 + K])
     kt, kw = a.read_kappa_xcorr(0.03, 0.09)
-    okw, n = oracle.kappa_window(oracle.gk_kappa(Xo.reshape(B * B, 3, 3, L), cnt, dt, TK, V),
-                                 dt, 0.03, 0.09)
+    okt = oracle.gk_kappa(Xo.reshape(B * B, 3, 3, L), cnt, dt, TK, V)
+    skt = oracle.gk_kappa(SX.reshape(B * B, 3, 3, L), cnt, dt, TK, V)
+    okw, n = oracle.kappa_window(okt, dt, 0.03, 0.09)
+    skw, _ = oracle.kappa_window(skt, dt, 0.03, 0.09)
     assert n == 7
-    errK = spectrum_rel_err(kw.reshape(B * B, 9), okw.reshape(B * B, 9))
-    report("kappa_xcorr", errK)
-    assert np.all(errK <= REL_TOL)
+    check(kt.reshape(okt.shape), okt, skt, True, REL_TOL, "kappa_xcorr(tau)")
+    check(kw.reshape(okw.shape), okw, skw, True, REL_TOL, "kappa_xcorr window")
     Xa, _ = a.read_xcorr()
     b = fresh()
     for t0 in range(0, 24, K):
@@ -79,14 +79,11 @@ def test_xcorr_with_direction_split():
     need_gpu()
     L, K, T, B = 6, 16, 40, 3
     c = make_case(N=40, M=120, T=T, B=B, seed=803)
-    od = oracle.modal_current_dir(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
-    Xo = oracle.gkma_xcorr(od["Jbd"].reshape(T, 3 * B, 3), L)
+    od = oracle_ref(c, direction=True)
     h, Jb, J = run_gpu(c, "fp16x3", K=K, L=L, xcorr=True, direction=True)
     X, _ = h.read_xcorr()
     assert X.shape == (3, B, 3, B, 3, 3, L)
-    err = series_rel_err(X.reshape(-1, L).T, Xo.reshape(-1, L).T)
-    report("xcorr direction", err)
-    assert np.all(err <= REL_TOL)
+    od.check_xcorr(X, L, REL_TOL, "xcorr direction")
     h.close()
 
 
@@ -130,17 +127,14 @@ def test_xcorr_several_row_and_column_tiles(B, direction):
     need_gpu()
     L, K, T = 20, 64, 150
     c = make_case(N=100, M=300, T=T, B=B, seed=804, drive=2e-3)
-    if direction:
-        od = oracle.modal_current_dir(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)
-        rows = od["Jbd"].reshape(T, 3 * B, 3)
-    else:
-        rows = oracle.modal_current(c["E"], c["mass"], c["v"], c["W"], c["bins"], B)["Jb"]
-    Xo = oracle.gkma_xcorr(rows, L)
+    o = oracle_ref(c, direction=direction)
     h, Jb, J = run_gpu(c, "fp16x3", K=K, L=L, xcorr=True, direction=direction)
     X, cnt = h.read_xcorr()
     np.testing.assert_array_equal(cnt, np.maximum(T - np.arange(L), 0))
-    n = 3 * rows.shape[1]   # rows (bin row, component) of the contraction
-    err = series_rel_err(X.reshape(-1, L).T, Xo.reshape(-1, L).T)
-    report(f"xcorr {n} rows", err)
-    assert np.all(err <= REL_TOL)
+    n = 3 * o.rows(o.Jb).shape[1]   # rows (bin row, component) of the contraction
+    o.check_xcorr(X, L, REL_TOL, f"xcorr {n} rows")
+    # the tensor-core stage alone, fed with the library's own binned currents
+    rows = o.rows(Jb)
+    check(X.reshape(-1), oracle.gkma_xcorr(rows, L).reshape(-1),
+          oracle.gkma_xcorr(np.abs(rows), L).reshape(-1), True, REL_TOL, f"xcorr {n} rows stage")
     h.close()
