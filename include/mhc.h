@@ -77,8 +77,8 @@ typedef enum { MHC_DOF_MAJOR = 0, MHC_MODE_MAJOR = 1 } mhc_layout;
 #define MHC_FLAG_PROFILE 0x4       /* time each projection launch with CUDA events (mhc_kernel_time);
                                       implies direct launches */
 #define MHC_FLAG_TEST_STALL 0x8    /* fault injection for tests of the failure path: the tensor-core
-                                      kernel arms its first stage barrier 16 bytes short of what its
-                                      copies deliver, so its bounded waits (0.1 s with this flag)
+                                      kernel arms its first stage barrier to expect 16 bytes more
+                                      than its copies deliver, so its bounded waits (0.1 s with this flag)
                                       give up and the next sync/read returns MHC_ERR_TIMEOUT; no
                                       memory is touched out of bounds.  Implies direct launches. */
 #define MHC_FLAG_DIRECTION 0x10    /* direction-resolved split (Sec. II.A: the current along a is the
@@ -241,8 +241,6 @@ mhc_status mhc_read_corr(mhc_handle *h, double *corr_sum, int64_t *count, int32_
 mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, double tau_hi,
                              double *kappa_w, int32_t where);
 
-/* Last basis check of mhc_set_modes (FP64 on the GPU): max |E^T E - I|.
- * Returns WARN_NOT_ORTHONORMAL above tol, INVALID_ARG if no check was run. */
 /*
  * Bin-bin cross-correlation sums (MHC_FLAG_XCORR): xsum [R][R][3][3][L] float64 with
  * xsum[b][b'][mu][nu][l] = sum_{t=l}^{T_s-1} J_b^mu(t) J_{b'}^nu(t-l), R = B (3B with the
@@ -255,6 +253,14 @@ mhc_status mhc_read_xcorr(mhc_handle *h, double *xsum, int64_t *count, int32_t w
 mhc_status mhc_read_kappa_xcorr(mhc_handle *h, double *kappa_tau, double tau_lo, double tau_hi,
                                 double *kappa_w, int32_t where);
 
+/*
+ * Orthonormality of the loaded eigenvectors, the property that makes Eq. 14 the inverse of
+ * Eq. 13 (sum_n e_{i,n} e_{j,n} = delta_ij for the full basis, and e_n . e_m = delta_nm for
+ * the kept modes, Sec. II.B).  Reports the last basis check of mhc_set_modes (run in FP64 on
+ * the GPU when mhc_params.ortho_probe >= 0: over all mode pairs, or P probe modes against
+ * all): *max_abs_err = max |E^T E - I|.  Returns WARN_NOT_ORTHONORMAL above tol,
+ * INVALID_ARG if no check was run.
+ */
 mhc_status mhc_check_orthonormality(mhc_handle *h, double tol, double *max_abs_err);
 
 /* Counters and sizes. */
@@ -366,17 +372,19 @@ mhc_status mhc_shc_read_kappa(mhc_shc *s, const double *f_THz, int32_t n_freq, i
  *   mass_amu     device [N] float64, every m_i > 0
  *   v, W         device [K][N][3] and [K][N][9] float32 (layouts as for mhc_push)
  *   Jb           device output [K][B][3] float32 (binned modal current)
- *   J            device output [K][3] float64 (total current, Eq. 10)
+ *   J            device output [K][3] float64 (total heat current sum_i W_i v_i)
  *   stream       cudaStream_t or NULL
  * Every intermediate array lives in one static device buffer of
  * MHC_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until exit; no
  * call allocates.  The first call on a device looks up the buffer's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.  Calls share
  * the buffer and keep the last call's contents (what must start at zero is cleared each
- * call); calls whose work overlaps on the GPU race.  The call synchronises `stream`.
+ * call); calls whose work overlaps on the GPU race.  Every call synchronises `stream`
+ * twice: once after the bins and masses are checked on the device, once at the end.
  * Errors: INVALID_ARG for bad sizes or pointers, bins that are out of range or
- * decreasing, non-positive masses, or a problem whose intermediates exceed the buffer
- * (roughly 4 (M_pad + 4K) D_pad + 16 K M_pad bytes with M_pad = M rounded up to 128 and
+ * decreasing, non-positive masses (then nothing is computed and Jb, J are not written),
+ * or a problem whose intermediates exceed the buffer (roughly
+ * 4 (M_pad + 4K) D_pad + 16 K M_pad bytes with M_pad = M rounded up to 128 and
  * D_pad = 3N rounded up to 64); CUDA for runtime errors.
  */
 #define MHC_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)

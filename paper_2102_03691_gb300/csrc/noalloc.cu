@@ -50,7 +50,8 @@ cudaError_t scratch_address(int device, void **out) {
 // Identity mode order, per-mode bin/slot tables and per-atom mass weights.  One CTA;
 // bins must be in [0, B) and non-decreasing (modes already ordered by bin).  A slot is
 // the last mode of a run of equal bins inside a 32-mode group; slot_begin[b] is the
-// first slot of bin b.  A violated precondition sets *status.
+// first slot of bin b.  A violated precondition sets *status.  Every slot entry is reset
+// first, so that no entry left by an earlier call survives a call that stops early.
 __global__ void noalloc_tables_kernel(const int32_t *bin_of_mode, int M, int M_pad, int B,
                                       const double *mass, int N, int *perm, int *mode_bin,
                                       int *mode_slot, int *slot_begin, float *sqm, float *isqm,
@@ -58,7 +59,9 @@ __global__ void noalloc_tables_kernel(const int32_t *bin_of_mode, int M, int M_p
     for (int n = threadIdx.x; n < M_pad; n += blockDim.x) {
         if (n < M) perm[n] = n;
         mode_bin[n] = n < M ? bin_of_mode[n] : -1;
+        mode_slot[n] = -1;
     }
+    for (int b = threadIdx.x; b <= B; b += blockDim.x) slot_begin[b] = 0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const double m = mass[i];
         if (!(m > 0.0)) atomicCAS(status, 0, 1);
@@ -149,6 +152,14 @@ extern "C" mhc_status mhc_binned_current_noalloc(int32_t n_atoms, int32_t n_mode
                                             (int)N, perm, mode_bin, mode_slot, slot_begin,
                                             reinterpret_cast<float *>(s + o_sqm),
                                             reinterpret_cast<float *>(s + o_isqm), status);
+    // Bins and masses are checked on the device; nothing else runs (and no output is
+    // written) unless they passed.
+    int h_status = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return MHC_ERR_CUDA;
+    if (h_status) return MHC_ERR_INVALID_ARG;
     launch_prepare_modes(E, MHC_F32, MHC_MODE_MAJOR, ld, D, M, perm, 0, SPLIT_FP32, nullptr,
                          nullptr, Et32, D_ld, M_pad, 0, st);
     PackArgs a{};
@@ -170,7 +181,6 @@ extern "C" mhc_status mhc_binned_current_noalloc(int32_t n_atoms, int32_t n_mode
                              partials, (int)M_pad, st);
     launch_bin_finish(partials, (int)M_pad, slot_begin, n_bins, K, Jb, hsum, J, jsum, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return MHC_ERR_CUDA;
-    int h_status = 0;
     if ((e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return MHC_ERR_CUDA;
