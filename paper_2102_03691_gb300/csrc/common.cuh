@@ -212,28 +212,6 @@ __device__ __forceinline__ void umma_f16_pair(uint32_t d_tmem, uint64_t a_desc, 
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
-// 2D tiled load multicast to the CTAs of `mask` in this cluster: the tile lands at the same
-// shared-memory offset in each, and each CTA's mbarrier at the offset of `bar` counts the bytes.
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const void *tmap, uint64_t *bar, int x,
-                                               int y, uint16_t mask, uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        ".L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5, %6;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask),
-        "l"(policy)
-        : "memory");
-}
-
-// One-SM MMAs: arrive once on the barrier at this offset in every CTA of `mask` when all
-// tcgen05 ops issued so far by this thread have completed.
-__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
-
 // Arrive once on the barrier at this shared-memory offset in every CTA of `mask`
 // when all tcgen05 ops issued so far by this thread have completed.
 __device__ __forceinline__ void umma_commit_pair(uint64_t *bar, uint16_t mask) {

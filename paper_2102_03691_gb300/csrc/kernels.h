@@ -119,7 +119,7 @@ struct TcParams {
     const int *cta_begin;    // [grid+1] offsets into sched
     int n_prob;              // problems in use (prob[0..n_prob-1])
     long long wait_limit;    // SM cycles a barrier wait may take before the CTA gives up
-    int stall_inject;        // test hook: arm the first stage barrier 16 bytes short of done
+    int stall_inject;        // test hook: arm the first stage barrier for 16 bytes more than its copies deliver
     int *status;
     uint32_t idesc;
     int dir_park_ctas;       // CTAs the direction-split scratch has room for
