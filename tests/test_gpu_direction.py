@@ -55,7 +55,8 @@ def test_direction_split_multi_segment(tile_config):
     o.check_current(Jb, REL_TOL, f"direction multi-segment cfg{tile_config}")
     # completeness per direction (all 3N modes): the bins of direction b add up to
     # J^{ab} = sum_i W_i^{ab} v_i^b, within the sum of the bins' bounds
-    check(Jb.sum(axis=2), o.Jd, o.S.sum(axis=2), True, REL_TOL, "completeness per direction")
+    check(Jb.sum(axis=2), o.Jd, o.S.sum(axis=2), o.Sd.sum(axis=2), REL_TOL,
+          "completeness per direction")
     info = h.info()
     if tile_config:
         assert (info["tile_n"], info["tile_pair"]) == TILES[tile_config]
@@ -80,7 +81,7 @@ def test_direction_split_adds_up_to_the_plain_path(precision):
     o = oracle_dir(c)
     o.check_current(Jd, TOL[precision], f"direction split {precision}")
     # the split summed over b against the plain path: each within its bound of the oracle
-    check(Jd.sum(axis=1), Jp, 2 * o.S.sum(axis=1), True, TOL[precision],
+    check(Jd.sum(axis=1), Jp, 2 * o.S.sum(axis=1), 2 * o.Sd.sum(axis=1), TOL[precision],
           f"direction sum vs plain {precision}")
 
 

@@ -97,7 +97,7 @@ def test_shc_one_atom_and_lags_beyond_the_run(precision):
     Ko, cnto = oracle.shc_corr(v, W, 10)
     np.testing.assert_array_equal(cnt, cnto)
     assert np.all(K[:, 6:] == 0)
-    check(K, Ko, oracle.shc_corr(np.abs(v), np.abs(W), 10)[0], True, REL_TOL,
+    check(K, Ko, oracle.shc_corr(np.abs(v), np.abs(W), 10)[0], None, REL_TOL,
           f"SHC one atom {precision}")
     s.close()
 
@@ -152,5 +152,5 @@ def test_green_kubo_read_out_beyond_1024_lags():
     C, cnt = h.read_corr()
     okt = oracle.gk_kappa(C, cnt, dt, TK, V)
     skt = oracle.gk_kappa(np.abs(C), cnt, dt, TK, V)
-    check(kt, okt, skt, True, 1e-12, "1100 lags Green-Kubo stage")
+    check(kt, okt, skt, None, 1e-11, "1100 lags Green-Kubo stage")
     h.close()

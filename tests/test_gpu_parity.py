@@ -367,6 +367,7 @@ def test_polarization_resolved_bins():
     o1 = ModalRef(c["E"], c["mass"], c["v"], c["W"], fb, B)
     o1.check_current(J1, REL_TOL, "frequency bins")
     # the two classes add up to the frequency binning, within the bound of either side
-    check(J2[:, :B] + J2[:, B:], J1, o2.S[:, :B] + o2.S[:, B:] + o1.S, True, REL_TOL,
+    check(J2[:, :B] + J2[:, B:], J1, o2.S[:, :B] + o2.S[:, B:] + o1.S,
+          o2.Sd[:, :B] + o2.Sd[:, B:] + o1.Sd, REL_TOL,
           "classes add up")
     h.close()

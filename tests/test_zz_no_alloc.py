@@ -71,7 +71,8 @@ def test_noalloc_matches_oracle_and_handle_path_on_calls_in_a_row():
         np.testing.assert_allclose(got_J, ref.J, rtol=1e-12, atol=1e-9)
         # the existing entry point on the same block, within the same bound of the oracle
         h.push(torch.from_numpy(v).to(dev), torch.from_numpy(W).to(dev))
-        check(got_Jb, h.read_binned_current(), 2 * ref.S, True, REL_TOL, what + " vs handle")
+        check(got_Jb, h.read_binned_current(), 2 * ref.S, 2 * ref.Sd, REL_TOL,
+              what + " vs handle")
         np.testing.assert_allclose(got_J, h.read_total_current(), rtol=1e-12, atol=1e-9)
 
     valid_call(*blocks[0], "no-alloc call 1")
