@@ -114,7 +114,11 @@ typedef struct {
     int32_t n_lags;      /* L: lags 0..L-1 of the Eq. 17 correlation (GKMA) */
     int32_t precision;   /* mhc_precision */
     int32_t flags;       /* MHC_FLAG_* */
-    int32_t tile_config; /* tensor-core tile: 0 = autotune on the first push of each K;
+    int32_t tile_config; /* tensor-core tile: 0 = autotune on the first push of each K (the
+                            shape and, see split_d, the d-axis split; the choice is kept for
+                            every handle of the process with the same device, precision, D, M
+                            and K, and in the file named by the environment variable
+                            MHC_TUNE_CACHE when it is set);
                             1..4 = one-SM tiles of 128 modes x (columns, k per stage, stages)
                             (256,64,2), (256,32,4), (128,64,3), (128,32,6); 5..8 = two-SM tiles
                             (CTA pair, 256 modes x columns) with (256,64,3), (256,32,6),
@@ -124,6 +128,13 @@ typedef struct {
     double T_K;          /* temperature T (Eq. 17, 19) */
     double V_A3;         /* cell volume V (Eq. 17, 19) */
     double F_e[3];       /* HNEMD driving-force parameter F_e (Eq. 12, 19), 1/A */
+    int32_t split_d;     /* d-axis splits of the tensor-core projection (the GEMM's reduction
+                            over the 3N degrees of freedom cut into split_d ranges of whole
+                            128-element chunks, run as separate units and added in a fixed order
+                            by a finish kernel; it fills the SMs when one block has few tiles):
+                            0 = autotuned with the tile shape (tile_config 0) or 1 (tile_config
+                            > 0); 1..16 = fixed.  Not with MHC_FLAG_DIRECTION (must be 0 or 1);
+                            grouped launches run unsplit. */
 } mhc_params;
 
 /* Counters and derived sizes of a handle. */
@@ -141,6 +152,7 @@ typedef struct {
     int64_t device_bytes;        /* device memory owned by the handle */
     int64_t kernel_launches;     /* kernels launched by the handle so far (graph nodes included) */
     int64_t graph_replays;       /* pushes executed by replaying a captured CUDA graph */
+    int32_t tile_split;          /* d-axis splits of the current tile configuration (1: none) */
 } mhc_info;
 
 /* Fill *p with defaults: device 0, default stream, k_max 256, no GKMA,
@@ -208,6 +220,18 @@ mhc_status mhc_set_bin_ids(mhc_handle *h, const int32_t *bin_of_mode, int32_t n_
  * Errors: INVALID_ARG (no modes/bins yet, K out of range, null), CUDA.
  */
 mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, int32_t where);
+
+/*
+ * Autotune the block length K (steps per push): for each of the n candidates (1 <= K <= k_max)
+ * times three pushes' pack and projection kernels (with the tile shape and split autotuned for
+ * that K, as on a first push) on a synthetic block of constant samples, and returns in *best_K
+ * the candidate with the most steps per second (the rate in *steps_per_s, may be NULL).  No
+ * accumulator changes; the operands of the last pushed block are overwritten, so
+ * mhc_read_binned_current / mhc_read_total_current return INVALID_ARG until the next push.
+ * Synchronises the stream.  Errors: INVALID_ARG (no modes/bins, candidate out of range), CUDA.
+ */
+mhc_status mhc_autotune_k(mhc_handle *h, const int32_t *candidates, int32_t n, int32_t *best_K,
+                          double *steps_per_s);
 
 /* Wait for the stream and report a sticky device status (TIMEOUT/STATE). */
 mhc_status mhc_sync(mhc_handle *h);

@@ -53,6 +53,17 @@ struct TcLayout {
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM columns");
 };
 
+// Unit t of a single problem -> (mode tile, column tile, d split): the column tiles of one
+// (mode tile, split) are adjacent, so the CTAs that share an E slice run side by side.
+__device__ __forceinline__ void split_unit(const TcProblem &P, int t, int &mt, int &ct, int &sp) {
+    const int S = P.n_split > 1 ? P.n_split : 1;
+    const int per_mt = P.n_col_tiles * S;
+    mt = t / per_mt;
+    const int r = t - mt * per_mt;
+    sp = r / P.n_col_tiles;
+    ct = r - sp * P.n_col_tiles;
+}
+
 template <int NPROB>
 struct TileIter {
     const TcParams<NPROB> &p;
@@ -66,25 +77,45 @@ struct TileIter {
             end = p.prob[0].n_tiles;
         }
     }
-    __device__ bool next(int &prob, int &mt, int &ct) {
+    __device__ bool next(int &prob, int &mt, int &ct, int &sp) {
         if (i >= end) return false;
         if (p.sched) {
             const uint32_t id = p.sched[i++];
             prob = (int)(id >> 28);
             ct = (int)((id >> 20) & 0xFFu);
             mt = (int)(id & 0xFFFFFu);
+            sp = 0;
         } else {
             const int t = i;
             i += gridDim.x;
             prob = 0;
-            mt = t / p.prob[0].n_col_tiles;
-            ct = t - mt * p.prob[0].n_col_tiles;
+            split_unit(p.prob[0], t, mt, ct, sp);
         }
         return true;
     }
 };
 
-constexpr int PROMOTE_D = 128;   // d elements per TMEM chunk accumulator
+constexpr int PROMOTE_D = TC_PROMOTE_D;   // d elements per TMEM chunk accumulator
+
+// k-blocks [lo, hi) of split sp of a tile (the whole d axis without a split).
+__device__ __forceinline__ void kb_range(const TcProblem &P, int sp, int &lo, int &hi) {
+    if (P.n_split > 1) {
+        lo = sp * P.kb_split;
+        hi = min(P.n_kb, lo + P.kb_split);
+    } else {
+        lo = 0;
+        hi = P.n_kb;
+    }
+}
+
+// A split unit's promoted sums (128 columns from col0 of mode n) to the split workspace
+// split_ws[sp][col][mode]: each warp stores 128 contiguous bytes per column.
+__device__ __forceinline__ void store_split(const float (&acc)[128], const TcProblem &P, int sp,
+                                            int n, int col0) {
+    float *dst = P.split_ws + ((size_t)sp * P.ws_cols + col0) * P.m_pad + n;
+#pragma unroll
+    for (int j = 0; j < 128; ++j) __stcg(dst + (size_t)j * P.m_pad, acc[j]);
+}
 
 // Direction-resolved split.  The d axis is stored direction-major (segment b holds the dofs
 // 3i+b), so every chunk lies inside one segment.  The epilogue keeps Xdot (columns 4s)
@@ -240,11 +271,13 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         int stage = 0;
         uint32_t phase = 0;
         TileIter<NPROB> it(p);
-        int prob, mt, ct;
+        int prob, mt, ct, sp;
         bool ok = true;
-        while (ok && it.next(prob, mt, ct)) {
+        while (ok && it.next(prob, mt, ct, sp)) {
             const TcProblem &P = p.prob[prob];
-            for (int kb = 0; kb < P.n_kb; ++kb) {
+            int kb_lo, kb_hi;
+            kb_range(P, sp, kb_lo, kb_hi);
+            for (int kb = kb_lo; kb < kb_hi; ++kb) {
                 if (!mbar_wait(&empty[stage], phase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 uint8_t *sa = smem + stage * L::STAGE_BYTES;
                 // test hook: 16 bytes more than the copies deliver keeps the barrier pending
@@ -277,16 +310,18 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         int stage = 0, abuf = 0;
         uint32_t phase = 0, aphase = 0;
         TileIter<NPROB> it(p);
-        int prob, mt, ct;
+        int prob, mt, ct, sp;
         bool ok = true;
         const uint32_t smem0 = smem_u32(smem);
-        while (ok && it.next(prob, mt, ct)) {
+        while (ok && it.next(prob, mt, ct, sp)) {
             const TcProblem &P = p.prob[prob];
-            for (int kb0 = 0; ok && kb0 < P.n_kb; kb0 += CHUNK_KB) {
+            int kb_lo, kb_hi;
+            kb_range(P, sp, kb_lo, kb_hi);
+            for (int kb0 = kb_lo; ok && kb0 < kb_hi; kb0 += CHUNK_KB) {
                 if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * BN);
-                const int kb1 = min(kb0 + CHUNK_KB, P.n_kb);
+                const int kb1 = min(kb0 + CHUNK_KB, kb_hi);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(&full[stage], phase, abort, p.wait_limit)) { ok = false; break; }
                     tc_fence_after();
@@ -330,10 +365,12 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         int abuf = 0;
         uint32_t aphase = 0;
         TileIter<NPROB> it(p);
-        int prob, mt, ct;
+        int prob, mt, ct, sp;
         bool ok = true;
-        while (ok && it.next(prob, mt, ct)) {
+        while (ok && it.next(prob, mt, ct, sp)) {
             const TcProblem &P = p.prob[prob];
+            int kb_lo, kb_hi;
+            kb_range(P, sp, kb_lo, kb_hi);
             const int n = mt * TC_BM + qw * 32 + lane;
             const int bin = P.mode_bin[n];
             const int slot = P.mode_slot[n];
@@ -342,7 +379,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0.f;
             // promotion of every chunk accumulator into FP32 registers
-            for (int kb0 = 0; kb0 < P.n_kb; kb0 += CHUNK_KB) {
+            for (int kb0 = kb_lo; kb0 < kb_hi; kb0 += CHUNK_KB) {
                 if (!mbar_wait(&acc_full[abuf], aphase, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(qw * 32) << 16) +
@@ -361,6 +398,10 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
                 if constexpr (DIR) dir_maybe_park(acc, P, kb0 + CHUNK_KB);
             }
             if (!ok) break;
+            if (P.n_split > 1) {   // the split finish kernel adds the splits and runs the epilogue
+                store_split(acc, P, sp, n, ct * BN + ch * 128);
+                continue;
+            }
             // Eq. 16 product and the bin-run sums of this warp's 32 steps
             const int kbase = ct * (BN / 4) + ch * 32;
             tile_epilogue<DIR>(acc, P, kbase, take, slot, lane);
@@ -421,17 +462,17 @@ struct PairTileIter {
             step = npairs;
         }
     }
-    __device__ bool next(int &prob, int &mp, int &ct) {
+    __device__ bool next(int &prob, int &mp, int &ct, int &sp) {
         if (i >= end) return false;
         if (p.sched) {
             const uint32_t id = p.sched[i];
             prob = (int)(id >> 28);
             ct = (int)((id >> 20) & 0xFFu);
             mp = (int)(id & 0xFFFFFu);
+            sp = 0;
         } else {
             prob = 0;
-            mp = i / p.prob[0].n_col_tiles;
-            ct = i - mp * p.prob[0].n_col_tiles;
+            split_unit(p.prob[0], i, mp, ct, sp);
         }
         i += step;
         return true;
@@ -498,13 +539,15 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
         int stage = 0;
         uint32_t phase = 0;
         PairTileIter<NPROB> it(p, pair, npairs);
-        int prob, mp, ct;
+        int prob, mp, ct, sp;
         bool ok = true;
-        while (ok && it.next(prob, mp, ct)) {
+        while (ok && it.next(prob, mp, ct, sp)) {
             const TcProblem &P = p.prob[prob];
             const int arow = mp * 2 * TC_BM + (int)rank * TC_BM;
             const int brow = ct * BN + (int)rank * (BN / 2);
-            for (int kb = 0; kb < P.n_kb; ++kb) {
+            int kb_lo, kb_hi;
+            kb_range(P, sp, kb_lo, kb_hi);
+            for (int kb = kb_lo; kb < kb_hi; ++kb) {
                 if (!mbar_wait(&empty[stage], phase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 if (leader)   // test hook as in the one-SM kernel
                     mbar_arrive_expect_tx(&full[stage], 2 * L::STAGE_BYTES + (p.stall_inject && kb == 0 ? 16 : 0));
@@ -538,16 +581,18 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
         int stage = 0, abuf = 0;
         uint32_t phase = 0, aphase = 0;
         PairTileIter<NPROB> it(p, pair, npairs);
-        int prob, mp, ct;
+        int prob, mp, ct, sp;
         bool ok = true;
         const uint32_t smem0 = smem_u32(smem);
-        while (ok && it.next(prob, mp, ct)) {
+        while (ok && it.next(prob, mp, ct, sp)) {
             const TcProblem &P = p.prob[prob];
-            for (int kb0 = 0; ok && kb0 < P.n_kb; kb0 += CHUNK_KB) {
+            int kb_lo, kb_hi;
+            kb_range(P, sp, kb_lo, kb_hi);
+            for (int kb0 = kb_lo; ok && kb0 < kb_hi; kb0 += CHUNK_KB) {
                 if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(abuf * BN);
-                const int kb1 = min(kb0 + CHUNK_KB, P.n_kb);
+                const int kb1 = min(kb0 + CHUNK_KB, kb_hi);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(&full[stage], phase, abort, p.wait_limit)) { ok = false; break; }
                     tc_fence_after();
@@ -591,10 +636,12 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
         const uint32_t empty_leader[2] = {mapa_shared(smem_u32(&acc_empty[0]), 0),
                                           mapa_shared(smem_u32(&acc_empty[1]), 0)};
         PairTileIter<NPROB> it(p, pair, npairs);
-        int prob, mp, ct;
+        int prob, mp, ct, sp;
         bool ok = true;
-        while (ok && it.next(prob, mp, ct)) {
+        while (ok && it.next(prob, mp, ct, sp)) {
             const TcProblem &P = p.prob[prob];
+            int kb_lo, kb_hi;
+            kb_range(P, sp, kb_lo, kb_hi);
             const int n = mp * 2 * TC_BM + (int)rank * TC_BM + qw * 32 + lane;
             const int bin = P.mode_bin[n];
             const int slot = P.mode_slot[n];
@@ -602,7 +649,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
             float acc[128];
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0.f;
-            for (int kb0 = 0; kb0 < P.n_kb; kb0 += CHUNK_KB) {
+            for (int kb0 = kb_lo; kb0 < kb_hi; kb0 += CHUNK_KB) {
                 if (!mbar_wait(&acc_full[abuf], aphase, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(qw * 32) << 16) +
@@ -626,6 +673,10 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
                 if constexpr (DIR) dir_maybe_park(acc, P, kb0 + CHUNK_KB);
             }
             if (!ok) break;
+            if (P.n_split > 1) {   // the split finish kernel adds the splits and runs the epilogue
+                store_split(acc, P, sp, n, ct * BN + ch * 128);
+                continue;
+            }
             const int kbase = ct * (BN / 4) + ch * 32;
             tile_epilogue<DIR>(acc, P, kbase, take, slot, lane);
         }
@@ -725,7 +776,38 @@ cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s
     return cudaErrorInvalidValue;
 }
 
+// Split finish: one warp per (32 modes, 32 steps), lane = mode.  Adds the splits' promoted
+// sums in split order and runs the tile epilogue of the fused kernel on them.
+__global__ void __launch_bounds__(128) tc_split_finish_kernel(const __grid_constant__ TcParams<1> p) {
+    const TcProblem &P = p.prob[0];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * 4 + warp;   // 32-mode group (warp-uniform)
+    if (g * 32 >= P.m_pad) return;
+    const int n = g * 32 + lane;
+    const int c0 = blockIdx.y * 128;       // first of the warp's 128 columns (32 steps)
+    const int bin = P.mode_bin[n];
+    const int slot = P.mode_slot[n];
+    const uint32_t take = seg_scan_masks(bin, lane);
+    float acc[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+    for (int s = 0; s < P.n_split; ++s) {
+        const float *src = P.split_ws + ((size_t)s * P.ws_cols + c0) * P.m_pad + n;
+#pragma unroll
+        for (int j = 0; j < 128; ++j) acc[j] += __ldcg(src + (size_t)j * P.m_pad);
+    }
+    tile_epilogue<false>(acc, P, blockIdx.y * 32, take, slot, lane);
+}
+
 }  // namespace
+
+cudaError_t launch_tc_split_finish(const TcParams<1> &p, cudaStream_t s) {
+    const TcProblem &P = p.prob[0];
+    if (P.n_split <= 1 || !P.split_ws || P.m_pad % 128) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)(P.m_pad / 128), (unsigned)((P.K + 31) / 32));
+    tc_split_finish_kernel<<<grid, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 const TcConfig TC_CONFIGS[TC_NUM_CONFIGS] = {
     {256, 64, 2, 0, 0}, {256, 32, 4, 0, 0}, {128, 64, 3, 0, 0}, {128, 32, 6, 0, 0},
@@ -749,6 +831,9 @@ size_t tc_smem_bytes(const TcConfig &c) {   // must match TcLayout / TcPairLayou
 }
 
 cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream_t s) {
+    if (p.prob[0].n_split > 1 && (p.prob[0].dir_seg_kb || !p.prob[0].split_ws ||
+                                  p.prob[0].kb_split % (PROMOTE_D / c.bk)))
+        return cudaErrorInvalidValue;
     if (p.prob[0].dir_seg_kb) {
         if (!p.prob[0].dir_park || c.grid > p.dir_park_ctas) return cudaErrorInvalidValue;
         return dispatch<1, true>(p, c, s);
@@ -756,8 +841,8 @@ cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream
     return dispatch<1, false>(p, c, s);
 }
 cudaError_t launch_tc_group(const TcParams<TC_MAX_GROUP> &p, const TcConfig &c, cudaStream_t s) {
-    for (int q = 0; q < p.n_prob; ++q)   // the direction split runs on single problems only
-        if (p.prob[q].dir_seg_kb) return cudaErrorInvalidValue;
+    for (int q = 0; q < p.n_prob; ++q)   // direction and d-axis splits run on single problems only
+        if (p.prob[q].dir_seg_kb || p.prob[q].n_split > 1) return cudaErrorInvalidValue;
     return dispatch<TC_MAX_GROUP, false>(p, c, s);
 }
 

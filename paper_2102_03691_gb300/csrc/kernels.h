@@ -10,6 +10,7 @@ namespace mhc {
 enum Split { SPLIT_FP32 = 0, SPLIT_BF16 = 1, SPLIT_FP16 = 2 };
 
 constexpr int TC_MAX_GROUP = 16;  // systems per grouped launch
+constexpr int TC_MAX_SPLIT = 16;  // d-axis splits of one projection
 
 // Sticky device status codes (same values as mhc_status).
 constexpr int DEV_OK = 0, DEV_TIMEOUT = 4, DEV_STATE = 5;
@@ -107,6 +108,12 @@ struct TcProblem {   // 128-byte aligned through CUtensorMap
     // segments ([grid][2][96][DIR_PARK_THREADS] floats, grid <= the SM count).
     int dir_seg_kb;
     float *dir_park;
+    // Split of the d axis (n_split > 1, single problems only): unit (mode tile, column tile,
+    // split s) accumulates the k-blocks [s kb_split, (s+1) kb_split) and stores its promoted
+    // FP32 sums to split_ws[s][column][mode] (ws_cols columns, m_pad modes); the finish kernel
+    // adds the splits in order and runs the tile epilogue.  n_split <= 1: one unit per tile.
+    int n_split, kb_split, ws_cols, m_pad;
+    float *split_ws;
 };
 constexpr int DIR_PARK_THREADS = 256;                        // epilogue threads of the widest tile
 constexpr int DIR_PARK_SEG_FLOATS = 96 * DIR_PARK_THREADS;   // one parked segment of a CTA
@@ -131,6 +138,7 @@ struct TcConfig {
     int stages;   // shared-memory pipeline depth
     int pair;     // 1: two-SM tile (cta_group::2, 256 modes per CTA pair, bn columns shared)
     int grid;
+    int split;    // d-axis splits of a single problem (0 or 1: none)
 };
 // Pipeline shapes the autotuner chooses from (index + 1 = mhc_params.tile_config).
 constexpr int TC_NUM_CONFIGS = 8;
@@ -143,6 +151,11 @@ bool tc_config_supported(const TcConfig &c);
 int tc_make_tmap(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint64_t ld,
                  uint32_t box_rows, uint32_t box_cols);
 cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream_t s);
+// With prob[0].n_split > 1: sum the splits' partial projections of the block (in split order)
+// and run the tile epilogue (Eq. 16 product, bin-run sums into partials).
+cudaError_t launch_tc_split_finish(const TcParams<1> &p, cudaStream_t s);
+// d elements per promotion chunk of the tensor-core kernels (splits are whole chunks)
+constexpr int TC_PROMOTE_D = 128;
 cudaError_t launch_tc_group(const TcParams<TC_MAX_GROUP> &p, const TcConfig &c, cudaStream_t s);
 // Pack a tile id for the scheduler.
 __host__ __device__ inline uint32_t tc_tile_id(int prob, int mt, int ct) {

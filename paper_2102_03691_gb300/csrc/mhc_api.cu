@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -76,6 +77,7 @@ struct mhc_handle {
     mhc_params prm{};
     cudaStream_t stream = nullptr;
     int sm_count = 0, cc_major = 0, cc_minor = 0;
+    std::string device_name;
     int split = SPLIT_BF16;
     std::string err;
 
@@ -442,8 +444,30 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
     return reset_accumulators(h);
 }
 
+// Bytes of the d-axis split workspace of configuration c: [split][columns of k_max][M_pad].
+size_t split_ws_bytes(const mhc_handle *h, const TcConfig &c) {
+    if (c.split <= 1) return 0;
+    const size_t cols = (size_t)((4 * h->prm.k_max + c.bn - 1) / c.bn) * c.bn;
+    return sizeof(float) * (size_t)c.split * cols * (size_t)h->M_pad;
+}
+
+// The split workspace of configuration c, grown if needed (outside any stream capture: a
+// larger workspace replaces the old one, so the graphs captured with its address are dropped).
+mhc_status ensure_split_ws(mhc_handle *h, const TcConfig &c) {
+    const size_t need = split_ws_bytes(h, c);
+    if (!need) return MHC_OK;
+    auto it = h->buf.find("split_ws");
+    if (it != h->buf.end() && it->second.bytes >= need) return MHC_OK;
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    return dev_alloc(h, "split_ws", need, false);
+}
+
 mhc_status set_tc_config(mhc_handle *h, const TcConfig &c) {
     if (!tc_config_supported(c)) return fail(h, MHC_ERR_INVALID_ARG, "unsupported tile configuration");
+    if (c.split > 1 && (h->dir || c.split > TC_MAX_SPLIT))
+        return fail(h, MHC_ERR_INVALID_ARG, "d-axis split %d not available here", c.split);
+    if (mhc_status s = ensure_split_ws(h, c); s != MHC_OK) return s;
     const bool remap = h->bins_ready && (c.bn != h->tc.bn || c.bk != h->tc.bk || c.pair != h->tc.pair);
     h->tc = c;
     if (remap) {
@@ -494,40 +518,172 @@ mhc_status run_projection(mhc_handle *h, int K) {
     h->tcp.wait_limit = stall ? 200000000ll : 2000000000ll;   // 0.1 s when testing the timeout
     P.K = K;
     P.n_col_tiles = (int)((4 * K + c.bn - 1) / c.bn);
-    P.n_tiles = mode_tiles(h, c) * P.n_col_tiles;
+    // d-axis split: whole promotion chunks per split, no empty split
+    const int chunk_kb = TC_PROMOTE_D / c.bk;
+    int kb_split = P.n_kb, S = 1;
+    if (c.split > 1) {
+        kb_split = ((P.n_kb + c.split - 1) / c.split + chunk_kb - 1) / chunk_kb * chunk_kb;
+        S = (P.n_kb + kb_split - 1) / kb_split;
+    }
+    P.n_split = S;
+    P.kb_split = kb_split;
+    P.ws_cols = P.n_col_tiles * c.bn;
+    P.m_pad = (int)h->M_pad;
+    P.split_ws = S > 1 ? dptr<float>(h, "split_ws") : nullptr;
+    P.n_tiles = mode_tiles(h, c) * P.n_col_tiles * S;
     c.grid = std::min(sched_units(h, c), P.n_tiles) * (c.pair ? 2 : 1);
     cudaError_t e = launch_tc_single(h->tcp, c, h->stream);
     h->launches++;
+    if (e == cudaSuccess && S > 1) {
+        e = launch_tc_split_finish(h->tcp, h->stream);
+        h->launches++;
+    }
     if (e != cudaSuccess)
         return fail(h, MHC_ERR_CUDA, "tensor-core kernel launch failed: %s", cudaGetErrorString(e));
     return MHC_OK;
 }
 
-// Autotune: time each supported tile configuration on the block just packed.
+// ---- autotuning of the tile shape and the d-axis split count
+// Results are kept per process (every handle of the same device, precision, shape and block
+// length reuses them) and, when the environment variable MHC_TUNE_CACHE names a file, in that
+// file across processes.
+struct TuneKey {
+    std::string device;
+    int sm, prec, dir, K, split_req;
+    int64_t D_ld, M_eff;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(device, sm, prec, dir, K, split_req, D_ld, M_eff) <
+               std::tie(o.device, o.sm, o.prec, o.dir, o.K, o.split_req, o.D_ld, o.M_eff);
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TcConfig> g_tune_cache;
+bool g_tune_file_read = false;
+
+TuneKey tune_key(const mhc_handle *h, int K) {
+    return TuneKey{h->device_name, h->sm_count, (int)h->split, h->dir ? 1 : 0, K,
+                   (int)h->prm.split_d, h->D_ld, h->M_eff};
+}
+
+// Cache file lines: sm prec dir K split_req D_ld M_eff bn bk stages pair split <device name>
+void tune_file_read_locked() {
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char *path = std::getenv("MHC_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        TuneKey k;
+        TcConfig c{};
+        long long D = 0, M = 0;
+        int used = 0;
+        if (std::sscanf(line, "%d %d %d %d %d %lld %lld %d %d %d %d %d %n", &k.sm, &k.prec, &k.dir, &k.K,
+                        &k.split_req, &D, &M, &c.bn, &c.bk, &c.stages, &c.pair, &c.split, &used) < 12)
+            continue;
+        std::string name(line + used);
+        while (!name.empty() && (name.back() == '\n' || name.back() == '\r')) name.pop_back();
+        k.device = name;
+        k.D_ld = D;
+        k.M_eff = M;
+        if (tc_config_supported(c) && c.split >= 1 && c.split <= TC_MAX_SPLIT) g_tune_cache[k] = c;
+    }
+    std::fclose(f);
+}
+
+void tune_file_append_locked(const TuneKey &k, const TcConfig &c) {
+    const char *path = std::getenv("MHC_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%d %d %d %d %d %lld %lld %d %d %d %d %d %s\n", k.sm, k.prec, k.dir, k.K,
+                 k.split_req, (long long)k.D_ld, (long long)k.M_eff, c.bn, c.bk, c.stages, c.pair,
+                 c.split, k.device.c_str());
+    std::fclose(f);
+}
+
+// Device time (ms) of `reps` projections of the block just packed with configuration c
+// (after one warm-up launch).
+mhc_status time_projection(mhc_handle *h, const TcConfig &c, int K, cudaEvent_t e0, cudaEvent_t e1,
+                           int reps, float &ms) {
+    mhc_status s = set_tc_config(h, c);
+    if (s != MHC_OK) return s;
+    if ((s = run_projection(h, K)) != MHC_OK) return s;   // warm-up
+    MHC_CUDA(h, cudaEventRecord(e0, h->stream));
+    for (int r = 0; r < reps; ++r)
+        if ((s = run_projection(h, K)) != MHC_OK) return s;
+    MHC_CUDA(h, cudaEventRecord(e1, h->stream));
+    MHC_CUDA(h, cudaEventSynchronize(e1));
+    MHC_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+    return MHC_OK;
+}
+
+// Autotune on the block just packed: time every tile shape unsplit (or with the fixed split of
+// mhc_params.split_d), then, when one block leaves schedulable units idle (fewer than three
+// waves of tiles), the d-axis splits 2..8 of the two fastest shapes.  The winner is cached.
 mhc_status autotune(mhc_handle *h, int K) {
+    const TuneKey key = tune_key(h, K);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        tune_file_read_locked();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->tuned[K] = it->second;
+            return set_tc_config(h, it->second);
+        }
+    }
     cudaEvent_t e0, e1;
     MHC_CUDA(h, cudaEventCreate(&e0));
     MHC_CUDA(h, cudaEventCreate(&e1));
-    float best = 1e30f;
-    TcConfig best_c = h->tc;
-    for (const TcConfig &c : TC_CONFIGS) {
-        mhc_status s = set_tc_config(h, c);
-        if (s != MHC_OK) return s;
-        if ((s = run_projection(h, K)) != MHC_OK) return s;   // warm-up
-        MHC_CUDA(h, cudaEventRecord(e0, h->stream));
-        for (int r = 0; r < 3; ++r)
-            if ((s = run_projection(h, K)) != MHC_OK) return s;
-        MHC_CUDA(h, cudaEventRecord(e1, h->stream));
-        MHC_CUDA(h, cudaEventSynchronize(e1));
+    std::vector<std::pair<float, TcConfig>> res;
+    const int fixed = std::max(1, (int)h->prm.split_d);
+    mhc_status s = MHC_OK;
+    for (TcConfig c : TC_CONFIGS) {
+        c.split = fixed;
         float ms = 0.f;
-        MHC_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_c = c;
+        if ((s = time_projection(h, c, K, e0, e1, 3, ms)) != MHC_OK) break;
+        res.emplace_back(ms, c);
+    }
+    if (s == MHC_OK && h->prm.split_d == 0 && !h->dir) {
+        std::sort(res.begin(), res.end(),
+                  [](const std::pair<float, TcConfig> &a, const std::pair<float, TcConfig> &b) {
+                      return a.first < b.first;
+                  });
+        const size_t n_shapes = std::min<size_t>(2, res.size());
+        const size_t budget = (size_t)512 << 20;   // largest split workspace tried
+        for (size_t q = 0; q < n_shapes && s == MHC_OK; ++q) {
+            TcConfig c = res[q].second;
+            const int n_kb = (int)(h->D_ld / c.bk), chunk_kb = TC_PROMOTE_D / c.bk;
+            const int64_t units = (int64_t)mode_tiles(h, c) * ((4 * K + c.bn - 1) / c.bn);
+            if (units >= 3 * (int64_t)sched_units(h, c)) continue;
+            for (int S : {2, 3, 4, 6, 8}) {
+                if (n_kb < S * chunk_kb) break;
+                c.split = S;
+                if (split_ws_bytes(h, c) > budget) break;
+                float ms = 0.f;
+                if ((s = time_projection(h, c, K, e0, e1, 3, ms)) != MHC_OK) break;
+                res.emplace_back(ms, c);
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (s != MHC_OK) return s;
+    TcConfig best_c = h->tc;
+    float best = 1e30f;
+    for (auto &r : res)
+        if (r.first < best) {
+            best = r.first;
+            best_c = r.second;
+        }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        if (!g_tune_cache.count(key)) {
+            g_tune_cache[key] = best_c;
+            tune_file_append_locked(key, best_c);
+        }
+    }
     h->tuned[K] = best_c;
     return set_tc_config(h, best_c);
 }
@@ -668,7 +824,8 @@ int config_index(const mhc_handle *h) {
 // Capture pack -> projection -> finish of one push into a graph (on a private stream) and
 // replay it on the handle's stream.  Inputs must already be in device memory.
 mhc_status push_graph(mhc_handle *h, const float *v, const float *W, int K) {
-    auto key = std::make_tuple(K, (const void *)v, (const void *)W, is_tc(h) ? config_index(h) : -1);
+    auto key = std::make_tuple(K, (const void *)v, (const void *)W,
+                               is_tc(h) ? config_index(h) * 64 + std::max(1, h->tc.split) : -1);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         if (h->graphs.size() >= 32) {   // evict the least recently used graph
@@ -735,6 +892,7 @@ void mhc_default_params(mhc_params *p) {
     p->precision = MHC_PREC_BF16X3;
     p->flags = 0;
     p->tile_config = 0;
+    p->split_d = 0;
     p->ortho_probe = -1;
     p->dt_ps = 0.01;
     p->T_K = 300.0;
@@ -775,6 +933,10 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
         return fail(nullptr, MHC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
     if (p->tile_config < 0 || p->tile_config > TC_NUM_CONFIGS)
         return fail(nullptr, MHC_ERR_INVALID_ARG, "tile_config must be in [0, %d]", TC_NUM_CONFIGS);
+    if (p->split_d < 0 || p->split_d > TC_MAX_SPLIT)
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "split_d must be in [0, %d]", TC_MAX_SPLIT);
+    if ((p->flags & MHC_FLAG_DIRECTION) && p->split_d > 1)
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "the direction split runs without d-axis splits");
     if (!(p->dt_ps > 0) || !(p->T_K > 0) || !(p->V_A3 > 0))
         return fail(nullptr, MHC_ERR_INVALID_ARG, "dt_ps, T_K and V_A3 must be positive");
     int ndev = 0;
@@ -794,6 +956,7 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
     h->prm = *p;
     h->stream = static_cast<cudaStream_t>(p->stream);
     h->sm_count = prop.multiProcessorCount;
+    h->device_name = prop.name;
     h->cc_major = prop.major;
     h->cc_minor = prop.minor;
     h->split = p->precision == MHC_PREC_FP32 ? SPLIT_FP32
@@ -801,6 +964,7 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
     h->dir = (p->flags & MHC_FLAG_DIRECTION) != 0;
     if (p->tile_config > 0) h->tc = TC_CONFIGS[p->tile_config - 1];
     else if (h->dir) h->tc = TC_CONFIGS[2];
+    h->tc.split = std::max(1, (int)p->split_d);
     if ((e = cudaSetDevice(p->device)) != cudaSuccess) {
         delete h;
         return fail(nullptr, MHC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -1001,6 +1165,7 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE) return fail(h, MHC_ERR_INVALID_ARG, "where");
     MHC_CUDA(h, cudaSetDevice(h->prm.device));
     mhc_status s;
+    if (is_tc(h) && (s = ensure_split_ws(h, h->tc)) != MHC_OK) return s;
     if ((s = stage_inputs(h, v, W, K, where)) != MHC_OK) return s;
     const bool tuned = !is_tc(h) || h->prm.tile_config != 0 || h->tuned.count(K);
     if (tuned && !(h->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL))) {
@@ -1034,6 +1199,64 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     if (ev1) MHC_CUDA(h, cudaEventRecord(ev1, h->stream));
     if ((s = finish_block(h, K)) != MHC_OK) return s;
     return release_stage(h);
+}
+
+mhc_status mhc_autotune_k(mhc_handle *h, const int32_t *candidates, int32_t n, int32_t *best_K,
+                          double *steps_per_s) {
+    if (!h) return MHC_ERR_INVALID_ARG;
+    if (!candidates || n < 1 || !best_K) return fail(h, MHC_ERR_INVALID_ARG, "need candidates and best_K");
+    if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "modes and bins must be set first");
+    for (int32_t q = 0; q < n; ++q)
+        if (candidates[q] < 1 || candidates[q] > h->prm.k_max)
+            return fail(h, MHC_ERR_INVALID_ARG, "candidate K=%d outside [1, %d]", candidates[q], h->prm.k_max);
+    MHC_CUDA(h, cudaSetDevice(h->prm.device));
+    // a block of the largest K of constant, finite samples in the first staging pair, after the
+    // pushes that may still read that pair
+    MHC_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->copy_stream) MHC_CUDA(h, cudaStreamSynchronize(h->copy_stream));
+    float *v = dptr<float>(h, "v_stage"), *W = dptr<float>(h, "W_stage");
+    MHC_CUDA(h, cudaMemsetAsync(v, 0x3f, sizeof(float) * h->prm.k_max * h->N * 3, h->stream));
+    MHC_CUDA(h, cudaMemsetAsync(W, 0x3f, sizeof(float) * h->prm.k_max * h->N * 9, h->stream));
+    cudaEvent_t e0, e1;
+    MHC_CUDA(h, cudaEventCreate(&e0));
+    MHC_CUDA(h, cudaEventCreate(&e1));
+    mhc_status s = MHC_OK;
+    double best = -1.0;
+    int32_t bestK = candidates[0];
+    for (int32_t q = 0; q < n && s == MHC_OK; ++q) {
+        const int K = candidates[q];
+        if ((s = pack_block(h, v, W, K)) != MHC_OK) break;
+        if (is_tc(h) && h->prm.tile_config == 0) {
+            auto it = h->tuned.find(K);
+            s = it == h->tuned.end() ? autotune(h, K) : set_tc_config(h, it->second);
+            if (s != MHC_OK) break;
+        }
+        const int reps = 3;
+        cudaError_t e = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && s == MHC_OK; ++r)
+            if ((s = pack_block(h, v, W, K)) == MHC_OK) s = run_projection(h, K);
+        if (s != MHC_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            s = fail(h, MHC_ERR_CUDA, "timing of K=%d failed: %s", K, cudaGetErrorString(e));
+            break;
+        }
+        const double rate = ms > 0 ? reps * (double)K / (ms * 1e-3) : 0.0;
+        if (rate > best) {
+            best = rate;
+            bestK = K;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != MHC_OK) return s;
+    h->K_last = 0;   // the packed operands no longer belong to the last pushed block
+    *best_K = bestK;
+    if (steps_per_s) *steps_per_s = best;
+    return MHC_OK;
 }
 
 mhc_status mhc_sync(mhc_handle *h) {
@@ -1184,6 +1407,7 @@ mhc_status mhc_get_info(mhc_handle *h, mhc_info *info) {
     info->tile_pair = is_tc(h) ? h->tc.pair : 0;
     info->tile_k = is_tc(h) ? h->tc.bk : 16;
     info->stages = is_tc(h) ? h->tc.stages : 0;
+    info->tile_split = is_tc(h) ? std::max(1, h->tc.split) : 1;
     info->grid = h->sm_count;
     info->e_exp = h->e_exp;
     info->ortho_err = h->ortho_err;
@@ -1335,6 +1559,8 @@ mhc_status group_encode(mhc_group *g) {
         mhc_handle *h = g->hs[j];
         TcProblem &P = g->tcp.prob[j];
         P = h->tcp.prob[0];
+        P.n_split = 1;   // grouped launches run every system unsplit
+        P.split_ws = nullptr;
         if (encode_maps(h, c, P))
             return fail(h0, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed (group member %zu)", j);
         P.n_kb = (int)(h->D_ld / c.bk);
@@ -1543,6 +1769,7 @@ mhc_status mhc_group_create(mhc_group **out, mhc_handle *const *handles, int32_t
     auto *g = new mhc_group();
     g->hs.assign(handles, handles + n);
     g->tc = h0->tc;
+    g->tc.split = 1;   // grouped launches run unsplit
     mhc_status s = group_encode(g);
     if (s != MHC_OK) {
         delete g;

@@ -31,6 +31,7 @@ FLAG_XCORR = 0x20
 EXPORTS = (
     "mhc_default_params", "mhc_create", "mhc_destroy", "mhc_last_error", "mhc_status_string",
     "mhc_set_modes", "mhc_set_bins_uniform", "mhc_set_bin_ids", "mhc_push", "mhc_sync",
+    "mhc_autotune_k",
     "mhc_read_binned_current", "mhc_read_total_current", "mhc_read_hnema", "mhc_read_corr",
     "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_set_flags",
     "mhc_kernel_time", "mhc_read_xcorr", "mhc_read_kappa_xcorr",
@@ -48,7 +49,7 @@ class MhcParams(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("tile_config", ctypes.c_int32), ("ortho_probe", ctypes.c_int32),
                 ("dt_ps", ctypes.c_double), ("T_K", ctypes.c_double), ("V_A3", ctypes.c_double),
-                ("F_e", ctypes.c_double * 3)]
+                ("F_e", ctypes.c_double * 3), ("split_d", ctypes.c_int32)]
 
 
 class MhcInfo(ctypes.Structure):
@@ -61,7 +62,8 @@ class MhcInfo(ctypes.Structure):
                 ("tile_pair", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("grid", ctypes.c_int32), ("e_exp", ctypes.c_int32),
                 ("ortho_err", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("tile_split", ctypes.c_int32)]
 
 
 class MhcError(RuntimeError):
@@ -97,6 +99,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_set_bin_ids.argtypes = [vp, vp, i32]
     L.mhc_push.argtypes = [vp, vp, vp, i32, i32]
     L.mhc_sync.argtypes = [vp]
+    L.mhc_autotune_k.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     L.mhc_read_binned_current.argtypes = [vp, vp, i32]
     L.mhc_read_total_current.argtypes = [vp, vp, i32]
     L.mhc_read_hnema.argtypes = [vp, vp, vp, i32]
@@ -328,7 +331,7 @@ class ModalHeatCurrent:
                  gkma: bool | None = None, dt_ps: float = 0.01, T_K: float = 300.0,
                  V_A3: float = 1.0, F_e=(1e-5, 0.0, 0.0), device: int = 0, stream=None,
                  tile_config: int = 0, ortho_probe: int = -1, flags: int = 0,
-                 direction: bool = False, xcorr: bool = False):
+                 direction: bool = False, xcorr: bool = False, split_d: int = 0):
         self._L = load()
         p = MhcParams()
         self._L.mhc_default_params(ctypes.byref(p))
@@ -342,6 +345,7 @@ class ModalHeatCurrent:
         p.flags = (flags | (FLAG_GKMA if gk else 0) | (FLAG_DIRECTION if direction else 0)
                    | (FLAG_XCORR if xcorr else 0))
         p.tile_config = tile_config
+        p.split_d = split_d
         p.ortho_probe = ortho_probe
         p.dt_ps, p.T_K, p.V_A3 = dt_ps, T_K, V_A3
         for i in range(3):
@@ -505,6 +509,17 @@ class ModalHeatCurrent:
         if st not in (MHC_OK, MHC_WARN_NOT_ORTHONORMAL):
             self._check(st)
         return e.value
+
+    def autotune_k(self, candidates):
+        """mhc_autotune_k: the candidate block length with the most steps per second, and that
+        rate (the last block's currents are unreadable until the next push)."""
+        c = np.ascontiguousarray(candidates, dtype=np.int32)
+        best = ctypes.c_int32()
+        rate = ctypes.c_double()
+        self._check(self._L.mhc_autotune_k(self._h, c.ctypes.data_as(ctypes.c_void_p), c.size,
+                                           ctypes.byref(best), ctypes.byref(rate)))
+        self._lastK = 0
+        return int(best.value), float(rate.value)
 
     def info(self) -> dict:
         i = MhcInfo()

@@ -38,7 +38,8 @@ def test_default_params_and_status_strings():
 
 
 @pytest.mark.parametrize("field,value", [("k_max", 0), ("k_max", 5000), ("n_lags", -1),
-                                         ("precision", 7), ("tile_config", 9), ("dt_ps", 0.0)])
+                                         ("precision", 7), ("tile_config", 9), ("dt_ps", 0.0),
+                                         ("split_d", -1), ("split_d", 17)])
 def test_create_rejects_bad_params(field, value):
     L = mhc.load()
     p = mhc.MhcParams()
@@ -60,15 +61,55 @@ def test_gkma_requires_lags():
     assert L.mhc_create(ctypes.byref(h), ctypes.byref(p)) == 1
 
 
+def test_direction_split_takes_no_d_axis_split():
+    L = mhc.load()
+    p = mhc.MhcParams()
+    L.mhc_default_params(ctypes.byref(p))
+    p.flags = mhc.FLAG_DIRECTION
+    p.split_d = 2
+    h = ctypes.c_void_p()
+    assert L.mhc_create(ctypes.byref(h), ctypes.byref(p)) == 1
+    assert b"split" in L.mhc_last_error(None)
+
+
 def test_null_handle_calls_are_rejected():
     L = mhc.load()
     assert L.mhc_push(None, None, None, 1, 0) == 1
     assert L.mhc_sync(None) == 1
     assert L.mhc_reset(None) == 1
+    best = ctypes.c_int32()
+    assert L.mhc_autotune_k(None, None, 0, ctypes.byref(best), None) == 1
     L.mhc_destroy(None)   # no-op
 
 
 def test_structs_match_header_sizes():
-    # mhc_params: 6 int32 + pointer (8, aligned) + 2 int32 + 6 doubles
-    assert ctypes.sizeof(mhc.MhcParams) == 4 + 4 + 8 + 4 * 6 + 8 * 6
+    # mhc_params: int32 + pointer (8, aligned) + 6 int32 + 6 doubles + int32 (padded to 8)
+    assert ctypes.sizeof(mhc.MhcParams) == 4 + 4 + 8 + 4 * 6 + 8 * 6 + 8
     assert ctypes.sizeof(mhc.MhcInfo) % 8 == 0
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    # the binding's ctypes structures against what a C compiler makes of include/mhc.h
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    fields_p = [f for f, _ in mhc.MhcParams._fields_]
+    fields_i = [f for f, _ in mhc.MhcInfo._fields_]
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "mhc.h"', "int main(void) {",
+           'printf("%zu %zu\\n", sizeof(mhc_params), sizeof(mhc_info));']
+    src += [f'printf("%zu\\n", offsetof(mhc_params, {f}));' for f in fields_p]
+    src += [f'printf("%zu\\n", offsetof(mhc_info, {f}));' for f in fields_i]
+    src += ["return 0; }"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(c), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    vals = [int(x) for x in out]
+    assert vals[0] == ctypes.sizeof(mhc.MhcParams) and vals[1] == ctypes.sizeof(mhc.MhcInfo)
+    offs = vals[2:]
+    want = [getattr(mhc.MhcParams, f).offset for f in fields_p] + \
+        [getattr(mhc.MhcInfo, f).offset for f in fields_i]
+    assert offs == want

@@ -29,8 +29,9 @@ def system(N, seed, E=None):
 
 
 def handle(s, K, L, precision="fp16x3", B=52):
+    # unsplit d axis, as in the grouped launch, so that solo pushes are bitwise comparable
     from paper_2102_03691_gb300.mhc import ModalHeatCurrent
-    h = ModalHeatCurrent(precision=precision, k_max=K, n_lags=L)
+    h = ModalHeatCurrent(precision=precision, k_max=K, n_lags=L, split_d=1)
     h.set_modes(s["E"], s["mass"], s["f"])
     h.set_bins_uniform(0.0, 52.0, B)
     return h

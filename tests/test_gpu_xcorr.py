@@ -106,7 +106,7 @@ def test_xcorr_in_grouped_pushes_equals_single_handles():
     def handles():
         hs = []
         for E, f, mass, _ in systems:
-            h = ModalHeatCurrent(precision="fp16x3", k_max=K, n_lags=L, xcorr=True)
+            h = ModalHeatCurrent(precision="fp16x3", k_max=K, n_lags=L, xcorr=True, split_d=1)
             h.set_modes(E, mass, f)
             h.set_bins_uniform(0.0, 52.0, B)
             hs.append(h)

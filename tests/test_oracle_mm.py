@@ -101,15 +101,15 @@ def test_bin_scale_is_the_sum_of_mode_magnitudes():
 
 
 def test_check_catches_planted_errors():
-    o = np.array([[1.0, -2.0, 0.0], [0.5, 0.005, 0.0]])
-    S = np.array([[40.0, 40.0, 0.0], [40.0, 40.0, 0.0]])
+    o = np.array([[1.0, -2.0, 0.0], [0.5, 0.05, 0.0]])
+    S = np.array([[4.0, 4.0, 0.0], [4.0, 4.0, 0.0]])
     live = S > 0
-    check(o + 3e-6 * live, o, S)                        # 7.5e-8 of S, at most 6e-6 of |o|
+    check(o + 3e-6 * live, o, S)                        # 7.5e-7 of S, at most 6e-6 of |o|
     g = o.copy()
-    g[1, 1] += 3.9e-4                                   # 9.75e-6 of S; |o| < 0.01 S: no
-    check(g, o, S)                                      # pointwise check, 7.8e-2 of |o| is fine
+    g[1, 1] += 3.9e-5                                   # 9.75e-6 of S; |o| < 0.1 S: no
+    check(g, o, S)                                      # pointwise check, 7.8e-4 of |o| is fine
     g = o.copy()
-    g[1, 1] += 5e-4                                     # 1.25e-5 of S
+    g[1, 1] += 5e-5                                     # 1.25e-5 of S
     with pytest.raises(AssertionError):
         check(g, o, S)
     g = o.copy()
@@ -117,8 +117,8 @@ def test_check_catches_planted_errors():
     with pytest.raises(AssertionError):
         check(g, o, S)
     g = o.copy()
-    g[0, 1] += 3.9e-5                                   # 9.75e-7 of S but 1.95e-5 of |o|,
-    with pytest.raises(AssertionError):                 # and |o| >= 0.01 S (condition <= 100)
+    g[0, 1] += 3.9e-5                                   # 9.75e-6 of S but 1.95e-5 of |o|,
+    with pytest.raises(AssertionError):                 # and |o| >= 0.1 S (condition <= 10)
         check(g, o, S)
     check(g, o, S, pointwise=False)                     # without the pointwise check: passes
-    check(g, o, S, S_wc=10 * S)                         # condition number 200: passes
+    check(g, o, S, S_wc=10 * S)                         # condition number 20: passes
