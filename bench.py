@@ -726,7 +726,7 @@ def main():
     h.set_flags(0)
     info = h.info()
     tile = {"columns": info["tile_n"], "k_per_stage": info["tile_k"], "stages": info["stages"],
-            "cta_pair": bool(info["tile_pair"])}
+            "cta_pair": bool(info["tile_pair"]), "d_splits": info["tile_split"]}
 
     # ---- end to end through the API from pinned host memory: every step uploads its block
     # (the library stages host inputs in two buffers on a copy stream, so the upload of one push
