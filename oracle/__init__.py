@@ -6,7 +6,9 @@ with it.  ``mhc_oracle.c`` holds the plain FP64 loops (Eqs. 10, 13, 16, 17,
 19 and frequency binning; the direction split of Sec. II.A; bin-bin cross-correlations; the SHC correlation and spectrum of Eqs. 20-23);
 ``brute.py`` restates the same definitions with per-atom 3-vectors in scalar
 Python for tiny systems.  ``modal_current_mm`` below writes the projections of Eqs. 13
-and 16 as FP64 matrix products for full-size systems.
+and 16 as FP64 matrix products for full-size systems.  ``lattice_modes`` is the Gamma-point
+lattice-dynamics eigen-solve (cyclic Jacobi) that produces eigenvectors and frequencies
+from force constants (Sec. II.B).
 
 This module compiles ``mhc_oracle.c`` with gcc on first use (or through
 ``build()``) and wraps it with ctypes and numpy.
@@ -68,6 +70,8 @@ def lib():
             L.orc_shc_kappa.argtypes = [_i32, _p, _p, _dbl, _dbl, _dbl, _dbl, _i32, _i32, _p, _p]
             L.orc_orthonormality.argtypes = [_i64, _i64, _p]
             L.orc_orthonormality.restype = _dbl
+            L.orc_lattice_modes.argtypes = [_i64, _p, _p, _i32, _dbl, _p, _p, _p]
+            L.orc_lattice_modes.restype = _i32
             _lib = L
     return _lib
 
@@ -293,3 +297,22 @@ def shc_kappa(Ksum, count, dt_ps: float, T_K: float, V_A3: float, Fe: float, f_T
     lib().orc_shc_kappa(nc, _ptr(Ksum), _ptr(count), dt_ps, T_K, V_A3, Fe, window, f.shape[0],
                         _ptr(f), _ptr(out))
     return out
+
+
+def lattice_modes(Phi, mass, max_sweeps: int = 60, tol: float = 1e-15):
+    """Gamma-point eigenmodes of the force constants Phi [3N][3N] (eV/A^2) and masses [N] (amu)
+    (Sec. II.B): w2 [3N] ascending (eV/(A^2 amu)), f_THz [3N], E [3N][3N] dof-major (column n
+    = eigenvector n, sign fixed by its first largest-magnitude component), and the sweeps taken
+    (cyclic Jacobi, FP64; -1 if max_sweeps ran out)."""
+    Phi = np.ascontiguousarray(Phi, dtype=np.float64)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    N = mass.shape[0]
+    D = 3 * N
+    if Phi.shape != (D, D):
+        raise ValueError("Phi must be [3N][3N]")
+    w2 = np.empty(D)
+    f = np.empty(D)
+    E = np.empty((D, D))
+    sweeps = lib().orc_lattice_modes(N, _ptr(Phi), _ptr(mass), max_sweeps, tol, _ptr(w2), _ptr(f),
+                                     _ptr(E))
+    return w2, f, E, int(sweeps)

@@ -400,3 +400,101 @@ void orc_shc_kappa(int32_t nc, const double *Ksum, const int64_t *count, double 
                 Fe > 0 ? 2.0 * Kt / (V_A3 * T_K * Fe) * ORC_WMK_PER_EV_PS_A_K : 0.0;
         }
 }
+
+/*
+ * Gamma-point lattice dynamics (Sec. II.B: the 3N eigenmodes of the harmonic solid whose
+ * eigenvectors e_{i,n} and frequencies the modal analysis uses; Sec. III.C: O(N^3) time,
+ * O(N^2) memory).  With force constants Phi[3i+a][3j+b] (eV/A^2, symmetric) and masses m_i
+ * (amu), the dynamical matrix
+ *   Dyn[3i+a][3j+b] = Phi[3i+a][3j+b] / sqrt(m_i m_j)
+ * has the eigenpairs Dyn e_n = w_n^2 e_n.  w^2 comes out in eV/(A^2 amu); times
+ * 9648.533212331 (1 eV/amu in A^2/ps^2) it is in rad^2/ps^2, and f_n = w_n / (2 pi) in THz
+ * (a negative w^2 gives a negative frequency).
+ * Method: cyclic Jacobi rotations over the pairs p < q in row order; each rotation J in the
+ * (p, q) plane (J_pp = J_qq = c, J_pq = s, J_qp = -s, t = s/c the smaller root of
+ * t^2 + 2 theta t - 1 = 0 with theta = (a_qq - a_pp) / (2 a_pq)) replaces A by J^T A J, which
+ * zeroes a_pq, and the eigenvector matrix V by V J.  Sweeps stop once the off-diagonal
+ * Frobenius norm is at most tol times the Frobenius norm of A.
+ * Output: w2[n], f_THz[n] in ascending order of w2 (stable), E[d * D + n] = component d of
+ * eigenvector n (dof-major), each eigenvector's sign chosen so that its first component of
+ * largest magnitude is positive.  Returns the number of sweeps, -1 if max_sweeps was reached.
+ */
+int32_t orc_lattice_modes(int64_t N, const double *Phi, const double *mass, int32_t max_sweeps,
+                          double tol, double *w2, double *f_THz, double *E)
+{
+    const int64_t D = 3 * N;
+    double *A = (double *)malloc(sizeof(double) * (size_t)(D * D));
+    double *V = (double *)malloc(sizeof(double) * (size_t)(D * D));
+    for (int64_t r = 0; r < D; ++r)
+        for (int64_t c = 0; c < D; ++c) {
+            A[r * D + c] = Phi[r * D + c] / sqrt(mass[r / 3] * mass[c / 3]);
+            V[r * D + c] = r == c ? 1.0 : 0.0;
+        }
+    int32_t sweeps = -1;
+    for (int32_t sw = 0; sw <= max_sweeps; ++sw) {
+        double off = 0.0, tot = 0.0;
+        for (int64_t r = 0; r < D; ++r)
+            for (int64_t c = 0; c < D; ++c) {
+                const double x = A[r * D + c] * A[r * D + c];
+                tot += x;
+                if (r != c) off += x;
+            }
+        if (sqrt(off) <= tol * sqrt(tot)) {
+            sweeps = sw;
+            break;
+        }
+        if (sw == max_sweeps) break;
+        for (int64_t p = 0; p < D - 1; ++p)
+            for (int64_t q = p + 1; q < D; ++q) {
+                const double apq = A[p * D + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[q * D + q] - A[p * D + p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int64_t k = 0; k < D; ++k) {   /* columns: A J */
+                    const double akp = A[k * D + p], akq = A[k * D + q];
+                    A[k * D + p] = c * akp - s * akq;
+                    A[k * D + q] = s * akp + c * akq;
+                }
+                for (int64_t k = 0; k < D; ++k) {   /* rows: J^T (A J) */
+                    const double apk = A[p * D + k], aqk = A[q * D + k];
+                    A[p * D + k] = c * apk - s * aqk;
+                    A[q * D + k] = s * apk + c * aqk;
+                }
+                A[p * D + q] = 0.0;
+                A[q * D + p] = 0.0;
+                for (int64_t k = 0; k < D; ++k) {   /* eigenvectors: V J */
+                    const double vkp = V[k * D + p], vkq = V[k * D + q];
+                    V[k * D + p] = c * vkp - s * vkq;
+                    V[k * D + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    /* ascending order of the eigenvalues (stable insertion sort of an index array) */
+    int64_t *ord = (int64_t *)malloc(sizeof(int64_t) * (size_t)D);
+    for (int64_t n = 0; n < D; ++n) {
+        int64_t j = n;
+        while (j > 0 && A[ord[j - 1] * D + ord[j - 1]] > A[n * D + n]) {
+            ord[j] = ord[j - 1];
+            --j;
+        }
+        ord[j] = n;
+    }
+    const double PI = 3.14159265358979323846;
+    for (int64_t n = 0; n < D; ++n) {
+        const int64_t src = ord[n];
+        const double lam = A[src * D + src];
+        w2[n] = lam;
+        const double w = sqrt(fabs(lam) * 9648.533212331);
+        f_THz[n] = (lam < 0.0 ? -w : w) / (2.0 * PI);
+        int64_t big = 0;
+        for (int64_t d = 1; d < D; ++d)
+            if (fabs(V[d * D + src]) > fabs(V[big * D + src])) big = d;
+        const double sg = V[big * D + src] < 0.0 ? -1.0 : 1.0;
+        for (int64_t d = 0; d < D; ++d) E[d * D + n] = sg * V[d * D + src];
+    }
+    free(ord);
+    free(A);
+    free(V);
+    return sweeps;
+}

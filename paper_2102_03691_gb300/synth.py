@@ -80,6 +80,40 @@ def eigvecs_device(D: int, M: int, seed: int, device="cuda"):
     return (Q * s[None, :]).contiguous()
 
 
+def force_constants(dims: tuple, seed: int, k_long=(6.0, 12.0), k_trans=(0.5, 2.0)) -> np.ndarray:
+    """Seeded harmonic force constants Phi [3N][3N] (eV/A^2) of a periodic simple-cubic
+    spring network with dims = (n1, n2, n3) cells of one atom (N = n1 n2 n3), the stand-in for
+    the lattice dynamics of a relaxed structure (Sec. II.B; no potential exists here).  Each
+    nearest-neighbour bond i-j along unit vector u gets a seeded stiffness tensor
+    K = k_L u u^T + k_T (I - u u^T) (k_L, k_T uniform on the given ranges), and
+    Phi_ij = -K (i != j), Phi_ii = sum_j K: symmetric, positive semi-definite, with the three
+    uniform translations as its zero modes (acoustic sum rule)."""
+    n1, n2, n3 = dims
+    N = n1 * n2 * n3
+    rng = _rng(seed + 6700417)
+    Phi = np.zeros((3 * N, 3 * N))
+
+    def idx(a, b, c):
+        return ((a % n1) * n2 + (b % n2)) * n3 + (c % n3)
+    for a in range(n1):
+        for b in range(n2):
+            for c in range(n3):
+                i = idx(a, b, c)
+                for ax, j in ((0, idx(a + 1, b, c)), (1, idx(a, b + 1, c)), (2, idx(a, b, c + 1))):
+                    kl = rng.uniform(*k_long)
+                    kt = rng.uniform(*k_trans)
+                    if j == i:
+                        continue
+                    u = np.zeros(3)
+                    u[ax] = 1.0
+                    K = kl * np.outer(u, u) + kt * (np.eye(3) - np.outer(u, u))
+                    Phi[3 * i:3 * i + 3, 3 * j:3 * j + 3] -= K
+                    Phi[3 * j:3 * j + 3, 3 * i:3 * i + 3] -= K
+                    Phi[3 * i:3 * i + 3, 3 * i:3 * i + 3] += K
+                    Phi[3 * j:3 * j + 3, 3 * j:3 * j + 3] += K
+    return Phi
+
+
 def frequencies(M: int, f_lo: float, f_hi: float, seed: int) -> np.ndarray:
     """i.i.d. uniform mode frequencies on [f_lo, f_hi) THz, float64."""
     return _rng(seed + 7919).uniform(f_lo, f_hi, size=M)
