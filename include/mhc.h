@@ -169,7 +169,7 @@ mhc_status mhc_create(mhc_handle **h, const mhc_params *p);
 void mhc_destroy(mhc_handle *h);
 
 /* Message of the last error on h (empty string if none); valid until the next call on h.
- * With h == NULL, the last error of a failed mhc_create on this thread. */
+ * With h == NULL, the last error of a failed mhc_create or mhc_lattice_modes on this thread. */
 const char *mhc_last_error(const mhc_handle *h);
 const char *mhc_status_string(mhc_status s);
 
@@ -381,6 +381,32 @@ mhc_status mhc_shc_read_corr(mhc_shc *s, double *Ksum, int64_t *count, int32_t w
 /* kappa [9][n_freq] for the host array of frequencies f_THz; window 0 (none) or 1 (Hann). */
 mhc_status mhc_shc_read_kappa(mhc_shc *s, const double *f_THz, int32_t n_freq, int32_t window,
                               double *kappa, int32_t where);
+
+/*
+ * Gamma-point lattice dynamics on the GPU (Sec. II.B: the modal analysis projects onto the
+ * 3N eigenmodes of the harmonic solid, found by lattice dynamics with the whole cell as the
+ * unit cell; Sec. III.C: O(N^3) time, O(N^2) memory).  With the force constants Phi and masses
+ * m_i, the dynamical matrix Dyn[3i+a][3j+b] = Phi[3i+a][3j+b] / sqrt(m_i m_j) is diagonalised,
+ * Dyn e_n = w_n^2 e_n, by parallel cyclic Jacobi rotations in FP64 until the off-diagonal
+ * Frobenius norm is at most tol times the total.
+ *   n_atoms    N (at most 10000; the cost grows as (3N)^3 and GB300's FP64 rate is low)
+ *   Phi        [3N][3N] float64, row-major, eV/A^2, symmetric; host or device (where_in)
+ *   mass_amu   [N] host, every m_i > 0
+ *   w2         [3N] host or NULL: w_n^2 in eV/(A^2 amu), ascending
+ *   freq_THz   [3N] host or NULL: f_n = w_n / (2 pi) with w in rad/ps (negative for w^2 < 0)
+ *   E          [3N][3N] float64 or NULL: eigenvectors dof-major, E[d * 3N + n] = component d
+ *              of mode n (the layout mhc_set_modes takes as MHC_DOF_MAJOR), each signed so its
+ *              first component of largest magnitude is positive; host or device (where_out)
+ *   sweeps     number of sweeps taken (may be NULL)
+ * Allocates its own work space (about 3 (3N)^2 doubles) and synchronises `stream`.  With E on
+ * the device the basis goes from the force constants to mhc_set_modes without leaving the GPU.
+ * Errors (message through mhc_last_error(NULL)): INVALID_ARG, OOM, CUDA, STATE (not converged
+ * within max_sweeps).
+ */
+mhc_status mhc_lattice_modes(int32_t device, void *stream, int64_t n_atoms, const double *Phi,
+                             const double *mass_amu, int32_t where_in, double tol,
+                             int32_t max_sweeps, double *w2, double *freq_THz, double *E,
+                             int32_t where_out, int32_t *sweeps);
 
 /*
  * No-allocation variant of one block's binned modal current.  The paper has no

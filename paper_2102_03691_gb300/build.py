@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmhc.so")
 SOURCES = ["mhc_api.cu", "k_pack.cu", "k_prep.cu", "k_fp32.cu", "k_tc.cu", "k_reduce.cu",
-           "noalloc.cu", "shc.cu", "k_shc_tc.cu", "k_xcorr.cu"]
+           "noalloc.cu", "shc.cu", "k_shc_tc.cu", "k_xcorr.cu", "k_lattice.cu"]
 HEADERS = ["common.cuh", "kernels.h", os.path.join("..", "..", "include", "mhc.h")]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

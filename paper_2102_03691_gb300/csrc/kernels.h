@@ -11,6 +11,7 @@ enum Split { SPLIT_FP32 = 0, SPLIT_BF16 = 1, SPLIT_FP16 = 2 };
 
 constexpr int TC_MAX_GROUP = 16;  // systems per grouped launch
 constexpr int TC_MAX_SPLIT = 16;  // d-axis splits of one projection
+constexpr double A2_PS2_PER_EV_AMU = 9648.533212331;   // 1 eV/amu in A^2/ps^2
 
 // Sticky device status codes (same values as mhc_status).
 constexpr int DEV_OK = 0, DEV_TIMEOUT = 4, DEV_STATE = 5;
@@ -282,5 +283,8 @@ cudaError_t launch_bin_xcorr(const XcPlan &pl, XcTcParams p, const float *ring, 
 void launch_xcorr_transpose(const float2 *X, int nb, int L, double *out, cudaStream_t s);
 // count[l] = max(T_s - l, 0)
 void launch_lag_counts(long long T_s, int L, long long *count, cudaStream_t s);
+
+// Message of the last failed call without a handle (read through mhc_last_error(NULL)).
+void set_handleless_error(const char *msg);
 
 }  // namespace mhc

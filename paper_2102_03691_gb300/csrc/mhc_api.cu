@@ -24,13 +24,17 @@
 using namespace mhc;
 
 namespace {
+thread_local std::string g_create_error;
+}  // namespace
+
+void mhc::set_handleless_error(const char *msg) { g_create_error = msg; }
+
+namespace {
 
 constexpr double KB_EV_PER_K = 8.617333262145179e-5;   // k_B / e (SI exact ratio)
 constexpr double WMK_PER_EV_PS_A_K = 1602.176634;      // 1 eV/(ps A K) in W/(m K)
 constexpr int K_MAX_LIMIT = 1024;
 constexpr uint32_t STATE_MAGIC = 0x4d484331u;         // "MHC1"
-
-thread_local std::string g_create_error;
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 

@@ -31,7 +31,7 @@ FLAG_XCORR = 0x20
 EXPORTS = (
     "mhc_default_params", "mhc_create", "mhc_destroy", "mhc_last_error", "mhc_status_string",
     "mhc_set_modes", "mhc_set_bins_uniform", "mhc_set_bin_ids", "mhc_push", "mhc_sync",
-    "mhc_autotune_k",
+    "mhc_autotune_k", "mhc_lattice_modes",
     "mhc_read_binned_current", "mhc_read_total_current", "mhc_read_hnema", "mhc_read_corr",
     "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_set_flags",
     "mhc_kernel_time", "mhc_read_xcorr", "mhc_read_kappa_xcorr",
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_push.argtypes = [vp, vp, vp, i32, i32]
     L.mhc_sync.argtypes = [vp]
     L.mhc_autotune_k.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
+    L.mhc_lattice_modes.argtypes = [i32, vp, i64, vp, vp, i32, dbl, i32, vp, vp, vp, i32,
+                                    ctypes.POINTER(i32)]
     L.mhc_read_binned_current.argtypes = [vp, vp, i32]
     L.mhc_read_total_current.argtypes = [vp, vp, i32]
     L.mhc_read_hnema.argtypes = [vp, vp, vp, i32]
@@ -273,6 +275,38 @@ class SpectralHeatCurrent:
             pass
 
 
+def lattice_modes(Phi, mass_amu, E_out=None, device: int = 0, stream=None, tol: float = 1e-14,
+                  max_sweeps: int = 60):
+    """mhc_lattice_modes: Gamma-point eigenmodes of the force constants Phi [3N][3N] (float64,
+    numpy or CUDA tensor) with masses [N].  Returns (w2, freq_THz, E, sweeps): w2 and the
+    frequencies as numpy arrays; E [3N][3N] dof-major float64 written into E_out (a CUDA tensor,
+    so that the basis stays on the GPU) or returned as a numpy array when E_out is None."""
+    L = load()
+    pphi, wphi, kphi = _ptr(Phi, np.float64)
+    mass = np.ascontiguousarray(mass_amu, dtype=np.float64)
+    N = mass.shape[0]
+    D = 3 * N
+    n_phi = kphi.numel() if _is_torch(kphi) else kphi.size
+    if n_phi != D * D:
+        raise ValueError(f"Phi must be [{D}][{D}]")
+    w2 = np.empty(D)
+    f = np.empty(D)
+    if E_out is None:
+        E = np.empty((D, D))
+        pe, we, ke = E.ctypes.data_as(ctypes.c_void_p), MEM_HOST, E
+    else:
+        pe, we, ke = _ptr(E_out, np.float64)
+        E = E_out
+    sweeps = ctypes.c_int32()
+    st = L.mhc_lattice_modes(device, stream if stream is not None else _current_stream(device), N,
+                             pphi, mass.ctypes.data_as(ctypes.c_void_p), wphi, tol, max_sweeps,
+                             w2.ctypes.data_as(ctypes.c_void_p), f.ctypes.data_as(ctypes.c_void_p),
+                             pe, we, ctypes.byref(sweeps))
+    if st != MHC_OK:
+        raise MhcError(st, L.mhc_last_error(None).decode())
+    return w2, f, E, int(sweeps.value)
+
+
 def binned_current_noalloc(E_mode_major, bin_of_mode, n_bins: int, mass_amu, v, W, Jb, J,
                            device: int = 0, stream=None) -> None:
     """mhc_binned_current_noalloc on torch CUDA tensors (see include/mhc.h): one block's
@@ -406,6 +440,18 @@ class ModalHeatCurrent:
         self.N = N
         self.M = M
         return self._check(st)
+
+    def set_modes_from_force_constants(self, Phi, mass_amu, tol: float = 1e-14):
+        """Gamma-point lattice dynamics of the force constants on the GPU (mhc_lattice_modes)
+        and its eigenvectors loaded with mhc_set_modes straight from device memory; returns
+        the frequencies (THz) for the binning."""
+        import torch
+        N = np.asarray(mass_amu).shape[0]
+        E = torch.empty((3 * N, 3 * N), dtype=torch.float64, device=f"cuda:{self.device}")
+        _, f, _, _ = lattice_modes(Phi, mass_amu, E_out=E, device=self.device,
+                                   stream=self.params.stream, tol=tol)
+        self.set_modes(E, mass_amu, f)
+        return f
 
     def set_bins_uniform(self, f_min: float, f_max: float, n_bins: int):
         self._check(self._L.mhc_set_bins_uniform(self._h, f_min, f_max, n_bins))
