@@ -195,9 +195,12 @@ class Trajectory:
 # Workload shapes (stand-ins for the paper's systems; Sec. III.A and III.C).
 # Si volume 20.02 A^3/atom; graphene / CNT wall 2.619 A^2 x 3.35 A = 8.77 A^3/atom.
 WORKLOADS = {
+    # K is autotuned here (the block length is not fixed by the workload): candidates that
+    # divide the 1000-step run
     "gkma_si_n512": dict(N=512, M=1536, mass=28.085, f=(0.0, 16.0), B=100,
                          T_s=1000, K=250, L=200, dt_ps=0.010, V_per_atom=20.02,
-                         T_K=300.0, Fe=(1e-5, 0.0, 0.0), gkma=True, seed=20210205),
+                         T_K=300.0, Fe=(1e-5, 0.0, 0.0), gkma=True, seed=20210205,
+                         K_candidates=(125, 250, 500, 1000)),
     "hnema_graphene_n4096": dict(N=4096, M=12288, mass=12.011, f=(0.0, 50.0), B=200,
                                  T_s=20000, K=128, L=0, dt_ps=0.008, V_per_atom=8.77,
                                  T_K=300.0, Fe=(1e-5, 0.0, 0.0), gkma=False,
