@@ -328,8 +328,10 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
     }
 }
 
+// Shared memory (48 B an atom) allows four CTAs of 256 threads (two of 512) per SM; the
+// register cap of the launch bounds lets as many be resident.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) pack_bulk_kernel(const PackArgs a) {
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 4 : 2) pack_bulk_kernel(const PackArgs a) {
     const uint32_t nrank = cluster_nctarank();
     pack_bulk_body<THREADS>(a, (int)(blockIdx.x / nrank), cluster_ctarank(), nrank);
 }
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(THREADS) pack_bulk_kernel(const PackArgs a) {
 // clusters of the common cluster size; ranks beyond a system's atoms hold no atoms and only
 // take part in the cluster's combination).
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) pack_bulk_group_kernel(const __grid_constant__ PackGroupArgs g) {
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 4 : 2) pack_bulk_group_kernel(const __grid_constant__ PackGroupArgs g) {
     int j = 0;
     while (j + 1 < g.n && (int)blockIdx.x >= g.cta_begin[j + 1]) ++j;
     const uint32_t nrank = cluster_nctarank();
