@@ -360,10 +360,9 @@ def run_group(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sizes = synth.cnt_group_sizes()
-    K, B, P = 128, 52, 4
-    handles, pools, hpools = [], [], []
-    units_per_step = 0.0
-    flops_launch = 0.0
+    B, P = 52, 4
+    K_CAND = (64, 128, 256)       # block lengths the group's K autotuner chooses from
+    handles, pools, hpools, trajs = [], [], [], []
     for j, N in enumerate(sizes):
         seed = 20210208 + 100 * j + 1000 * rank
         D = 3 * N
@@ -377,20 +376,26 @@ def run_group(args):
         mass = synth.masses(N, 12.011)
         V = N * 8.77
         g_drive = synth.drive_coupling(2100.0, 300.0, V, 2e-6, mass)
-        h = ModalHeatCurrent(precision=args.precision, k_max=K, dt_ps=0.008, T_K=300.0, V_A3=V,
-                             F_e=(2e-6, 0.0, 0.0), device=local, tile_config=args.tile_config)
+        h = ModalHeatCurrent(precision=args.precision, k_max=max(K_CAND), dt_ps=0.008, T_K=300.0,
+                             V_A3=V, F_e=(2e-6, 0.0, 0.0), device=local, tile_config=args.tile_config)
         h.set_modes(E, mass, f)
         h.set_bins_uniform(0.0, 52.0, B)
         del E
-        tr = synth.Trajectory(mass, drive_g=g_drive, seed=seed)
+        trajs.append(synth.Trajectory(mass, drive_g=g_drive, seed=seed))
+        handles.append(h)
+    grp = ModalHeatCurrentGroup(handles)
+    # the group's block length from its K autotuner (grouped packs + projection timed per K)
+    K, k_rate = grp.autotune_k(list(K_CAND))
+    units_per_step = 0.0
+    flops_launch = 0.0
+    for N, tr in zip(sizes, trajs):
+        D = 3 * N
         blocks = [tr.next_block(K) for _ in range(P)]
         hpools.append([(torch.from_numpy(v).pin_memory(), torch.from_numpy(W).pin_memory())
                        for v, W in blocks])
         pools.append([(hv.to(dev), hw.to(dev)) for hv, hw in hpools[-1]])
-        handles.append(h)
         units_per_step += float(D) * N * K
         flops_launch += 3 * 2.0 * D * D * 4 * K
-    grp = ModalHeatCurrentGroup(handles)
     out_dev = torch.empty(len(handles) * B * 3, dtype=torch.float64, device=dev)
     n_e2e = max(3, args.e2e_steps)   # its own step count: the loop is host-driven
     out_host = torch.empty((n_e2e, len(handles) * B * 3), dtype=torch.float64).pin_memory()
@@ -460,7 +465,10 @@ def run_group(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": "cnt_group16", "systems": len(sizes), "N_atoms": sizes,
-                   "K_steps_per_block": K, "bins": B, "hnema": True, "precision": args.precision,
+                   "K_steps_per_block": K,
+                   "K_autotune": {"candidates": list(K_CAND), "chosen": K,
+                                  "kernel_units_per_s": k_rate},
+                   "bins": B, "hnema": True, "precision": args.precision,
                    "l2": "inputs larger than L2 (sum of eigenvector bytes streamed every step)"},
         "roofline": {"bound": "tensor", "kernel": "tc_modal_kernel (grouped)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,

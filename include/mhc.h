@@ -334,6 +334,15 @@ void mhc_group_destroy(mhc_group *g);
  * handle times the grouped tensor-core launches. */
 mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *const *W,
                           const int32_t *K, int32_t where);
+/* Block length of the group (every member pushes K steps): for each of the n candidates times
+ * three grouped pushes' packs and grouped projection (the group's tile shape autotuned on the
+ * first candidate if it was not yet) on constant synthetic blocks, and returns in *best_K the
+ * candidate with the most mode*atom*steps per second (summed over the members; the rate in
+ * *units_per_s, may be NULL).  No accumulator changes; the members' last-block operands are
+ * overwritten (their binned and total currents are unreadable until the next push).
+ * Synchronises the stream.  Errors: INVALID_ARG (a candidate above a member's k_max), CUDA. */
+mhc_status mhc_group_autotune_k(mhc_group *g, const int32_t *candidates, int32_t n, int32_t *best_K,
+                                double *units_per_s);
 /* HNEMA read-out (as mhc_read_hnema) of every member in one call: kappa and mean_J receive
  * the members' [B_j][3] arrays one after another (either may be NULL); host outputs cost one
  * synchronisation for the whole group. */

@@ -1834,6 +1834,71 @@ mhc_status mhc_group_read_hnema(mhc_group *g, double *kappa, double *mean_J, int
     return MHC_OK;
 }
 
+mhc_status mhc_group_autotune_k(mhc_group *g, const int32_t *candidates, int32_t n, int32_t *best_K,
+                                double *units_per_s) {
+    if (!g) return MHC_ERR_INVALID_ARG;
+    mhc_handle *h0 = g->hs[0];
+    if (!candidates || n < 1 || !best_K) return fail(h0, MHC_ERR_INVALID_ARG, "need candidates and best_K");
+    const size_t m = g->hs.size();
+    for (int32_t q = 0; q < n; ++q)
+        for (size_t j = 0; j < m; ++j)
+            if (candidates[q] < 1 || candidates[q] > g->hs[j]->prm.k_max)
+                return fail(h0, MHC_ERR_INVALID_ARG, "candidate K=%d outside [1, k_max] of system %zu",
+                            candidates[q], j);
+    MHC_CUDA(h0, cudaSetDevice(h0->prm.device));
+    // constant, finite samples of the largest K in every member's first staging pair, after
+    // whatever may still read those pairs
+    std::vector<const float *> vs(m), ws(m);
+    for (size_t j = 0; j < m; ++j) {
+        mhc_handle *h = g->hs[j];
+        MHC_CUDA(h0, cudaStreamSynchronize(h->stream));
+        if (h->copy_stream) MHC_CUDA(h0, cudaStreamSynchronize(h->copy_stream));
+        float *v = dptr<float>(h, "v_stage"), *W = dptr<float>(h, "W_stage");
+        MHC_CUDA(h0, cudaMemsetAsync(v, 0x3f, sizeof(float) * h->prm.k_max * h->N * 3, h0->stream));
+        MHC_CUDA(h0, cudaMemsetAsync(W, 0x3f, sizeof(float) * h->prm.k_max * h->N * 9, h0->stream));
+        vs[j] = v;
+        ws[j] = W;
+    }
+    double units_per_step = 0.0;   // mode * atom per step summed over the members
+    for (size_t j = 0; j < m; ++j) units_per_step += (double)g->hs[j]->M_eff * (double)g->hs[j]->N;
+    cudaEvent_t e0, e1;
+    MHC_CUDA(h0, cudaEventCreate(&e0));
+    MHC_CUDA(h0, cudaEventCreate(&e1));
+    mhc_status s = MHC_OK;
+    double best = -1.0;
+    int32_t bestK = candidates[0];
+    for (int32_t q = 0; q < n && s == MHC_OK; ++q) {
+        const std::vector<int> Ks(m, candidates[q]);
+        if ((s = group_pack(g, vs, ws, Ks)) != MHC_OK) break;
+        if (!g->tuned && h0->prm.tile_config == 0 && (s = group_autotune(g, Ks)) != MHC_OK) break;
+        const int reps = 3;
+        cudaError_t e = cudaEventRecord(e0, h0->stream);
+        for (int r = 0; r < reps && s == MHC_OK; ++r)
+            if ((s = group_pack(g, vs, ws, Ks)) == MHC_OK) s = group_launch(g, Ks);
+        if (s != MHC_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h0->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            s = fail(h0, MHC_ERR_CUDA, "timing of K=%d failed: %s", candidates[q], cudaGetErrorString(e));
+            break;
+        }
+        const double rate = ms > 0 ? reps * units_per_step * candidates[q] / (ms * 1e-3) : 0.0;
+        if (rate > best) {
+            best = rate;
+            bestK = candidates[q];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != MHC_OK) return s;
+    for (size_t j = 0; j < m; ++j) g->hs[j]->K_last = 0;   // operands overwritten
+    *best_K = bestK;
+    if (units_per_s) *units_per_s = best;
+    return MHC_OK;
+}
+
 mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *const *W,
                           const int32_t *K, int32_t where) {
     if (!g || !v || !W || !K) return MHC_ERR_INVALID_ARG;

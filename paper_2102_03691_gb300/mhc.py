@@ -31,7 +31,7 @@ FLAG_XCORR = 0x20
 EXPORTS = (
     "mhc_default_params", "mhc_create", "mhc_destroy", "mhc_last_error", "mhc_status_string",
     "mhc_set_modes", "mhc_set_bins_uniform", "mhc_set_bin_ids", "mhc_push", "mhc_sync",
-    "mhc_autotune_k", "mhc_lattice_modes",
+    "mhc_autotune_k", "mhc_lattice_modes", "mhc_group_autotune_k",
     "mhc_read_binned_current", "mhc_read_total_current", "mhc_read_hnema", "mhc_read_corr",
     "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_set_flags",
     "mhc_kernel_time", "mhc_read_xcorr", "mhc_read_kappa_xcorr",
@@ -123,6 +123,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_group_push.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                  ctypes.POINTER(i32), i32]
     L.mhc_group_read_hnema.argtypes = [vp, vp, vp, i32]
+    L.mhc_group_autotune_k.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     L.mhc_shc_create.argtypes = [ctypes.POINTER(vp), i32, vp, i64, i32, i32, dbl, dbl, dbl, vp]
     L.mhc_shc_destroy.argtypes = [vp]
     L.mhc_shc_destroy.restype = None
@@ -157,6 +158,20 @@ class ModalHeatCurrentGroup:
         if st != MHC_OK:
             raise MhcError(st, self._L.mhc_last_error(self.members[0]._h).decode())
         self._g = g
+
+    def autotune_k(self, candidates):
+        """mhc_group_autotune_k: the block length (for every member) with the most
+        mode*atom*steps per second, and that rate."""
+        c = np.ascontiguousarray(candidates, dtype=np.int32)
+        best = ctypes.c_int32()
+        rate = ctypes.c_double()
+        st = self._L.mhc_group_autotune_k(self._g, c.ctypes.data_as(ctypes.c_void_p), c.size,
+                                          ctypes.byref(best), ctypes.byref(rate))
+        if st != MHC_OK:
+            raise MhcError(st, self._L.mhc_last_error(self.members[0]._h).decode())
+        for m in self.members:
+            m._lastK = 0
+        return int(best.value), float(rate.value)
 
     def push(self, vs, Ws):
         n = len(self.members)

@@ -204,3 +204,32 @@ def test_group_pack_large_system_uses_wide_ctas():
             np.testing.assert_array_equal(hs.read_binned_current(), hg.read_binned_current())
             np.testing.assert_array_equal(hs.read_total_current(), hg.read_total_current())
     grp.close()
+
+
+def test_group_autotune_k_leaves_the_accumulators_alone():
+    # mhc_group_autotune_k times grouped packs and projections on synthetic blocks: the
+    # members' sums afterwards are bitwise those of a group that never ran it
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import MhcError, ModalHeatCurrentGroup
+    sizes, L = [120, 80, 200], 6
+    systems = [system(N, 1400 + j) for j, N in enumerate(sizes)]
+    blocks = [[s["tr"].next_block(16) for _ in range(2)] for s in systems]
+    out = []
+    for tune in (True, False):
+        hs = [handle(s, 32, L) for s in systems]
+        grp = ModalHeatCurrentGroup(hs)
+        if tune:
+            hs[0].push(*blocks[0][0])            # one solo push first: its reads then fail
+            best, rate = grp.autotune_k([8, 16, 32])
+            assert best in (8, 16, 32) and rate > 0
+            with pytest.raises(MhcError):
+                hs[0].read_total_current()
+            hs[0].reset()
+        for step in range(2):
+            grp.push([bl[step][0] for bl in blocks], [bl[step][1] for bl in blocks])
+        out.append(([h.read_corr()[0] for h in hs], [h.read_hnema()[0] for h in hs],
+                    [h.read_binned_current() for h in hs]))
+        grp.close()
+    for a, b in zip(out[0], out[1]):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
