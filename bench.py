@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-config", type=int, default=0,
                     help="tensor-core tile shape (0 = autotune, 1..4 as in include/mhc.h)")
+    ap.add_argument("--split-d", type=int, default=0,
+                    help="d-axis split of the projection (0 = autotune, 1 = none, 2..16 uniform "
+                         "ranges, -1 = balanced; include/mhc.h)")
     ap.add_argument("--basis", default="qr", choices=["qr", "gaussian"],
                     help="qr: orthonormal E from a seeded QR; gaussian: seeded N(0, 1/3N) "
                          "entries (same sizes and work, for tools that cannot load torch.linalg)")
@@ -687,7 +690,8 @@ def main():
         h = ModalHeatCurrent(precision=precision, k_max=K, n_lags=L, dt_ps=w["dt_ps"],
                              T_K=w["T_K"], V_A3=V, F_e=w["Fe"], device=local,
                              tile_config=args.tile_config, direction=args.direction,
-                             xcorr=args.xcorr and L > 0)
+                             xcorr=args.xcorr and L > 0,
+                             split_d=0 if args.precision == "fp32" else args.split_d)
         h.set_modes(E, mass, f)
         h.set_bins_uniform(w["f"][0], w["f"][1], B)
         return h

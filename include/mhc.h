@@ -133,8 +133,11 @@ typedef struct {
                             128-element chunks, run as separate units and added in a fixed order
                             by a finish kernel; it fills the SMs when one block has few tiles):
                             0 = autotuned with the tile shape (tile_config 0) or 1 (tile_config
-                            > 0); 1..16 = fixed.  Not with MHC_FLAG_DIRECTION (must be 0 or 1);
-                            grouped launches run unsplit. */
+                            > 0); 1..16 = fixed; -1 = balanced: the chunks of all tiles, tile
+                            after tile, cut into one range of equal length per CTA (or CTA
+                            pair), a tile cut by a range boundary finished by the same kernel.
+                            Not with MHC_FLAG_DIRECTION (must be 0 or 1); grouped launches run
+                            unsplit. */
 } mhc_params;
 
 /* Counters and derived sizes of a handle. */
@@ -152,7 +155,8 @@ typedef struct {
     int64_t device_bytes;        /* device memory owned by the handle */
     int64_t kernel_launches;     /* kernels launched by the handle so far (graph nodes included) */
     int64_t graph_replays;       /* pushes executed by replaying a captured CUDA graph */
-    int32_t tile_split;          /* d-axis splits of the current tile configuration (1: none) */
+    int32_t tile_split;          /* d-axis splits of the current tile configuration (1: none,
+                                    -1: balanced) */
 } mhc_info;
 
 /* Fill *p with defaults: device 0, default stream, k_max 256, no GKMA,

@@ -53,60 +53,97 @@ struct TcLayout {
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM columns");
 };
 
-// Unit t of a single problem -> (mode tile, column tile, d split): the column tiles of one
-// (mode tile, split) are adjacent, so the CTAs that share an E slice run side by side.
-__device__ __forceinline__ void split_unit(const TcProblem &P, int t, int &mt, int &ct, int &sp) {
-    const int S = P.n_split > 1 ? P.n_split : 1;
-    const int per_mt = P.n_col_tiles * S;
-    mt = t / per_mt;
-    const int r = t - mt * per_mt;
-    sp = r / P.n_col_tiles;
-    ct = r - sp * P.n_col_tiles;
+// A unit of work of a CTA (one-SM tiles) or CTA pair: tile (mt, ct) of problem `prob` over the
+// k-blocks [kb_lo, kb_hi).  seg < 0: the whole d axis, so the kernel runs the tile epilogue;
+// seg >= 0: a part of the d axis, whose promoted sums go to split_ws[seg] for the finish kernel.
+struct Unit {
+    int prob, mt, ct, kb_lo, kb_hi, seg;
+};
+
+// Balanced split: the tile-major chunk space (n_tiles tiles x sk_nch promotion chunks, tile =
+// mode tile * n_col_tiles + column tile) cut into sk_parts contiguous ranges of equal length
+// (to one chunk); part q starts at chunk floor(q T / sk_parts).
+__device__ __forceinline__ long long sk_begin(const TcProblem &P, int q) {
+    return (long long)q * ((long long)P.n_tiles * P.sk_nch) / P.sk_parts;
+}
+// The part whose range holds chunk g: the largest q with sk_begin(q) <= g.
+__device__ __forceinline__ int sk_part_of(const TcProblem &P, long long g) {
+    const long long T = (long long)P.n_tiles * P.sk_nch;
+    return (int)(((g + 1) * P.sk_parts + T - 1) / T - 1);
+}
+// Segments of a tile under the balanced split (1: one part holds the whole tile).  Every part
+// holds at least one chunk (sk_parts <= T), so the segments of a tile are the parts that touch
+// it, in chunk order.
+__device__ __forceinline__ int sk_segments(const TcProblem &P, int tile) {
+    const long long g0 = (long long)tile * P.sk_nch;
+    return 1 + sk_part_of(P, g0 + P.sk_nch - 1) - sk_part_of(P, g0);
 }
 
-template <int NPROB>
-struct TileIter {
+// The units of CTA (pair) `part` of `nparts`: a scheduled tile list (grouped launches), the
+// balanced split's chunk range, or round-robin over the units of a single problem (tiles, or
+// tile x range with the uniform split; the column tiles of one (mode tile, range) are
+// adjacent, so the CTAs that share an E slice run side by side).  CHUNK_KB: k-blocks a chunk.
+template <int NPROB, int CHUNK_KB>
+struct UnitIter {
     const TcParams<NPROB> &p;
-    int i, end;
-    __device__ TileIter(const TcParams<NPROB> &pp) : p(pp) {
+    int i = 0, end = 0, step = 1;
+    long long g = 0, g_end = 0;
+    __device__ UnitIter(const TcParams<NPROB> &pp, int part, int nparts) : p(pp) {
         if (p.sched) {
-            i = p.cta_begin[blockIdx.x];
-            end = p.cta_begin[blockIdx.x + 1];
+            i = p.cta_begin[part];
+            end = p.cta_begin[part + 1];
+        } else if (p.prob[0].sk_parts > 0) {
+            g = sk_begin(p.prob[0], part);
+            g_end = sk_begin(p.prob[0], part + 1);
         } else {
-            i = blockIdx.x;
+            i = part;
             end = p.prob[0].n_tiles;
+            step = nparts;
         }
     }
-    __device__ bool next(int &prob, int &mt, int &ct, int &sp) {
+    __device__ bool next(Unit &u) {
+        const TcProblem &P = p.prob[0];
+        if (!p.sched && P.sk_parts > 0) {
+            if (g >= g_end) return false;
+            const int tile = (int)(g / P.sk_nch);
+            const int c0 = (int)(g - (long long)tile * P.sk_nch);
+            const int c1 = (int)min((long long)P.sk_nch, (long long)c0 + (g_end - g));
+            u.prob = 0;
+            u.mt = tile / P.n_col_tiles;
+            u.ct = tile - u.mt * P.n_col_tiles;
+            u.kb_lo = c0 * CHUNK_KB;
+            u.kb_hi = min(P.n_kb, c1 * CHUNK_KB);
+            u.seg = (c0 == 0 && c1 == P.sk_nch) ? -1 : sk_part_of(P, g) - sk_part_of(P, g - c0);
+            g += c1 - c0;
+            return true;
+        }
         if (i >= end) return false;
         if (p.sched) {
-            const uint32_t id = p.sched[i++];
-            prob = (int)(id >> 28);
-            ct = (int)((id >> 20) & 0xFFu);
-            mt = (int)(id & 0xFFFFFu);
-            sp = 0;
+            const uint32_t id = p.sched[i];
+            u.prob = (int)(id >> 28);
+            u.ct = (int)((id >> 20) & 0xFFu);
+            u.mt = (int)(id & 0xFFFFFu);
+            u.kb_lo = 0;
+            u.kb_hi = p.prob[u.prob].n_kb;
+            u.seg = -1;
         } else {
-            const int t = i;
-            i += gridDim.x;
-            prob = 0;
-            split_unit(p.prob[0], t, mt, ct, sp);
+            const int S = P.n_split > 1 ? P.n_split : 1;
+            const int per_mt = P.n_col_tiles * S;
+            u.prob = 0;
+            u.mt = i / per_mt;
+            const int r = i - u.mt * per_mt;
+            const int sp = r / P.n_col_tiles;
+            u.ct = r - sp * P.n_col_tiles;
+            u.kb_lo = S > 1 ? sp * P.kb_split : 0;
+            u.kb_hi = S > 1 ? min(P.n_kb, u.kb_lo + P.kb_split) : P.n_kb;
+            u.seg = S > 1 ? sp : -1;
         }
+        i += step;
         return true;
     }
 };
 
 constexpr int PROMOTE_D = TC_PROMOTE_D;   // d elements per TMEM chunk accumulator
-
-// k-blocks [lo, hi) of split sp of a tile (the whole d axis without a split).
-__device__ __forceinline__ void kb_range(const TcProblem &P, int sp, int &lo, int &hi) {
-    if (P.n_split > 1) {
-        lo = sp * P.kb_split;
-        hi = min(P.n_kb, lo + P.kb_split);
-    } else {
-        lo = 0;
-        hi = P.n_kb;
-    }
-}
 
 // A split unit's promoted sums (128 columns from col0 of mode n) to the split workspace
 // split_ws[sp][col][mode]: each warp stores 128 contiguous bytes per column.
@@ -150,18 +187,20 @@ __device__ __forceinline__ void dir_maybe_park(float (&acc)[128], const TcProble
         park_y(acc, dir_park_base(P) + (size_t)(kn / P.dir_seg_kb - 1) * DIR_PARK_SEG_FLOATS);
 }
 
-// Eq. 16 product and bin-run sums of one warp's 32 steps kbase .. kbase+31 (those < K), from
+// Eq. 16 product and bin-run sums of one warp's NS steps kbase .. kbase+NS-1 (those < K), from
 // the promoted sums in acc (columns 4s: Xdot, 4s+1+a: the bracket sums): the products
 // overwrite the bracket columns, and each run tail stores its sums to
 // partials[(k*3 + a) * row + col0 + slot].  `sc` holds lane l's four row scales of step
 // kbase + l.  Written to be throughput-bound: the scales come by broadcast shuffles, and the
-// 96 segmented scans advance level by level so that their shuffles overlap (each value still
-// takes the same additions in the same order as a scan on its own).
-__device__ __forceinline__ void epilogue_steps(float (&acc)[128], const float4 sc, const TcProblem &P,
+// 3 NS segmented scans advance level by level so that their shuffles overlap (each value still
+// takes the same additions in the same order as a scan on its own, so any NS gives the same
+// bits for a step).
+template <int NS = 32>
+__device__ __forceinline__ void epilogue_steps(float (&acc)[4 * NS], const float4 sc, const TcProblem &P,
                                                int kbase, uint32_t take, int slot, size_t row,
                                                size_t col0) {
 #pragma unroll
-    for (int s4 = 0; s4 < 32; ++s4) {
+    for (int s4 = 0; s4 < NS; ++s4) {
         const float x = acc[4 * s4] * __shfl_sync(FULL_MASK, sc.x, s4);
         acc[4 * s4 + 1] = x * (acc[4 * s4 + 1] * __shfl_sync(FULL_MASK, sc.y, s4));
         acc[4 * s4 + 2] = x * (acc[4 * s4 + 2] * __shfl_sync(FULL_MASK, sc.z, s4));
@@ -171,7 +210,7 @@ __device__ __forceinline__ void epilogue_steps(float (&acc)[128], const float4 s
     for (int r = 0; r < 5; ++r) {
         const bool add = (take >> r) & 1u;
 #pragma unroll
-        for (int j = 0; j < 96; ++j) {
+        for (int j = 0; j < 3 * NS; ++j) {
             const int c = 4 * (j / 3) + 1 + j % 3;
             const float o = __shfl_up_sync(FULL_MASK, acc[c], 1u << r);
             if (add) acc[c] += o;
@@ -180,7 +219,7 @@ __device__ __forceinline__ void epilogue_steps(float (&acc)[128], const float4 s
     if (slot < 0) return;
     const int nk = P.K - kbase;   // steps of this warp inside the block
 #pragma unroll
-    for (int s4 = 0; s4 < 32; ++s4) {
+    for (int s4 = 0; s4 < NS; ++s4) {
         if (s4 >= nk) break;
         float *dst = P.partials + ((size_t)(kbase + s4) * 3) * row + col0 + (size_t)slot;
         dst[0] = acc[4 * s4 + 1];
@@ -270,13 +309,12 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         for (int s = 0; s < STAGES; ++s) issued[s] = false;
         int stage = 0;
         uint32_t phase = 0;
-        TileIter<NPROB> it(p);
-        int prob, mt, ct, sp;
+        UnitIter<NPROB, CHUNK_KB> it(p, blockIdx.x, gridDim.x);
+        Unit u;
         bool ok = true;
-        while (ok && it.next(prob, mt, ct, sp)) {
-            const TcProblem &P = p.prob[prob];
-            int kb_lo, kb_hi;
-            kb_range(P, sp, kb_lo, kb_hi);
+        while (ok && it.next(u)) {
+            const TcProblem &P = p.prob[u.prob];
+            const int mt = u.mt, ct = u.ct, kb_lo = u.kb_lo, kb_hi = u.kb_hi;
             for (int kb = kb_lo; kb < kb_hi; ++kb) {
                 if (!mbar_wait(&empty[stage], phase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 uint8_t *sa = smem + stage * L::STAGE_BYTES;
@@ -309,14 +347,13 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         const uint32_t idesc = p.idesc;
         int stage = 0, abuf = 0;
         uint32_t phase = 0, aphase = 0;
-        TileIter<NPROB> it(p);
-        int prob, mt, ct, sp;
+        UnitIter<NPROB, CHUNK_KB> it(p, blockIdx.x, gridDim.x);
+        Unit u;
         bool ok = true;
         const uint32_t smem0 = smem_u32(smem);
-        while (ok && it.next(prob, mt, ct, sp)) {
-            const TcProblem &P = p.prob[prob];
-            int kb_lo, kb_hi;
-            kb_range(P, sp, kb_lo, kb_hi);
+        while (ok && it.next(u)) {
+            const TcProblem &P = p.prob[u.prob];
+            const int kb_lo = u.kb_lo, kb_hi = u.kb_hi;
             for (int kb0 = kb_lo; ok && kb0 < kb_hi; kb0 += CHUNK_KB) {
                 if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
@@ -364,13 +401,12 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
         const int ch = (warp - 4) >> 2;   // which 128-column half of the tile
         int abuf = 0;
         uint32_t aphase = 0;
-        TileIter<NPROB> it(p);
-        int prob, mt, ct, sp;
+        UnitIter<NPROB, CHUNK_KB> it(p, blockIdx.x, gridDim.x);
+        Unit u;
         bool ok = true;
-        while (ok && it.next(prob, mt, ct, sp)) {
-            const TcProblem &P = p.prob[prob];
-            int kb_lo, kb_hi;
-            kb_range(P, sp, kb_lo, kb_hi);
+        while (ok && it.next(u)) {
+            const TcProblem &P = p.prob[u.prob];
+            const int mt = u.mt, ct = u.ct, kb_lo = u.kb_lo, kb_hi = u.kb_hi;
             const int n = mt * TC_BM + qw * 32 + lane;
             const int bin = P.mode_bin[n];
             const int slot = P.mode_slot[n];
@@ -398,8 +434,8 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
                 if constexpr (DIR) dir_maybe_park(acc, P, kb0 + CHUNK_KB);
             }
             if (!ok) break;
-            if (P.n_split > 1) {   // the split finish kernel adds the splits and runs the epilogue
-                store_split(acc, P, sp, n, ct * BN + ch * 128);
+            if (u.seg >= 0) {   // the split finish kernel adds the segments and runs the epilogue
+                store_split(acc, P, u.seg, n, ct * BN + ch * 128);
                 continue;
             }
             // Eq. 16 product and the bin-run sums of this warp's 32 steps
@@ -445,38 +481,6 @@ struct TcPairLayout {
     static_assert(BN == 128 || BN == 256, "BN");
     static constexpr int THREADS = 128 + 32 * EPI_WARPS;
     static_assert(STAGES * 2 + 5 <= 28, "barrier area");
-};
-
-template <int NPROB>
-struct PairTileIter {
-    const TcParams<NPROB> &p;
-    int i, end, step;
-    __device__ PairTileIter(const TcParams<NPROB> &pp, int pair, int npairs) : p(pp) {
-        if (p.sched) {
-            i = p.cta_begin[pair];
-            end = p.cta_begin[pair + 1];
-            step = 1;
-        } else {
-            i = pair;
-            end = p.prob[0].n_tiles;
-            step = npairs;
-        }
-    }
-    __device__ bool next(int &prob, int &mp, int &ct, int &sp) {
-        if (i >= end) return false;
-        if (p.sched) {
-            const uint32_t id = p.sched[i];
-            prob = (int)(id >> 28);
-            ct = (int)((id >> 20) & 0xFFu);
-            mp = (int)(id & 0xFFFFFu);
-            sp = 0;
-        } else {
-            prob = 0;
-            split_unit(p.prob[0], i, mp, ct, sp);
-        }
-        i += step;
-        return true;
-    }
 };
 
 template <int BN, int BK, int STAGES, int NPROB, bool DIR>
@@ -538,15 +542,14 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
         for (int s = 0; s < STAGES; ++s) issued[s] = false;
         int stage = 0;
         uint32_t phase = 0;
-        PairTileIter<NPROB> it(p, pair, npairs);
-        int prob, mp, ct, sp;
+        UnitIter<NPROB, CHUNK_KB> it(p, pair, npairs);
+        Unit u;
         bool ok = true;
-        while (ok && it.next(prob, mp, ct, sp)) {
-            const TcProblem &P = p.prob[prob];
-            const int arow = mp * 2 * TC_BM + (int)rank * TC_BM;
-            const int brow = ct * BN + (int)rank * (BN / 2);
-            int kb_lo, kb_hi;
-            kb_range(P, sp, kb_lo, kb_hi);
+        while (ok && it.next(u)) {
+            const TcProblem &P = p.prob[u.prob];
+            const int arow = u.mt * 2 * TC_BM + (int)rank * TC_BM;
+            const int brow = u.ct * BN + (int)rank * (BN / 2);
+            const int kb_lo = u.kb_lo, kb_hi = u.kb_hi;
             for (int kb = kb_lo; kb < kb_hi; ++kb) {
                 if (!mbar_wait(&empty[stage], phase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 if (leader)   // test hook as in the one-SM kernel
@@ -580,14 +583,12 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
         const uint32_t idesc = p.idesc;
         int stage = 0, abuf = 0;
         uint32_t phase = 0, aphase = 0;
-        PairTileIter<NPROB> it(p, pair, npairs);
-        int prob, mp, ct, sp;
+        UnitIter<NPROB, CHUNK_KB> it(p, pair, npairs);
+        Unit u;
         bool ok = true;
         const uint32_t smem0 = smem_u32(smem);
-        while (ok && it.next(prob, mp, ct, sp)) {
-            const TcProblem &P = p.prob[prob];
-            int kb_lo, kb_hi;
-            kb_range(P, sp, kb_lo, kb_hi);
+        while (ok && it.next(u)) {
+            const int kb_lo = u.kb_lo, kb_hi = u.kb_hi;
             for (int kb0 = kb_lo; ok && kb0 < kb_hi; kb0 += CHUNK_KB) {
                 if (!mbar_wait(&acc_empty[abuf], aphase ^ 1u, abort, p.wait_limit)) { ok = false; break; }
                 tc_fence_after();
@@ -635,13 +636,12 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
         uint32_t aphase = 0;
         const uint32_t empty_leader[2] = {mapa_shared(smem_u32(&acc_empty[0]), 0),
                                           mapa_shared(smem_u32(&acc_empty[1]), 0)};
-        PairTileIter<NPROB> it(p, pair, npairs);
-        int prob, mp, ct, sp;
+        UnitIter<NPROB, CHUNK_KB> it(p, pair, npairs);
+        Unit u;
         bool ok = true;
-        while (ok && it.next(prob, mp, ct, sp)) {
-            const TcProblem &P = p.prob[prob];
-            int kb_lo, kb_hi;
-            kb_range(P, sp, kb_lo, kb_hi);
+        while (ok && it.next(u)) {
+            const TcProblem &P = p.prob[u.prob];
+            const int mp = u.mt, ct = u.ct, kb_lo = u.kb_lo, kb_hi = u.kb_hi;
             const int n = mp * 2 * TC_BM + (int)rank * TC_BM + qw * 32 + lane;
             const int bin = P.mode_bin[n];
             const int slot = P.mode_slot[n];
@@ -673,8 +673,8 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
                 if constexpr (DIR) dir_maybe_park(acc, P, kb0 + CHUNK_KB);
             }
             if (!ok) break;
-            if (P.n_split > 1) {   // the split finish kernel adds the splits and runs the epilogue
-                store_split(acc, P, sp, n, ct * BN + ch * 128);
+            if (u.seg >= 0) {   // the split finish kernel adds the segments and runs the epilogue
+                store_split(acc, P, u.seg, n, ct * BN + ch * 128);
                 continue;
             }
             const int kbase = ct * (BN / 4) + ch * 32;
@@ -776,36 +776,69 @@ cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s
     return cudaErrorInvalidValue;
 }
 
-// Split finish: one warp per (32 modes, 32 steps), lane = mode.  Adds the splits' promoted
-// sums in split order and runs the tile epilogue of the fused kernel on them.
+// Split finish: one warp per (32 modes, 8 steps), lane = mode.  Adds a tile's segments (the
+// uniform split's ranges, or the balanced split's parts that cut it) in order and runs the
+// fused kernel's epilogue on the sums; under the balanced split, warps of tiles that one part
+// held whole return at once (the projection kernel ran their epilogue).  The segments come
+// into shared memory by 16-byte asynchronous copies, FIN_SEGS at a time (up to 16 KB a warp
+// in flight without holding registers), and each lane then reads its own mode's values.
+constexpr int FIN_STEPS = 8;
+constexpr int FIN_SEGS = 4;
+constexpr int FIN_COLS = 4 * FIN_STEPS;                          // columns of a warp
+constexpr int FIN_SMEM = 4 * FIN_SEGS * FIN_COLS * 32 * 4;       // 4 warps, 64 KB
 __global__ void __launch_bounds__(128) tc_split_finish_kernel(const __grid_constant__ TcParams<1> p) {
+    extern __shared__ float4 fin_smem4[];
     const TcProblem &P = p.prob[0];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x * 4 + warp;   // 32-mode group (warp-uniform)
     if (g * 32 >= P.m_pad) return;
-    const int n = g * 32 + lane;
-    const int c0 = blockIdx.y * 128;       // first of the warp's 128 columns (32 steps)
-    const int bin = P.mode_bin[n];
-    const int slot = P.mode_slot[n];
-    const uint32_t take = seg_scan_masks(bin, lane);
-    float acc[128];
-#pragma unroll
-    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
-    for (int s = 0; s < P.n_split; ++s) {
-        const float *src = P.split_ws + ((size_t)s * P.ws_cols + c0) * P.m_pad + n;
-#pragma unroll
-        for (int j = 0; j < 128; ++j) acc[j] += __ldcg(src + (size_t)j * P.m_pad);
+    const int n0 = g * 32;
+    const int kbase = blockIdx.y * FIN_STEPS;
+    const int c0 = kbase * 4;              // first of the warp's columns
+    int nseg = P.n_split;
+    if (P.sk_parts > 0) {
+        nseg = sk_segments(P, (n0 / P.sk_tm) * P.n_col_tiles + c0 / P.sk_bn);
+        if (nseg < 2) return;
     }
-    tile_epilogue<false>(acc, P, blockIdx.y * 32, take, slot, lane);
+    const int bin = P.mode_bin[n0 + lane];
+    const int slot = P.mode_slot[n0 + lane];
+    const uint32_t take = seg_scan_masks(bin, lane);
+    float *st = reinterpret_cast<float *>(fin_smem4) + (size_t)warp * FIN_SEGS * FIN_COLS * 32;
+    const size_t sstride = (size_t)P.ws_cols * P.m_pad;
+    const float *src = P.split_ws + (size_t)c0 * P.m_pad + n0;
+    float acc[FIN_COLS];
+#pragma unroll
+    for (int j = 0; j < FIN_COLS; ++j) acc[j] = 0.f;
+    for (int s0 = 0; s0 < nseg; s0 += FIN_SEGS) {
+        const int ns = min(FIN_SEGS, nseg - s0);
+        // segment s, column j: 32 modes = 128 contiguous bytes, eight 16-byte copies
+        for (int q = lane; q < ns * FIN_COLS * 8; q += 32) {
+            const int s = q / (FIN_COLS * 8), r = q - s * (FIN_COLS * 8), j = r >> 3, part = r & 7;
+            cp_async16(st + (s * FIN_COLS + j) * 32 + part * 4,
+                       src + (size_t)(s0 + s) * sstride + (size_t)j * P.m_pad + part * 4);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        for (int s = 0; s < ns; ++s)   // segment order
+#pragma unroll
+            for (int j = 0; j < FIN_COLS; ++j) acc[j] += st[(s * FIN_COLS + j) * 32 + lane];
+        __syncwarp();                  // the staging area is refilled by the next batch
+    }
+    epilogue_steps<FIN_STEPS>(acc, step_scales(P, kbase, lane), P, kbase, take, slot,
+                              (size_t)P.n_slots, 0);
 }
 
 }  // namespace
 
 cudaError_t launch_tc_split_finish(const TcParams<1> &p, cudaStream_t s) {
     const TcProblem &P = p.prob[0];
-    if (P.n_split <= 1 || !P.split_ws || P.m_pad % 128) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)(P.m_pad / 128), (unsigned)((P.K + 31) / 32));
-    tc_split_finish_kernel<<<grid, 128, 0, s>>>(p);
+    if ((P.n_split <= 1 && P.sk_parts <= 0) || !P.split_ws || P.m_pad % 128 || P.ws_cols % FIN_COLS)
+        return cudaErrorInvalidValue;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        tc_split_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FIN_SMEM);
+    if (attr != cudaSuccess) return attr;
+    const dim3 grid((unsigned)(P.m_pad / 128), (unsigned)((P.K + FIN_STEPS - 1) / FIN_STEPS));
+    tc_split_finish_kernel<<<grid, 128, FIN_SMEM, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -831,8 +864,15 @@ size_t tc_smem_bytes(const TcConfig &c) {   // must match TcLayout / TcPairLayou
 }
 
 cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream_t s) {
-    if (p.prob[0].n_split > 1 && (p.prob[0].dir_seg_kb || !p.prob[0].split_ws ||
-                                  p.prob[0].kb_split % (PROMOTE_D / c.bk)))
+    const TcProblem &P = p.prob[0];
+    if (P.n_split > 1 && (P.dir_seg_kb || !P.split_ws || P.sk_parts > 0 ||
+                          P.kb_split % (PROMOTE_D / c.bk)))
+        return cudaErrorInvalidValue;
+    if (P.sk_parts > 0 && (P.dir_seg_kb || !P.split_ws || P.sk_bn != c.bn ||
+                           P.sk_nch != (P.n_kb + PROMOTE_D / c.bk - 1) / (PROMOTE_D / c.bk) ||
+                           P.sk_tm != (c.pair ? 2 : 1) * TC_BM ||
+                           (long long)P.sk_parts > (long long)P.n_tiles * P.sk_nch ||
+                           c.grid != P.sk_parts * (c.pair ? 2 : 1)))
         return cudaErrorInvalidValue;
     if (p.prob[0].dir_seg_kb) {
         if (!p.prob[0].dir_park || c.grid > p.dir_park_ctas) return cudaErrorInvalidValue;
@@ -842,7 +882,8 @@ cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream
 }
 cudaError_t launch_tc_group(const TcParams<TC_MAX_GROUP> &p, const TcConfig &c, cudaStream_t s) {
     for (int q = 0; q < p.n_prob; ++q)   // direction and d-axis splits run on single problems only
-        if (p.prob[q].dir_seg_kb || p.prob[q].n_split > 1) return cudaErrorInvalidValue;
+        if (p.prob[q].dir_seg_kb || p.prob[q].n_split > 1 || p.prob[q].sk_parts > 0)
+            return cudaErrorInvalidValue;
     return dispatch<TC_MAX_GROUP, false>(p, c, s);
 }
 

@@ -115,6 +115,13 @@ struct TcProblem {   // 128-byte aligned through CUtensorMap
     // adds the splits in order and runs the tile epilogue.  n_split <= 1: one unit per tile.
     int n_split, kb_split, ws_cols, m_pad;
     float *split_ws;
+    // Balanced split (sk_parts > 0, single problems only; n_tiles then counts tiles): the
+    // n_tiles x sk_nch promotion chunks of the block, tile-major (tile = mode tile x
+    // n_col_tiles + column tile), cut into sk_parts contiguous ranges of equal length, one per
+    // CTA (pair).  A tile cut by range boundaries stores segment s (the s-th range that touches
+    // it, in chunk order) to split_ws[s]; the finish kernel adds its segments in order.  sk_tm:
+    // modes per tile (128, or 256 for CTA pairs); sk_bn: columns per tile.
+    int sk_parts, sk_nch, sk_tm, sk_bn;
 };
 constexpr int DIR_PARK_THREADS = 256;                        // epilogue threads of the widest tile
 constexpr int DIR_PARK_SEG_FLOATS = 96 * DIR_PARK_THREADS;   // one parked segment of a CTA
@@ -139,8 +146,10 @@ struct TcConfig {
     int stages;   // shared-memory pipeline depth
     int pair;     // 1: two-SM tile (cta_group::2, 256 modes per CTA pair, bn columns shared)
     int grid;
-    int split;    // d-axis splits of a single problem (0 or 1: none)
+    int split;    // d-axis splits of a single problem (0 or 1: none; TC_SPLIT_BALANCED: one
+                  // range of equal chunk count per CTA or pair over all tiles)
 };
+constexpr int TC_SPLIT_BALANCED = -1;
 // Pipeline shapes the autotuner chooses from (index + 1 = mhc_params.tile_config).
 constexpr int TC_NUM_CONFIGS = 8;
 extern const TcConfig TC_CONFIGS[TC_NUM_CONFIGS];

@@ -448,8 +448,43 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
     return reset_accumulators(h);
 }
 
-// Bytes of the d-axis split workspace of configuration c: [split][columns of k_max][M_pad].
+// Balanced split, host side (the kernels' arithmetic): the part holding chunk g when T chunks
+// are cut into `parts` ranges, and the plan of one block: chunks per tile, tiles, parts and the
+// largest number of segments any tile is cut into.
+int sk_part_of_host(long long g, long long T, int parts) {
+    return (int)(((g + 1) * parts + T - 1) / T - 1);
+}
+
+struct SkPlan {
+    int nch = 0, tiles = 0, parts = 0, max_seg = 1;
+};
+
+SkPlan sk_plan(const mhc_handle *h, const TcConfig &c, int n_col_tiles) {
+    SkPlan q;
+    const int chunk_kb = TC_PROMOTE_D / c.bk;
+    q.nch = (int)((h->D_ld / c.bk + chunk_kb - 1) / chunk_kb);
+    q.tiles = mode_tiles(h, c) * n_col_tiles;
+    const long long T = (long long)q.tiles * q.nch;
+    q.parts = (int)std::min<long long>(sched_units(h, c), T);
+    for (int t = 0; t < q.tiles; ++t) {
+        const long long g0 = (long long)t * q.nch;
+        q.max_seg = std::max(q.max_seg, 1 + sk_part_of_host(g0 + q.nch - 1, T, q.parts) -
+                                            sk_part_of_host(g0, T, q.parts));
+    }
+    return q;
+}
+
+// Bytes of the d-axis split workspace of configuration c: [segment][columns][M_pad], for the
+// largest block (the uniform split), or the largest segments x columns of any block length up
+// to k_max (the balanced split: short blocks have fewer tiles, cut into more segments).
 size_t split_ws_bytes(const mhc_handle *h, const TcConfig &c) {
+    if (c.split == TC_SPLIT_BALANCED) {
+        size_t worst = 0;
+        const int nct_max = (4 * h->prm.k_max + c.bn - 1) / c.bn;
+        for (int nct = 1; nct <= nct_max; ++nct)
+            worst = std::max(worst, (size_t)sk_plan(h, c, nct).max_seg * nct * c.bn);
+        return sizeof(float) * worst * (size_t)h->M_pad;
+    }
     if (c.split <= 1) return 0;
     const size_t cols = (size_t)((4 * h->prm.k_max + c.bn - 1) / c.bn) * c.bn;
     return sizeof(float) * (size_t)c.split * cols * (size_t)h->M_pad;
@@ -469,7 +504,9 @@ mhc_status ensure_split_ws(mhc_handle *h, const TcConfig &c) {
 
 mhc_status set_tc_config(mhc_handle *h, const TcConfig &c) {
     if (!tc_config_supported(c)) return fail(h, MHC_ERR_INVALID_ARG, "unsupported tile configuration");
-    if (c.split > 1 && (h->dir || c.split > TC_MAX_SPLIT))
+    if ((c.split > 1 || c.split == TC_SPLIT_BALANCED) && (h->dir || c.split > TC_MAX_SPLIT))
+        return fail(h, MHC_ERR_INVALID_ARG, "d-axis split %d not available here", c.split);
+    if (c.split < 1 && c.split != TC_SPLIT_BALANCED)
         return fail(h, MHC_ERR_INVALID_ARG, "d-axis split %d not available here", c.split);
     if (mhc_status s = ensure_split_ws(h, c); s != MHC_OK) return s;
     const bool remap = h->bins_ready && (c.bn != h->tc.bn || c.bk != h->tc.bk || c.pair != h->tc.pair);
@@ -522,6 +559,36 @@ mhc_status run_projection(mhc_handle *h, int K) {
     h->tcp.wait_limit = stall ? 200000000ll : 2000000000ll;   // 0.1 s when testing the timeout
     P.K = K;
     P.n_col_tiles = (int)((4 * K + c.bn - 1) / c.bn);
+    P.sk_parts = 0;
+    P.ws_cols = P.n_col_tiles * c.bn;
+    P.m_pad = (int)h->M_pad;
+    if (c.split == TC_SPLIT_BALANCED) {
+        // balanced split: one range of chunks per CTA (pair); tiles cut by a range boundary
+        // are finished by the split finish kernel
+        const SkPlan q = sk_plan(h, c, P.n_col_tiles);
+        const size_t need = sizeof(float) * (size_t)q.max_seg * P.ws_cols * (size_t)h->M_pad;
+        auto it = h->buf.find("split_ws");
+        if (it == h->buf.end() || it->second.bytes < need)
+            return fail(h, MHC_ERR_STATE, "balanced split workspace too small (%zu bytes needed)", need);
+        P.n_split = 1;
+        P.kb_split = P.n_kb;
+        P.sk_parts = q.parts;
+        P.sk_nch = q.nch;
+        P.sk_tm = (c.pair ? 2 : 1) * TC_BM;
+        P.sk_bn = c.bn;
+        P.split_ws = dptr<float>(h, "split_ws");
+        P.n_tiles = q.tiles;
+        c.grid = q.parts * (c.pair ? 2 : 1);
+        cudaError_t e = launch_tc_single(h->tcp, c, h->stream);
+        h->launches++;
+        if (e == cudaSuccess && q.max_seg > 1) {
+            e = launch_tc_split_finish(h->tcp, h->stream);
+            h->launches++;
+        }
+        if (e != cudaSuccess)
+            return fail(h, MHC_ERR_CUDA, "tensor-core kernel launch failed: %s", cudaGetErrorString(e));
+        return MHC_OK;
+    }
     // d-axis split: whole promotion chunks per split, no empty split
     const int chunk_kb = TC_PROMOTE_D / c.bk;
     int kb_split = P.n_kb, S = 1;
@@ -531,8 +598,6 @@ mhc_status run_projection(mhc_handle *h, int K) {
     }
     P.n_split = S;
     P.kb_split = kb_split;
-    P.ws_cols = P.n_col_tiles * c.bn;
-    P.m_pad = (int)h->M_pad;
     P.split_ws = S > 1 ? dptr<float>(h, "split_ws") : nullptr;
     P.n_tiles = mode_tiles(h, c) * P.n_col_tiles * S;
     c.grid = std::min(sched_units(h, c), P.n_tiles) * (c.pair ? 2 : 1);
@@ -591,7 +656,8 @@ void tune_file_read_locked() {
         k.device = name;
         k.D_ld = D;
         k.M_eff = M;
-        if (tc_config_supported(c) && c.split >= 1 && c.split <= TC_MAX_SPLIT) g_tune_cache[k] = c;
+        if (tc_config_supported(c) && ((c.split >= 1 && c.split <= TC_MAX_SPLIT) || c.split == TC_SPLIT_BALANCED))
+            g_tune_cache[k] = c;
     }
     std::fclose(f);
 }
@@ -625,7 +691,8 @@ mhc_status time_projection(mhc_handle *h, const TcConfig &c, int K, cudaEvent_t 
 
 // Autotune on the block just packed: time every tile shape unsplit (or with the fixed split of
 // mhc_params.split_d), then, when one block leaves schedulable units idle (fewer than three
-// waves of tiles), the d-axis splits 2..8 of the two fastest shapes.  The winner is cached.
+// waves of tiles), the balanced split and the uniform d-axis splits 2..8 of the two fastest
+// shapes.  The winner is cached.
 mhc_status autotune(mhc_handle *h, int K) {
     const TuneKey key = tune_key(h, K);
     {
@@ -641,7 +708,8 @@ mhc_status autotune(mhc_handle *h, int K) {
     MHC_CUDA(h, cudaEventCreate(&e0));
     MHC_CUDA(h, cudaEventCreate(&e1));
     std::vector<std::pair<float, TcConfig>> res;
-    const int fixed = std::max(1, (int)h->prm.split_d);
+    const int fixed =
+        h->prm.split_d == TC_SPLIT_BALANCED ? TC_SPLIT_BALANCED : std::max(1, (int)h->prm.split_d);
     mhc_status s = MHC_OK;
     for (TcConfig c : TC_CONFIGS) {
         c.split = fixed;
@@ -661,6 +729,12 @@ mhc_status autotune(mhc_handle *h, int K) {
             const int n_kb = (int)(h->D_ld / c.bk), chunk_kb = TC_PROMOTE_D / c.bk;
             const int64_t units = (int64_t)mode_tiles(h, c) * ((4 * K + c.bn - 1) / c.bn);
             if (units >= 3 * (int64_t)sched_units(h, c)) continue;
+            c.split = TC_SPLIT_BALANCED;
+            if (split_ws_bytes(h, c) <= budget) {
+                float ms = 0.f;
+                if ((s = time_projection(h, c, K, e0, e1, 3, ms)) != MHC_OK) break;
+                res.emplace_back(ms, c);
+            }
             for (int S : {2, 3, 4, 6, 8}) {
                 if (n_kb < S * chunk_kb) break;
                 c.split = S;
@@ -828,8 +902,9 @@ int config_index(const mhc_handle *h) {
 // Capture pack -> projection -> finish of one push into a graph (on a private stream) and
 // replay it on the handle's stream.  Inputs must already be in device memory.
 mhc_status push_graph(mhc_handle *h, const float *v, const float *W, int K) {
+    const int split_code = h->tc.split == TC_SPLIT_BALANCED ? 63 : std::max(1, h->tc.split);
     auto key = std::make_tuple(K, (const void *)v, (const void *)W,
-                               is_tc(h) ? config_index(h) * 64 + std::max(1, h->tc.split) : -1);
+                               is_tc(h) ? config_index(h) * 64 + split_code : -1);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         if (h->graphs.size() >= 32) {   // evict the least recently used graph
@@ -937,9 +1012,9 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
         return fail(nullptr, MHC_ERR_INVALID_ARG, "unknown precision %d", p->precision);
     if (p->tile_config < 0 || p->tile_config > TC_NUM_CONFIGS)
         return fail(nullptr, MHC_ERR_INVALID_ARG, "tile_config must be in [0, %d]", TC_NUM_CONFIGS);
-    if (p->split_d < 0 || p->split_d > TC_MAX_SPLIT)
-        return fail(nullptr, MHC_ERR_INVALID_ARG, "split_d must be in [0, %d]", TC_MAX_SPLIT);
-    if ((p->flags & MHC_FLAG_DIRECTION) && p->split_d > 1)
+    if (p->split_d < TC_SPLIT_BALANCED || p->split_d > TC_MAX_SPLIT)
+        return fail(nullptr, MHC_ERR_INVALID_ARG, "split_d must be in [-1, %d]", TC_MAX_SPLIT);
+    if ((p->flags & MHC_FLAG_DIRECTION) && (p->split_d > 1 || p->split_d == TC_SPLIT_BALANCED))
         return fail(nullptr, MHC_ERR_INVALID_ARG, "the direction split runs without d-axis splits");
     if (!(p->dt_ps > 0) || !(p->T_K > 0) || !(p->V_A3 > 0))
         return fail(nullptr, MHC_ERR_INVALID_ARG, "dt_ps, T_K and V_A3 must be positive");
@@ -968,7 +1043,7 @@ mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
     h->dir = (p->flags & MHC_FLAG_DIRECTION) != 0;
     if (p->tile_config > 0) h->tc = TC_CONFIGS[p->tile_config - 1];
     else if (h->dir) h->tc = TC_CONFIGS[2];
-    h->tc.split = std::max(1, (int)p->split_d);
+    h->tc.split = p->split_d == TC_SPLIT_BALANCED ? TC_SPLIT_BALANCED : std::max(1, (int)p->split_d);
     if ((e = cudaSetDevice(p->device)) != cudaSuccess) {
         delete h;
         return fail(nullptr, MHC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -1411,7 +1486,8 @@ mhc_status mhc_get_info(mhc_handle *h, mhc_info *info) {
     info->tile_pair = is_tc(h) ? h->tc.pair : 0;
     info->tile_k = is_tc(h) ? h->tc.bk : 16;
     info->stages = is_tc(h) ? h->tc.stages : 0;
-    info->tile_split = is_tc(h) ? std::max(1, h->tc.split) : 1;
+    info->tile_split = !is_tc(h) ? 1 : h->tc.split == TC_SPLIT_BALANCED ? TC_SPLIT_BALANCED
+                                                                        : std::max(1, h->tc.split);
     info->grid = h->sm_count;
     info->e_exp = h->e_exp;
     info->ortho_err = h->ortho_err;
@@ -1564,6 +1640,7 @@ mhc_status group_encode(mhc_group *g) {
         TcProblem &P = g->tcp.prob[j];
         P = h->tcp.prob[0];
         P.n_split = 1;   // grouped launches run every system unsplit
+        P.sk_parts = 0;
         P.split_ws = nullptr;
         if (encode_maps(h, c, P))
             return fail(h0, MHC_ERR_CUDA, "cuTensorMapEncodeTiled failed (group member %zu)", j);

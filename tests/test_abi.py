@@ -39,7 +39,7 @@ def test_default_params_and_status_strings():
 
 @pytest.mark.parametrize("field,value", [("k_max", 0), ("k_max", 5000), ("n_lags", -1),
                                          ("precision", 7), ("tile_config", 9), ("dt_ps", 0.0),
-                                         ("split_d", -1), ("split_d", 17)])
+                                         ("split_d", -2), ("split_d", 17)])
 def test_create_rejects_bad_params(field, value):
     L = mhc.load()
     p = mhc.MhcParams()
@@ -61,12 +61,13 @@ def test_gkma_requires_lags():
     assert L.mhc_create(ctypes.byref(h), ctypes.byref(p)) == 1
 
 
-def test_direction_split_takes_no_d_axis_split():
+@pytest.mark.parametrize("split_d", [2, -1])
+def test_direction_split_takes_no_d_axis_split(split_d):
     L = mhc.load()
     p = mhc.MhcParams()
     L.mhc_default_params(ctypes.byref(p))
     p.flags = mhc.FLAG_DIRECTION
-    p.split_d = 2
+    p.split_d = split_d          # a uniform or the balanced split
     h = ctypes.c_void_p()
     assert L.mhc_create(ctypes.byref(h), ctypes.byref(p)) == 1
     assert b"split" in L.mhc_last_error(None)

@@ -4,7 +4,10 @@ and block length, through the C ABI against the FP64 oracle.
 A split cuts the reduction of Eqs. 13 and 16 over the 3N degrees of freedom into ranges of
 whole 128-element promotion chunks; each (mode tile, column tile, range) runs as its own unit
 and a finish kernel adds the ranges in a fixed order before the Eq. 16 product and the bin
-sums.  The results differ from the unsplit kernel only in the order of FP32 additions."""
+sums.  The balanced split (split_d = -1) cuts the chunks of all tiles, tile after tile, into
+one range of equal length per CTA (pair); a tile that a range boundary cuts is finished the
+same way, the others by the projection kernel itself.  The results differ from the unsplit
+kernel only in the order of FP32 additions."""
 import os
 import subprocess
 import sys
@@ -29,8 +32,10 @@ def case_n400():
 
 
 @pytest.mark.parametrize("tile_config", [1, 2, 3, 4, 5, 6, 7, 8])
-@pytest.mark.parametrize("split_d", [2, 3, 4])
+@pytest.mark.parametrize("split_d", [2, 3, 4, -1])
 def test_split_matches_oracle_on_every_tile(case_n400, tile_config, split_d):
+    # split_d = -1 on this case: 10 chunks a tile, 10-30 tiles on 76 CTA pairs or 152 CTAs, so
+    # every tile is cut into ~5-9 segments (more than the finish kernel stages at once)
     need_gpu()
     c = case_n400
     L = 9
@@ -46,14 +51,37 @@ def test_split_matches_oracle_on_every_tile(case_n400, tile_config, split_d):
     check(Jb, Jb1, 2 * c["ref"].S, 2 * c["ref"].Sd, REL_TOL, "split vs unsplit")
 
 
+@pytest.fixture(scope="module")
+def case_n1000():
+    # D = 3000 (24 chunks a tile), 3000 modes, one block of 1024 steps: 192 CTA-pair tiles
+    # (4608 chunks, ~61 a pair) or 768 one-SM tiles of 128 columns (~121 chunks a CTA), so the
+    # balanced split leaves most tiles whole and cuts the rest in two or three
+    c = make_case(N=1000, M=3000, T=1024, B=12, seed=1102, drive=1e-3)
+    c["ref"] = oracle_ref(c)
+    return c
+
+
+@pytest.mark.parametrize("tile_config", [4, 5])
+def test_balanced_split_mixes_whole_and_cut_tiles(case_n1000, tile_config):
+    need_gpu()
+    c = case_n1000
+    h, Jb, _ = run_gpu(c, "fp16x3", K=1024, tile_config=tile_config, split_d=-1)
+    assert h.info()["tile_split"] == -1
+    c["ref"].check_current(Jb, REL_TOL, f"balanced split, tile {tile_config}")
+    h.close()
+    _, Jb1, _ = run_gpu(c, "fp16x3", K=1024, tile_config=tile_config, split_d=1)
+    check(Jb, Jb1, 2 * c["ref"].S, 2 * c["ref"].Sd, REL_TOL, "balanced vs unsplit")
+
+
+@pytest.mark.parametrize("split_d", [3, -1])
 @pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
-def test_split_graph_replay_and_repeat_are_bitwise(case_n400, precision):
+def test_split_graph_replay_and_repeat_are_bitwise(case_n400, precision, split_d):
     need_gpu()
     from paper_2102_03691_gb300.mhc import FLAG_NO_GRAPH
     c = case_n400
     outs = []
     for flags in (FLAG_NO_GRAPH, 0, 0):
-        h, Jb, _ = run_gpu(c, precision, K=65, L=5, tile_config=5, split_d=3, flags=flags)
+        h, Jb, _ = run_gpu(c, precision, K=65, L=5, tile_config=5, split_d=split_d, flags=flags)
         C, _ = h.read_corr()
         outs.append((Jb, C, h.info()["graph_replays"]))
         h.close()
