@@ -42,6 +42,17 @@ __device__ __forceinline__ void acc_exact(float &s, float &c, float w, float v) 
     c = __fadd_rn(c, __fadd_rn(er, pe));
 }
 
+// (s, c) += (s2, c2): the leading parts added error-free (TwoSum), the rounding error and the
+// trailing parts into c.  FP32 instructions only: GB300's FP64 pipe is too narrow for a
+// warp-wide FP64 reduction per CTA (it cost ~5 us of a 26 us pack).
+__device__ __forceinline__ void pair_add(float &s, float &c, float s2, float c2) {
+    const float t = __fadd_rn(s, s2);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, e));
+}
+
 __global__ void __launch_bounds__(PACK_THREADS) pack_kernel(const PackArgs a) {
     const int k = blockIdx.x;
     const float *v = a.v + (size_t)k * a.N * 3;
@@ -175,10 +186,17 @@ __device__ __forceinline__ void store_split4(const PackArgs &a, size_t idx, floa
 
 // A cluster of ceil(N / (4 THREADS)) CTAs per step k.  CTA r bulk-copies the contiguous
 // velocities and virials of its atoms r*4*THREADS .. into shared memory (TMA, so the loads are
-// asynchronous and the inputs are read once); thread t takes the four consecutive atoms 4t ..
-// 4t+3: row maxima and the exact total-current pairs (acc_exact), combined per CTA (FP64, fixed
-// order) and across the cluster in rank order through distributed shared memory (the result is
-// deterministic); then the four B rows of step k from shared memory with 8-byte stores.
+// asynchronous and the inputs are read once).  Phase 1, thread t takes the atoms t, t+THREADS,
+// t+2 THREADS, t+3 THREADS (shared-memory strides of 3 and 9 words across a warp: no bank
+// conflicts): row maxima and the exact total-current pairs (acc_exact), combined per CTA in a
+// fixed order (unevaluated float pairs across the warp, FP64 across the warps); one cluster
+// barrier, then every CTA combines all ranks' maxima in rank order through distributed shared
+// memory (each computes the same scales) and rank 0 the current (FP64, rank order).
+// Phase 2 writes the four B rows of the CTA's atoms: each row is one contiguous run of
+// 16-bit values (three per atom; three runs of one per atom, one per direction, with the
+// direction-major columns), cut into groups of four values that consecutive threads take in
+// order, so that every warp store covers 256 contiguous bytes.  A CTA leaves only after the
+// second half of the cluster barrier: its peers may still be reading its partial sums.
 // The body of one CTA: step k of the system `a`, rank `rank` of its cluster of `nrank` CTAs.
 template <int THREADS>
 __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_t rank, uint32_t nrank) {
@@ -187,13 +205,13 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
     float *sv = reinterpret_cast<float *>(pk_smem4);   // [APC][3]
     float *sw = sv + APC * 3;                          // [APC][9]
     __shared__ float s_mx[THREADS / 32][4];
-    __shared__ double s_j[THREADS / 32][3];
+    __shared__ float s_js[THREADS / 32][3], s_jcc[THREADS / 32][3];
     __shared__ float s_loc[4], s_mul[4];
     __shared__ double s_jc[3];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int abort_flag;
     const int a0 = (int)rank * APC;
-    const int na = max(0, min(APC, a.N - a0));
+    const int na = max(0, min(APC, a.N - a0));   // a multiple of 4 (N % 4 == 0)
     const long long limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT_CYCLES;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -213,54 +231,52 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
     }
     bool ok = true;
     if (na > 0) ok = mbar_wait(&bar, 0, &abort_flag, limit);
-    const int i = 4 * (int)threadIdx.x;   // this thread's first atom within the CTA
-    const bool in = ok && i < na;         // N % 4 == 0: all four atoms or none
     float mx[4] = {0.f, 0.f, 0.f, 0.f};
     float js[3] = {0.f, 0.f, 0.f}, jc[3] = {0.f, 0.f, 0.f};
-    float sm[4] = {0.f, 0.f, 0.f, 0.f}, ism[4] = {0.f, 0.f, 0.f, 0.f};
-    if (in) {
-        const float4 s4 = *reinterpret_cast<const float4 *>(a.sqm + a0 + i);
-        const float4 is4 = *reinterpret_cast<const float4 *>(a.isqm + a0 + i);
-        sm[0] = s4.x; sm[1] = s4.y; sm[2] = s4.z; sm[3] = s4.w;
-        ism[0] = is4.x; ism[1] = is4.y; ism[2] = is4.z; ism[3] = is4.w;
+    if (ok) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float *vu = sv + (i + u) * 3, *wu = sw + (i + u) * 9;
+            const int ia = (int)threadIdx.x + u * THREADS;
+            if (ia >= na) break;
+            const float sm = __ldg(a.sqm + a0 + ia), ism = __ldg(a.isqm + a0 + ia);
+            const float *vu = sv + ia * 3, *wu = sw + ia * 9;
 #pragma unroll
-            for (int b = 0; b < 3; ++b) mx[0] = fmaxf(mx[0], fabsf(sm[u] * vu[b]));
+            for (int b = 0; b < 3; ++b) mx[0] = fmaxf(mx[0], fabsf(sm * vu[b]));
 #pragma unroll
             for (int al = 0; al < 3; ++al)
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    mx[1 + al] = fmaxf(mx[1 + al], fabsf(wu[3 * al + b] * ism[u]));
+                    mx[1 + al] = fmaxf(mx[1 + al], fabsf(wu[3 * al + b] * ism));
                     acc_exact(js[al], jc[al], wu[3 * al + b], vu[b]);
                 }
         }
     }
-    double j[3];
-#pragma unroll
-    for (int al = 0; al < 3; ++al) j[al] = (double)js[al] + (double)jc[al];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) mx[c] = fmaxf(mx[c], __shfl_down_sync(FULL_MASK, mx[c], o));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) j[c] += __shfl_down_sync(FULL_MASK, j[c], o);
+        for (int c = 0; c < 3; ++c)
+            pair_add(js[c], jc[c], __shfl_down_sync(FULL_MASK, js[c], o), __shfl_down_sync(FULL_MASK, jc[c], o));
     }
     if (lane == 0) {
         for (int c = 0; c < 4; ++c) s_mx[warp][c] = mx[c];
-        for (int c = 0; c < 3; ++c) s_j[warp][c] = j[c];
+        for (int c = 0; c < 3; ++c) {
+            s_js[warp][c] = js[c];
+            s_jcc[warp][c] = jc[c];
+        }
     }
     __syncthreads();
     if (threadIdx.x < 4) {
         float m = 0.f;
         for (int w = 0; w < THREADS / 32; ++w) m = fmaxf(m, s_mx[w][threadIdx.x]);
         s_loc[threadIdx.x] = m;
-    } else if (threadIdx.x >= 32 && threadIdx.x < 35) {
+    } else if (threadIdx.x >= 32 && threadIdx.x < 35) {   // the warps' pairs in FP64, warp order
+        const int c = threadIdx.x - 32;
         double t = 0.0;
-        for (int w = 0; w < THREADS / 32; ++w) t += s_j[w][threadIdx.x - 32];
-        s_jc[threadIdx.x - 32] = t;
+        for (int w = 0; w < THREADS / 32; ++w) t += (double)s_js[w][c] + (double)s_jcc[w][c];
+        s_jc[c] = t;
     }
     cluster_sync_all();   // every CTA's maxima and current partials are complete
     if (threadIdx.x < 4) {
@@ -285,7 +301,8 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
             a.Jring[((t0 + k) % a.R) * 3 + c] = t;
         }
     }
-    cluster_sync_all();   // peers are done reading this CTA's partials; s_mul is visible
+    cluster_arrive_release();   // this CTA has read its peers' partials
+    __syncthreads();            // s_mul is visible to the CTA
     if (!ok) {   // the CTA stays alive until its copy has landed (bounded) or given up on
         if (threadIdx.x == 0) {
             if (a.status) set_status(a.status, DEV_TIMEOUT);
@@ -293,39 +310,50 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
             while (!mbar_try_wait(&bar, 0) && clock64() - c0 < limit) {
             }
         }
-        return;
-    }
-    if (!in) return;
-    const float m0 = s_mul[0], m1 = s_mul[1], m2 = s_mul[2], m3 = s_mul[3];
-    const float mul[4] = {m0, m1, m2, m3};
-    const size_t ld = (size_t)a.D_ld;
-    const size_t r0 = (size_t)(4 * k) * ld;
-    const int g = a0 + i;   // global index of the first atom
-    float x[4][12];         // per row c: the 12 values of the four atoms (3 per atom, b fastest)
+    } else {
+        const size_t ld = (size_t)a.D_ld;
+        const size_t r0 = (size_t)(4 * k) * ld;
+        const int q4 = na / 4;              // groups of four atoms (direction-major runs)
+        const int G = 3 * q4;               // groups of four values a row
+#pragma unroll 1
+        for (int g = (int)threadIdx.x; g < G; g += THREADS) {
+            int ia[4], bb[4];
+            size_t col;
+            if (a.npad) {   // direction-major: run b holds atoms a0 .. a0+na-1 at columns b*npad + i
+                const int b = g / q4, i0 = 4 * (g - b * q4);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const float *vu = sv + (i + u) * 3, *wu = sw + (i + u) * 9;
+                for (int e = 0; e < 4; ++e) {
+                    ia[e] = i0 + e;
+                    bb[e] = b;
+                }
+                col = (size_t)b * a.npad + a0 + i0;
+            } else {        // column 3i+b: values 4g .. 4g+3 of the CTA's run
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            x[0][3 * u + b] = (sm[u] * vu[b]) * mul[0];
+                for (int e = 0; e < 4; ++e) {
+                    ia[e] = (4 * g + e) / 3;
+                    bb[e] = (4 * g + e) - 3 * ia[e];
+                }
+                col = 3 * (size_t)a0 + 4 * (size_t)g;
+            }
+            float sm[4], ism[4];
 #pragma unroll
-            for (int al = 0; al < 3; ++al) x[1 + al][3 * u + b] = (wu[3 * al + b] * ism[u]) * mul[1 + al];
+            for (int e = 0; e < 4; ++e) {
+                sm[e] = __ldg(a.sqm + a0 + ia[e]);
+                ism[e] = __ldg(a.isqm + a0 + ia[e]);
+            }
+            float x[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) x[e] = (sm[e] * sv[3 * ia[e] + bb[e]]) * s_mul[0];
+            store_split4(a, r0 + col, x[0], x[1], x[2], x[3]);
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[e] = (sw[9 * ia[e] + 3 * al + bb[e]] * ism[e]) * s_mul[1 + al];
+                store_split4(a, r0 + (size_t)(1 + al) * ld + col, x[0], x[1], x[2], x[3]);
+            }
         }
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const size_t row = r0 + (size_t)c * ld;
-        if (a.npad) {   // direction-major: column b*npad + i, four consecutive atoms per b
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-                store_split4(a, row + (size_t)b * a.npad + g, x[c][b], x[c][3 + b], x[c][6 + b], x[c][9 + b]);
-        } else {        // column 3i+b: twelve consecutive values
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                store_split4(a, row + 3 * (size_t)g + 4 * q, x[c][4 * q], x[c][4 * q + 1], x[c][4 * q + 2],
-                             x[c][4 * q + 3]);
-        }
-    }
+    cluster_wait_acquire();   // peers have read this CTA's partials: its shared memory may go
 }
 
 // Shared memory (48 B an atom) allows four CTAs of 256 threads (two of 512) per SM; the
