@@ -265,6 +265,8 @@ mhc_status mhc_read_corr(mhc_handle *h, double *corr_sum, int64_t *count, int32_
  *   kappa_tau [B][3][3][L]  running integral kappa_b^{mu nu}(l dt), W/(m K); may be NULL
  *   kappa_w   [B][3][3]     its average over lags with tau_lo <= l dt <= tau_hi
  *                           (the tau window of Sec. III.A), may be NULL.
+ * With kappa_tau NULL the window average is evaluated directly as a weighted sum of the
+ * correlation over the lags (the same value up to FP64 rounding order, and faster).
  */
 mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, double tau_hi,
                              double *kappa_w, int32_t where);

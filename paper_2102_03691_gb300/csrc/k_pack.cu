@@ -356,10 +356,10 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
     cluster_wait_acquire();   // peers have read this CTA's partials: its shared memory may go
 }
 
-// Shared memory (48 B an atom) allows four CTAs of 256 threads (two of 512) per SM; the
-// register cap of the launch bounds lets as many be resident.
+// Shared memory (48 B an atom) allows eight CTAs of 128 threads, four of 256 or two of 512 per
+// SM; the register cap of the launch bounds lets as many be resident.
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 4 : 2) pack_bulk_kernel(const PackArgs a) {
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) pack_bulk_kernel(const PackArgs a) {
     const uint32_t nrank = cluster_nctarank();
     pack_bulk_body<THREADS>(a, (int)(blockIdx.x / nrank), cluster_ctarank(), nrank);
 }
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 4 : 2) pack_bulk_ker
 // clusters of the common cluster size; ranks beyond a system's atoms hold no atoms and only
 // take part in the cluster's combination).
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 4 : 2) pack_bulk_group_kernel(const __grid_constant__ PackGroupArgs g) {
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) pack_bulk_group_kernel(const __grid_constant__ PackGroupArgs g) {
     int j = 0;
     while (j + 1 < g.n && (int)blockIdx.x >= g.cta_begin[j + 1]) ++j;
     const uint32_t nrank = cluster_nctarank();
@@ -402,6 +402,11 @@ cudaError_t launch_pack_bulk(const PackArgs &a, cudaStream_t s) {
 }  // namespace
 
 namespace {
+// CTA size of the bulk-copy pack of a system of N atoms (four atoms a thread): one CTA a step
+// and eight an SM up to 512 atoms, clusters of up to 8 CTAs of 256 (four an SM) up to 8192,
+// of 512 beyond.
+int pack_threads(int N) { return N <= 4 * 128 ? 128 : N <= 8 * 1024 ? 256 : 512; }
+
 bool bulk_ok(const PackArgs &a) {
     const auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
     return a.N % 4 == 0 && al16(a.v) && al16(a.W) && al16(a.sqm) && al16(a.isqm) &&
@@ -443,26 +448,35 @@ cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s, int *n_lau
         nmax = std::max(nmax, g.a[j].N);
     }
     if (nmax > 8 * 2048) return cudaErrorNotSupported;
-    // one launch per cluster size (systems of similar size together), so no rank is idle
-    const int threads = nmax <= 8 * 1024 ? 256 : 512, apc = 4 * threads;
-    for (int cs = 1; cs <= 8; ++cs) {
-        PackGroupArgs sub{};
-        for (int j = 0; j < g.n; ++j)
-            if ((g.a[j].N + apc - 1) / apc == cs || (g.a[j].N == 0 && cs == 1)) sub.a[sub.n++] = g.a[j];
-        if (sub.n == 0) continue;
-        const cudaError_t e = threads == 256 ? launch_pack_bulk_group<256>(sub, cs, s)
-                                             : launch_pack_bulk_group<512>(sub, cs, s);
-        if (e != cudaSuccess) return e;
-        ++*n_launches;
+    // one launch per (CTA size, cluster size): every system is packed by the CTA size it gets
+    // alone (so its results are bitwise those of a solo push), and no rank is idle
+    for (const int threads : {128, 256, 512}) {
+        const int apc = 4 * threads;
+        for (int cs = 1; cs <= 8; ++cs) {
+            PackGroupArgs sub{};
+            for (int j = 0; j < g.n; ++j)
+                if (pack_threads(g.a[j].N) == threads &&
+                    ((g.a[j].N + apc - 1) / apc == cs || (g.a[j].N == 0 && cs == 1)))
+                    sub.a[sub.n++] = g.a[j];
+            if (sub.n == 0) continue;
+            const cudaError_t e = threads == 128 ? launch_pack_bulk_group<128>(sub, cs, s)
+                                  : threads == 256 ? launch_pack_bulk_group<256>(sub, cs, s)
+                                                   : launch_pack_bulk_group<512>(sub, cs, s);
+            if (e != cudaSuccess) return e;
+            ++*n_launches;
+        }
     }
     return cudaSuccess;
 }
 
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
-    const bool bulk = bulk_ok(a);
-    if (bulk && a.N <= 8 * 1024) return launch_pack_bulk<256>(a, s);
-    if (bulk && a.N <= 8 * 2048) return launch_pack_bulk<512>(a, s);
+    if (bulk_ok(a) && a.N <= 8 * 2048) {
+        const int threads = pack_threads(a.N);
+        return threads == 128 ? launch_pack_bulk<128>(a, s)
+               : threads == 256 ? launch_pack_bulk<256>(a, s)
+                                : launch_pack_bulk<512>(a, s);
+    }
     pack_kernel<<<a.K, PACK_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -262,6 +262,37 @@ __global__ void __launch_bounds__(GK_THREADS) gk_kappa_kernel(const double *Csum
     }
 }
 
+// Window average alone (no kappa(tau) wanted): with S(l) the running trapezoid sum above,
+//   sum_{l = l_lo..l_hi} S(l) = sum_m C(m) w(m),  w(m) = [m >= 1] cnt(m) + cnt(m + 1),
+// cnt(x) = #{l in [l_lo, l_hi] : l >= x} (C(m) enters S(l) as the right end of the step m-1 -> m
+// for l >= m >= 1 and as the left end of the step m -> m+1 for l >= m+1).  The integer weights
+// and the reciprocal counts are folded into one table tw(m) = inv(m) w(m), so a row takes one
+// FP64 FMA a lag instead of the scan's few FP64 operations a lag on GB300's narrow FP64 pipe.
+__global__ void gk_window_weights_kernel(long long T_s, int L, int l_lo, int l_hi, double *tw) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= L) return;
+    const auto cnt = [&](int x) {
+        const int lo = max(x, l_lo);
+        return l_hi >= lo ? l_hi - lo + 1 : 0;
+    };
+    const double inv = T_s > m ? 1.0 / (double)(T_s - m) : 0.0;
+    tw[m] = inv * (double)((m >= 1 ? cnt(m) : 0) + cnt(m + 1));
+}
+
+// One warp per row: kappa_w = scale sum_m Csum(m) tw(m) (lanes stride the lags; fixed tree).
+__global__ void __launch_bounds__(128) gk_window_kernel(const double *Csum, int rows, int L,
+                                                        const double *__restrict__ tw, double scale,
+                                                        double *kappa_w) {
+    const int r = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const double *cs = Csum + (size_t)r * L;
+    double acc = 0.0;
+    for (int m = lane; m < L; m += 32) acc = fma(cs[m], tw[m], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL_MASK, acc, o);
+    if (lane == 0) kappa_w[r] = scale * acc;
+}
+
 __global__ void hnema_finalize_kernel(const double *hsum, int n, long long T_s, double coef,
                                       double *mean, double *kappa) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -343,6 +374,14 @@ void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coe
             l_lo = std::min(l_lo, l);
             l_hi = l;
         }
+    }
+    if (!kappa_tau) {   // the window average alone
+        const int n = l_hi >= l_lo ? l_hi - l_lo + 1 : 0;
+        const int rows = B * 9;
+        gk_window_weights_kernel<<<(L + 255) / 256, 256, 0, s>>>(T_s, L, l_lo, l_hi, inv_scratch);
+        gk_window_kernel<<<(rows + 3) / 4, 128, 0, s>>>(Csum, rows, L, inv_scratch,
+                                                        n > 0 ? 0.5 * coef_dt / n : 0.0, kappa_w);
+        return;
     }
     inv_counts_kernel<<<(L + 255) / 256, 256, 0, s>>>(T_s, L, inv_scratch);
     gk_kappa_kernel<<<B * 9, GK_THREADS, 0, s>>>(Csum, L, inv_scratch, 0.5 * coef_dt, l_lo, l_hi,

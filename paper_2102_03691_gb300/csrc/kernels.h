@@ -239,7 +239,8 @@ void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, 
                      int L, long long t0, const long long *t0_dev, cudaStream_t s);
 // *steps += K (one thread; last kernel of a push)
 void launch_advance_steps(long long *steps, int K, cudaStream_t s);
-// kappa_tau[r][l] (r = b*9+mu*3+nu) and window averages kappa_w[r], FP64.
+// kappa_tau[r][l] (r = b*9+mu*3+nu) and window averages kappa_w[r], FP64; kappa_tau null:
+// the window averages alone, as one weighted sum of C(l) a row.
 // inv_scratch: [L] doubles of device scratch (the reciprocal lag counts of this read).
 void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
                      double tau_lo, double tau_hi, double dt, double *kappa_tau,

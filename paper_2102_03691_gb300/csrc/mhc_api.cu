@@ -1404,8 +1404,9 @@ mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, do
     if ((s = dev_alloc(h, "gk_out", sizeof(double) * (rows * (L + 1) + L), false)) != MHC_OK) return s;
     double *dk = dptr<double>(h, "gk_out"), *dw = dk + rows * L;
     const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
+    // without a kappa(tau) output only the window average is computed (one FMA a lag)
     launch_gk_kappa(dptr<double>(h, "Csum"), (int)n_out_bins(h), L, h->steps, coef * h->prm.dt_ps, tau_lo, tau_hi,
-                    h->prm.dt_ps, dk, dw, dw + rows, h->stream);
+                    h->prm.dt_ps, kappa_tau ? dk : nullptr, dw, dw + rows, h->stream);
     h->launches += 2;
     MHC_CUDA(h, cudaGetLastError());
     if (kappa_tau && (s = copy_out(h, kappa_tau, dk, sizeof(double) * rows * L, where)) != MHC_OK) return s;
@@ -1453,7 +1454,7 @@ mhc_status mhc_read_kappa_xcorr(mhc_handle *h, double *kappa_tau, double tau_lo,
     double *dk = dptr<double>(h, "xk_out"), *dw = dk + rows * L;
     const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
     launch_gk_kappa(dptr<double>(h, "xc_out"), nb * nb, L, h->steps, coef * h->prm.dt_ps, tau_lo,
-                    tau_hi, h->prm.dt_ps, dk, dw, dw + rows, h->stream);
+                    tau_hi, h->prm.dt_ps, kappa_tau ? dk : nullptr, dw, dw + rows, h->stream);
     h->launches += 3;
     MHC_CUDA(h, cudaGetLastError());
     if (kappa_tau && (s = copy_out(h, kappa_tau, dk, sizeof(double) * rows * L, where)) != MHC_OK) return s;

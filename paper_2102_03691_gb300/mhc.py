@@ -544,6 +544,13 @@ class ModalHeatCurrent:
                                               MEM_HOST))
         return kt, kw
 
+    def read_kappa_window(self, tau_lo: float, tau_hi: float):
+        """The window averages of read_kappa_gk alone [rows][3][3] (no kappa(tau) output, so the
+        library evaluates them as one weighted sum of C(l) a row)."""
+        kw = np.empty((*self._rows(), 3, 3))
+        self.read_kappa_gk_into(kw, tau_lo, tau_hi)
+        return kw
+
     def read_xcorr(self):
         """Bin-bin cross-correlation sums [rows][rows][3][3][L] and origin counts [L]
         (rows = B, or (3, B) with the direction split)."""
@@ -554,14 +561,16 @@ class ModalHeatCurrent:
                                            cnt.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
         return X, cnt
 
-    def read_kappa_xcorr(self, tau_lo: float, tau_hi: float):
-        """Eq. 17 running integral of every bin pair: kappa_tau [rows][rows][3][3][L] and its
-        tau-window average [rows][rows][3][3], W/(m K)."""
+    def read_kappa_xcorr(self, tau_lo: float, tau_hi: float, with_tau: bool = True):
+        """Eq. 17 running integral of every bin pair: kappa_tau [rows][rows][3][3][L] (None
+        without with_tau: then only the window averages are evaluated) and its tau-window
+        average [rows][rows][3][3], W/(m K)."""
         L_ = self.params.n_lags
-        kt = np.empty((*self._rows(), *self._rows(), 3, 3, L_))
+        kt = np.empty((*self._rows(), *self._rows(), 3, 3, L_)) if with_tau else None
         kw = np.empty((*self._rows(), *self._rows(), 3, 3))
-        self._check(self._L.mhc_read_kappa_xcorr(self._h, kt.ctypes.data_as(ctypes.c_void_p), tau_lo,
-                                                 tau_hi, kw.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
+        self._check(self._L.mhc_read_kappa_xcorr(
+            self._h, kt.ctypes.data_as(ctypes.c_void_p) if with_tau else None, tau_lo, tau_hi,
+            kw.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
         return kt, kw
 
     def check_orthonormality(self, tol: float = 1e-6) -> float:

@@ -70,6 +70,12 @@ def test_single_bin_single_lag_and_lags_beyond_the_run(precision):
     assert np.all(np.isfinite(kt)) and np.all(np.isfinite(kw))
     o.check_kappa(kt, None, 20, 0.01, 300.0, 1.0, 0.0, 0.19, TOL[precision],
                   f"kappa beyond the run {precision}")
+    # the window average alone (weighted sum over the lags, lag 0 and empty lags included)
+    for lo, hi in ((0.0, 0.19), (0.0, 0.0), (0.05, 0.14), (0.3, 0.5)):
+        kw2 = h.read_kappa_window(lo, hi)
+        _, kw1 = h.read_kappa_gk(lo, hi)
+        np.testing.assert_allclose(kw2, kw1, rtol=1e-10, atol=1e-11 * max(np.abs(kw1).max(), 1e-300))
+    assert np.all(h.read_kappa_window(0.3, 0.5) == 0)   # no lag in the window
     h.close()
 
 
@@ -148,6 +154,10 @@ def test_green_kubo_read_out_beyond_1024_lags():
     kt, kw = h.read_kappa_gk(8.0, 10.5)
     _, n = o.check_kappa(kt, kw, L, dt, TK, V, 8.0, 10.5, REL_TOL, "1100 lags kappa")
     assert n == 251
+    # the window average alone (one weighted sum a row) against the oracle
+    kw2 = h.read_kappa_window(8.0, 10.5)
+    o.check_kappa(kt, kw2, L, dt, TK, V, 8.0, 10.5, REL_TOL, "1100 lags kappa window alone")
+    np.testing.assert_allclose(kw2, kw, rtol=1e-10, atol=1e-11 * np.abs(kw).max())
     # the Green-Kubo stage alone: the oracle's integral of the library's own Eq. 17 sums
     C, cnt = h.read_corr()
     okt = oracle.gk_kappa(C, cnt, dt, TK, V)

@@ -63,6 +63,8 @@ def test_xcorr_kappa_and_state_roundtrip():
     assert n == 7
     check(kt.reshape(okt.shape), okt, skt, sdt, REL_TOL, "kappa_xcorr(tau)")
     check(kw.reshape(okw.shape), okw, skw, sdw, REL_TOL, "kappa_xcorr window")
+    _, kw_only = a.read_kappa_xcorr(0.03, 0.09, with_tau=False)   # one weighted sum a row
+    check(kw_only.reshape(okw.shape), okw, skw, sdw, REL_TOL, "kappa_xcorr window alone")
     Xa, _ = a.read_xcorr()
     b = fresh()
     for t0 in range(0, 24, K):
