@@ -192,7 +192,8 @@ __device__ __forceinline__ void store_split4(const PackArgs &a, size_t idx, floa
 // fixed order (unevaluated float pairs across the warp, FP64 across the warps); one cluster
 // barrier, then every CTA combines all ranks' maxima in rank order through distributed shared
 // memory (each computes the same scales) and rank 0 the current (FP64, rank order).
-// Phase 2 writes the four B rows of the CTA's atoms: each row is one contiguous run of
+// Phase 1 also replaces each atom's inputs in shared memory by its row values sqrt(m) v and
+// W / sqrt(m).  Phase 2 writes the four B rows of the CTA's atoms: each row is one contiguous run of
 // 16-bit values (three per atom; three runs of one per atom, one per direction, with the
 // direction-major columns), cut into groups of four values that consecutive threads take in
 // order, so that every warp store covers 256 contiguous bytes.  A CTA leaves only after the
@@ -239,16 +240,27 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
             const int ia = (int)threadIdx.x + u * THREADS;
             if (ia >= na) break;
             const float sm = __ldg(a.sqm + a0 + ia), ism = __ldg(a.isqm + a0 + ia);
-            const float *vu = sv + ia * 3, *wu = sw + ia * 9;
+            float *vu = sv + ia * 3, *wu = sw + ia * 9;
+            float x[12];   // the atom's row values sqrt(m) v^b and W^{ab} / sqrt(m)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) mx[0] = fmaxf(mx[0], fabsf(sm * vu[b]));
+            for (int b = 0; b < 3; ++b) {
+                x[b] = sm * vu[b];
+                mx[0] = fmaxf(mx[0], fabsf(x[b]));
+            }
 #pragma unroll
             for (int al = 0; al < 3; ++al)
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    mx[1 + al] = fmaxf(mx[1 + al], fabsf(wu[3 * al + b] * ism));
+                    x[3 + 3 * al + b] = wu[3 * al + b] * ism;
+                    mx[1 + al] = fmaxf(mx[1 + al], fabsf(x[3 + 3 * al + b]));
                     acc_exact(js[al], jc[al], wu[3 * al + b], vu[b]);
                 }
+            // the scaled values replace the inputs in shared memory (this thread's atom alone),
+            // so phase 2 reads them without the masses
+#pragma unroll
+            for (int b = 0; b < 3; ++b) vu[b] = x[b];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) wu[q] = x[3 + q];
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -335,20 +347,14 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
                 }
                 col = 3 * (size_t)a0 + 4 * (size_t)g;
             }
-            float sm[4], ism[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                sm[e] = __ldg(a.sqm + a0 + ia[e]);
-                ism[e] = __ldg(a.isqm + a0 + ia[e]);
-            }
             float x[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) x[e] = (sm[e] * sv[3 * ia[e] + bb[e]]) * s_mul[0];
+            for (int e = 0; e < 4; ++e) x[e] = sv[3 * ia[e] + bb[e]] * s_mul[0];
             store_split4(a, r0 + col, x[0], x[1], x[2], x[3]);
 #pragma unroll
             for (int al = 0; al < 3; ++al) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) x[e] = (sw[9 * ia[e] + 3 * al + bb[e]] * ism[e]) * s_mul[1 + al];
+                for (int e = 0; e < 4; ++e) x[e] = sw[9 * ia[e] + 3 * al + bb[e]] * s_mul[1 + al];
                 store_split4(a, r0 + (size_t)(1 + al) * ld + col, x[0], x[1], x[2], x[3]);
             }
         }
