@@ -60,22 +60,29 @@ struct Unit {
     int prob, mt, ct, kb_lo, kb_hi, seg;
 };
 
-// Balanced split: the tile-major chunk space (n_tiles tiles x sk_nch promotion chunks, tile =
-// mode tile * n_col_tiles + column tile) cut into sk_parts contiguous ranges of equal length
-// (to one chunk); part q starts at chunk floor(q T / sk_parts).
-__device__ __forceinline__ long long sk_begin(const TcProblem &P, int q) {
-    return (long long)q * ((long long)P.n_tiles * P.sk_nch) / P.sk_parts;
+// Balanced split: the tiles below sk_t0 (whole waves of the round-robin over all CTAs or pairs)
+// run whole, round-robin; the tile-major chunk space of the remaining tiles (tile = mode tile *
+// n_col_tiles + column tile, sk_nch promotion chunks each) is cut into sk_parts contiguous
+// ranges of equal length (to one chunk), one for each of the first sk_parts CTAs (pairs): the
+// last, partial wave is spread over all of them instead of leaving most idle.  Tail-local chunk
+// g; part q starts at chunk floor(q T / sk_parts), T = the tail's chunks.
+__device__ __forceinline__ long long sk_tail_chunks(const TcProblem &P) {
+    return (long long)(P.n_tiles - P.sk_t0) * P.sk_nch;
 }
-// The part whose range holds chunk g: the largest q with sk_begin(q) <= g.
+__device__ __forceinline__ long long sk_begin(const TcProblem &P, int q) {
+    return (long long)q * sk_tail_chunks(P) / P.sk_parts;
+}
+// The part whose range holds tail chunk g: the largest q with sk_begin(q) <= g.
 __device__ __forceinline__ int sk_part_of(const TcProblem &P, long long g) {
-    const long long T = (long long)P.n_tiles * P.sk_nch;
+    const long long T = sk_tail_chunks(P);
     return (int)(((g + 1) * P.sk_parts + T - 1) / T - 1);
 }
-// Segments of a tile under the balanced split (1: one part holds the whole tile).  Every part
-// holds at least one chunk (sk_parts <= T), so the segments of a tile are the parts that touch
-// it, in chunk order.
+// Segments of a tile under the balanced split (1: one part holds the whole tile).  Every tail
+// part holds at least one chunk (sk_parts <= T), so the segments of a tail tile are the parts
+// that touch it, in chunk order.
 __device__ __forceinline__ int sk_segments(const TcProblem &P, int tile) {
-    const long long g0 = (long long)tile * P.sk_nch;
+    if (tile < P.sk_t0) return 1;
+    const long long g0 = (long long)(tile - P.sk_t0) * P.sk_nch;
     return 1 + sk_part_of(P, g0 + P.sk_nch - 1) - sk_part_of(P, g0);
 }
 
@@ -93,8 +100,13 @@ struct UnitIter {
             i = p.cta_begin[part];
             end = p.cta_begin[part + 1];
         } else if (p.prob[0].sk_parts > 0) {
-            g = sk_begin(p.prob[0], part);
-            g_end = sk_begin(p.prob[0], part + 1);
+            i = part;                      // whole tiles first
+            end = p.prob[0].sk_t0;
+            step = nparts;
+            if (part < p.prob[0].sk_parts) {   // then this part's range of the tail's chunks
+                g = sk_begin(p.prob[0], part);
+                g_end = sk_begin(p.prob[0], part + 1);
+            }
         } else {
             i = part;
             end = p.prob[0].n_tiles;
@@ -104,9 +116,19 @@ struct UnitIter {
     __device__ bool next(Unit &u) {
         const TcProblem &P = p.prob[0];
         if (!p.sched && P.sk_parts > 0) {
+            if (i < end) {
+                u.prob = 0;
+                u.mt = i / P.n_col_tiles;
+                u.ct = i - u.mt * P.n_col_tiles;
+                u.kb_lo = 0;
+                u.kb_hi = P.n_kb;
+                u.seg = -1;
+                i += step;
+                return true;
+            }
             if (g >= g_end) return false;
-            const int tile = (int)(g / P.sk_nch);
-            const int c0 = (int)(g - (long long)tile * P.sk_nch);
+            const int tl = (int)(g / P.sk_nch), tile = P.sk_t0 + tl;
+            const int c0 = (int)(g - (long long)tl * P.sk_nch);
             const int c1 = (int)min((long long)P.sk_nch, (long long)c0 + (g_end - g));
             u.prob = 0;
             u.mt = tile / P.n_col_tiles;
@@ -868,11 +890,12 @@ cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream
     if (P.n_split > 1 && (P.dir_seg_kb || !P.split_ws || P.sk_parts > 0 ||
                           P.kb_split % (PROMOTE_D / c.bk)))
         return cudaErrorInvalidValue;
+    const int parts = c.grid / (c.pair ? 2 : 1);
     if (P.sk_parts > 0 && (P.dir_seg_kb || !P.split_ws || P.sk_bn != c.bn ||
                            P.sk_nch != (P.n_kb + PROMOTE_D / c.bk - 1) / (PROMOTE_D / c.bk) ||
-                           P.sk_tm != (c.pair ? 2 : 1) * TC_BM ||
-                           (long long)P.sk_parts > (long long)P.n_tiles * P.sk_nch ||
-                           c.grid != P.sk_parts * (c.pair ? 2 : 1)))
+                           P.sk_tm != (c.pair ? 2 : 1) * TC_BM || P.sk_t0 < 0 ||
+                           P.sk_t0 % parts || P.sk_t0 >= P.n_tiles || P.sk_parts > parts ||
+                           (long long)P.sk_parts > (long long)(P.n_tiles - P.sk_t0) * P.sk_nch))
         return cudaErrorInvalidValue;
     if (p.prob[0].dir_seg_kb) {
         if (!p.prob[0].dir_park || c.grid > p.dir_park_ctas) return cudaErrorInvalidValue;

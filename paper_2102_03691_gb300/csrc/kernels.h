@@ -115,13 +115,15 @@ struct TcProblem {   // 128-byte aligned through CUtensorMap
     // adds the splits in order and runs the tile epilogue.  n_split <= 1: one unit per tile.
     int n_split, kb_split, ws_cols, m_pad;
     float *split_ws;
-    // Balanced split (sk_parts > 0, single problems only; n_tiles then counts tiles): the
-    // n_tiles x sk_nch promotion chunks of the block, tile-major (tile = mode tile x
-    // n_col_tiles + column tile), cut into sk_parts contiguous ranges of equal length, one per
-    // CTA (pair).  A tile cut by range boundaries stores segment s (the s-th range that touches
-    // it, in chunk order) to split_ws[s]; the finish kernel adds its segments in order.  sk_tm:
-    // modes per tile (128, or 256 for CTA pairs); sk_bn: columns per tile.
-    int sk_parts, sk_nch, sk_tm, sk_bn;
+    // Balanced split (sk_parts > 0, single problems only; n_tiles then counts tiles): the tiles
+    // below sk_t0 (whole waves: a multiple of the launch's CTAs or pairs) run whole,
+    // round-robin; the sk_nch promotion chunks of each remaining tile, tile-major (tile = mode
+    // tile x n_col_tiles + column tile), are cut into sk_parts contiguous ranges of equal
+    // length, one for each of the first sk_parts CTAs (pairs).  A tile cut by range boundaries
+    // stores segment s (the s-th range that touches it, in chunk order) to split_ws[s]; the
+    // finish kernel adds its segments in order.  sk_tm: modes per tile (128, or 256 for CTA
+    // pairs); sk_bn: columns per tile.
+    int sk_parts, sk_nch, sk_tm, sk_bn, sk_t0;
 };
 constexpr int DIR_PARK_THREADS = 256;                        // epilogue threads of the widest tile
 constexpr int DIR_PARK_SEG_FLOATS = 96 * DIR_PARK_THREADS;   // one parked segment of a CTA

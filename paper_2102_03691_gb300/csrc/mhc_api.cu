@@ -448,15 +448,16 @@ mhc_status apply_bins(mhc_handle *h, const std::vector<int> &bin_of_mode, int32_
     return reset_accumulators(h);
 }
 
-// Balanced split, host side (the kernels' arithmetic): the part holding chunk g when T chunks
-// are cut into `parts` ranges, and the plan of one block: chunks per tile, tiles, parts and the
-// largest number of segments any tile is cut into.
+// Balanced split, host side (the kernels' arithmetic): the part holding tail chunk g when T
+// chunks are cut into `parts` ranges, and the plan of one block: whole waves of tiles first
+// (t0 tiles on all `parts_all` CTAs or pairs), then the remaining tiles' chunks over
+// `parts` <= parts_all ranges; max_seg is the largest number of segments a tail tile is cut into.
 int sk_part_of_host(long long g, long long T, int parts) {
     return (int)(((g + 1) * parts + T - 1) / T - 1);
 }
 
 struct SkPlan {
-    int nch = 0, tiles = 0, parts = 0, max_seg = 1;
+    int nch = 0, tiles = 0, parts_all = 0, t0 = 0, parts = 0, max_seg = 1;
 };
 
 SkPlan sk_plan(const mhc_handle *h, const TcConfig &c, int n_col_tiles) {
@@ -464,10 +465,13 @@ SkPlan sk_plan(const mhc_handle *h, const TcConfig &c, int n_col_tiles) {
     const int chunk_kb = TC_PROMOTE_D / c.bk;
     q.nch = (int)((h->D_ld / c.bk + chunk_kb - 1) / chunk_kb);
     q.tiles = mode_tiles(h, c) * n_col_tiles;
-    const long long T = (long long)q.tiles * q.nch;
-    q.parts = (int)std::min<long long>(sched_units(h, c), T);
-    for (int t = 0; t < q.tiles; ++t) {
-        const long long g0 = (long long)t * q.nch;
+    q.parts_all = std::max(1, sched_units(h, c));
+    q.t0 = q.tiles / q.parts_all * q.parts_all;
+    if (q.t0 == q.tiles) return q;   // whole waves only: no tail, nothing to split
+    const long long T = (long long)(q.tiles - q.t0) * q.nch;
+    q.parts = (int)std::min<long long>(q.parts_all, T);
+    for (int t = q.t0; t < q.tiles; ++t) {
+        const long long g0 = (long long)(t - q.t0) * q.nch;
         q.max_seg = std::max(q.max_seg, 1 + sk_part_of_host(g0 + q.nch - 1, T, q.parts) -
                                             sk_part_of_host(g0, T, q.parts));
     }
@@ -562,10 +566,11 @@ mhc_status run_projection(mhc_handle *h, int K) {
     P.sk_parts = 0;
     P.ws_cols = P.n_col_tiles * c.bn;
     P.m_pad = (int)h->M_pad;
-    if (c.split == TC_SPLIT_BALANCED) {
-        // balanced split: one range of chunks per CTA (pair); tiles cut by a range boundary
-        // are finished by the split finish kernel
-        const SkPlan q = sk_plan(h, c, P.n_col_tiles);
+    const SkPlan skq = c.split == TC_SPLIT_BALANCED ? sk_plan(h, c, P.n_col_tiles) : SkPlan{};
+    if (c.split == TC_SPLIT_BALANCED && skq.parts > 0) {
+        // balanced split: whole waves of tiles, then one range of the tail's chunks per CTA
+        // (pair); tiles cut by a range boundary are finished by the split finish kernel
+        const SkPlan &q = skq;
         const size_t need = sizeof(float) * (size_t)q.max_seg * P.ws_cols * (size_t)h->M_pad;
         auto it = h->buf.find("split_ws");
         if (it == h->buf.end() || it->second.bytes < need)
@@ -576,9 +581,10 @@ mhc_status run_projection(mhc_handle *h, int K) {
         P.sk_nch = q.nch;
         P.sk_tm = (c.pair ? 2 : 1) * TC_BM;
         P.sk_bn = c.bn;
+        P.sk_t0 = q.t0;
         P.split_ws = dptr<float>(h, "split_ws");
         P.n_tiles = q.tiles;
-        c.grid = q.parts * (c.pair ? 2 : 1);
+        c.grid = q.parts_all * (c.pair ? 2 : 1);
         cudaError_t e = launch_tc_single(h->tcp, c, h->stream);
         h->launches++;
         if (e == cudaSuccess && q.max_seg > 1) {
@@ -589,7 +595,8 @@ mhc_status run_projection(mhc_handle *h, int K) {
             return fail(h, MHC_ERR_CUDA, "tensor-core kernel launch failed: %s", cudaGetErrorString(e));
         return MHC_OK;
     }
-    // d-axis split: whole promotion chunks per split, no empty split
+    // d-axis split: whole promotion chunks per split, no empty split (a balanced split whose
+    // tiles fill whole waves runs unsplit)
     const int chunk_kb = TC_PROMOTE_D / c.bk;
     int kb_split = P.n_kb, S = 1;
     if (c.split > 1) {
@@ -690,9 +697,9 @@ mhc_status time_projection(mhc_handle *h, const TcConfig &c, int K, cudaEvent_t 
 }
 
 // Autotune on the block just packed: time every tile shape unsplit (or with the fixed split of
-// mhc_params.split_d), then, when one block leaves schedulable units idle (fewer than three
-// waves of tiles), the balanced split and the uniform d-axis splits 2..8 of the two fastest
-// shapes.  The winner is cached.
+// mhc_params.split_d), then, for the two fastest shapes, the balanced split when the last wave
+// of tiles is partial and the uniform d-axis splits 2..8 when one block gives fewer than three
+// waves.  The winner is cached.
 mhc_status autotune(mhc_handle *h, int K) {
     const TuneKey key = tune_key(h, K);
     {
@@ -728,13 +735,14 @@ mhc_status autotune(mhc_handle *h, int K) {
             TcConfig c = res[q].second;
             const int n_kb = (int)(h->D_ld / c.bk), chunk_kb = TC_PROMOTE_D / c.bk;
             const int64_t units = (int64_t)mode_tiles(h, c) * ((4 * K + c.bn - 1) / c.bn);
-            if (units >= 3 * (int64_t)sched_units(h, c)) continue;
-            c.split = TC_SPLIT_BALANCED;
-            if (split_ws_bytes(h, c) <= budget) {
+            const int64_t su = sched_units(h, c);
+            c.split = TC_SPLIT_BALANCED;   // whenever the last wave is partial
+            if (units % su && split_ws_bytes(h, c) <= budget) {
                 float ms = 0.f;
                 if ((s = time_projection(h, c, K, e0, e1, 3, ms)) != MHC_OK) break;
                 res.emplace_back(ms, c);
             }
+            if (units >= 3 * su) continue;
             for (int S : {2, 3, 4, 6, 8}) {
                 if (n_kb < S * chunk_kb) break;
                 c.split = S;
