@@ -151,7 +151,7 @@ struct GroupSchedule {
 struct mhc_group {
     std::vector<mhc_handle *> hs;
     TcConfig tc{256, 64, 2, 0, 0};
-    bool tuned = false;
+    std::map<std::vector<int>, TcConfig> tuned;   // autotuned tile shape of each block-length vector
     TcParams<TC_MAX_GROUP> tcp{};
     std::map<std::pair<int, std::vector<int>>, GroupSchedule> sched_cache;   // (bn, Ks)
     // graphs of whole group pushes keyed by (Ks, input pointers, tile shape)
@@ -680,20 +680,36 @@ void tune_file_append_locked(const TuneKey &k, const TcConfig &c) {
     std::fclose(f);
 }
 
-// Device time (ms) of `reps` projections of the block just packed with configuration c
-// (after one warm-up launch).
-mhc_status time_projection(mhc_handle *h, const TcConfig &c, int K, cudaEvent_t e0, cudaEvent_t e1,
-                           int reps, float &ms) {
-    mhc_status s = set_tc_config(h, c);
-    if (s != MHC_OK) return s;
-    if ((s = run_projection(h, K)) != MHC_OK) return s;   // warm-up
-    MHC_CUDA(h, cudaEventRecord(e0, h->stream));
-    for (int r = 0; r < reps; ++r)
-        if ((s = run_projection(h, K)) != MHC_OK) return s;
-    MHC_CUDA(h, cudaEventRecord(e1, h->stream));
-    MHC_CUDA(h, cudaEventSynchronize(e1));
-    MHC_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
-    return MHC_OK;
+// Time candidate configurations in interleaved rounds (one warm-up launch each, then
+// `rounds` rounds of one timed launch of every candidate) and keep each candidate's fastest
+// launch: the candidates see the same clock and power state, where timing them one after the
+// other let the power cap, reached during the first candidates' launches, slow the last ones.
+mhc_status time_candidates(mhc_handle *h, int K, std::vector<std::pair<float, TcConfig>> &cands,
+                           int rounds = 3) {
+    cudaEvent_t e0, e1;
+    MHC_CUDA(h, cudaEventCreate(&e0));
+    MHC_CUDA(h, cudaEventCreate(&e1));
+    mhc_status s = MHC_OK;
+    for (auto &x : cands) {
+        x.first = 1e30f;
+        if ((s = set_tc_config(h, x.second)) != MHC_OK || (s = run_projection(h, K)) != MHC_OK) break;
+    }
+    for (int r = 0; r < rounds && s == MHC_OK; ++r)
+        for (auto &x : cands) {
+            float ms = 0.f;
+            if ((s = set_tc_config(h, x.second)) != MHC_OK) break;
+            if (cudaEventRecord(e0, h->stream) != cudaSuccess) { s = fail(h, MHC_ERR_CUDA, "event record"); break; }
+            if ((s = run_projection(h, K)) != MHC_OK) break;
+            if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                s = fail(h, MHC_ERR_CUDA, "autotune timing failed");
+                break;
+            }
+            x.first = std::min(x.first, ms);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
 }
 
 // Autotune on the block just packed: time every tile shape unsplit (or with the fixed split of
@@ -711,50 +727,44 @@ mhc_status autotune(mhc_handle *h, int K) {
             return set_tc_config(h, it->second);
         }
     }
-    cudaEvent_t e0, e1;
-    MHC_CUDA(h, cudaEventCreate(&e0));
-    MHC_CUDA(h, cudaEventCreate(&e1));
     std::vector<std::pair<float, TcConfig>> res;
     const int fixed =
         h->prm.split_d == TC_SPLIT_BALANCED ? TC_SPLIT_BALANCED : std::max(1, (int)h->prm.split_d);
-    mhc_status s = MHC_OK;
     for (TcConfig c : TC_CONFIGS) {
         c.split = fixed;
-        float ms = 0.f;
-        if ((s = time_projection(h, c, K, e0, e1, 3, ms)) != MHC_OK) break;
-        res.emplace_back(ms, c);
+        res.emplace_back(0.f, c);
     }
+    mhc_status s = time_candidates(h, K, res);
     if (s == MHC_OK && h->prm.split_d == 0 && !h->dir) {
         std::sort(res.begin(), res.end(),
                   [](const std::pair<float, TcConfig> &a, const std::pair<float, TcConfig> &b) {
                       return a.first < b.first;
                   });
+        // the two fastest shapes again, unsplit, beside their splits (timed in the same rounds)
+        std::vector<std::pair<float, TcConfig>> sp;
         const size_t n_shapes = std::min<size_t>(2, res.size());
         const size_t budget = (size_t)512 << 20;   // largest split workspace tried
-        for (size_t q = 0; q < n_shapes && s == MHC_OK; ++q) {
+        for (size_t q = 0; q < n_shapes; ++q) {
             TcConfig c = res[q].second;
+            sp.emplace_back(0.f, c);
             const int n_kb = (int)(h->D_ld / c.bk), chunk_kb = TC_PROMOTE_D / c.bk;
             const int64_t units = (int64_t)mode_tiles(h, c) * ((4 * K + c.bn - 1) / c.bn);
             const int64_t su = sched_units(h, c);
             c.split = TC_SPLIT_BALANCED;   // whenever the last wave is partial
-            if (units % su && split_ws_bytes(h, c) <= budget) {
-                float ms = 0.f;
-                if ((s = time_projection(h, c, K, e0, e1, 3, ms)) != MHC_OK) break;
-                res.emplace_back(ms, c);
-            }
+            if (units % su && split_ws_bytes(h, c) <= budget) sp.emplace_back(0.f, c);
             if (units >= 3 * su) continue;
             for (int S : {2, 3, 4, 6, 8}) {
                 if (n_kb < S * chunk_kb) break;
                 c.split = S;
                 if (split_ws_bytes(h, c) > budget) break;
-                float ms = 0.f;
-                if ((s = time_projection(h, c, K, e0, e1, 3, ms)) != MHC_OK) break;
-                res.emplace_back(ms, c);
+                sp.emplace_back(0.f, c);
             }
         }
+        if (sp.size() > n_shapes) {
+            s = time_candidates(h, K, sp);
+            res = sp;
+        }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (s != MHC_OK) return s;
     TcConfig best_c = h->tc;
     float best = 1e30f;
@@ -1805,33 +1815,53 @@ mhc_status group_launch(mhc_group *g, const std::vector<int> &Ks) {
 }
 
 mhc_status group_autotune(mhc_group *g, const std::vector<int> &Ks) {
+    // interleaved rounds over the shapes, each shape's fastest launch (as time_candidates)
     mhc_handle *h0 = g->hs[0];
     cudaEvent_t e0, e1;
     MHC_CUDA(h0, cudaEventCreate(&e0));
     MHC_CUDA(h0, cudaEventCreate(&e1));
-    float best = 1e30f;
-    TcConfig best_c = g->tc;
-    mhc_status s;
-    for (const TcConfig &c : TC_CONFIGS) {
-        g->tc = c;
-        if ((s = group_encode(g)) != MHC_OK) return s;
-        if ((s = group_launch(g, Ks)) != MHC_OK) return s;   // warm-up
-        MHC_CUDA(h0, cudaEventRecord(e0, h0->stream));
-        for (int r = 0; r < 3; ++r)
-            if ((s = group_launch(g, Ks)) != MHC_OK) return s;
-        MHC_CUDA(h0, cudaEventRecord(e1, h0->stream));
-        MHC_CUDA(h0, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        MHC_CUDA(h0, cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_c = c;
-        }
+    float best_ms[TC_NUM_CONFIGS];
+    mhc_status s = MHC_OK;
+    for (int q = 0; q < TC_NUM_CONFIGS && s == MHC_OK; ++q) {   // warm-up (and schedules)
+        best_ms[q] = 1e30f;
+        g->tc = TC_CONFIGS[q];
+        if ((s = group_encode(g)) == MHC_OK) s = group_launch(g, Ks);
     }
+    for (int r = 0; r < 3 && s == MHC_OK; ++r)
+        for (int q = 0; q < TC_NUM_CONFIGS && s == MHC_OK; ++q) {
+            g->tc = TC_CONFIGS[q];
+            if ((s = group_encode(g)) != MHC_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e0, h0->stream) != cudaSuccess) { s = fail(h0, MHC_ERR_CUDA, "event record"); break; }
+            if ((s = group_launch(g, Ks)) != MHC_OK || (s = group_launch(g, Ks)) != MHC_OK) break;
+            if (cudaEventRecord(e1, h0->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                s = fail(h0, MHC_ERR_CUDA, "group autotune timing failed");
+                break;
+            }
+            best_ms[q] = std::min(best_ms[q], ms);   // two launches back to back, as in a run
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    g->tc = best_c;
-    g->tuned = true;
+    if (s != MHC_OK) return s;
+    int best = 0;
+    for (int q = 1; q < TC_NUM_CONFIGS; ++q)
+        if (best_ms[q] < best_ms[best]) best = q;
+    g->tc = TC_CONFIGS[best];
+    g->tuned[Ks] = g->tc;
+    return group_encode(g);
+}
+
+// The tile shape for block lengths Ks: fixed (tile_config), cached, or autotuned now (on the
+// blocks just packed).  Re-encodes the tensor maps when the shape changes.
+mhc_status group_select(mhc_group *g, const std::vector<int> &Ks) {
+    if (g->hs[0]->prm.tile_config != 0) return MHC_OK;
+    auto it = g->tuned.find(Ks);
+    if (it == g->tuned.end()) return group_autotune(g, Ks);
+    const TcConfig &c = it->second;
+    if (c.bn == g->tc.bn && c.bk == g->tc.bk && c.stages == g->tc.stages && c.pair == g->tc.pair)
+        return MHC_OK;
+    g->tc = c;
     return group_encode(g);
 }
 
@@ -1956,7 +1986,7 @@ mhc_status mhc_group_autotune_k(mhc_group *g, const int32_t *candidates, int32_t
     for (int32_t q = 0; q < n && s == MHC_OK; ++q) {
         const std::vector<int> Ks(m, candidates[q]);
         if ((s = group_pack(g, vs, ws, Ks)) != MHC_OK) break;
-        if (!g->tuned && h0->prm.tile_config == 0 && (s = group_autotune(g, Ks)) != MHC_OK) break;
+        if ((s = group_select(g, Ks)) != MHC_OK) break;   // each K with its own tile shape
         const int reps = 3;
         cudaError_t e = cudaEventRecord(e0, h0->stream);
         for (int r = 0; r < reps && s == MHC_OK; ++r)
@@ -1980,6 +2010,7 @@ mhc_status mhc_group_autotune_k(mhc_group *g, const int32_t *candidates, int32_t
     cudaEventDestroy(e1);
     if (s != MHC_OK) return s;
     for (size_t j = 0; j < m; ++j) g->hs[j]->K_last = 0;   // operands overwritten
+    if ((s = group_select(g, std::vector<int>(m, bestK))) != MHC_OK) return s;
     *best_K = bestK;
     if (units_per_s) *units_per_s = best;
     return MHC_OK;
@@ -2007,7 +2038,8 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
         if ((s = stage_issue(g->hs[j], vs[j], ws[j], Ks[j], where)) != MHC_OK) return s;
     for (size_t j = 0; j < n; ++j)
         if ((s = stage_wait(g->hs[j])) != MHC_OK) return s;
-    const bool tuned = g->tuned || h0->prm.tile_config != 0;
+    const bool tuned = h0->prm.tile_config != 0 || g->tuned.count(Ks);
+    if (tuned && (s = group_select(g, Ks)) != MHC_OK) return s;
     const bool profile = (h0->prm.flags & MHC_FLAG_PROFILE) != 0;
     if (tuned && !(h0->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL))) {
         // replay (or capture once) the whole group push as one CUDA graph
@@ -2073,9 +2105,7 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
         return MHC_OK;
     }
     if ((s = group_pack(g, vs, ws, Ks)) != MHC_OK) return s;
-    if (!g->tuned && h0->prm.tile_config == 0) {
-        if ((s = group_autotune(g, Ks)) != MHC_OK) return s;
-    }
+    if ((s = group_select(g, Ks)) != MHC_OK) return s;
     cudaEvent_t ev1 = nullptr;
     if (profile) {   // time the grouped launch with the first handle's event pairs
         if (h0->prof_used == h0->prof_events.size()) {
