@@ -50,7 +50,9 @@ def parse():
                     choices=sorted(synth.WORKLOADS) + ["cnt_group16", "shc_si_n8000"])
     ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "bf16x3", "fp32"])
     ap.add_argument("--fp32-steps", type=int, default=12)
-    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="steps of the end-to-end loop (0: as many as --steps, so that both loops "
+                         "run about as long and see the same clock and power state)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-config", type=int, default=0,
@@ -400,7 +402,7 @@ def run_group(args):
         units_per_step += float(D) * N * K
         flops_launch += 3 * 2.0 * D * D * 4 * K
     out_dev = torch.empty(len(handles) * B * 3, dtype=torch.float64, device=dev)
-    n_e2e = max(3, args.e2e_steps)   # its own step count: the loop is host-driven
+    n_e2e = max(3, args.e2e_steps or args.steps)
     out_host = torch.empty((n_e2e, len(handles) * B * 3), dtype=torch.float64).pin_memory()
 
     def step(i, host=False):
@@ -513,7 +515,7 @@ def run_shc(args):
     out = torch.empty((9, f.size), dtype=torch.float64, device=dev)
     unit = "atom·lag·steps/s"
 
-    n_e2e = max(3, args.e2e_steps)   # its own step count: the loop is host-driven
+    n_e2e = max(3, args.e2e_steps or args.steps)
     res_host = torch.empty((n_e2e, 9, f.size), dtype=torch.float64, pin_memory=True)
 
     def step(i, host=False):
@@ -759,7 +761,7 @@ def main():
     # (the library stages host inputs in two buffers on a copy stream, so the upload of one push
     # overlaps the kernels of the previous one) and copies that step's kappa back into pinned
     # host memory; the host waits once, at the end
-    n_e2e = max(3, args.e2e_steps)   # its own step count: the loop is host-driven
+    n_e2e = max(3, args.e2e_steps or args.steps)
     res_host = torch.empty((n_e2e, kap_w.numel()), dtype=torch.float64, pin_memory=True)
 
     def e2e_step(i):
