@@ -18,7 +18,7 @@ least 48 modes -- every bin of these workloads), the ratio S / |o| at the worst 
 the median; and, over all bins, which bin is worst.
 
   python tests/perbin_error_table.py --workload gkma_si_n8000 --steps 2048 \
-      --precision fp16x3 bf16x3 --out gpurun_out/perbin_gkma_si_n8000
+      --precision fp16x3 bf16x3 --out perbin_gkma_si_n8000
 """
 from __future__ import annotations
 
