@@ -445,7 +445,8 @@ cudaError_t launch_pack_bulk_group(PackGroupArgs g, int csize, cudaStream_t s) {
 }
 }  // namespace
 
-cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s, int *n_launches) {
+cudaError_t launch_pack_group(const PackGroupArgs &g, const cudaStream_t *streams, int n_streams,
+                              int *n_launches) {
     *n_launches = 0;
     if (g.n < 1 || g.n > TC_MAX_GROUP) return cudaErrorInvalidValue;
     int nmax = 0;
@@ -465,6 +466,7 @@ cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s, int *n_lau
                     ((g.a[j].N + apc - 1) / apc == cs || (g.a[j].N == 0 && cs == 1)))
                     sub.a[sub.n++] = g.a[j];
             if (sub.n == 0) continue;
+            const cudaStream_t s = streams[*n_launches % n_streams];   // independent systems
             const cudaError_t e = threads == 128 ? launch_pack_bulk_group<128>(sub, cs, s)
                                   : threads == 256 ? launch_pack_bulk_group<256>(sub, cs, s)
                                                    : launch_pack_bulk_group<512>(sub, cs, s);

@@ -61,7 +61,11 @@ struct PackGroupArgs {
     int cta_begin[TC_MAX_GROUP + 1];
     int n;
 };
-cudaError_t launch_pack_group(const PackGroupArgs &g, cudaStream_t s, int *n_launches);
+// The launches go round-robin to streams[0 .. n_streams) (the systems of different launches are
+// independent); the caller orders the other streams after streams[0] before the call and
+// streams[0] after them afterwards.
+cudaError_t launch_pack_group(const PackGroupArgs &g, const cudaStream_t *streams, int n_streams,
+                              int *n_launches);
 
 // ---------------------------------------------------------------- E preparation
 // max |E| over the valid D x M region (bit pattern of a non-negative float)

@@ -163,6 +163,10 @@ struct mhc_group {
     std::map<std::tuple<std::vector<int>, std::vector<const void *>, int>, GraphEntry> graphs;
     uint64_t graph_clock = 0;
     cudaStream_t cap_stream = nullptr;
+    // side streams for the grouped packs (fork after the main stream, join before it goes on)
+    static constexpr int PACK_SIDE = 3;
+    cudaStream_t pack_side[PACK_SIDE] = {};
+    cudaEvent_t pack_fork = nullptr, pack_join[PACK_SIDE] = {};
 };
 
 namespace {
@@ -1746,8 +1750,25 @@ mhc_status group_pack(mhc_group *g, const std::vector<const float *> &vs,
     PackGroupArgs pg{};
     pg.n = (int)g->hs.size();
     for (int j = 0; j < pg.n; ++j) pg.a[j] = pack_args(g->hs[j], vs[j], ws[j], Ks[j]);
+    if (!g->pack_fork) {
+        MHC_CUDA(h0, cudaEventCreateWithFlags(&g->pack_fork, cudaEventDisableTiming));
+        for (int q = 0; q < mhc_group::PACK_SIDE; ++q) {
+            MHC_CUDA(h0, cudaStreamCreateWithFlags(&g->pack_side[q], cudaStreamNonBlocking));
+            MHC_CUDA(h0, cudaEventCreateWithFlags(&g->pack_join[q], cudaEventDisableTiming));
+        }
+    }
+    cudaStream_t streams[1 + mhc_group::PACK_SIDE] = {h0->stream};
+    MHC_CUDA(h0, cudaEventRecord(g->pack_fork, h0->stream));
+    for (int q = 0; q < mhc_group::PACK_SIDE; ++q) {
+        streams[1 + q] = g->pack_side[q];
+        MHC_CUDA(h0, cudaStreamWaitEvent(g->pack_side[q], g->pack_fork, 0));
+    }
     int nl = 0;
-    const cudaError_t e = launch_pack_group(pg, h0->stream, &nl);
+    const cudaError_t e = launch_pack_group(pg, streams, 1 + mhc_group::PACK_SIDE, &nl);
+    for (int q = 0; q < mhc_group::PACK_SIDE; ++q) {   // join every side stream (also on error)
+        MHC_CUDA(h0, cudaEventRecord(g->pack_join[q], g->pack_side[q]));
+        MHC_CUDA(h0, cudaStreamWaitEvent(h0->stream, g->pack_join[q], 0));
+    }
     if (e == cudaErrorNotSupported) {
         for (int j = 0; j < pg.n; ++j) {
             const mhc_status s = pack_block(g->hs[j], vs[j], ws[j], Ks[j]);
@@ -1905,6 +1926,11 @@ void mhc_group_destroy(mhc_group *g) {
     for (auto &kv : g->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    for (int q = 0; q < mhc_group::PACK_SIDE; ++q) {
+        if (g->pack_side[q]) cudaStreamDestroy(g->pack_side[q]);
+        if (g->pack_join[q]) cudaEventDestroy(g->pack_join[q]);
+    }
+    if (g->pack_fork) cudaEventDestroy(g->pack_fork);
     for (auto &kv : g->sched_cache) {
         if (kv.second.sched.p) cudaFree(kv.second.sched.p);
         if (kv.second.cta_begin.p) cudaFree(kv.second.cta_begin.p);
