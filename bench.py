@@ -499,7 +499,7 @@ def run_shc(args):
     step = one block of K = 256 samples + the spectrum read-out (Eq. 22-23).  Unit: atom.lag.steps/s."""
     world, rank, local = dist_init(args)
     import torch
-    from paper_2102_03691_gb300.mhc import SpectralHeatCurrent
+    from paper_2102_03691_gb300.mhc import SpectralHeatCurrent, measure_fp32_fma
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     N, nc, K, P = 8000, 250, 256, 8
@@ -578,12 +578,12 @@ def run_shc(args):
     flops_step = 2.0 * 9 * N * nc * K            # Eq. 21 by its definition: 9 products per atom, lag, step
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_src = measured_peaks()
-    fp32_peak = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     k_launch_s = kms / 1e3 / kn if kn else None
     if args.precision == "fp32":
         roof = {"bound": "alu", "kernel": "shc_corr_kernel (FP32 CUDA cores)",
-                "achieved": flops_step / k_launch_s / 1e12, "unit": "TFLOP/s", "peak": fp32_peak,
-                "peak_source": "derived: SMs x 128 FP32 FMA/clk x 2 flop x max SM clock"}
+                "achieved": flops_step / k_launch_s / 1e12, "unit": "TFLOP/s",
+                "peak": measure_fp32_fma(local),
+                "peak_source": "measured: FP32 FMA microbenchmark (mhc_measure_fp32_fma)"}
     else:
         # 128 (tau) x 256 (t) tiles touching the band 0 <= t - tau < nc of a block at t0 = 4K
         t0s, Tt, Ts = 4 * K, 128, 256
@@ -645,7 +645,7 @@ def main():
 
     world, rank, local = dist_init(args)
     import torch
-    from paper_2102_03691_gb300.mhc import FLAG_PROFILE, ModalHeatCurrent
+    from paper_2102_03691_gb300.mhc import FLAG_PROFILE, ModalHeatCurrent, measure_fp32_fma
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     N, M, K, L, B = w["N"], w["M"], w["K"], w["L"], w["B"]
@@ -839,6 +839,10 @@ def main():
         props = torch.cuda.get_device_properties(dev)
         fp32["fp32_peak_derived_tflops"] = (props.multi_processor_count * 128 * 2 *
                                             float(measured_peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6 / 1e12)
+        fp32["fp32_peak_measured_tflops"] = measure_fp32_fma(local)   # FMA microbenchmark
+        fp32["projection_frac_of_measured_fp32_peak"] = (
+            fp32["projection_tflops"] / fp32["fp32_peak_measured_tflops"]
+            if fp32.get("projection_tflops") else None)
         del a, b
 
     if rank != 0:

@@ -126,7 +126,52 @@ __global__ void __launch_bounds__(128) fp32_dir_epilogue_kernel(const float *__r
     }
 }
 
+// FP32 FMA throughput: every thread runs FMA_CHAINS independent dependency chains of
+// a = a * m + c (m just below 1, so values stay finite), the chains interleaved so that the
+// pipe never waits on one; one value per thread is stored so that nothing is dropped.
+constexpr int FMA_CHAINS = 16;
+__global__ void __launch_bounds__(256) fma_peak_kernel(float *out, int iters) {
+    float a[FMA_CHAINS];
+#pragma unroll
+    for (int q = 0; q < FMA_CHAINS; ++q) a[q] = 1e-3f * (float)(threadIdx.x + q);
+    const float m = 0.9999999f, c = 1e-7f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < FMA_CHAINS; ++q) a[q] = fmaf(a[q], m, c);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < FMA_CHAINS; ++q) t += a[q];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 }  // namespace
+
+cudaError_t measure_fp32_fma(cudaStream_t s, int sm_count, double *tflops) {
+    const int blocks = sm_count * 8, threads = 256, iters = 4096;
+    float *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, sizeof(float) * blocks * threads);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0.f;
+    for (int r = 0; r < 4 && e == cudaSuccess; ++r) {   // launch 0 warms up
+        cudaEventRecord(e0, s);
+        fma_peak_kernel<<<blocks, threads, 0, s>>>(out, iters);
+        cudaEventRecord(e1, s);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && (best == 0.f || ms < best)) best = ms;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && best > 0.f)
+        *tflops = 2.0 * (double)blocks * threads * iters * FMA_CHAINS / (best * 1e-3) / 1e12;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    return e;
+}
 
 void launch_sgemm(const float *Et32, const float *Bt32, float *R, int Dk, int ld, int Mp, int C,
                   cudaStream_t s) {

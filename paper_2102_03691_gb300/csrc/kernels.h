@@ -86,6 +86,8 @@ void launch_orthonormality(const void *E, int dtype, int layout, int64_t ld, int
 // ---------------------------------------------------------------- FP32 path
 // R[c][n] = sum_{d < Dk} Bt32[c][d] Et32[n][d] for c < C (rows of the block), n < Mp;
 // both operands have row pitch ld (Dk a multiple of 16).
+// Measured FP32 FMA throughput of the device (the comparison path's peak), TFLOP/s.
+cudaError_t measure_fp32_fma(cudaStream_t s, int sm_count, double *tflops);
 void launch_sgemm(const float *Et32, const float *Bt32, float *R, int Dk, int ld, int Mp, int C,
                   cudaStream_t s);
 // J_n^a(k) = R[4k][n] R[4k+1+a][n]; segmented bin sums into partials[k][a][slot].

@@ -1019,6 +1019,24 @@ const char *mhc_last_error(const mhc_handle *h) {
     return h ? h->err.c_str() : g_create_error.c_str();
 }
 
+mhc_status mhc_measure_fp32_fma(int32_t device, void *stream, double *tflops) {
+    set_handleless_error("");
+    if (!tflops) {
+        set_handleless_error("mhc_measure_fp32_fma: null output");
+        return MHC_ERR_INVALID_ARG;
+    }
+    int sms = 0;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = measure_fp32_fma(static_cast<cudaStream_t>(stream), sms, tflops);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_handleless_error(cudaGetErrorString(e));
+        return MHC_ERR_CUDA;
+    }
+    return MHC_OK;
+}
+
 mhc_status mhc_create(mhc_handle **out, const mhc_params *p) {
     if (!out || !p) return fail(nullptr, MHC_ERR_INVALID_ARG, "null argument");
     *out = nullptr;

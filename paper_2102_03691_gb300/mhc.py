@@ -31,7 +31,7 @@ FLAG_XCORR = 0x20
 EXPORTS = (
     "mhc_default_params", "mhc_create", "mhc_destroy", "mhc_last_error", "mhc_status_string",
     "mhc_set_modes", "mhc_set_bins_uniform", "mhc_set_bin_ids", "mhc_push", "mhc_sync",
-    "mhc_autotune_k", "mhc_lattice_modes", "mhc_group_autotune_k",
+    "mhc_autotune_k", "mhc_lattice_modes", "mhc_group_autotune_k", "mhc_measure_fp32_fma",
     "mhc_read_binned_current", "mhc_read_total_current", "mhc_read_hnema", "mhc_read_corr",
     "mhc_read_kappa_gk", "mhc_check_orthonormality", "mhc_get_info", "mhc_set_flags",
     "mhc_kernel_time", "mhc_read_xcorr", "mhc_read_kappa_xcorr",
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.mhc_autotune_k.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     L.mhc_lattice_modes.argtypes = [i32, vp, i64, vp, vp, i32, dbl, i32, vp, vp, vp, i32,
                                     ctypes.POINTER(i32)]
+    L.mhc_measure_fp32_fma.argtypes = [i32, vp, ctypes.POINTER(dbl)]
     L.mhc_read_binned_current.argtypes = [vp, vp, i32]
     L.mhc_read_total_current.argtypes = [vp, vp, i32]
     L.mhc_read_hnema.argtypes = [vp, vp, vp, i32]
@@ -288,6 +289,17 @@ class SpectralHeatCurrent:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp32_fma(device: int = 0, stream=None) -> float:
+    """mhc_measure_fp32_fma: the device's measured FP32 FMA throughput, TFLOP/s."""
+    L = load()
+    out = ctypes.c_double()
+    st = L.mhc_measure_fp32_fma(device, stream if stream is not None else _current_stream(device),
+                                ctypes.byref(out))
+    if st != 0:
+        raise MhcError(st, L.mhc_last_error(None).decode())
+    return out.value
 
 
 def lattice_modes(Phi, mass_amu, E_out=None, device: int = 0, stream=None, tol: float = 1e-14,

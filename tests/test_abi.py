@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(__file__), "..", "include", "mhc.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mhc_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mhc_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_lists_match_binding():

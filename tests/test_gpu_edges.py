@@ -164,3 +164,14 @@ def test_green_kubo_read_out_beyond_1024_lags():
     skt = oracle.gk_kappa(np.abs(C), cnt, dt, TK, V)
     check(kt, okt, skt, None, 1e-11, "1100 lags Green-Kubo stage")
     h.close()
+
+
+def test_fp32_fma_measurement():
+    # the FP32 comparison path's peak: a plausible FMA throughput (152 SMs x 128 lanes x 2 flops
+    # at 1-2.1 GHz is 39-82 TFLOP/s), and the C ABI rejects a null output
+    need_gpu()
+    import ctypes
+    from paper_2102_03691_gb300 import mhc
+    t = mhc.measure_fp32_fma(0)
+    assert 20.0 < t < 200.0, t
+    assert mhc.load().mhc_measure_fp32_fma(0, None, None) == 1
