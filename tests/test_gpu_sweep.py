@@ -1,6 +1,6 @@
 """Seeded random sweep of shapes and options through the C ABI against the FP64 oracle: atoms,
 kept modes, block length, bins, lags, excluded modes, precision, the direction split and the
-cross-correlations drawn at random, every output compared (binned currents, total current,
+cross-correlations and the d-axis split drawn at random, every output compared (binned currents, total current,
 Eq. 17 sums, HNEMA means, cross-correlations)."""
 import numpy as np
 import pytest
@@ -23,13 +23,18 @@ def draw(i):
     T = max(T, 1)
     B = int(rng.integers(1, 12))
     L = int(rng.integers(1, 40))
-    return dict(N=N, M=M, K=K, T=T, B=B, L=L, f_hi=float(rng.uniform(10, 20)),
-                cut=float(rng.uniform(0.6, 1.0)), precision=["fp32", "fp16x3"][i % 2],
-                direction=bool(rng.integers(0, 2)), xcorr=bool(rng.integers(0, 2)),
-                layout=["dof", "mode"][int(rng.integers(0, 2))], host=bool(rng.integers(0, 2)))
+    d = dict(N=N, M=M, K=K, T=T, B=B, L=L, f_hi=float(rng.uniform(10, 20)),
+             cut=float(rng.uniform(0.6, 1.0)), precision=["fp32", "fp16x3"][i % 2],
+             direction=bool(rng.integers(0, 2)), xcorr=bool(rng.integers(0, 2)),
+             layout=["dof", "mode"][int(rng.integers(0, 2))], host=bool(rng.integers(0, 2)))
+    # d-axis split of the tensor-core path: autotuned, none, uniform or balanced (the direction
+    # split takes none)
+    split = [0, 1, 2, 3, -1][int(rng.integers(0, 5))]
+    d["split_d"] = split if d["precision"] != "fp32" and not d["direction"] else 0
+    return d
 
 
-@pytest.mark.parametrize("i", range(12))
+@pytest.mark.parametrize("i", range(20))
 def test_random_shapes_and_options(i):
     need_gpu()
     from paper_2102_03691_gb300.mhc import ModalHeatCurrent
@@ -42,7 +47,7 @@ def test_random_shapes_and_options(i):
     f_max = d["cut"] * d["f_hi"]   # modes above f_max are excluded
     bins = oracle.bins_uniform(f, 0.0, f_max, B)
     h = ModalHeatCurrent(precision=d["precision"], k_max=K, n_lags=L, direction=d["direction"],
-                         xcorr=d["xcorr"])
+                         xcorr=d["xcorr"], split_d=d["split_d"])
     Ein = E if d["layout"] == "dof" else np.ascontiguousarray(E.T)
     h.set_modes(Ein, mass, f, layout=d["layout"])
     h.set_bins_uniform(0.0, f_max, B)
