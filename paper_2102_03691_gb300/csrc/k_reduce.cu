@@ -48,11 +48,13 @@ __device__ __forceinline__ void bin_finish_body(const float *__restrict__ partia
     }
 }
 
+// steps: the step counter to advance by K here (no later kernel of the push reads it), or null.
 __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__restrict__ partials,
                                                                 int n_slots, const int *slot_begin,
                                                                 int B, int K, float *Jb,
                                                                 double *hsum, const double *Jtot,
-                                                                double *Jsum) {
+                                                                double *Jsum, long long *steps) {
+    if (steps && blockIdx.x == 0 && threadIdx.x == 0) *steps += K;
     bin_finish_body(partials, n_slots, slot_begin, B, K, Jb, hsum, Jtot, Jsum, blockIdx.x);
 }
 
@@ -60,6 +62,7 @@ __global__ void __launch_bounds__(BF_THREADS) bin_finish_kernel(const float *__r
 __global__ void __launch_bounds__(BF_THREADS) bin_finish_group_kernel(const __grid_constant__ FinishGroupArgs g) {
     int j = 0;
     while (j + 1 < g.n && (int)blockIdx.x >= g.cta_begin[j + 1]) ++j;
+    if (g.advance && (int)blockIdx.x == g.cta_begin[j] && threadIdx.x == 0) *g.steps[j] += g.K[j];
     bin_finish_body(g.partials[j], g.n_slots[j], g.slot_begin[j], g.B[j], g.K[j], g.Jb[j],
                     g.hsum[j], g.Jtot[j], g.Jsum[j], (int)blockIdx.x - g.cta_begin[j]);
 }
@@ -322,9 +325,11 @@ __global__ void lag_counts_kernel(long long T_s, int L, long long *count) {
 }  // namespace
 
 void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin, int B, int K,
-                       float *Jb, double *hsum, const double *Jtot, double *Jsum, cudaStream_t s) {
+                       float *Jb, double *hsum, const double *Jtot, double *Jsum, long long *steps,
+                       cudaStream_t s) {
     if (B <= 0 || K <= 0) return;
-    bin_finish_kernel<<<B, BF_THREADS, 0, s>>>(partials, n_slots, slot_begin, B, K, Jb, hsum, Jtot, Jsum);
+    bin_finish_kernel<<<B, BF_THREADS, 0, s>>>(partials, n_slots, slot_begin, B, K, Jb, hsum, Jtot, Jsum,
+                                               steps);
 }
 
 namespace {

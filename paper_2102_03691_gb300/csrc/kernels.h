@@ -220,8 +220,11 @@ void launch_shc_tc_reduce(const ShcTcParams &p, double *Ksum, cudaStream_t s);
 // ---------------------------------------------------------------- K3 .. K5
 // Jb[k][b][a] = sum of partial slots of bin b; HNEMA sums += sum_k Jb (FP64);
 // Jsum[a] += sum_k Jtot[k][a].
+// steps (or null): the device step counter, advanced by K by the same launch when no later
+// kernel of the push reads it.
 void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin, int B, int K,
-                       float *Jb, double *hsum, const double *Jtot, double *Jsum, cudaStream_t s);
+                       float *Jb, double *hsum, const double *Jtot, double *Jsum, long long *steps,
+                       cudaStream_t s);
 // The bin finish (as launch_bin_finish) and the step counters (*steps += K) of up to
 // TC_MAX_GROUP systems, one launch each; cta_begin is filled by the launcher.
 struct FinishGroupArgs {
@@ -236,6 +239,7 @@ struct FinishGroupArgs {
     long long *steps[TC_MAX_GROUP];
     int cta_begin[TC_MAX_GROUP + 1];
     int n;
+    int advance;   // 1: the bin finish also advances the step counters (no correlation kernels)
 };
 void launch_bin_finish_group(FinishGroupArgs g, cudaStream_t s);
 void launch_advance_steps_group(const FinishGroupArgs &g, cudaStream_t s);

@@ -889,14 +889,19 @@ mhc_status correlate_block(mhc_handle *h, int K) {
 
 // Kernels that close a push: bin finish + HNEMA sums, correlations, step counter.
 mhc_status finish_kernels(mhc_handle *h, int K) {
+    // without correlation kernels (which read the step counter) the bin finish advances it
+    const bool corr = (h->prm.flags & MHC_FLAG_GKMA) || has_xcorr(h);
     launch_bin_finish(dptr<float>(h, "partials"), (int)slot_stride(h), dptr<int>(h, "slot_begin"),
                       (int)n_out_bins(h), K, dptr<float>(h, "Jb"), dptr<double>(h, "hsum"),
-                      dptr<double>(h, "Jtot"), dptr<double>(h, "Jsum"), h->stream);
+                      dptr<double>(h, "Jtot"), dptr<double>(h, "Jsum"),
+                      corr ? nullptr : dptr<long long>(h, "steps_dev"), h->stream);
     h->launches++;
-    mhc_status s = correlate_block(h, K);
-    if (s != MHC_OK) return s;
-    launch_advance_steps(dptr<long long>(h, "steps_dev"), K, h->stream);
-    h->launches++;
+    if (corr) {
+        mhc_status s = correlate_block(h, K);
+        if (s != MHC_OK) return s;
+        launch_advance_steps(dptr<long long>(h, "steps_dev"), K, h->stream);
+        h->launches++;
+    }
     MHC_CUDA(h, cudaGetLastError());
     return MHC_OK;
 }
@@ -1818,9 +1823,14 @@ mhc_status group_finish(mhc_group *g, const std::vector<int> &Ks) {
         fg.Jsum[j] = dptr<double>(h, "Jsum");
         fg.steps[j] = dptr<long long>(h, "steps_dev");
     }
+    // without correlation kernels (which read the step counters) the bin finish advances them
+    bool corr = false;
+    for (mhc_handle *h : g->hs) corr = corr || (h->prm.flags & MHC_FLAG_GKMA) || has_xcorr(h);
+    fg.advance = corr ? 0 : 1;
     launch_bin_finish_group(fg, h0->stream);
     h0->launches++;
     MHC_CUDA(h0, cudaGetLastError());
+    if (!corr) return MHC_OK;
     for (int j = 0; j < fg.n; ++j) {
         const mhc_status s = correlate_block(g->hs[j], Ks[j]);
         if (s != MHC_OK) return s;

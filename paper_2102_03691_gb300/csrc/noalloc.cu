@@ -179,7 +179,7 @@ extern "C" mhc_status mhc_binned_current_noalloc(int32_t n_atoms, int32_t n_mode
                  4 * K, st);
     launch_fp32_bin_epilogue(reinterpret_cast<float *>(s + o_R), (int)M_pad, K, mode_bin, mode_slot,
                              partials, (int)M_pad, st);
-    launch_bin_finish(partials, (int)M_pad, slot_begin, n_bins, K, Jb, hsum, J, jsum, st);
+    launch_bin_finish(partials, (int)M_pad, slot_begin, n_bins, K, Jb, hsum, J, jsum, nullptr, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return MHC_ERR_CUDA;
     if ((e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
