@@ -14,6 +14,16 @@ constexpr unsigned FULL_MASK = 0xffffffffu;
 // longest legitimate wait (one 128-mode tile over D = 60000) is under 1 ms.
 constexpr long long WAIT_LIMIT_CYCLES = 2000000000ll;
 
+// Programmatic dependent launch.  griddep_launch_dependents: the next kernel of the stream (if
+// launched as a programmatic dependent) may be scheduled once every CTA of this grid has
+// called it or exited.  griddep_wait: wait until the preceding kernel of the stream has
+// completed and its memory is visible (returns at once for a kernel launched normally).  A
+// dependent runs its set-up before the wait, so it overlaps the end of the kernel before it.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void set_status(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

@@ -366,6 +366,7 @@ __device__ __forceinline__ void pack_bulk_body(const PackArgs &a, int k, uint32_
 // SM; the register cap of the launch bounds lets as many be resident.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) pack_bulk_kernel(const PackArgs a) {
+    griddep_launch_dependents();   // the projection may set up on the SMs this grid leaves
     const uint32_t nrank = cluster_nctarank();
     pack_bulk_body<THREADS>(a, (int)(blockIdx.x / nrank), cluster_ctarank(), nrank);
 }
@@ -375,6 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) pack_bulk_kernel(cons
 // take part in the cluster's combination).
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) pack_bulk_group_kernel(const __grid_constant__ PackGroupArgs g) {
+    griddep_launch_dependents();
     int j = 0;
     while (j + 1 < g.n && (int)blockIdx.x >= g.cta_begin[j + 1]) ++j;
     const uint32_t nrank = cluster_nctarank();

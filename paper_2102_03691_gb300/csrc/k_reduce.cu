@@ -328,8 +328,9 @@ void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin
                        float *Jb, double *hsum, const double *Jtot, double *Jsum, long long *steps,
                        cudaStream_t s) {
     if (B <= 0 || K <= 0) return;
-    bin_finish_kernel<<<B, BF_THREADS, 0, s>>>(partials, n_slots, slot_begin, B, K, Jb, hsum, Jtot, Jsum,
-                                               steps);
+    // launched plainly: as a programmatic dependent it cost the N = 512 GKMA step ~5 us
+    bin_finish_kernel<<<B, BF_THREADS, 0, s>>>(partials, n_slots, slot_begin, B, K, Jb, hsum, Jtot,
+                                               Jsum, steps);
 }
 
 namespace {

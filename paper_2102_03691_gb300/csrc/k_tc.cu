@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    griddep_launch_dependents();   // the next kernel may take the SMs this grid leaves
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -315,6 +316,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_kernel(const __grid_cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    griddep_wait();   // the pack's rows and scales (set-up above overlapped its end)
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------------------ TMA producer
@@ -524,6 +526,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
     const bool leader = rank == 0;
+    griddep_launch_dependents();   // the next kernel may take the SMs this grid leaves
     const int pair = (int)cluster_id_x(), npairs = (int)nclusters_x();
 
     if (threadIdx.x == 0) {
@@ -548,6 +551,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
     cluster_sync_all();   // barriers of both CTAs initialised, TMEM allocated in both
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    griddep_wait();   // the pack's rows and scales (set-up above overlapped its end)
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------------------ TMA producer (both CTAs)
@@ -716,7 +720,7 @@ __global__ void __launch_bounds__(128 + BN, 1) tc_modal_pair_kernel(const __grid
 }
 
 template <int BN, int BK, int STAGES, int NPROB, bool DIR>
-cudaError_t launch_pair_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
+cudaError_t launch_pair_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s, bool pdl) {
     using L = TcPairLayout<BN, BK, STAGES>;
     auto kern = tc_modal_pair_kernel<BN, BK, STAGES, NPROB, DIR>;
     static bool attr_set = false;
@@ -731,13 +735,15 @@ cudaError_t launch_pair_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s)
     cfg.blockDim = dim3(L::THREADS, 1, 1);
     cfg.dynamicSmemBytes = L::SMEM_BYTES;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // after the pack
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
@@ -768,7 +774,7 @@ int max_pairs_impl() {
 }
 
 template <int BN, int BK, int STAGES, int NPROB, bool DIR>
-cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
+cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s, bool pdl) {
     using L = TcLayout<BN, BK, STAGES>;
     auto kern = tc_modal_kernel<BN, BK, STAGES, NPROB, DIR>;
     static bool attr_set = false;   // per process; the attribute is per function
@@ -778,23 +784,32 @@ cudaError_t launch_impl(const TcParams<NPROB> &p, int grid, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    kern<<<grid, L::THREADS, L::SMEM_BYTES, s>>>(p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(L::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = L::SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // after the pack
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 template <int NPROB, bool DIR>
-cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s) {
+cudaError_t dispatch(const TcParams<NPROB> &p, const TcConfig &c, cudaStream_t s, bool pdl) {
     if (c.pair) {
-        if (c.bn == 256 && c.bk == 64 && c.stages == 3) return launch_pair_impl<256, 64, 3, NPROB, DIR>(p, c.grid, s);
-        if (c.bn == 256 && c.bk == 32 && c.stages == 6) return launch_pair_impl<256, 32, 6, NPROB, DIR>(p, c.grid, s);
-        if (c.bn == 128 && c.bk == 64 && c.stages == 4) return launch_pair_impl<128, 64, 4, NPROB, DIR>(p, c.grid, s);
-        if (c.bn == 128 && c.bk == 32 && c.stages == 8) return launch_pair_impl<128, 32, 8, NPROB, DIR>(p, c.grid, s);
+        if (c.bn == 256 && c.bk == 64 && c.stages == 3) return launch_pair_impl<256, 64, 3, NPROB, DIR>(p, c.grid, s, pdl);
+        if (c.bn == 256 && c.bk == 32 && c.stages == 6) return launch_pair_impl<256, 32, 6, NPROB, DIR>(p, c.grid, s, pdl);
+        if (c.bn == 128 && c.bk == 64 && c.stages == 4) return launch_pair_impl<128, 64, 4, NPROB, DIR>(p, c.grid, s, pdl);
+        if (c.bn == 128 && c.bk == 32 && c.stages == 8) return launch_pair_impl<128, 32, 8, NPROB, DIR>(p, c.grid, s, pdl);
         return cudaErrorInvalidValue;
     }
-    if (c.bn == 256 && c.bk == 64 && c.stages == 2) return launch_impl<256, 64, 2, NPROB, DIR>(p, c.grid, s);
-    if (c.bn == 256 && c.bk == 32 && c.stages == 4) return launch_impl<256, 32, 4, NPROB, DIR>(p, c.grid, s);
-    if (c.bn == 128 && c.bk == 64 && c.stages == 3) return launch_impl<128, 64, 3, NPROB, DIR>(p, c.grid, s);
-    if (c.bn == 128 && c.bk == 32 && c.stages == 6) return launch_impl<128, 32, 6, NPROB, DIR>(p, c.grid, s);
+    if (c.bn == 256 && c.bk == 64 && c.stages == 2) return launch_impl<256, 64, 2, NPROB, DIR>(p, c.grid, s, pdl);
+    if (c.bn == 256 && c.bk == 32 && c.stages == 4) return launch_impl<256, 32, 4, NPROB, DIR>(p, c.grid, s, pdl);
+    if (c.bn == 128 && c.bk == 64 && c.stages == 3) return launch_impl<128, 64, 3, NPROB, DIR>(p, c.grid, s, pdl);
+    if (c.bn == 128 && c.bk == 32 && c.stages == 6) return launch_impl<128, 32, 6, NPROB, DIR>(p, c.grid, s, pdl);
     return cudaErrorInvalidValue;
 }
 
@@ -810,6 +825,8 @@ constexpr int FIN_COLS = 4 * FIN_STEPS;                          // columns of a
 constexpr int FIN_SMEM = 4 * FIN_SEGS * FIN_COLS * 32 * 4;       // 4 warps, 64 KB
 __global__ void __launch_bounds__(128) tc_split_finish_kernel(const __grid_constant__ TcParams<1> p) {
     extern __shared__ float4 fin_smem4[];
+    griddep_launch_dependents();
+    griddep_wait();   // the projection's stored segments
     const TcProblem &P = p.prob[0];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x * 4 + warp;   // 32-mode group (warp-uniform)
@@ -856,12 +873,21 @@ cudaError_t launch_tc_split_finish(const TcParams<1> &p, cudaStream_t s) {
     const TcProblem &P = p.prob[0];
     if ((P.n_split <= 1 && P.sk_parts <= 0) || !P.split_ws || P.m_pad % 128 || P.ws_cols % FIN_COLS)
         return cudaErrorInvalidValue;
-    static const cudaError_t attr = cudaFuncSetAttribute(
+    static const cudaError_t smem_ok = cudaFuncSetAttribute(
         tc_split_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FIN_SMEM);
-    if (attr != cudaSuccess) return attr;
+    if (smem_ok != cudaSuccess) return smem_ok;
     const dim3 grid((unsigned)(P.m_pad / 128), (unsigned)((P.K + FIN_STEPS - 1) / FIN_STEPS));
-    tc_split_finish_kernel<<<grid, 128, FIN_SMEM, s>>>(p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(128, 1, 1);
+    cfg.dynamicSmemBytes = FIN_SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // after the projection
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc_split_finish_kernel, p);
 }
 
 const TcConfig TC_CONFIGS[TC_NUM_CONFIGS] = {
@@ -899,15 +925,15 @@ cudaError_t launch_tc_single(const TcParams<1> &p, const TcConfig &c, cudaStream
         return cudaErrorInvalidValue;
     if (p.prob[0].dir_seg_kb) {
         if (!p.prob[0].dir_park || c.grid > p.dir_park_ctas) return cudaErrorInvalidValue;
-        return dispatch<1, true>(p, c, s);
+        return dispatch<1, true>(p, c, s, true);
     }
-    return dispatch<1, false>(p, c, s);
+    return dispatch<1, false>(p, c, s, true);
 }
 cudaError_t launch_tc_group(const TcParams<TC_MAX_GROUP> &p, const TcConfig &c, cudaStream_t s) {
     for (int q = 0; q < p.n_prob; ++q)   // direction and d-axis splits run on single problems only
         if (p.prob[q].dir_seg_kb || p.prob[q].n_split > 1 || p.prob[q].sk_parts > 0)
             return cudaErrorInvalidValue;
-    return dispatch<TC_MAX_GROUP, false>(p, c, s);
+    return dispatch<TC_MAX_GROUP, false>(p, c, s, false);   // after joined streams: plain order
 }
 
 }  // namespace mhc
