@@ -74,14 +74,18 @@ __global__ void advance_steps_group_kernel(const __grid_constant__ FinishGroupAr
 
 // ------------------------------------------------------------------ K4
 // Register-tiled like a GEMM micro-kernel.  A CTA owns 32 consecutive lags (one per lane) and
-// LC_ROWS rows (b, mu) of LC_ROWS / 3 bins; warp s of the CTA takes the block's steps
-// 32 s .. 32 s + 31.  Per step a thread loads its lag's total current J(t - l) (one 16-byte
-// shared-memory load from the CTA's window of J samples) and the step's LC_ROWS binned currents
-// (broadcast 16-byte loads) and does 3 LC_ROWS FMAs into FP32 partial sums over the warp's
-// 32 steps.  The warps' partials are then added in step order in an unevaluated float pair
-// (TwoSum, ~48 bits; GB300's FP64 pipe is narrow) and each lag sum gets one FP64 add.
+// LC_ROWS rows (b, mu) of LC_ROWS / 3 bins; its W <= LC_WARPS warps take consecutive ranges of
+// ceil(K / W) steps of the block.  Per step a thread loads its lag's total current J(t - l)
+// (one 16-byte shared-memory load from the CTA's window of J samples) and the step's LC_ROWS
+// binned currents (broadcast 16-byte loads) and does 3 LC_ROWS FMAs into FP32 partial sums over
+// the warp's steps.  The warps' partials are then added in step order in an unevaluated float
+// pair (TwoSum, ~48 bits; GB300's FP64 pipe is narrow) and each lag sum gets one FP64 add.
+// At most 16 warps a CTA, so that two CTAs share an SM: one CTA's staging and final sums then
+// overlap the other's FMAs, and a grid a little larger than the SM count (N = 512: 175 CTAs)
+// still runs in one wave.
 constexpr int LC_ROWS = 12;   // 4 bins x 3 components a thread
 constexpr int LC_OUT = 3 * LC_ROWS;
+constexpr int LC_WARPS = 16;
 
 // (s, c) += x exactly as an unevaluated float pair (_rn keeps it from being contracted)
 __device__ __forceinline__ void lc_pair_add(float &s, float &c, float x) {
@@ -91,10 +95,13 @@ __device__ __forceinline__ void lc_pair_add(float &s, float &c, float x) {
     s = t;
     c = __fadd_rn(c, e);
 }
-__global__ void __launch_bounds__(1024) lag_corr_kernel(const float *__restrict__ Jb,
-                                                        const double *__restrict__ Jring, int R,
-                                                        double *Csum, int K, int B, int L,
-                                                        long long t0_host, const long long *t0_dev) {
+__global__ void __launch_bounds__(32 * LC_WARPS, 2) lag_corr_kernel(const float *__restrict__ Jb,
+                                                                    const double *__restrict__ Jring,
+                                                                    int R, double *Csum, int K,
+                                                                    int B, int L, long long t0_host,
+                                                                    const long long *t0_dev,
+                                                                    long long *steps,
+                                                                    unsigned *ticket) {
     const long long t0 = t0_dev ? *t0_dev : t0_host;
     // staging: rows [K][LC_ROWS], then the J window [K + 31] as float4 (x, y, z, 0); after the
     // step loop the same space holds the warps' partials [warp][LC_OUT][32]
@@ -105,24 +112,40 @@ __global__ void __launch_bounds__(1024) lag_corr_kernel(const float *__restrict_
     const int l0 = blockIdx.x * 32;
     const int b0 = blockIdx.y * (LC_ROWS / 3);
     const int nthreads = blockDim.x;
-    for (int q = threadIdx.x; q < K * LC_ROWS; q += nthreads) {
-        const int k = q / LC_ROWS, r = q % LC_ROWS, b = b0 + r / 3;
-        sA[q] = b < B ? Jb[((size_t)k * B + b) * 3 + r % 3] : 0.f;
+    if (B % 4 == 0 && (reinterpret_cast<uintptr_t>(Jb) & 15) == 0) {
+        // every bin group is whole and its 12 floats of a step start on a 16-byte boundary:
+        // three asynchronous 16-byte copies a step, all in flight at once
+        for (int q = threadIdx.x; q < 3 * K; q += nthreads) {
+            const int k = q / 3, j = q - 3 * k;
+            cp_async16(sA + k * LC_ROWS + 4 * j, Jb + ((size_t)k * B + b0) * 3 + 4 * j);
+        }
+    } else {
+        for (int q = threadIdx.x; q < K * LC_ROWS; q += nthreads) {
+            const int k = q / LC_ROWS, r = q % LC_ROWS, b = b0 + r / 3;
+            sA[q] = b < B ? Jb[((size_t)k * B + b) * 3 + r % 3] : 0.f;
+        }
     }
-    // window entry w holds J(tw0 + w), tw0 = t0 - l0 - 31: lane l at step k reads w = k - l + 31
+    // window entry w holds J(tw0 + w), tw0 = t0 - l0 - 31: lane l at step k reads w = k - l + 31.
+    // Ring slot of entry w: (tw0 mod R) + w brought into [0, R) with 32-bit arithmetic (one
+    // 64-bit remainder a thread instead of one an entry).
     const long long tw0 = t0 - l0 - 31;
+    const int m0 = (int)(tw0 % R);   // in (-R, R)
     for (int w = threadIdx.x; w < K + 31; w += nthreads) {
-        const long long tt = tw0 + w;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (tt >= 0) {
-            const double *src = Jring + (tt % R) * 3;
+        if (tw0 + w >= 0) {
+            int slot = m0 + w;
+            if (slot < 0) slot += R;
+            if (slot >= R) slot %= R;
+            const double *src = Jring + (size_t)slot * 3;
             v = make_float4((float)src[0], (float)src[1], (float)src[2], 0.f);
         }
         sW[w] = v;
     }
+    cp_async_wait_all();
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int k_begin = 32 * warp, k_end = min(K, k_begin + 32);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = nthreads >> 5;
+    const int ks = (K + nwarps - 1) / nwarps;
+    const int k_begin = min(K, ks * warp), k_end = min(K, k_begin + ks);
     float acc[LC_OUT];
 #pragma unroll
     for (int o = 0; o < LC_OUT; ++o) acc[o] = 0.f;
@@ -152,20 +175,33 @@ __global__ void __launch_bounds__(1024) lag_corr_kernel(const float *__restrict_
 #pragma unroll
     for (int o = 0; o < LC_OUT; ++o) sP[(warp * LC_OUT + o) * 32 + lane] = acc[o];
     __syncthreads();
-    const int nwarps = nthreads >> 5;
     for (int q = threadIdx.x; q < LC_OUT * 32; q += nthreads) {
         const int o = q >> 5, ln = q & 31;
         const int l = l0 + ln, r = o / 3, b = b0 + r / 3;
         if (l >= L || b >= B) continue;
+        double *dst = Csum + ((size_t)b * 9 + (r % 3) * 3 + o % 3) * L + l;
+        const double old = *dst;   // in flight while the partials are added
         float s = 0.f, c = 0.f;
         for (int w = 0; w < nwarps; ++w) lc_pair_add(s, c, sP[(w * LC_OUT + o) * 32 + ln]);
-        Csum[((size_t)b * 9 + (r % 3) * 3 + o % 3) * L + l] += (double)s + (double)c;
+        *dst = old + ((double)s + (double)c);
+    }
+    if (steps) {   // the last CTA to finish advances the step counter: every CTA has read it
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1) {
+                *steps += K;
+                *ticket = 0;
+            }
+        }
     }
 }
 
+int lag_corr_warps(int K) { return std::max(1, std::min(LC_WARPS, (K + 31) / 32)); }
+
 size_t lag_corr_smem(int K) {
     const size_t staging = (size_t)K * LC_ROWS * sizeof(float) + (size_t)(K + 31) * sizeof(float4);
-    const size_t partials = (size_t)((K + 31) / 32) * LC_OUT * 32 * sizeof(float);
+    const size_t partials = (size_t)lag_corr_warps(K) * LC_OUT * 32 * sizeof(float);
     return staging > partials ? staging : partials;
 }
 
@@ -271,22 +307,36 @@ __global__ void __launch_bounds__(GK_THREADS) gk_kappa_kernel(const double *Csum
 // for l >= m >= 1 and as the left end of the step m -> m+1 for l >= m+1).  The integer weights
 // and the reciprocal counts are folded into one table tw(m) = inv(m) w(m), so a row takes one
 // FP64 FMA a lag instead of the scan's few FP64 operations a lag on GB300's narrow FP64 pipe.
-__global__ void gk_window_weights_kernel(long long T_s, int L, int l_lo, int l_hi, double *tw) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= L) return;
+__device__ __forceinline__ double gk_window_weight(long long T_s, int m, int l_lo, int l_hi) {
     const auto cnt = [&](int x) {
         const int lo = max(x, l_lo);
         return l_hi >= lo ? l_hi - lo + 1 : 0;
     };
     const double inv = T_s > m ? 1.0 / (double)(T_s - m) : 0.0;
-    tw[m] = inv * (double)((m >= 1 ? cnt(m) : 0) + cnt(m + 1));
+    return inv * (double)((m >= 1 ? cnt(m) : 0) + cnt(m + 1));
 }
 
-// One warp per row: kappa_w = scale sum_m Csum(m) tw(m) (lanes stride the lags; fixed tree).
-__global__ void __launch_bounds__(128) gk_window_kernel(const double *Csum, int rows, int L,
-                                                        const double *__restrict__ tw, double scale,
-                                                        double *kappa_w) {
-    const int r = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+__global__ void gk_window_weights_kernel(long long T_s, int L, int l_lo, int l_hi, double *tw) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < L) tw[m] = gk_window_weight(T_s, m, l_lo, l_hi);
+}
+
+// One warp per row, GK_ROWS rows a CTA: kappa_w = scale sum_m Csum(m) tw(m) (lanes stride the
+// lags; fixed tree).  tw null: each CTA first builds the table in shared memory (L FP64
+// divisions spread over its threads), cheaper than a launch of its own while the grid is about
+// one CTA an SM; larger grids (the bin-bin read) take the table from one weights launch.
+constexpr int GK_ROWS = 8;
+__global__ void __launch_bounds__(32 * GK_ROWS) gk_window_kernel(const double *Csum, int rows, int L,
+                                                                 const double *__restrict__ tw,
+                                                                 long long T_s, int l_lo, int l_hi,
+                                                                 double scale, double *kappa_w) {
+    extern __shared__ double gk_tw[];
+    if (!tw) {
+        for (int m = threadIdx.x; m < L; m += blockDim.x) gk_tw[m] = gk_window_weight(T_s, m, l_lo, l_hi);
+        __syncthreads();
+        tw = gk_tw;
+    }
+    const int r = blockIdx.x * GK_ROWS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (r >= rows) return;
     const double *cs = Csum + (size_t)r * L;
     double acc = 0.0;
@@ -335,6 +385,9 @@ void launch_bin_finish(const float *partials, int n_slots, const int *slot_begin
 
 namespace {
 size_t lc_sm_set = 48 * 1024;   // the largest dynamic shared memory opted into so far
+// the per-CTA weight table: up to two CTAs an SM and a table within the default 48 KB
+constexpr int GK_TABLE_CTAS = 304;
+constexpr int GK_TABLE_LAGS = 6144;
 }
 
 cudaError_t lag_corr_prepare(int k_max) {
@@ -358,20 +411,22 @@ void launch_advance_steps_group(const FinishGroupArgs &g, cudaStream_t s) {
 }
 
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
-                     int L, long long t0, const long long *t0_dev, cudaStream_t s) {
+                     int L, long long t0, const long long *t0_dev, long long *steps,
+                     unsigned *ticket, cudaStream_t s) {
     if (L <= 0 || K <= 0 || B <= 0) return;
     dim3 grid((L + 31) / 32, (B + LC_ROWS / 3 - 1) / (LC_ROWS / 3));
-    const int threads = 32 * ((K + 31) / 32);   // one warp per 32 steps (K <= 1024)
+    const int threads = 32 * lag_corr_warps(K);
     const size_t sm = lag_corr_smem(K);
     if (sm > lc_sm_set && lag_corr_prepare(K) != cudaSuccess)
         return;   // the launch is skipped; the caller's cudaGetLastError reports the failure
-    lag_corr_kernel<<<grid, threads, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0, t0_dev);
+    lag_corr_kernel<<<grid, threads, sm, s>>>(Jb, Jring, R, Csum, K, B, L, t0, t0_dev, steps,
+                                              ticket);
 }
 
-void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
-                     double tau_lo, double tau_hi, double dt, double *kappa_tau, double *kappa_w,
-                     double *inv_scratch, cudaStream_t s) {
-    if (L <= 0 || B <= 0) return;
+int launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
+                    double tau_lo, double tau_hi, double dt, double *kappa_tau, double *kappa_w,
+                    double *inv_scratch, cudaStream_t s) {
+    if (L <= 0 || B <= 0) return 0;
     // the window's lags: l dt in [tau_lo, tau_hi], tested in FP64 as the oracle tests it
     int l_lo = L, l_hi = -1;
     for (int l = 0; l < L; ++l) {
@@ -384,14 +439,22 @@ void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coe
     if (!kappa_tau) {   // the window average alone
         const int n = l_hi >= l_lo ? l_hi - l_lo + 1 : 0;
         const int rows = B * 9;
+        const int ctas = (rows + GK_ROWS - 1) / GK_ROWS;
+        const double scale = n > 0 ? 0.5 * coef_dt / n : 0.0;
+        if (ctas <= GK_TABLE_CTAS && L <= GK_TABLE_LAGS) {   // each CTA builds the table
+            gk_window_kernel<<<ctas, 32 * GK_ROWS, sizeof(double) * L, s>>>(
+                Csum, rows, L, nullptr, T_s, l_lo, l_hi, scale, kappa_w);
+            return 1;
+        }
         gk_window_weights_kernel<<<(L + 255) / 256, 256, 0, s>>>(T_s, L, l_lo, l_hi, inv_scratch);
-        gk_window_kernel<<<(rows + 3) / 4, 128, 0, s>>>(Csum, rows, L, inv_scratch,
-                                                        n > 0 ? 0.5 * coef_dt / n : 0.0, kappa_w);
-        return;
+        gk_window_kernel<<<ctas, 32 * GK_ROWS, 0, s>>>(Csum, rows, L, inv_scratch, T_s, l_lo, l_hi,
+                                                       scale, kappa_w);
+        return 2;
     }
     inv_counts_kernel<<<(L + 255) / 256, 256, 0, s>>>(T_s, L, inv_scratch);
     gk_kappa_kernel<<<B * 9, GK_THREADS, 0, s>>>(Csum, L, inv_scratch, 0.5 * coef_dt, l_lo, l_hi,
                                                  kappa_tau, kappa_w);
+    return 2;
 }
 
 void launch_hnema_finalize(const double *hsum, int B, long long T_s, double coef, double *mean,

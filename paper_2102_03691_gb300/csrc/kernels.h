@@ -247,16 +247,20 @@ void launch_advance_steps_group(const FinishGroupArgs &g, cudaStream_t s);
 // lag_corr_prepare(k_max): opt into the shared memory of blocks up to k_max steps (call outside
 // any stream capture).
 cudaError_t lag_corr_prepare(int k_max);
+// steps, ticket: when steps is not null, the last CTA to finish adds K to *steps (the push's
+// last reader of the counter) and resets *ticket, a device counter that starts at 0.
 void launch_lag_corr(const float *Jb, const double *Jring, int R, double *Csum, int K, int B,
-                     int L, long long t0, const long long *t0_dev, cudaStream_t s);
+                     int L, long long t0, const long long *t0_dev, long long *steps,
+                     unsigned *ticket, cudaStream_t s);
 // *steps += K (one thread; last kernel of a push)
 void launch_advance_steps(long long *steps, int K, cudaStream_t s);
 // kappa_tau[r][l] (r = b*9+mu*3+nu) and window averages kappa_w[r], FP64; kappa_tau null:
 // the window averages alone, as one weighted sum of C(l) a row.
 // inv_scratch: [L] doubles of device scratch (the reciprocal lag counts of this read).
-void launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
-                     double tau_lo, double tau_hi, double dt, double *kappa_tau,
-                     double *kappa_w, double *inv_scratch, cudaStream_t s);
+// Returns the number of kernels launched.
+int launch_gk_kappa(const double *Csum, int B, int L, long long T_s, double coef_dt,
+                    double tau_lo, double tau_hi, double dt, double *kappa_tau,
+                    double *kappa_w, double *inv_scratch, cudaStream_t s);
 // mean[b][a] = hsum/T_s; kappa[b][a] = mean * coef
 void launch_hnema_finalize(const double *hsum, int B, long long T_s, double coef, double *mean,
                            double *kappa, cudaStream_t s);

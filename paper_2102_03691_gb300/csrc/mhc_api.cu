@@ -265,6 +265,7 @@ mhc_status reset_accumulators(mhc_handle *h) {
     if (h->prm.flags & MHC_FLAG_GKMA) {
         if ((s = dev_alloc(h, "Csum", sizeof(double) * B * 9 * L)) != MHC_OK) return s;
         if ((s = dev_alloc(h, "Jring", sizeof(double) * h->R_ring * 3)) != MHC_OK) return s;
+        if ((s = dev_alloc(h, "lc_ticket", sizeof(unsigned))) != MHC_OK) return s;
         MHC_CUDA(h, lag_corr_prepare(h->prm.k_max));
     }
     if (has_xcorr(h)) {   // lag-major [L][3R][3R] float-pair sums, the ring of past binned
@@ -868,11 +869,18 @@ mhc_status pack_block(mhc_handle *h, const float *v, const float *W, int K) {
 
 // The correlation kernels of a push (after its bin finish): GKMA lag correlation and the
 // cross-correlations.
-mhc_status correlate_block(mhc_handle *h, int K) {
+// advance: the lag correlation, when no cross-correlation kernel follows it, also advances the
+// device step counter (*advanced is set then).
+mhc_status correlate_block(mhc_handle *h, int K, bool advance = false, bool *advanced = nullptr) {
+    if (advanced) *advanced = false;
     if (h->prm.flags & MHC_FLAG_GKMA) {
+        const bool adv = advance && !has_xcorr(h);
         launch_lag_corr(dptr<float>(h, "Jb"), dptr<double>(h, "Jring"), h->R_ring,
                         dptr<double>(h, "Csum"), K, (int)n_out_bins(h), h->prm.n_lags, h->steps,
-                        dptr<long long>(h, "steps_dev"), h->stream);
+                        dptr<long long>(h, "steps_dev"),
+                        adv ? dptr<long long>(h, "steps_dev") : nullptr,
+                        dptr<unsigned>(h, "lc_ticket"), h->stream);
+        if (advanced) *advanced = adv;
         h->launches++;
     }
     if (has_xcorr(h)) {
@@ -889,7 +897,8 @@ mhc_status correlate_block(mhc_handle *h, int K) {
 
 // Kernels that close a push: bin finish + HNEMA sums, correlations, step counter.
 mhc_status finish_kernels(mhc_handle *h, int K) {
-    // without correlation kernels (which read the step counter) the bin finish advances it
+    // without correlation kernels (which read the step counter) the bin finish advances it, and
+    // with the lag correlation alone that kernel does
     const bool corr = (h->prm.flags & MHC_FLAG_GKMA) || has_xcorr(h);
     launch_bin_finish(dptr<float>(h, "partials"), (int)slot_stride(h), dptr<int>(h, "slot_begin"),
                       (int)n_out_bins(h), K, dptr<float>(h, "Jb"), dptr<double>(h, "hsum"),
@@ -897,10 +906,13 @@ mhc_status finish_kernels(mhc_handle *h, int K) {
                       corr ? nullptr : dptr<long long>(h, "steps_dev"), h->stream);
     h->launches++;
     if (corr) {
-        mhc_status s = correlate_block(h, K);
+        bool advanced = false;
+        mhc_status s = correlate_block(h, K, true, &advanced);
         if (s != MHC_OK) return s;
-        launch_advance_steps(dptr<long long>(h, "steps_dev"), K, h->stream);
-        h->launches++;
+        if (!advanced) {
+            launch_advance_steps(dptr<long long>(h, "steps_dev"), K, h->stream);
+            h->launches++;
+        }
     }
     MHC_CUDA(h, cudaGetLastError());
     return MHC_OK;
@@ -1450,9 +1462,9 @@ mhc_status mhc_read_kappa_gk(mhc_handle *h, double *kappa_tau, double tau_lo, do
     double *dk = dptr<double>(h, "gk_out"), *dw = dk + rows * L;
     const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
     // without a kappa(tau) output only the window average is computed (one FMA a lag)
-    launch_gk_kappa(dptr<double>(h, "Csum"), (int)n_out_bins(h), L, h->steps, coef * h->prm.dt_ps, tau_lo, tau_hi,
-                    h->prm.dt_ps, kappa_tau ? dk : nullptr, dw, dw + rows, h->stream);
-    h->launches += 2;
+    h->launches += launch_gk_kappa(dptr<double>(h, "Csum"), (int)n_out_bins(h), L, h->steps,
+                                   coef * h->prm.dt_ps, tau_lo, tau_hi, h->prm.dt_ps,
+                                   kappa_tau ? dk : nullptr, dw, dw + rows, h->stream);
     MHC_CUDA(h, cudaGetLastError());
     if (kappa_tau && (s = copy_out(h, kappa_tau, dk, sizeof(double) * rows * L, where)) != MHC_OK) return s;
     if (kappa_w && (s = copy_out(h, kappa_w, dw, sizeof(double) * rows, where)) != MHC_OK) return s;
@@ -1498,9 +1510,9 @@ mhc_status mhc_read_kappa_xcorr(mhc_handle *h, double *kappa_tau, double tau_lo,
     launch_xcorr_transpose(dptr<float2>(h, "Xsum"), nb, L, dptr<double>(h, "xc_out"), h->stream);
     double *dk = dptr<double>(h, "xk_out"), *dw = dk + rows * L;
     const double coef = WMK_PER_EV_PS_A_K / (KB_EV_PER_K * h->prm.T_K * h->prm.T_K * h->prm.V_A3);
-    launch_gk_kappa(dptr<double>(h, "xc_out"), nb * nb, L, h->steps, coef * h->prm.dt_ps, tau_lo,
-                    tau_hi, h->prm.dt_ps, kappa_tau ? dk : nullptr, dw, dw + rows, h->stream);
-    h->launches += 3;
+    h->launches += 1 + launch_gk_kappa(dptr<double>(h, "xc_out"), nb * nb, L, h->steps,
+                                       coef * h->prm.dt_ps, tau_lo, tau_hi, h->prm.dt_ps,
+                                       kappa_tau ? dk : nullptr, dw, dw + rows, h->stream);
     MHC_CUDA(h, cudaGetLastError());
     if (kappa_tau && (s = copy_out(h, kappa_tau, dk, sizeof(double) * rows * L, where)) != MHC_OK) return s;
     if (kappa_w && (s = copy_out(h, kappa_w, dw, sizeof(double) * rows, where)) != MHC_OK) return s;
