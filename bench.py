@@ -407,7 +407,7 @@ def run_group(args):
 
     def step(i, host=False):
         src = hpools if host else pools
-        grp.push([p[i % P][0] for p in src], [p[i % P][1] for p in src])
+        grp.push([p[i % P][0] for p in src], [p[i % P][1] for p in src], async_inputs=host)
         grp.read_hnema(out_dev)
         if host:   # the step's result back to pinned host memory, no wait
             out_host[i % n_e2e].copy_(out_dev, non_blocking=True)
@@ -759,14 +759,15 @@ def main():
 
     # ---- end to end through the API from pinned host memory: every step uploads its block
     # (the library stages host inputs in two buffers on a copy stream, so the upload of one push
-    # overlaps the kernels of the previous one) and copies that step's kappa back into pinned
-    # host memory; the host waits once, at the end
+    # overlaps the kernels of the previous one; asynchronous host inputs, so that uploads follow
+    # each other without a host round trip: the pool's blocks are never written meanwhile) and
+    # copies that step's kappa back into pinned host memory; the host waits once, at the end
     n_e2e = max(3, args.e2e_steps or args.steps)
     res_host = torch.empty((n_e2e, kap_w.numel()), dtype=torch.float64, pin_memory=True)
 
     def e2e_step(i):
         v, W = host_pool[i % POOL]
-        h.push(v, W)
+        h.push(v, W, async_inputs=True)
         if L:
             h.read_kappa_gk_into(kap_w, tau_lo, tau_hi)
         else:

@@ -61,7 +61,10 @@ typedef enum {
                             scaling, 3 products, FP32 accumulation */
 } mhc_precision;
 
-typedef enum { MHC_MEM_HOST = 0, MHC_MEM_DEVICE = 1 } mhc_mem;
+/* MHC_MEM_HOST_ASYNC (mhc_push / mhc_group_push inputs only): host memory read after the call
+ * returns; the caller keeps it unchanged until the next mhc_push / mhc_group_push of that
+ * handle or mhc_sync on it returns MHC_OK. */
+typedef enum { MHC_MEM_HOST = 0, MHC_MEM_DEVICE = 1, MHC_MEM_HOST_ASYNC = 2 } mhc_mem;
 typedef enum { MHC_F32 = 0, MHC_F64 = 1 } mhc_dtype;
 /* DOF_MAJOR: E[d * ld + n] (rows are degrees of freedom, as printed in Eq. 13).
  * MODE_MAJOR: E[n * ld + d] (each eigenvector contiguous). */
@@ -220,7 +223,10 @@ mhc_status mhc_set_bin_ids(mhc_handle *h, const int32_t *bin_of_mode, int32_t n_
  * correlation sums (Eq. 17).  Asynchronous: device inputs must stay valid until
  * the stream reaches the push; host inputs are copied before the call returns (into one of
  * two device staging buffers, on an internal copy stream, so that the upload overlaps the
- * kernels of the previous push; page-locked host memory uploads fastest).
+ * kernels of the previous push; page-locked host memory uploads fastest).  With
+ * MHC_MEM_HOST_ASYNC the call returns once the upload and the kernels are queued and waits
+ * instead, before it returns, for the upload of the previous asynchronous push: uploads then
+ * follow each other on the copy stream without a host round trip between them.
  * Errors: INVALID_ARG (no modes/bins yet, K out of range, null), CUDA.
  */
 mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, int32_t where);
@@ -237,7 +243,8 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
 mhc_status mhc_autotune_k(mhc_handle *h, const int32_t *candidates, int32_t n, int32_t *best_K,
                           double *steps_per_s);
 
-/* Wait for the stream and report a sticky device status (TIMEOUT/STATE). */
+/* Wait for the stream (and an asynchronous upload of host inputs) and report a sticky device
+ * status (TIMEOUT/STATE). */
 mhc_status mhc_sync(mhc_handle *h);
 
 /* Binned modal current of the last pushed block, out [K_last][B][3] float32. */

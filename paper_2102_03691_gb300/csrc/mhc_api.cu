@@ -130,6 +130,7 @@ struct mhc_handle {
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, use_done[2] = {nullptr, nullptr};
     bool use_pending[2] = {false, false};
     int stage_next = 0, stage_used = -1;
+    int async_stage = -1;   // staging pair of an MHC_MEM_HOST_ASYNC upload not yet waited for
 
     // optional CUDA-event timing of the projection kernel (MHC_FLAG_PROFILE)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
@@ -790,8 +791,10 @@ mhc_status autotune(mhc_handle *h, int K) {
 }
 
 // Host inputs: copy into the next staging pair on the copy stream once the push that last
-// read that pair is done (stage_issue), then wait for the copy (stage_wait: host inputs are
-// read before the call returns); the previous push's kernels keep running meanwhile.
+// read that pair is done (stage_issue); the push's kernels wait for the copy on the device
+// (stage_order) and are queued before the host waits for it (stage_wait_on: host inputs are
+// read before the call returns), so the previous push's kernels keep running meanwhile and the
+// launches of this one overlap its upload.
 mhc_status stage_issue(mhc_handle *h, const float *&v, const float *&W, int K, int where) {
     if (where == MHC_MEM_DEVICE) return MHC_OK;
     if (!h->copy_stream) {
@@ -815,14 +818,18 @@ mhc_status stage_issue(mhc_handle *h, const float *&v, const float *&W, int K, i
     return MHC_OK;
 }
 
-mhc_status stage_wait(mhc_handle *h) {
-    if (h->stage_used >= 0) MHC_CUDA(h, cudaEventSynchronize(h->copy_done[h->stage_used]));
+mhc_status stage_order(mhc_handle *h, cudaStream_t s) {
+    if (h->stage_used >= 0) MHC_CUDA(h, cudaStreamWaitEvent(s, h->copy_done[h->stage_used], 0));
     return MHC_OK;
 }
 
-mhc_status stage_inputs(mhc_handle *h, const float *&v, const float *&W, int K, int where) {
-    mhc_status s = stage_issue(h, v, W, K, where);
-    return s == MHC_OK ? stage_wait(h) : s;
+// Host wait for staging pair b (b < 0: nothing was staged); keeps an earlier failure status.
+mhc_status stage_wait_on(mhc_handle *h, int b, mhc_status prior) {
+    if (b < 0) return prior;
+    const cudaError_t e = cudaEventSynchronize(h->copy_done[b]);
+    if (prior != MHC_OK) return prior;
+    if (e != cudaSuccess) return fail(h, MHC_ERR_CUDA, "upload of host inputs failed: %s", cudaGetErrorString(e));
+    return MHC_OK;
 }
 
 // After the kernels of a push that read a staging pair: mark when the pair is free again.
@@ -993,6 +1000,44 @@ mhc_status copy_out(mhc_handle *h, void *dst, const void *src, size_t bytes, int
     MHC_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
     MHC_CUDA(h, cudaStreamSynchronize(h->stream));
     return check_device_status(h);
+}
+
+// The kernels of a push whose inputs are in device memory (or staged there, ordered on the
+// handle's stream): a graph replay once the tile is tuned, else direct launches.
+mhc_status push_staged(mhc_handle *h, const float *v, const float *W, int K) {
+    mhc_status s;
+    const bool tuned = !is_tc(h) || h->prm.tile_config != 0 || h->tuned.count(K);
+    if (tuned && !(h->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL))) {
+        if (is_tc(h) && h->prm.tile_config == 0 && (s = set_tc_config(h, h->tuned[K])) != MHC_OK) return s;
+        if ((s = push_graph(h, v, W, K)) != MHC_OK) return s;
+        return release_stage(h);
+    }
+    if ((s = pack_block(h, v, W, K)) != MHC_OK) return s;
+    if (is_tc(h) && h->prm.tile_config == 0) {
+        auto it = h->tuned.find(K);
+        if (it == h->tuned.end()) {
+            if ((s = autotune(h, K)) != MHC_OK) return s;
+        } else if ((s = set_tc_config(h, it->second)) != MHC_OK) {
+            return s;
+        }
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (h->prm.flags & MHC_FLAG_PROFILE) {
+        if (h->prof_used == h->prof_events.size()) {
+            cudaEvent_t a0, a1;
+            MHC_CUDA(h, cudaEventCreate(&a0));
+            MHC_CUDA(h, cudaEventCreate(&a1));
+            h->prof_events.emplace_back(a0, a1);
+        }
+        ev0 = h->prof_events[h->prof_used].first;
+        ev1 = h->prof_events[h->prof_used].second;
+        ++h->prof_used;
+        MHC_CUDA(h, cudaEventRecord(ev0, h->stream));
+    }
+    if ((s = run_projection(h, K)) != MHC_OK) return s;
+    if (ev1) MHC_CUDA(h, cudaEventRecord(ev1, h->stream));
+    if ((s = finish_block(h, K)) != MHC_OK) return s;
+    return release_stage(h);
 }
 
 }  // namespace
@@ -1298,44 +1343,26 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     if (!h->bins_ready) return fail(h, MHC_ERR_INVALID_ARG, "modes and bins must be set before pushing");
     if (!v || !W) return fail(h, MHC_ERR_INVALID_ARG, "v and W are required");
     if (K < 1 || K > h->prm.k_max) return fail(h, MHC_ERR_INVALID_ARG, "K=%d outside [1, %d]", K, h->prm.k_max);
-    if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE) return fail(h, MHC_ERR_INVALID_ARG, "where");
+    if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE && where != MHC_MEM_HOST_ASYNC)
+        return fail(h, MHC_ERR_INVALID_ARG, "where");
     MHC_CUDA(h, cudaSetDevice(h->prm.device));
     mhc_status s;
     if (is_tc(h) && (s = ensure_split_ws(h, h->tc)) != MHC_OK) return s;
-    if ((s = stage_inputs(h, v, W, K, where)) != MHC_OK) return s;
-    const bool tuned = !is_tc(h) || h->prm.tile_config != 0 || h->tuned.count(K);
-    if (tuned && !(h->prm.flags & (MHC_FLAG_NO_GRAPH | MHC_FLAG_PROFILE | MHC_FLAG_TEST_STALL))) {
-        if (is_tc(h) && h->prm.tile_config == 0 && (s = set_tc_config(h, h->tuned[K])) != MHC_OK) return s;
-        if ((s = push_graph(h, v, W, K)) != MHC_OK) return s;
-        return release_stage(h);
+    if ((s = stage_issue(h, v, W, K, where)) != MHC_OK) return s;
+    const int staged = h->stage_used;
+    s = stage_order(h, h->stream);
+    if (s == MHC_OK) s = push_staged(h, v, W, K);
+    // the previous asynchronous upload was queued before this one's
+    const int pending = h->async_stage;
+    h->async_stage = -1;
+    s = stage_wait_on(h, pending, s);
+    if (where == MHC_MEM_HOST_ASYNC && s == MHC_OK) {
+        h->async_stage = staged;
+        return MHC_OK;
     }
-    if ((s = pack_block(h, v, W, K)) != MHC_OK) return s;
-    if (is_tc(h) && h->prm.tile_config == 0) {
-        auto it = h->tuned.find(K);
-        if (it == h->tuned.end()) {
-            if ((s = autotune(h, K)) != MHC_OK) return s;
-        } else if ((s = set_tc_config(h, it->second)) != MHC_OK) {
-            return s;
-        }
-    }
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (h->prm.flags & MHC_FLAG_PROFILE) {
-        if (h->prof_used == h->prof_events.size()) {
-            cudaEvent_t a0, a1;
-            MHC_CUDA(h, cudaEventCreate(&a0));
-            MHC_CUDA(h, cudaEventCreate(&a1));
-            h->prof_events.emplace_back(a0, a1);
-        }
-        ev0 = h->prof_events[h->prof_used].first;
-        ev1 = h->prof_events[h->prof_used].second;
-        ++h->prof_used;
-        MHC_CUDA(h, cudaEventRecord(ev0, h->stream));
-    }
-    if ((s = run_projection(h, K)) != MHC_OK) return s;
-    if (ev1) MHC_CUDA(h, cudaEventRecord(ev1, h->stream));
-    if ((s = finish_block(h, K)) != MHC_OK) return s;
-    return release_stage(h);
+    return stage_wait_on(h, staged, s);
 }
+
 
 mhc_status mhc_autotune_k(mhc_handle *h, const int32_t *candidates, int32_t n, int32_t *best_K,
                           double *steps_per_s) {
@@ -1398,7 +1425,10 @@ mhc_status mhc_autotune_k(mhc_handle *h, const int32_t *candidates, int32_t n, i
 mhc_status mhc_sync(mhc_handle *h) {
     if (!h) return MHC_ERR_INVALID_ARG;
     MHC_CUDA(h, cudaStreamSynchronize(h->stream));
-    return check_device_status(h);
+    const int pending = h->async_stage;
+    h->async_stage = -1;
+    const mhc_status s = stage_wait_on(h, pending, MHC_OK);
+    return s != MHC_OK ? s : check_device_status(h);
 }
 
 mhc_status mhc_read_binned_current(mhc_handle *h, float *out, int32_t where) {
@@ -1928,6 +1958,11 @@ mhc_status group_select(mhc_group *g, const std::vector<int> &Ks) {
 
 }  // namespace
 
+namespace {
+mhc_status group_push_staged(mhc_group *g, const std::vector<const float *> &vs,
+                             const std::vector<const float *> &ws, const std::vector<int> &Ks);
+}  // namespace
+
 extern "C" {
 
 mhc_status mhc_group_create(mhc_group **out, mhc_handle *const *handles, int32_t n) {
@@ -2086,7 +2121,8 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
                           const int32_t *K, int32_t where) {
     if (!g || !v || !W || !K) return MHC_ERR_INVALID_ARG;
     mhc_handle *h0 = g->hs[0];
-    if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE) return fail(h0, MHC_ERR_INVALID_ARG, "where");
+    if (where != MHC_MEM_HOST && where != MHC_MEM_DEVICE && where != MHC_MEM_HOST_ASYNC)
+        return fail(h0, MHC_ERR_INVALID_ARG, "where");
     const size_t n = g->hs.size();
     std::vector<int> Ks(n);
     for (size_t j = 0; j < n; ++j) {
@@ -2097,13 +2133,41 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
         Ks[j] = K[j];
     }
     MHC_CUDA(h0, cudaSetDevice(h0->prm.device));
-    mhc_status s;
+    mhc_status s = MHC_OK;
     std::vector<const float *> vs(v, v + n), ws(W, W + n);
-    // all systems' uploads first, one wait after them
-    for (size_t j = 0; j < n; ++j)
-        if ((s = stage_issue(g->hs[j], vs[j], ws[j], Ks[j], where)) != MHC_OK) return s;
-    for (size_t j = 0; j < n; ++j)
-        if ((s = stage_wait(g->hs[j])) != MHC_OK) return s;
+    // all systems' uploads first, ordered before the group's kernels on the device; the host
+    // waits for them after the push is queued
+    std::vector<int> staged(n, -1);
+    for (size_t j = 0; j < n && s == MHC_OK; ++j) {
+        s = stage_issue(g->hs[j], vs[j], ws[j], Ks[j], where);
+        if (s == MHC_OK) {
+            staged[j] = g->hs[j]->stage_used;
+            s = stage_order(g->hs[j], h0->stream);
+        }
+    }
+    if (s == MHC_OK) s = group_push_staged(g, vs, ws, Ks);
+    for (size_t j = 0; j < n; ++j) {   // earlier asynchronous uploads, queued before these
+        const int pending = g->hs[j]->async_stage;
+        g->hs[j]->async_stage = -1;
+        s = stage_wait_on(g->hs[j], pending, s);
+    }
+    const bool keep = where == MHC_MEM_HOST_ASYNC && s == MHC_OK;
+    for (size_t j = 0; j < n; ++j) {
+        if (keep) g->hs[j]->async_stage = staged[j];
+        else s = stage_wait_on(g->hs[j], staged[j], s);
+    }
+    return s;
+}
+
+}  // extern "C"
+
+namespace {
+
+mhc_status group_push_staged(mhc_group *g, const std::vector<const float *> &vs,
+                             const std::vector<const float *> &ws, const std::vector<int> &Ks) {
+    mhc_handle *h0 = g->hs[0];
+    const size_t n = g->hs.size();
+    mhc_status s;
     const bool tuned = h0->prm.tile_config != 0 || g->tuned.count(Ks);
     if (tuned && (s = group_select(g, Ks)) != MHC_OK) return s;
     const bool profile = (h0->prm.flags & MHC_FLAG_PROFILE) != 0;
@@ -2194,4 +2258,4 @@ mhc_status mhc_group_push(mhc_group *g, const float *const *v, const float *cons
     return MHC_OK;
 }
 
-}  // extern "C"
+}  // namespace

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmhc.so")
 MHC_OK = 0
 MHC_WARN_NOT_ORTHONORMAL = 100
 PRECISIONS = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
-MEM_HOST, MEM_DEVICE = 0, 1
+MEM_HOST, MEM_DEVICE, MEM_HOST_ASYNC = 0, 1, 2
 F32, F64 = 0, 1
 DOF_MAJOR, MODE_MAJOR = 0, 1
 FLAG_GKMA, FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_TEST_STALL = 0x1, 0x2, 0x4, 0x8
@@ -174,7 +174,10 @@ class ModalHeatCurrentGroup:
             m._lastK = 0
         return int(best.value), float(rate.value)
 
-    def push(self, vs, Ws):
+    def push(self, vs, Ws, async_inputs: bool = False):
+        """async_inputs: host inputs are uploaded after the call returns and must stay unchanged
+        until the next push of the group or a sync of its handles returns (references to them
+        are kept until then)."""
         n = len(self.members)
         keep, pv, pw, ks, where = [], [], [], [], None
         for m, v, W in zip(self.members, vs, Ws):
@@ -188,9 +191,11 @@ class ModalHeatCurrentGroup:
             pv.append(a)
             pw.append(b)
             ks.append(int(ka.shape[0]))
-        self._keep = keep
+        if async_inputs and where == MEM_HOST:
+            where = MEM_HOST_ASYNC
         st = self._L.mhc_group_push(self._g, (ctypes.c_void_p * n)(*pv), (ctypes.c_void_p * n)(*pw),
                                     (ctypes.c_int32 * n)(*ks), where)
+        self._keep = keep   # after the call: the previous inputs may have been read in it
         if st != MHC_OK:
             raise MhcError(st, self._L.mhc_last_error(self.members[0]._h).decode())
         for m, k in zip(self.members, ks):
@@ -490,8 +495,10 @@ class ModalHeatCurrent:
         self.B = n_bins
 
     # ------------------------------------------------------------------ stream
-    def push(self, v, W):
-        """v [K][N][3], W [K][N][9] float32 (numpy: host, torch CUDA tensor: device)."""
+    def push(self, v, W, async_inputs: bool = False):
+        """v [K][N][3], W [K][N][9] float32 (numpy: host, torch CUDA tensor: device).
+        async_inputs: host inputs are uploaded after the call returns and must stay unchanged
+        until the next push or sync() returns (references to them are kept until then)."""
         pv, wv, kv = _ptr(v, np.float32)
         pw, ww, kw = _ptr(W, np.float32)
         if wv != ww:
@@ -501,8 +508,11 @@ class ModalHeatCurrent:
         nw = int(np.prod(kw.shape)) if not _is_torch(kw) else kw.numel()
         if nv != K * self.N * 3 or nw != K * self.N * 9:
             raise ValueError(f"v must be [K][{self.N}][3] and W [K][{self.N}][9]")
-        self._keep = (kv, kw)
-        self._check(self._L.mhc_push(self._h, pv, pw, K, wv))
+        if async_inputs and wv == MEM_HOST:
+            wv = MEM_HOST_ASYNC
+        st = self._L.mhc_push(self._h, pv, pw, K, wv)
+        self._keep = (kv, kw)   # after the call: the previous inputs may have been read in it
+        self._check(st)
         self._lastK = K
 
     def sync(self):

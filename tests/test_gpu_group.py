@@ -130,7 +130,9 @@ def test_group_graph_replay_matches_direct():
 
 def test_group_host_inputs_back_to_back():
     # host inputs of every system are uploaded before the group push returns (staging
-    # overlaps the previous push); the caller's buffers are refilled right after each push
+    # overlaps the previous push); the caller's buffers are refilled right after each push.
+    # Asynchronous host inputs: two pinned buffers a system, each refilled as soon as the
+    # push after the one that used it has returned
     need_gpu()
     from paper_2102_03691_gb300.mhc import ModalHeatCurrentGroup
     sizes = [120, 80, 200]
@@ -138,23 +140,34 @@ def test_group_host_inputs_back_to_back():
     systems = [system(N, 700 + j) for j, N in enumerate(sizes)]
     blocks = [[s["tr"].next_block(K) for _ in range(T)] for s in systems]
     res = []
-    for host in (True, False):
+    for mode in ("host", "device", "async"):
         hs = [handle(s, K, L) for s in systems]
         grp = ModalHeatCurrentGroup(hs)
         bufs = [(np.empty_like(bl[0][0]), np.empty_like(bl[0][1])) for bl in blocks]
+        pinned = [[(torch.empty(bl[0][0].shape).pin_memory(), torch.empty(bl[0][1].shape).pin_memory())
+                   for _ in range(2)] for bl in blocks]
         for step in range(T):
-            if host:
+            if mode == "host":
                 for (bv, bw), bl in zip(bufs, blocks):
                     bv[:], bw[:] = bl[step]
                 grp.push([b[0] for b in bufs], [b[1] for b in bufs])
+            elif mode == "async":
+                cur = [p[step % 2] for p in pinned]
+                for (bv, bw), bl in zip(cur, blocks):
+                    bv.copy_(torch.from_numpy(bl[step][0]))
+                    bw.copy_(torch.from_numpy(bl[step][1]))
+                grp.push([b[0] for b in cur], [b[1] for b in cur], async_inputs=True)
             else:
                 grp.push([torch.from_numpy(bl[step][0]).cuda() for bl in blocks],
                          [torch.from_numpy(bl[step][1]).cuda() for bl in blocks])
+        for h in hs:
+            h.sync()
         res.append(([h.read_corr()[0] for h in hs], grp.read_hnema()))
         grp.close()
-    for x, y in zip(res[0][0], res[1][0]):
-        np.testing.assert_array_equal(x, y)
-    np.testing.assert_array_equal(res[0][1], res[1][1])
+    for r in res[1:]:
+        for x, y in zip(res[0][0], r[0]):
+            np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(res[0][1], r[1])
 
 
 @pytest.mark.parametrize("sizes", [[1100, 40, 200], [81, 120, 50]])

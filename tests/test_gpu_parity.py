@@ -145,6 +145,44 @@ def test_graph_replay_matches_direct_launches():
     o.check_corr(outs[1][1], L)
 
 
+def test_async_host_inputs_match_synchronous_pushes():
+    # MHC_MEM_HOST_ASYNC: the push returns before its upload; the caller refills a buffer as
+    # soon as the push after the one that used it has returned (two pinned buffers), and mixes
+    # in device and synchronous host pushes: bitwise the results of synchronous host pushes
+    need_gpu()
+    from paper_2102_03691_gb300.mhc import ModalHeatCurrent
+    c = make_case(N=64, M=192, T=128, B=6, seed=109)
+    K, L = 16, 20
+    outs = []
+    for mode in ("sync", "async"):
+        h = ModalHeatCurrent(precision="fp16x3", k_max=K, n_lags=L)
+        h.set_modes(c["E"], c["mass"], c["f"])
+        h.set_bins_uniform(0.0, 16.0, 6)
+        pinned = [(torch.empty((K, 64, 3)).pin_memory(), torch.empty((K, 64, 9)).pin_memory())
+                  for _ in range(2)]
+        for i, t0 in enumerate(range(0, 128, K)):   # no reads in between: they would wait
+            v = np.ascontiguousarray(c["v"][t0:t0 + K])
+            W = np.ascontiguousarray(c["W"][t0:t0 + K])
+            if mode == "sync":
+                h.push(v, W)
+            elif i == 3:
+                h.push(torch.from_numpy(v).cuda(), torch.from_numpy(W).cuda())
+            elif i == 5:
+                h.push(v, W)
+            else:
+                bv, bw = pinned[i % 2]
+                bv.copy_(torch.from_numpy(v))
+                bw.copy_(torch.from_numpy(W))
+                h.push(bv, bw, async_inputs=True)
+        h.sync()
+        C, cnt = h.read_corr()
+        outs.append((h.read_binned_current().copy(), C, *h.read_hnema()))
+        h.close()
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    oracle_ref(c).check_corr(outs[1][1], L)
+
+
 def test_deterministic_repeat():
     need_gpu()
     c = make_case(N=64, M=192, T=32, B=6, seed=104)
