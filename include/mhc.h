@@ -431,6 +431,15 @@ mhc_status mhc_lattice_modes(int32_t device, void *stream, int64_t n_atoms, cons
                              int32_t where_out, int32_t *sweeps);
 
 /*
+ * Measured FP32 FMA throughput of `device` (TFLOP/s, 2 flops an FMA), the peak of the FP32
+ * comparison path: the best of three launches of a kernel in which every thread runs 16
+ * independent FMA chains (one warm-up launch first), on `stream` (cudaStream_t or NULL;
+ * synchronised).  Allocates and frees a small device buffer.  Errors: INVALID_ARG for a null
+ * output, CUDA for runtime errors (message in mhc_last_error(NULL)).
+ */
+mhc_status mhc_measure_fp32_fma(int32_t device, void *stream, double *tflops);
+
+/*
  * No-allocation variant of one block's binned modal current.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device memory,
  * e.g. an MD engine calling from inside its time-step loop (where cudaMalloc would
@@ -449,7 +458,8 @@ mhc_status mhc_lattice_modes(int32_t device, void *stream, int64_t n_atoms, cons
  * Every intermediate array lives in one static device buffer of
  * MHC_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until exit; no
  * call allocates.  The first call on a device looks up the buffer's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.  Calls share
+ * (cudaGetSymbolAddress).  No call can be captured into a CUDA graph (each reads a status
+ * word back and synchronises `stream`).  Calls share
  * the buffer and keep the last call's contents (what must start at zero is cleared each
  * call); calls whose work overlaps on the GPU race.  Every call synchronises `stream`
  * twice: once after the bins and masses are checked on the device, once at the end.
@@ -459,15 +469,6 @@ mhc_status mhc_lattice_modes(int32_t device, void *stream, int64_t n_atoms, cons
  * 4 (M_pad + 4K) D_pad + 16 K M_pad bytes with M_pad = M rounded up to 128 and
  * D_pad = 3N rounded up to 64); CUDA for runtime errors.
  */
-/*
- * Measured FP32 FMA throughput of `device` (TFLOP/s, 2 flops an FMA), the peak of the FP32
- * comparison path: the best of three launches of a kernel in which every thread runs 16
- * independent FMA chains (one warm-up launch first), on `stream` (cudaStream_t or NULL;
- * synchronised).  Allocates and frees a small device buffer.  Errors: INVALID_ARG for a null
- * output, CUDA for runtime errors (message in mhc_last_error(NULL)).
- */
-mhc_status mhc_measure_fp32_fma(int32_t device, void *stream, double *tflops);
-
 #define MHC_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 mhc_status mhc_binned_current_noalloc(int32_t n_atoms, int32_t n_modes, const float *E, int64_t ld,
                                       const int32_t *bin_of_mode, int32_t n_bins,
