@@ -1363,7 +1363,6 @@ mhc_status mhc_push(mhc_handle *h, const float *v, const float *W, int32_t K, in
     return stage_wait_on(h, staged, s);
 }
 
-
 mhc_status mhc_autotune_k(mhc_handle *h, const int32_t *candidates, int32_t n, int32_t *best_K,
                           double *steps_per_s) {
     if (!h) return MHC_ERR_INVALID_ARG;
