@@ -444,7 +444,8 @@ def run_group(args):
     prof_s = p0.elapsed_time(p1) / 1e3
     kms, kn = handles[0].kernel_time()
     handles[0].set_flags(0)
-    # end to end from pinned host buffers (uploads overlap the previous push, one wait at the end)
+    # end to end from pinned host buffers (asynchronous host inputs: each upload starts when the
+    # previous one ends and overlaps the previous push's kernels; one wait at the end)
     for i in range(2):
         step(i, host=True)
     torch.cuda.synchronize()
@@ -486,7 +487,8 @@ def run_group(args):
                               "stages": info["stages"], "cta_pair": bool(info["tile_pair"])}},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_units / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": 8 * B * 3 * len(sizes), "steps": n_e2e},
+                "d2h_bytes_per_step": 8 * B * 3 * len(sizes), "steps": n_e2e,
+                "ms_per_step": 1e3 * e2e_max / n_e2e},
         "clocks": clk, "gpu_launches": int(launches) * world,
         "graph_replays": info["graph_replays"],
     }), flush=True)
