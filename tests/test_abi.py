@@ -21,6 +21,31 @@ def test_header_lists_match_binding():
     assert declared_functions() == sorted(mhc.EXPORTS)
 
 
+def header_constants():
+    """Every `MHC_X = v` enumerator and `#define MHC_X v` integer of the header."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    vals = {n: int(v, 0) for n, v in re.findall(r"\b(MHC_[A-Z0-9_]+)\s*=\s*(-?(?:0x)?[0-9a-fA-F]+)\b", src)}
+    vals.update({n: int(v, 0) for n, v in re.findall(r"#define\s+(MHC_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+|\d+)\s*$",
+                                                      src, flags=re.M)})
+    return vals
+
+
+def test_binding_constants_match_header():
+    c = header_constants()
+    pairs = {"MHC_MEM_HOST": mhc.MEM_HOST, "MHC_MEM_DEVICE": mhc.MEM_DEVICE,
+             "MHC_MEM_HOST_ASYNC": mhc.MEM_HOST_ASYNC, "MHC_F32": mhc.F32, "MHC_F64": mhc.F64,
+             "MHC_DOF_MAJOR": mhc.DOF_MAJOR, "MHC_MODE_MAJOR": mhc.MODE_MAJOR,
+             "MHC_FLAG_GKMA": mhc.FLAG_GKMA, "MHC_FLAG_NO_GRAPH": mhc.FLAG_NO_GRAPH,
+             "MHC_FLAG_PROFILE": mhc.FLAG_PROFILE, "MHC_FLAG_TEST_STALL": mhc.FLAG_TEST_STALL,
+             "MHC_FLAG_DIRECTION": mhc.FLAG_DIRECTION, "MHC_FLAG_XCORR": mhc.FLAG_XCORR,
+             "MHC_OK": mhc.MHC_OK, "MHC_WARN_NOT_ORTHONORMAL": mhc.MHC_WARN_NOT_ORTHONORMAL,
+             "MHC_PREC_FP32": mhc.PRECISIONS["fp32"], "MHC_PREC_BF16X3": mhc.PRECISIONS["bf16x3"],
+             "MHC_PREC_FP16X3": mhc.PRECISIONS["fp16x3"]}
+    missing = [n for n in pairs if n not in c]
+    assert not missing, missing
+    assert {n: c[n] for n in pairs} == pairs
+
+
 def test_library_exports_every_declared_symbol():
     L = mhc.load()
     missing = [n for n in declared_functions() if not hasattr(L, n)]
